@@ -1,0 +1,415 @@
+#!/usr/bin/env python3
+"""Benchmark of the MFA ray-casting hot path on one GB300 (or N independent replicas).
+
+Workload (one step): degree-3 MFA model with 128^3 FP32 control points (64 Gaussians +
+noise, clamped uniform knots), already resident on the device; one perspective 1024^2
+frame with 1024 samples per ray, Phong shading and early termination at alpha 0.99; plus
+one decode of 2^24 uniform random points (value + 3-component gradient).  Every sample
+and every decode point is one MFA value+gradient query.
+
+Printed metric (one JSON line on rank 0): MFA samples/s (value+grad) = (render samples
+actually evaluated + decode queries) / step time, with frames/s at 1024^2 and p50/p99
+frame latency beside it.  Steps are timed with CUDA events on the launching stream; a
+256 MiB buffer is written between steps to flush L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (the correctness reference; there is no
+other implementation of this method to run) on bounded samples of the same workload.
+Under torchrun (N > 1) each rank runs an independent replica of the workload on its own
+GPU (the method is not sharded: no collective in the data path); value is the sum over
+ranks of the work done, divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MFA samples/s (value+grad) & frames/s at 1024^2; p50/p99 frame latency vs plain FP32"
+UNIT = "samples/s"
+WORKLOAD = "mfa_p3_128cube_f32: persp 1024x1024, 1024 samples/ray, Phong, ERT 0.99 + decode 2^24 pts"
+SMS = 152
+FP32_LANES = 128
+
+# Algorithmic FP32 flops per value+grad query at degree p (q = p + 1):
+#   contraction (sum-factorised)       2 (2q^3 + 3q^2 + 4q)
+#   basis values + first derivatives   3 (2p(p+1) + 2p + 3q)   (span-local Cox-de Boor, 3 axes)
+#   parameter map + chain rule         9
+# A render sample adds 40 (transfer-function lerp, Phong, over).
+
+
+def query_flops(p: int) -> int:
+    q = p + 1
+    return 2 * (2 * q ** 3 + 3 * q ** 2 + 4 * q) + 3 * (2 * p * (p + 1) + 2 * p + 3 * q) + 9
+
+
+RENDER_EXTRA_FLOPS = 40
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def build_workload(with_points=True):
+    import synth
+    return synth.config2(decode_n=1 << 24, with_points=with_points)
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and the reference arm)
+# ------------------------------------------------------------------------------------------
+
+def oracle_rates(wl, budget_s: float, seed: int = 7):
+    """Times the FP64 oracle on bounded samples of the workload: seeded pixels of the
+    frame and seeded decode points.  Returns (render samples/s, decode queries/s, info)."""
+    import oracle
+    oracle.build()
+    spec, job = wl.model, wl.render
+    ref = oracle.Model.from_spec(spec)
+    rng = np.random.default_rng(seed)
+    W, H = job.width, job.height
+    threads = oracle.default_threads()
+
+    def run_pixels(npx):
+        pix = rng.choice(W * H, npx, replace=False)
+        t = time.perf_counter()
+        _, ns = oracle.render(ref, job.camera, job.tf, W, H, job.n_samples, shading=job.shading, ka=job.ka, kd=job.kd,
+                              ks=job.ks, shininess=job.shininess, ert_alpha=job.ert_alpha, pixels=pix,
+                              nthreads=threads)
+        return ns, time.perf_counter() - t
+
+    # grow the pixel sample until it takes about 70 % of the budget
+    npx = 256
+    while True:
+        ns1, t1 = run_pixels(npx)
+        if t1 >= 0.35 * budget_s or npx >= W * H:
+            break
+        npx = int(min(W * H, npx * max(2.0, 0.7 * budget_s / max(t1, 1e-3))))
+    rate0 = ns1 / t1
+    n_dec = int(min(len(wl.decode_points) if wl.decode_points is not None else 1 << 20,
+                    max(4096, 0.2 * budget_s * rate0)))
+    pts = wl.decode_points[:n_dec] if wl.decode_points is not None else rng.random((n_dec, 3), dtype=np.float32)
+    t = time.perf_counter()
+    ref.decode(pts, nthreads=threads)
+    td = time.perf_counter() - t
+    info = dict(pixels=npx, render_samples=ns1, render_s=t1, decode_points=len(pts), decode_s=td, threads=threads)
+    return ns1 / t1, len(pts) / td, info
+
+
+# ------------------------------------------------------------------------------------------
+# reference arm: the oracle, as it stands
+# ------------------------------------------------------------------------------------------
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    wl = build_workload(with_points=True)
+    import oracle
+    oracle.build()
+    spec, job = wl.model, wl.render
+    ref = oracle.Model.from_spec(spec)
+    threads = oracle.default_threads()
+    rng = np.random.default_rng(11)
+    W, H = job.width, job.height
+    # per step: a bounded sample of the frame (pixels) and of the decode points, sized so
+    # the whole run takes a few minutes
+    total_steps = args.steps + args.warmup
+    per_step_budget = min(20.0, 150.0 / max(total_steps, 1))
+    _, _, cal = oracle_rates(wl, budget_s=min(8.0, per_step_budget))
+    r_rate = cal["render_samples"] / cal["render_s"]
+    px_per = cal["render_samples"] / cal["pixels"]
+    npx = int(min(W * H, max(64, 0.85 * per_step_budget * r_rate / px_per)))
+    nd = int(min(len(wl.decode_points) // 2, max(1024, 0.15 * per_step_budget * cal["decode_points"] / cal["decode_s"])))
+    times, units = [], []
+    for step in range(total_steps):
+        pix = rng.choice(W * H, npx, replace=False)
+        off = (step * nd) % (len(wl.decode_points) - nd)
+        pts = wl.decode_points[off: off + nd]
+        t = time.perf_counter()
+        _, ns = oracle.render(ref, job.camera, job.tf, W, H, job.n_samples, shading=job.shading, ka=job.ka,
+                              kd=job.kd, ks=job.ks, shininess=job.shininess, ert_alpha=job.ert_alpha, pixels=pix,
+                              nthreads=threads)
+        ref.decode(pts, nthreads=threads)
+        dt = time.perf_counter() - t
+        if step >= args.warmup:
+            times.append(dt)
+            units.append(ns + nd)
+    value = sum(units) / sum(times)
+    sample = (f"{npx} seeded pixels of the 1024^2 frame + {nd} decode points per step, "
+              f"FP64 oracle on {threads} threads")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "oracle_sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import paper_2312_15073_gb300 as mfa
+    from paper_2312_15073_gb300 import build as mfa_build
+    if not os.path.exists(mfa.LIB_PATH):
+        mfa_build.build()
+
+    wl = build_workload(with_points=True)
+    spec, job = wl.model, wl.render
+    p = spec.degree[0]
+    model = mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl)
+    tf = mfa.transfer_fn(job.tf, shading=job.shading, ka=job.ka, kd=job.kd, ks=job.ks, shininess=job.shininess,
+                         ert_alpha=job.ert_alpha)
+    W, H, NS = job.width, job.height, job.n_samples
+    n_pts = wl.decode_points.shape[0]
+    stream = torch.cuda.current_stream()
+
+    # device-resident inputs / outputs
+    pts_d = torch.from_numpy(wl.decode_points).cuda()
+    val_d = torch.empty(n_pts, device="cuda")
+    grad_d = torch.empty((n_pts, 3), device="cuda")
+    img_d = torch.empty((H, W, 4), device="cuda")
+    cnt_d = torch.zeros(1, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(record=None):
+        if record is not None:
+            record[0].record(stream)
+        mfa.render(model, job.camera, tf, W, H, NS, out=img_d, samples_out=cnt_d)
+        if record is not None:
+            record[1].record(stream)
+        mfa.decode(model, pts_d, val_d, grad_d)
+        if record is not None:
+            record[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    cnt_d.zero_()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            step(evs[k])
+            flush.zero_()
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    render_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    decode_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    step_ms = [r + d for r, d in zip(render_ms, decode_ms)]
+    samples = int(cnt_d.item())                      # evaluated render samples over the K steps
+    units = samples + args.steps * n_pts
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s, float(units)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+        total_s, units = float(tmax[0]), float(t[1])
+    value = units / total_s
+
+    # end to end through the public API with host buffers (pinned), copies inside the region
+    pts_h = torch.from_numpy(wl.decode_points).pin_memory()
+    img_h = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
+    val_h = torch.empty(n_pts, dtype=torch.float32).pin_memory()
+    grad_h = torch.empty((n_pts, 3), dtype=torch.float32).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    e2e_ms = []
+    cnt_e = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for k in range(e2e_steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pts_d.copy_(pts_h, non_blocking=True)
+        mfa.render(model, job.camera, tf, W, H, NS, out=img_d, samples_out=cnt_e)
+        mfa.decode(model, pts_d, val_d, grad_d)
+        img_h.copy_(img_d, non_blocking=True)
+        val_h.copy_(val_d, non_blocking=True)
+        grad_h.copy_(grad_d, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        if k > 0:                                          # first pass warms the copy engines
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_samples = int(cnt_e.item()) * e2e_steps / (e2e_steps + 1)
+    e2e_value = (e2e_samples + e2e_steps * n_pts) / (sum(e2e_ms) / 1e3)
+    h2d = pts_h.numel() * 4
+    d2h = (img_h.numel() + val_h.numel() + grad_h.numel()) * 4
+
+    if rank != 0:
+        return 0
+
+    render_s = statistics.mean(render_ms) / 1e3
+    samples_per_frame = samples / args.steps
+    flops_sample = query_flops(p) + RENDER_EXTRA_FLOPS
+    achieved_tflops = samples_per_frame * flops_sample / render_s / 1e12
+    clk = clocks.summary()
+    peak_tflops = SMS * FP32_LANES * 2 * 2070e6 / 1e12
+    sorted_ms = sorted(render_ms)
+
+    def pct(q):
+        return sorted_ms[min(len(sorted_ms) - 1, int(math.ceil(q * len(sorted_ms))) - 1)]
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "model": "degree 3, 128^3 FP32 control points, 64 Gaussians + noise",
+                   "image": f"{W}x{H}", "n_samples": NS, "decode_points": n_pts,
+                   "l2": "flushed between steps (256 MiB write outside the timed events)",
+                   "parallelism": f"replicas x{ws}"},
+        "frames_per_s": 1.0 / render_s,
+        "frame_latency_ms": {"p50": pct(0.5), "p99": pct(0.99), "mean": statistics.mean(render_ms)},
+        "render_samples_per_frame": samples_per_frame,
+        "nominal_samples_per_frame": W * H * NS,
+        "render_samples_per_s": samples_per_frame / render_s,
+        "decode_queries_per_s": n_pts / (statistics.mean(decode_ms) / 1e3),
+        "roofline": {"bound": "alu", "kernel": "k_render", "achieved": achieved_tflops, "peak": peak_tflops,
+                     "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops, "traffic": None,
+                     "flops_per_sample": flops_sample,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
+                     "peak_at_median_clock": (SMS * FP32_LANES * 2 * clk["sm_mhz"] * 1e6 / 1e12)
+                     if clk["sm_mhz"] else None},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": statistics.mean(e2e_ms)},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        r_rate, d_rate, info = oracle_rates(wl, budget_s=args.cpu_budget)
+        cpu_step_s = samples_per_frame / r_rate + n_pts / d_rate
+        line["cpu_baseline"] = {
+            "value": (samples_per_frame + n_pts) / cpu_step_s, "unit": UNIT, "cores": info["threads"],
+            "kind": "oracle",
+            "sample": (f"FP64 oracle: {info['pixels']} seeded pixels of the frame ({info['render_samples']} samples, "
+                       f"{info['render_s']:.1f} s) + {info['decode_points']} decode points ({info['decode_s']:.1f} s); "
+                       "step time extrapolated from the two rates"),
+        }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)      # at least three untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

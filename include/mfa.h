@@ -1,0 +1,173 @@
+/*
+ * mfa.h -- C ABI of libmfa: MFA value/gradient queries and MFA ray casting on one GPU.
+ *
+ * The MFA model (Sec. III-A) is a tensor-product B-spline volume: degrees p_x, p_y, p_z,
+ * clamped knot vectors U_x, U_y, U_z on [0,1] and control points P_ijk.  Its value
+ *     f(u,v,w) = sum_ijk N_{i,p_x}(u) N_{j,p_y}(v) N_{k,p_z}(w) P_ijk
+ * and its analytic gradient (Sec. III-B) are the two queries every volume-visualization
+ * sample makes (Sec. III-C, Sec. IV-A.4).  MFA-VV ray casting (Sec. IV-A.4) casts one ray
+ * per pixel, queries value and gradient at samples along it, maps them through a user
+ * transfer function with shading (Sec. IV-B) and combines neighbouring samples with the
+ * over operation (Sec. IV-A.4, IV-A.5).
+ *
+ * Conventions shared by every call
+ *  - Parameter domain = world box = the unit cube [0,1]^3, so world gradients equal
+ *    parameter gradients.
+ *  - Control-point arrays are [n_z][n_y][n_x] with x fastest.
+ *  - Every call except mfa_model_create* returns an mfa_status (0 = MFA_OK).  Arguments
+ *    are checked on the host before any launch; a rejected call launches nothing and
+ *    leaves every output untouched.  mfa_last_error() returns a text for the last failure
+ *    on the calling thread.
+ *  - Compute calls are asynchronous on the stream bound with mfa_set_stream on the
+ *    calling thread (the legacy default stream if none).  Device pointers passed in must
+ *    stay valid until that stream has finished the work.  The library never frees or
+ *    keeps caller buffers.
+ *  - A model lives on the device that was current when it was created; calls that use it
+ *    must run with that device current.
+ *
+ * Thread safety: distinct models may be used from distinct threads.  A model may be
+ * read by many concurrent calls; destroying it while a call that uses it is running or
+ * queued is the caller's error.
+ */
+#ifndef MFA_H
+#define MFA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { MFA_F64 = 0, MFA_F32 = 1, MFA_F16 = 2, MFA_BF16 = 3 } mfa_dtype;
+
+typedef enum {
+    MFA_OK = 0,
+    MFA_ERR_ARG = -1,          /* an argument is out of range or inconsistent */
+    MFA_ERR_NOMEM = -2,        /* a device or host allocation failed */
+    MFA_ERR_CUDA = -3,         /* a CUDA call failed; mfa_last_error() has its text */
+    MFA_ERR_TIMEOUT = -4,      /* a bounded wait ran out */
+    MFA_ERR_BUSY = -5,         /* no capacity right now; retry later */
+    MFA_ERR_UNSUPPORTED = -6   /* valid request this build does not handle */
+} mfa_status;
+
+typedef struct mfa_model mfa_model;   /* opaque; owns all of its device memory */
+
+/*
+ * Creates an MFA model on the current device (Sec. III-A; the model-fetch step of
+ * Sec. IV-A.3 becomes this one upload).
+ *   degree[d]  1..4 for d = x, y, z.
+ *   nctrl[d]   control points along d, >= degree[d] + 1.
+ *   knots      knots[d] is a HOST array of nctrl[d] + degree[d] + 1 FP64 values,
+ *              non-decreasing, clamped (the first degree+1 equal 0, the last degree+1
+ *              equal 1).  knots == NULL or knots[d] == NULL selects the clamped uniform
+ *              vector (interior knots i / (nctrl - degree)).
+ *   ctrl       HOST array of nctrl[0]*nctrl[1]*nctrl[2] values of type `dtype`,
+ *              [n_z][n_y][n_x], x fastest.  Copied; the caller keeps ownership.
+ *   dtype      type of ctrl.  Storage is FP32 for F64/F32 input, FP16 for F16, BF16 for
+ *              BF16 (see mfa_model_create_ex to choose).
+ * The padded window layout the kernels read takes about 16 bytes per control point
+ * (FP32 storage) or 8 bytes (FP16/BF16); the product of the padded sizes
+ * (n_x+4)(n_y+4)(n_z+4) must stay below 2^31.
+ * Synchronous: returns after the model is ready.  Returns NULL on error (reason in
+ * mfa_last_error()).
+ */
+mfa_model* mfa_model_create(const int degree[3], const int nctrl[3], const double* const knots[3],
+                            const void* ctrl, mfa_dtype dtype);
+
+/* As mfa_model_create, with the storage type chosen: storage_dtype is MFA_F32, MFA_F16 or
+ * MFA_BF16.  Input values are rounded ONCE, to nearest even, from in_dtype to storage
+ * (FP64 -> BF16 directly, never through FP32).  Basis values and all accumulation stay
+ * FP32 whatever the storage type. */
+mfa_model* mfa_model_create_ex(const int degree[3], const int nctrl[3], const double* const knots[3],
+                               const void* ctrl, mfa_dtype in_dtype, mfa_dtype storage_dtype);
+
+/* Frees the model and its device memory.  NULL is a no-op. */
+void mfa_model_destroy(mfa_model* model);
+
+typedef struct {
+    int degree[3];
+    int nctrl[3];
+    mfa_dtype storage;
+    float vmin, vmax;          /* min / max of the stored control points */
+    size_t device_bytes;       /* device memory the model holds */
+    int device;                /* CUDA ordinal the model lives on */
+} mfa_model_info;
+
+/* Fills *info.  MFA_ERR_ARG on NULL arguments. */
+int mfa_model_get_info(const mfa_model* model, mfa_model_info* info);
+
+/* Binds a CUDA stream (a cudaStream_t passed as void*) for later calls on the calling
+ * thread; NULL selects the legacy default stream.  Always MFA_OK. */
+int mfa_set_stream(void* cuda_stream);
+
+/*
+ * Value and gradient queries at n arbitrary points (Sec. III-B; the query of Fig. 8,
+ * Sec. V-D.3).
+ *   pts   DEVICE, n * 3 FP32, (x, y, z) per point; coordinates outside [0,1] are clamped
+ *         to it and NaN is read as 0.
+ *   val   DEVICE, n FP32: f at each point.
+ *   grad  DEVICE, n * 3 FP32 (df/dx, df/dy, df/dz) per point, or NULL for values only.
+ * n = 0 is a no-op.  MFA_ERR_ARG on NULL model/pts/val with n > 0 or n < 0.
+ */
+int mfa_decode(const mfa_model* model, const float* pts, long long n, float* val, float* grad);
+
+/*
+ * Knot spans of n points, as the query above finds them: spans[3i + d] = the largest s
+ * in [degree_d, nctrl_d - 1] with U_d[s] <= u_d after clamping (a coordinate on an interior
+ * knot goes to the span on its right; u = 1 goes to the last span).  The comparison is
+ * exact against the FP64 knots.
+ *   pts    DEVICE, n * 3 FP32.   spans  DEVICE, n * 3 int32.
+ */
+int mfa_locate_spans(const mfa_model* model, const float* pts, long long n, int* spans);
+
+typedef struct {
+    int projection;                  /* 0 orthographic, 1 perspective */
+    double eye[3], target[3], up[3]; /* right-handed look-at; up must not be parallel to
+                                        target - eye */
+    double fov_y_deg;                /* perspective: full vertical field of view, (0, 180) */
+    double ortho_height;             /* orthographic: view height (> 0); width = height W/H */
+} mfa_camera;
+
+typedef struct {
+    int n_entries;        /* rows of the table, 1..256 */
+    const float* rgba;    /* HOST, n_entries * 4, non-premultiplied, row i at t = i/(n-1),
+                             linear interpolation between rows, clamped at the ends */
+    float vmin, vmax;     /* t = (f - vmin)/(vmax - vmin); NaN selects the model's min/max */
+    int shading;          /* 0 none; 1 Phong with a headlight, two-sided */
+    float ka, kd, ks, shininess;
+    float ert_alpha;      /* early ray termination once accumulated alpha >= ert_alpha;
+                             >= 1 disables it */
+} mfa_transfer_fn;
+
+typedef struct {
+    unsigned long long* samples_out;  /* DEVICE counter or NULL: the number of samples
+                                         evaluated (after box clipping and early
+                                         termination) is ADDED to it */
+    int reserved[8];                  /* zero */
+} mfa_render_opts;
+
+/*
+ * MFA-VV ray casting of one image (Sec. IV-A.4).  For the pixel in column c, row r
+ * (row 0 at the top) the ray goes through the pixel centre, is clipped to the unit box,
+ * and n_samples samples sit at the midpoints of n_samples equal pieces of the clipped
+ * segment.  Each sample queries f and grad f, looks f up in the transfer function,
+ * shades with grad f if asked, and is composited front to back with the over operation
+ * (premultiplied; background transparent black) until ert_alpha is reached.
+ *   rgba_out  DEVICE, height * width * 4 FP32, premultiplied RGBA, row-major from the top.
+ * width, height in 1..32768; n_samples in 1..1048576.
+ */
+int mfa_render(const mfa_model* model, const mfa_camera* camera, const mfa_transfer_fn* tf,
+               int width, int height, int n_samples, float* rgba_out);
+
+/* mfa_render with options (opts may be NULL). */
+int mfa_render_ex(const mfa_model* model, const mfa_camera* camera, const mfa_transfer_fn* tf,
+                  int width, int height, int n_samples, float* rgba_out, const mfa_render_opts* opts);
+
+/* Text of the last error on the calling thread ("" if none). */
+const char* mfa_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MFA_H */

@@ -1,0 +1,250 @@
+"""GB300 (sm_103a) MFA value/gradient queries and MFA ray casting.
+
+Thin Python binding over the C ABI of libmfa (include/mfa.h): the functions here only
+marshal arguments -- every step of a query or a render runs in the library's CUDA
+kernels.  PyTorch provides device memory and the current CUDA stream; nothing else.
+
+    import paper_2312_15073_gb300 as mfa
+    m = mfa.Model((3, 3, 3), (128, 128, 128), None, ctrl_numpy)   # clamped uniform knots
+    val, grad = mfa.decode(m, pts_cuda)                             # (n,), (n, 3)
+    img = mfa.render(m, camera, tf, 1024, 1024, 1024)               # (H, W, 4) premultiplied
+
+The library must have been built (``paper_2312_15073_gb300.build.build()``); a missing
+library raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from ctypes import POINTER, c_double, c_float, c_int, c_longlong, c_size_t, c_ulonglong, c_void_p
+
+import numpy as np
+
+__all__ = ["Model", "decode", "locate_spans", "render", "lib", "MFA_F64", "MFA_F32", "MFA_F16", "MFA_BF16",
+           "MfaError", "camera", "transfer_fn"]
+
+MFA_F64, MFA_F32, MFA_F16, MFA_BF16 = 0, 1, 2, 3
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmfa.so")
+
+
+class MfaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"mfa error {code}: {msg}")
+        self.code = code
+
+
+class _Camera(ctypes.Structure):
+    _fields_ = [("projection", c_int), ("eye", c_double * 3), ("target", c_double * 3), ("up", c_double * 3),
+                ("fov_y_deg", c_double), ("ortho_height", c_double)]
+
+
+class _TF(ctypes.Structure):
+    _fields_ = [("n_entries", c_int), ("rgba", c_void_p), ("vmin", c_float), ("vmax", c_float),
+                ("shading", c_int), ("ka", c_float), ("kd", c_float), ("ks", c_float), ("shininess", c_float),
+                ("ert_alpha", c_float)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("samples_out", c_void_p), ("reserved", c_int * 8)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("degree", c_int * 3), ("nctrl", c_int * 3), ("storage", c_int), ("vmin", c_float),
+                ("vmax", c_float), ("device_bytes", c_size_t), ("device", c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libmfa (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2312_15073_gb300.build.build() "
+                               "(there is no fallback implementation)")
+        L = ctypes.CDLL(LIB_PATH)
+        L.mfa_last_error.restype = ctypes.c_char_p
+        L.mfa_last_error.argtypes = []
+        L.mfa_set_stream.restype = c_int
+        L.mfa_set_stream.argtypes = [c_void_p]
+        L.mfa_model_create_ex.restype = c_void_p
+        L.mfa_model_create_ex.argtypes = [POINTER(c_int * 3), POINTER(c_int * 3), POINTER(c_void_p * 3), c_void_p,
+                                          c_int, c_int]
+        L.mfa_model_create.restype = c_void_p
+        L.mfa_model_create.argtypes = [POINTER(c_int * 3), POINTER(c_int * 3), POINTER(c_void_p * 3), c_void_p, c_int]
+        L.mfa_model_destroy.restype = None
+        L.mfa_model_destroy.argtypes = [c_void_p]
+        L.mfa_model_get_info.restype = c_int
+        L.mfa_model_get_info.argtypes = [c_void_p, POINTER(_Info)]
+        L.mfa_decode.restype = c_int
+        L.mfa_decode.argtypes = [c_void_p, c_void_p, c_longlong, c_void_p, c_void_p]
+        L.mfa_locate_spans.restype = c_int
+        L.mfa_locate_spans.argtypes = [c_void_p, c_void_p, c_longlong, c_void_p]
+        L.mfa_render.restype = c_int
+        L.mfa_render.argtypes = [c_void_p, POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int, c_void_p]
+        L.mfa_render_ex.restype = c_int
+        L.mfa_render_ex.argtypes = [c_void_p, POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int, c_void_p,
+                                    POINTER(_Opts)]
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise MfaError(rc, lib().mfa_last_error().decode())
+
+
+def _bind_stream():
+    import torch
+    lib().mfa_set_stream(c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+_NP2MFA = {np.dtype(np.float64): MFA_F64, np.dtype(np.float32): MFA_F32, np.dtype(np.float16): MFA_F16}
+
+
+class Model:
+    """An MFA model on the current CUDA device (owns its device memory).
+
+    ctrl: host array (n_z, n_y, n_x).  Its numpy dtype gives the input type (float64,
+    float32, float16; pass `in_dtype=MFA_BF16` with a uint16 array for BF16 bits).
+    knots: None for clamped uniform, or a list of three FP64 arrays (entries may be None).
+    storage: MFA_F32 / MFA_F16 / MFA_BF16 (default: F32 for 64/32-bit input).
+    """
+
+    def __init__(self, degree, nctrl, knots, ctrl, storage: int | None = None, in_dtype: int | None = None):
+        import torch  # noqa: F401  (makes sure the CUDA context exists on the current device)
+        ctrl = np.ascontiguousarray(ctrl)
+        if in_dtype is None:
+            if ctrl.dtype not in _NP2MFA:
+                raise TypeError(f"unsupported control-point dtype {ctrl.dtype}")
+            in_dtype = _NP2MFA[ctrl.dtype]
+        if storage is None:
+            storage = {MFA_F64: MFA_F32, MFA_F32: MFA_F32, MFA_F16: MFA_F16, MFA_BF16: MFA_BF16}[in_dtype]
+        deg = (c_int * 3)(*[int(d) for d in degree])
+        nc = (c_int * 3)(*[int(n) for n in nctrl])
+        self._knots = None
+        kp = None
+        if knots is not None:
+            self._knots = [None if k is None else np.ascontiguousarray(k, dtype=np.float64) for k in knots]
+            kp = (c_void_p * 3)(*[None if k is None else k.ctypes.data for k in self._knots])
+        self._ctrl_keep = ctrl
+        _bind_stream()
+        h = lib().mfa_model_create_ex(ctypes.byref(deg), ctypes.byref(nc), ctypes.byref(kp) if kp is not None else None,
+                                      ctrl.ctypes.data, in_dtype, storage)
+        self._ctrl_keep = None
+        if not h:
+            raise MfaError(-1, lib().mfa_last_error().decode())
+        self._h = h
+        self.degree = tuple(int(d) for d in degree)
+        self.nctrl = tuple(int(n) for n in nctrl)
+        self.storage = storage
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    def info(self) -> dict:
+        i = _Info()
+        _check(lib().mfa_model_get_info(self._h, ctypes.byref(i)))
+        return dict(degree=tuple(i.degree), nctrl=tuple(i.nctrl), storage=i.storage, vmin=i.vmin, vmax=i.vmax,
+                    device_bytes=i.device_bytes, device=i.device)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mfa_model_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _dev_ptr(t, dtype, shape_tail, name):
+    import torch
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous CUDA tensor of {dtype}")
+    if shape_tail is not None and tuple(t.shape[1:]) != tuple(shape_tail):
+        raise ValueError(f"{name} must have shape (n, {', '.join(map(str, shape_tail))})")
+    return t.data_ptr()
+
+
+def decode(model: Model, pts, val=None, grad=None, want_grad: bool = True):
+    """Value (n,) and gradient (n, 3) at pts (n, 3) FP32 CUDA; outputs allocated if not given."""
+    import torch
+    n = pts.shape[0]
+    if val is None:
+        val = torch.empty(n, device=pts.device, dtype=torch.float32)
+    if grad is None and want_grad:
+        grad = torch.empty((n, 3), device=pts.device, dtype=torch.float32)
+    _bind_stream()
+    _check(lib().mfa_decode(model.handle, _dev_ptr(pts, torch.float32, (3,), "pts"), n,
+                            _dev_ptr(val, torch.float32, None, "val"), _dev_ptr(grad, torch.float32, (3,), "grad")))
+    return val, grad
+
+
+def locate_spans(model: Model, pts, spans=None):
+    import torch
+    n = pts.shape[0]
+    if spans is None:
+        spans = torch.empty((n, 3), device=pts.device, dtype=torch.int32)
+    _bind_stream()
+    _check(lib().mfa_locate_spans(model.handle, _dev_ptr(pts, torch.float32, (3,), "pts"), n,
+                                  _dev_ptr(spans, torch.int32, (3,), "spans")))
+    return spans
+
+
+def camera(cam: dict) -> _Camera:
+    c = _Camera()
+    c.projection = int(cam["projection"])
+    for a in range(3):
+        c.eye[a] = float(cam["eye"][a])
+        c.target[a] = float(cam["target"][a])
+        c.up[a] = float(cam["up"][a])
+    c.fov_y_deg = float(cam.get("fov_y_deg", 0.0))
+    c.ortho_height = float(cam.get("ortho_height", 0.0))
+    return c
+
+
+class transfer_fn:
+    """Transfer function + shading parameters (the table stays alive with this object)."""
+
+    def __init__(self, rgba, *, shading=False, ka=0.3, kd=0.6, ks=0.3, shininess=32.0, ert_alpha=0.99,
+                 vmin=math.nan, vmax=math.nan):
+        self.table = np.ascontiguousarray(rgba, dtype=np.float32).reshape(-1, 4)
+        s = _TF()
+        s.n_entries = self.table.shape[0]
+        s.rgba = self.table.ctypes.data
+        s.vmin, s.vmax = vmin, vmax
+        s.shading = 1 if shading else 0
+        s.ka, s.kd, s.ks, s.shininess = ka, kd, ks, shininess
+        s.ert_alpha = ert_alpha
+        self.struct = s
+
+
+def render(model: Model, cam, tf: transfer_fn, width: int, height: int, n_samples: int, out=None,
+           samples_out=None):
+    """Premultiplied RGBA image (height, width, 4) FP32 on the current device.
+    samples_out: optional 1-element int64 CUDA tensor to which the number of evaluated
+    samples is added."""
+    import torch
+    if out is None:
+        out = torch.empty((height, width, 4), device="cuda", dtype=torch.float32)
+    if not (out.is_cuda and out.dtype == torch.float32 and out.is_contiguous() and out.numel() == height * width * 4):
+        raise ValueError("out must be a contiguous (height, width, 4) FP32 CUDA tensor")
+    c = cam if isinstance(cam, _Camera) else camera(cam)
+    opts = _Opts()
+    if samples_out is not None:
+        if not (samples_out.is_cuda and samples_out.dtype == torch.int64):
+            raise TypeError("samples_out must be an int64 CUDA tensor")
+        opts.samples_out = samples_out.data_ptr()
+    _bind_stream()
+    _check(lib().mfa_render_ex(model.handle, ctypes.byref(c), ctypes.byref(tf.struct), width, height, n_samples,
+                               out.data_ptr(), ctypes.byref(opts)))
+    return out

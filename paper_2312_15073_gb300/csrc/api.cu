@@ -1,0 +1,381 @@
+// api.cu -- the C ABI declared in include/mfa.h: argument checks, model ownership,
+// stream binding, error text, and the host-side set-up of each launch.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mfa.h"
+#include "mfa_internal.cuh"
+
+using namespace mfa;
+
+struct mfa_model {
+    int device = 0;
+    int degree[3] = { 0, 0, 0 };
+    int nctrl[3] = { 0, 0, 0 };
+    mfa_dtype storage = MFA_F32;
+    float vmin = 0.0f, vmax = 0.0f, maxabs = 0.0f;
+    size_t bytes = 0;
+    void* d_win = nullptr;      // window array
+    void* d_tables = nullptr;   // kup, grid and records of the three axes, one allocation
+    ModelDev dev{};
+};
+
+namespace {
+
+thread_local std::string g_error;
+thread_local cudaStream_t g_stream = nullptr;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? MFA_ERR_NOMEM : MFA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool valid_dtype(int d) { return d >= MFA_F64 && d <= MFA_BF16; }
+size_t dtype_size(int d) { return d == MFA_F64 ? 8 : d == MFA_F32 ? 4 : 2; }
+
+// Checks one knot vector: length n+p+1, non-decreasing, clamped on [0,1] with exactly
+// p+1 end knots at each end (the first and last spans are non-empty).
+bool check_knots(const double* U, int n, int p, int axis)
+{
+    const int m = n + p + 1;
+    for (int i = 0; i < m; ++i) {
+        if (!std::isfinite(U[i])) return fail(MFA_ERR_ARG, "knots[%d][%d] is not finite", axis, i), false;
+        if (i > 0 && U[i] < U[i - 1]) return fail(MFA_ERR_ARG, "knots[%d] decrease at %d", axis, i), false;
+    }
+    for (int i = 0; i <= p; ++i) {
+        if (U[i] != 0.0) return fail(MFA_ERR_ARG, "knots[%d]: the first %d knots must be 0", axis, p + 1), false;
+        if (U[n + i] != 1.0) return fail(MFA_ERR_ARG, "knots[%d]: the last %d knots must be 1", axis, p + 1), false;
+    }
+    if (n > p + 1 && !(U[p + 1] > 0.0 && U[n - 1] < 1.0))
+        return fail(MFA_ERR_ARG, "knots[%d]: interior knots must lie strictly inside (0,1)", axis), false;
+    return true;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int check_model_device(const mfa_model* m)
+{
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != m->device) return fail(MFA_ERR_ARG, "model lives on device %d but device %d is current", m->device, cur);
+    return MFA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mfa_last_error(void) { return g_error.c_str(); }
+
+int mfa_set_stream(void* cuda_stream)
+{
+    g_stream = static_cast<cudaStream_t>(cuda_stream);
+    return MFA_OK;
+}
+
+void mfa_model_destroy(mfa_model* m)
+{
+    if (!m) return;
+    DeviceGuard g(m->device);
+    if (m->d_win) cudaFree(m->d_win);
+    if (m->d_tables) cudaFree(m->d_tables);
+    delete m;
+}
+
+mfa_model* mfa_model_create_ex(const int degree[3], const int nctrl[3], const double* const knots[3],
+                               const void* ctrl, mfa_dtype in_dtype, mfa_dtype storage)
+{
+    g_error.clear();
+    if (!degree || !nctrl || !ctrl) return fail(MFA_ERR_ARG, "degree, nctrl and ctrl must be non-NULL"), nullptr;
+    if (!valid_dtype(in_dtype)) return fail(MFA_ERR_ARG, "unknown input dtype %d", (int)in_dtype), nullptr;
+    if (storage != MFA_F32 && storage != MFA_F16 && storage != MFA_BF16)
+        return fail(MFA_ERR_UNSUPPORTED, "storage dtype must be F32, F16 or BF16"), nullptr;
+    int qmax = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (degree[a] < 1 || degree[a] > kMaxDegree)
+            return fail(MFA_ERR_UNSUPPORTED, "degree[%d] = %d outside 1..%d", a, degree[a], kMaxDegree), nullptr;
+        if (nctrl[a] < degree[a] + 1 || nctrl[a] > (1 << 24))
+            return fail(MFA_ERR_ARG, "nctrl[%d] = %d must be in degree+1..2^24", a, nctrl[a]), nullptr;
+        qmax = degree[a] + 1 > qmax ? degree[a] + 1 : qmax;
+    }
+    const long long nxp = nctrl[0] + kPad, nyp = nctrl[1] + kPad, nzp = nctrl[2] + kPad;
+    if (nxp * nyp * nzp >= (1LL << 31))
+        return fail(MFA_ERR_UNSUPPORTED, "model too large: (nx+4)(ny+4)(nz+4) must stay below 2^31"), nullptr;
+
+    // knot vectors (host, FP64): caller's or clamped uniform
+    std::vector<double> U[3];
+    for (int a = 0; a < 3; ++a) {
+        const int n = nctrl[a], p = degree[a], m = n + p + 1;
+        U[a].resize(m);
+        if (knots && knots[a]) {
+            std::memcpy(U[a].data(), knots[a], sizeof(double) * m);
+            if (!check_knots(U[a].data(), n, p, a)) return nullptr;
+        } else {
+            for (int i = 0; i < m; ++i)
+                U[a][i] = i <= p ? 0.0 : (i >= n ? 1.0 : static_cast<double>(i - p) / static_cast<double>(n - p));
+        }
+    }
+
+    mfa_model* M = new mfa_model();
+    cudaGetDevice(&M->device);
+    for (int a = 0; a < 3; ++a) {
+        M->degree[a] = degree[a];
+        M->nctrl[a] = nctrl[a];
+    }
+    M->storage = storage;
+    const int Q = qmax;
+    cudaStream_t st = g_stream;
+
+    // one allocation for the three axes' tables: kup | grid | records, each 256-B aligned
+    size_t off_kup[3], off_grid[3], off_rec[3], tab = 0;
+    int G[3];
+    for (int a = 0; a < 3; ++a) {
+        const int n = nctrl[a], p = degree[a];
+        G[a] = 4 * (n - p);
+        off_kup[a] = tab;
+        tab = align_up(tab + sizeof(float) * (n + p + 1), 256);
+        off_grid[a] = tab;
+        tab = align_up(tab + sizeof(int) * G[a], 256);
+        off_rec[a] = tab;
+        tab = align_up(tab + sizeof(float) * rec_stride(Q) * (n - p), 256);
+    }
+    const size_t win_elem = storage == MFA_F32 ? 16 : 8;
+    const size_t win_bytes = static_cast<size_t>(nxp * nyp * nzp) * win_elem;
+    const size_t nctrl_total = static_cast<size_t>(nctrl[0]) * nctrl[1] * nctrl[2];
+    const size_t in_bytes = nctrl_total * dtype_size(in_dtype);
+    size_t knot_bytes = 0;
+    for (int a = 0; a < 3; ++a) knot_bytes += sizeof(double) * U[a].size();
+
+    void* d_stage = nullptr;   // uploaded knots, stats and input control points; freed below
+    const size_t stage_bytes = align_up(knot_bytes, 256) + 256 + in_bytes;
+    cudaError_t e;
+    auto cleanup = [&](int code, const char* what, cudaError_t err) -> mfa_model* {
+        if (err != cudaSuccess) cuda_fail(err, what); else fail(code, "%s", what);
+        if (d_stage) cudaFree(d_stage);
+        mfa_model_destroy(M);
+        return nullptr;
+    };
+    if ((e = cudaMalloc(&M->d_tables, tab)) != cudaSuccess) return cleanup(0, "cudaMalloc(tables)", e);
+    if ((e = cudaMalloc(&M->d_win, win_bytes)) != cudaSuccess) return cleanup(0, "cudaMalloc(window)", e);
+    if ((e = cudaMalloc(&d_stage, stage_bytes)) != cudaSuccess) return cleanup(0, "cudaMalloc(staging)", e);
+
+    char* stage = static_cast<char*>(d_stage);
+    double* d_knots[3];
+    size_t koff = 0;
+    for (int a = 0; a < 3; ++a) {
+        d_knots[a] = reinterpret_cast<double*>(stage + koff);
+        if ((e = cudaMemcpyAsync(d_knots[a], U[a].data(), sizeof(double) * U[a].size(), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+            return cleanup(0, "upload knots", e);
+        koff += sizeof(double) * U[a].size();
+    }
+    int* d_stats = reinterpret_cast<int*>(stage + align_up(knot_bytes, 256));
+    void* d_in = stage + align_up(knot_bytes, 256) + 256;
+    if ((e = cudaMemcpyAsync(d_in, ctrl, in_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cleanup(0, "upload control points", e);
+
+    char* tabs = static_cast<char*>(M->d_tables);
+    for (int a = 0; a < 3; ++a) {
+        AxisDev& A = M->dev.ax[a];
+        A.kup = reinterpret_cast<const float*>(tabs + off_kup[a]);
+        A.grid = reinterpret_cast<const int*>(tabs + off_grid[a]);
+        A.rec = reinterpret_cast<const float*>(tabs + off_rec[a]);
+        A.n = nctrl[a];
+        A.p = degree[a];
+        A.G = G[a];
+        A.Gf = static_cast<float>(G[a]);
+        if ((e = launch_prep_axis(d_knots[a], A.n, A.p, Q, const_cast<float*>(A.kup), const_cast<float*>(A.rec),
+                                  const_cast<int*>(A.grid), A.G, st)) != cudaSuccess)
+            return cleanup(0, "span tables", e);
+    }
+    if ((e = launch_prep_window(d_in, in_dtype, storage, nctrl[0], nctrl[1], nctrl[2], M->d_win, st)) != cudaSuccess)
+        return cleanup(0, "window array", e);
+    if ((e = launch_prep_stats(M->d_win, storage, nctrl[0], nctrl[1], nctrl[2], d_stats, st)) != cudaSuccess)
+        return cleanup(0, "control-point statistics", e);
+    int stats[3];
+    if ((e = cudaMemcpyAsync(stats, d_stats, sizeof stats, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cleanup(0, "read statistics", e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cleanup(0, "model preparation", e);
+    cudaFree(d_stage);
+    d_stage = nullptr;
+
+    auto ord2f = [](int i) {
+        int b = i >= 0 ? i : i ^ 0x7FFFFFFF;
+        float f;
+        std::memcpy(&f, &b, sizeof f);
+        return f;
+    };
+    M->vmin = ord2f(stats[0]);
+    M->vmax = ord2f(stats[1]);
+    M->maxabs = ord2f(stats[2]);
+    M->dev.win = M->d_win;
+    M->dev.nxp = static_cast<int>(nxp);
+    M->dev.nyp = static_cast<int>(nyp);
+    M->dev.nzp = static_cast<int>(nzp);
+    M->dev.q = Q;
+    M->dev.storage = storage;
+    M->bytes = tab + win_bytes;
+    return M;
+}
+
+mfa_model* mfa_model_create(const int degree[3], const int nctrl[3], const double* const knots[3], const void* ctrl,
+                            mfa_dtype dtype)
+{
+    mfa_dtype storage = (dtype == MFA_F16) ? MFA_F16 : (dtype == MFA_BF16) ? MFA_BF16 : MFA_F32;
+    return mfa_model_create_ex(degree, nctrl, knots, ctrl, dtype, storage);
+}
+
+int mfa_model_get_info(const mfa_model* m, mfa_model_info* info)
+{
+    if (!m || !info) return fail(MFA_ERR_ARG, "model and info must be non-NULL");
+    for (int a = 0; a < 3; ++a) {
+        info->degree[a] = m->degree[a];
+        info->nctrl[a] = m->nctrl[a];
+    }
+    info->storage = m->storage;
+    info->vmin = m->vmin;
+    info->vmax = m->vmax;
+    info->device_bytes = m->bytes;
+    info->device = m->device;
+    return MFA_OK;
+}
+
+int mfa_decode(const mfa_model* m, const float* pts, long long n, float* val, float* grad)
+{
+    if (!m) return fail(MFA_ERR_ARG, "model is NULL");
+    if (n < 0) return fail(MFA_ERR_ARG, "n = %lld < 0", n);
+    if (n == 0) return MFA_OK;
+    if (!pts || !val) return fail(MFA_ERR_ARG, "pts and val must be non-NULL");
+    if (int rc = check_model_device(m)) return rc;
+    cudaError_t e = launch_decode(m->dev, pts, n, val, grad, g_stream);
+    return e == cudaSuccess ? MFA_OK : cuda_fail(e, "decode launch");
+}
+
+int mfa_locate_spans(const mfa_model* m, const float* pts, long long n, int* spans)
+{
+    if (!m) return fail(MFA_ERR_ARG, "model is NULL");
+    if (n < 0) return fail(MFA_ERR_ARG, "n = %lld < 0", n);
+    if (n == 0) return MFA_OK;
+    if (!pts || !spans) return fail(MFA_ERR_ARG, "pts and spans must be non-NULL");
+    if (int rc = check_model_device(m)) return rc;
+    cudaError_t e = launch_spans(m->dev, pts, n, spans, g_stream);
+    return e == cudaSuccess ? MFA_OK : cuda_fail(e, "span launch");
+}
+
+int mfa_render_ex(const mfa_model* m, const mfa_camera* cam, const mfa_transfer_fn* tf, int width, int height,
+                  int n_samples, float* rgba_out, const mfa_render_opts* opts)
+{
+    if (!m || !cam || !tf || !rgba_out) return fail(MFA_ERR_ARG, "model, camera, tf and rgba_out must be non-NULL");
+    if (width < 1 || width > 32768 || height < 1 || height > 32768)
+        return fail(MFA_ERR_ARG, "image size %dx%d outside 1..32768", width, height);
+    if (n_samples < 1 || n_samples > (1 << 20)) return fail(MFA_ERR_ARG, "n_samples = %d outside 1..2^20", n_samples);
+    if (tf->n_entries < 1 || tf->n_entries > kTfMax || !tf->rgba)
+        return fail(MFA_ERR_ARG, "transfer function needs 1..%d rows and a table", kTfMax);
+    if (cam->projection != 0 && cam->projection != 1) return fail(MFA_ERR_ARG, "projection must be 0 or 1");
+    if (int rc = check_model_device(m)) return rc;
+
+    // camera frame in FP64, handed to the kernel in FP32
+    double f[3], r[3], u[3];
+    for (int a = 0; a < 3; ++a) f[a] = cam->target[a] - cam->eye[a];
+    double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    if (!(fl > 0.0) || !std::isfinite(fl)) return fail(MFA_ERR_ARG, "camera eye and target coincide");
+    for (double& x : f) x /= fl;
+    r[0] = f[1] * cam->up[2] - f[2] * cam->up[1];
+    r[1] = f[2] * cam->up[0] - f[0] * cam->up[2];
+    r[2] = f[0] * cam->up[1] - f[1] * cam->up[0];
+    double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    double ul = std::sqrt(cam->up[0] * cam->up[0] + cam->up[1] * cam->up[1] + cam->up[2] * cam->up[2]);
+    if (!(rl > 1e-12 * ul) || !std::isfinite(rl)) return fail(MFA_ERR_ARG, "camera up is parallel to the view direction");
+    for (double& x : r) x /= rl;
+    u[0] = r[1] * f[2] - r[2] * f[1];
+    u[1] = r[2] * f[0] - r[0] * f[2];
+    u[2] = r[0] * f[1] - r[1] * f[0];
+    const double aspect = static_cast<double>(width) / height;
+    double sxs, sys;
+    if (cam->projection == 0) {
+        if (!(cam->ortho_height > 0.0) || !std::isfinite(cam->ortho_height))
+            return fail(MFA_ERR_ARG, "ortho_height must be > 0");
+        sys = 0.5 * cam->ortho_height;
+        sxs = sys * aspect;
+    } else {
+        if (!(cam->fov_y_deg > 0.0 && cam->fov_y_deg < 180.0)) return fail(MFA_ERR_ARG, "fov_y_deg outside (0,180)");
+        sys = std::tan(0.5 * cam->fov_y_deg * M_PI / 180.0);
+        sxs = sys * aspect;
+    }
+
+    RenderParams P;
+    std::memset(&P, 0, sizeof P);
+    for (int a = 0; a < 3; ++a) {
+        P.eye[a] = static_cast<float>(cam->eye[a]);
+        P.fwd[a] = static_cast<float>(f[a]);
+        P.rx[a] = static_cast<float>(r[a] * sxs);
+        P.uy[a] = static_cast<float>(u[a] * sys);
+    }
+    P.projection = cam->projection;
+    P.width = width;
+    P.height = height;
+    P.n_samples = n_samples;
+    P.inv_w = 1.0f / static_cast<float>(width);
+    P.inv_h = 1.0f / static_cast<float>(height);
+    const float vmin = std::isnan(tf->vmin) ? m->vmin : tf->vmin;
+    const float vmax = std::isnan(tf->vmax) ? m->vmax : tf->vmax;
+    P.vmin = vmin;
+    P.inv_range = vmax > vmin ? static_cast<float>(1.0 / (static_cast<double>(vmax) - vmin)) : 0.0f;
+    P.tf_n = tf->n_entries;
+    P.shading = tf->shading ? 1 : 0;
+    P.ka = tf->ka;
+    P.kd = tf->kd;
+    P.ks = tf->ks;
+    P.shininess = tf->shininess;
+    P.ert_alpha = tf->ert_alpha >= 1.0f ? INFINITY : tf->ert_alpha;
+    int spans = 0;
+    for (int a = 0; a < 3; ++a) spans = std::max(spans, m->nctrl[a] - m->degree[a]);
+    double scale = std::max(static_cast<double>(m->vmax) - m->vmin, static_cast<double>(m->maxabs));
+    double gt = 1e-6 * scale * spans;
+    P.gtiny2 = static_cast<float>(gt * gt);
+    P.samples_out = opts ? opts->samples_out : nullptr;
+    P.out = reinterpret_cast<float4*>(rgba_out);
+    for (int i = 0; i < tf->n_entries; ++i)
+        P.tf[i] = make_float4(tf->rgba[4 * i], tf->rgba[4 * i + 1], tf->rgba[4 * i + 2], tf->rgba[4 * i + 3]);
+
+    cudaError_t e = launch_render(m->dev, P, g_stream);
+    return e == cudaSuccess ? MFA_OK : cuda_fail(e, "render launch");
+}
+
+int mfa_render(const mfa_model* m, const mfa_camera* cam, const mfa_transfer_fn* tf, int width, int height,
+               int n_samples, float* rgba_out)
+{
+    return mfa_render_ex(m, cam, tf, width, height, n_samples, rgba_out, nullptr);
+}
+
+}  // extern "C"

@@ -1,0 +1,80 @@
+// mfa_internal.cuh -- device-side model description shared by the libmfa translation units.
+//
+// Data layout in HBM (one model):
+//   * window array  W[(n_z+4)][(n_y+4)][(n_x+4)]: entry (k, j, i) holds the four control
+//     points P[k][j][i..i+3] (zero past the end), as float4 (FP32 storage) or as four
+//     16-bit values in 8 bytes (FP16 / BF16).  One aligned vector load then fetches the
+//     whole x-row of a (p+1)^3 support for p <= 3 (two loads for p = 4), instead of p+1
+//     scalar loads at an unaligned offset.  Costs 4x the plain array.
+//   * per axis: kup[n+p+1]  the FP64 knots rounded UP to FP32, so that for an FP32
+//     coordinate u, (u >= kup[s]) is exactly (u >= U[s]) in real arithmetic;
+//     grid[G]  (G = 4 (n - p)) the span containing g / G, a starting guess for the span
+//     search; rec[(n-p) * RS(Q)]  one record per knot span: {U_s, 1/h, c[0..Q-1][0..Q-1]}
+//     with c[r][k] the power-basis coefficient of t^k of N_{s-p+r,p} on that span,
+//     t = (u - U_s)/h, h = U_{s+1} - U_s (computed in FP64, rounded to FP32).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mfa {
+
+constexpr int kMaxDegree = 4;
+constexpr int kMaxQ = kMaxDegree + 1;
+constexpr int kTfMax = 256;
+constexpr int kPad = 4;                 // zero padding added to every axis of the window array
+
+// floats per span record for Q = p_max + 1: {U_s, 1/h} + Q*Q coefficients, padded to float4
+__host__ __device__ constexpr int rec_stride(int q) { return ((2 + q * q) + 3) / 4 * 4; }
+
+struct AxisDev {
+    const float* kup;   // n + p + 1 knots rounded up to FP32
+    const float* rec;   // n - p span records of rec_stride(Q) floats
+    const int* grid;    // G starting spans
+    int n, p;           // control points and degree on this axis
+    int G;              // grid cells
+    float Gf;           // (float)G
+};
+
+struct ModelDev {
+    AxisDev ax[3];
+    const void* win;    // window array (see above)
+    int nxp, nyp, nzp;  // padded sizes n + kPad
+    int q;              // Q = max degree + 1 (kernel template parameter)
+    int storage;        // mfa_dtype of the window values
+};
+
+// Render parameters passed by value as kernel arguments (about 4.3 KB with the table).
+struct RenderParams {
+    float eye[3];       // ray origin (perspective) / view centre (orthographic)
+    float fwd[3];       // unit view direction
+    float rx[3];        // image-plane step for sx in [-1,1]: right * half-width (ortho) or
+                        // right * tan(fov/2) * aspect (perspective)
+    float uy[3];        // same for sy: up * half-height or up * tan(fov/2)
+    int projection;     // 0 ortho, 1 perspective
+    int width, height, n_samples;
+    float inv_w, inv_h; // 1/width, 1/height
+    float vmin, inv_range;   // transfer-function normalisation (inv_range 0 if vmax <= vmin)
+    int tf_n;           // table rows
+    int shading;
+    float ka, kd, ks, shininess;
+    float ert_alpha;    // >= 1: no early termination
+    float gtiny2;       // squared gradient-norm threshold for an undefined normal
+    unsigned long long* samples_out;   // optional device counter
+    float4* out;        // height * width premultiplied RGBA
+    float4 tf[kTfMax];  // non-premultiplied RGBA rows
+};
+
+// launchers (defined in the .cu files), all asynchronous on `stream`
+cudaError_t launch_prep_axis(const double* d_knots, int n, int p, int q, float* kup, float* rec, int* grid,
+                             int G, cudaStream_t stream);
+cudaError_t launch_prep_window(const void* d_ctrl, int in_dtype, int storage, int nx, int ny, int nz,
+                               void* win, cudaStream_t stream);
+cudaError_t launch_prep_stats(const void* win, int storage, int nx, int ny, int nz, int* d_stats,
+                              cudaStream_t stream);
+cudaError_t launch_decode(const ModelDev& m, const float* pts, long long n, float* val, float* grad,
+                          cudaStream_t stream);
+cudaError_t launch_spans(const ModelDev& m, const float* pts, long long n, int* spans, cudaStream_t stream);
+cudaError_t launch_render(const ModelDev& m, const RenderParams& rp, cudaStream_t stream);
+
+}  // namespace mfa

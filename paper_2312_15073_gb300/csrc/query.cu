@@ -1,0 +1,91 @@
+// query.cu -- value+gradient queries at arbitrary points (decode; Sec. III-B, the query of
+// Fig. 8 in Sec. V-D.3) and the knot-span search on its own.
+//
+// One thread per point, grid-stride.  Per point: clamp to [0,1], locate the three spans,
+// evaluate the span-local basis and derivatives, contract the (p+1)^3 support.  Points
+// are read as three scalar FP32 loads (12 B, coalesced across the warp), values and
+// gradients written as scalar stores; for random points the control-point gathers hit
+// L2 (the window array of a 128^3 FP32 model is 32 MiB).
+#include "bspline.cuh"
+
+namespace mfa {
+namespace {
+
+template <int Q, int STORAGE>
+__global__ void __launch_bounds__(256) k_decode(ModelDev M, const float* __restrict__ pts, long long n,
+                                                float* __restrict__ val, float* __restrict__ grad)
+{
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const float u = clamp01(__ldg(pts + 3 * i + 0));
+        const float v = clamp01(__ldg(pts + 3 * i + 1));
+        const float w = clamp01(__ldg(pts + 3 * i + 2));
+        const int sx = locate_span(M.ax[0], u);
+        const int sy = locate_span(M.ax[1], v);
+        const int sz = locate_span(M.ax[2], w);
+        const float4 r = query<Q, STORAGE>(M, u, v, w, sx, sy, sz);
+        val[i] = r.x;
+        if (grad) {
+            grad[3 * i + 0] = r.y;
+            grad[3 * i + 1] = r.z;
+            grad[3 * i + 2] = r.w;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_spans(ModelDev M, const float* __restrict__ pts, long long n,
+                                               int* __restrict__ spans)
+{
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) spans[3 * i + a] = locate_span(M.ax[a], clamp01(__ldg(pts + 3 * i + a)));
+    }
+}
+
+int grid_for(long long n, int threads)
+{
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = (n + threads - 1) / threads;
+    const long long cap = static_cast<long long>(sms) * 32;   // enough resident blocks to fill every SM
+    return static_cast<int>(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+template <int Q>
+cudaError_t decode_q(const ModelDev& m, const float* pts, long long n, float* val, float* grad, cudaStream_t st)
+{
+    const int blocks = grid_for(n, 256);
+    switch (m.storage) {
+    case 1: k_decode<Q, 1><<<blocks, 256, 0, st>>>(m, pts, n, val, grad); break;
+    case 2: k_decode<Q, 2><<<blocks, 256, 0, st>>>(m, pts, n, val, grad); break;
+    case 3: k_decode<Q, 3><<<blocks, 256, 0, st>>>(m, pts, n, val, grad); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_decode(const ModelDev& m, const float* pts, long long n, float* val, float* grad,
+                          cudaStream_t stream)
+{
+    if (n <= 0) return cudaSuccess;
+    switch (m.q) {
+    case 2: return decode_q<2>(m, pts, n, val, grad, stream);
+    case 3: return decode_q<3>(m, pts, n, val, grad, stream);
+    case 4: return decode_q<4>(m, pts, n, val, grad, stream);
+    case 5: return decode_q<5>(m, pts, n, val, grad, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_spans(const ModelDev& m, const float* pts, long long n, int* spans, cudaStream_t stream)
+{
+    if (n <= 0) return cudaSuccess;
+    k_spans<<<grid_for(n, 256), 256, 0, stream>>>(m, pts, n, spans);
+    return cudaGetLastError();
+}
+
+}  // namespace mfa

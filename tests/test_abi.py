@@ -1,0 +1,91 @@
+"""The C-ABI library builds, loads without a GPU, exports every function include/mfa.h
+declares, and rejects bad arguments on the host before touching CUDA (CPU only)."""
+import ctypes
+import math
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b(mfa_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def libmfa():
+    from paper_2312_15073_gb300 import build
+    build.build()
+    import paper_2312_15073_gb300 as mfa
+    return mfa.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for want in ("mfa_model_create", "mfa_decode", "mfa_render", "mfa_model_destroy", "mfa_last_error"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(libmfa):
+    from paper_2312_15073_gb300 import LIB_PATH
+    out = subprocess.run(["nm", "-D", "--defined-only", LIB_PATH], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    for name in _declared_functions():
+        assert name in exported, name
+        assert hasattr(libmfa, name)
+
+
+def test_host_side_argument_checks(libmfa):
+    import paper_2312_15073_gb300 as mfa
+    L = libmfa
+    assert L.mfa_decode(None, None, 10, None, None) == -1
+    assert "NULL" in L.mfa_last_error().decode()
+    assert L.mfa_decode(None, None, 0, None, None) == -1          # model is still required
+    assert L.mfa_locate_spans(None, None, -1, None) == -1
+    cam = mfa.camera(dict(projection=0, eye=(0, 0, 2), target=(0, 0, 0), up=(0, 1, 0), ortho_height=1.0))
+    tf = mfa.transfer_fn(np.zeros((4, 4)))
+    assert L.mfa_render(None, ctypes.byref(cam), ctypes.byref(tf.struct), 8, 8, 8, None) == -1
+    # model creation rejects bad degrees, counts and knots before any device work
+    deg = (ctypes.c_int * 3)(3, 3, 5)
+    nc = (ctypes.c_int * 3)(8, 8, 8)
+    ctrl = np.zeros(512)
+    assert not L.mfa_model_create(ctypes.byref(deg), ctypes.byref(nc), None, ctrl.ctypes.data, 0)
+    assert "degree" in L.mfa_last_error().decode()
+    deg = (ctypes.c_int * 3)(3, 3, 3)
+    nc = (ctypes.c_int * 3)(8, 3, 8)
+    assert not L.mfa_model_create(ctypes.byref(deg), ctypes.byref(nc), None, ctrl.ctypes.data, 0)
+    assert "nctrl" in L.mfa_last_error().decode()
+    nc = (ctypes.c_int * 3)(8, 8, 8)
+    bad = np.array([0, 0, 0, 0, 0.5, 0.4, 0.8, 0.9, 1, 1, 1, 1.0])      # decreasing
+    ok = np.array([0, 0, 0, 0, 0.2, 0.4, 0.8, 0.9, 1, 1, 1, 1.0])
+    kp = (ctypes.c_void_p * 3)(ok.ctypes.data, bad.ctypes.data, None)
+    assert not L.mfa_model_create(ctypes.byref(deg), ctypes.byref(nc), ctypes.byref(kp), ctrl.ctypes.data, 0)
+    assert "knots[1]" in L.mfa_last_error().decode()
+    unclamped = np.array([0, 0, 0, 0.1, 0.2, 0.4, 0.8, 0.9, 1, 1, 1, 1.0])
+    kp = (ctypes.c_void_p * 3)(unclamped.ctypes.data, None, None)
+    assert not L.mfa_model_create(ctypes.byref(deg), ctypes.byref(nc), ctypes.byref(kp), ctrl.ctypes.data, 0)
+    assert "knots[0]" in L.mfa_last_error().decode()
+    assert not L.mfa_model_create_ex(ctypes.byref(deg), ctypes.byref(nc), None, ctrl.ctypes.data, 0, 0)
+    assert "storage" in L.mfa_last_error().decode()
+    L.mfa_model_destroy(None)          # a no-op
+
+
+def test_library_fails_loudly_when_missing(monkeypatch, tmp_path):
+    import paper_2312_15073_gb300 as mfa
+    monkeypatch.setattr(mfa, "LIB_PATH", str(tmp_path / "nope.so"))
+    monkeypatch.setattr(mfa, "_lib", None)
+    with pytest.raises(RuntimeError, match="no fallback"):
+        mfa.lib()

@@ -1,0 +1,284 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by
+element on the same seeded inputs.
+
+Gates (FP32 arithmetic): value e_v <= 1e-5, gradient e_g <= 1e-4, image RMSE <= 1e-3 per
+channel; knot spans bit-exact.  For FP16 / BF16 storage the gates apply to the KERNEL
+error, i.e. against the oracle run on the same rounded control points; the error
+against the unrounded FP64 control points is measured and printed, not gated.
+"""
+import math
+import zlib
+
+import numpy as np
+import pytest
+
+import synth
+from metrics import GRAD_TOL, IMAGE_RMSE_TOL, VALUE_TOL, grad_error, image_rmse, value_error
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mfa():
+    import torch
+    from paper_2312_15073_gb300 import build
+    build.build()
+    import paper_2312_15073_gb300 as m
+    assert torch.cuda.is_available()
+    return m
+
+
+def _seed(*key) -> int:
+    """A seed that is the same in every process (str hashing is randomised)."""
+    return zlib.crc32(repr(key).encode())
+
+
+def _stored(ctrl64, storage, orc):
+    """The control-point values a model with this storage type holds, as FP64."""
+    if storage == 1:
+        return np.asarray(ctrl64, np.float64).astype(np.float32).astype(np.float64)
+    if storage == 2:
+        return orc.round_to_f16(ctrl64)
+    return orc.round_to_bf16(ctrl64)
+
+
+def _edge_points(knots, rng, n_random):
+    """Random points plus corners, the FP32 values nearest every knot (and their FP32
+    neighbours), out-of-domain points and a NaN."""
+    pts = [rng.uniform(0, 1, (n_random, 3)).astype(np.float32)]
+    specials = []
+    for a in range(3):
+        for kv in np.unique(knots[a]):
+            f = np.float32(kv)
+            for v in (np.nextafter(f, np.float32(-1)), f, np.nextafter(f, np.float32(2))):
+                p = rng.uniform(0, 1, 3).astype(np.float32)
+                p[a] = v
+                specials.append(p)
+    for c in np.array(np.meshgrid([0, 1], [0, 1], [0, 1])).T.reshape(-1, 3):
+        specials.append(c.astype(np.float32))
+    specials += [np.array([-0.5, 0.3, 1.5], np.float32), np.array([2.0, -1.0, 0.5], np.float32),
+                 np.array([np.nan, 0.25, 0.75], np.float32)]
+    pts.append(np.stack(specials))
+    return np.concatenate(pts)
+
+
+def _make(mfa, orc, rng, degree, nctrl, uniform, storage=1, field=None):
+    knots = [synth.knots_uniform(nctrl[a], degree[a]) if uniform[a] else synth.knots_nonuniform(nctrl[a], degree[a], rng)
+             for a in range(3)]
+    if field is None:
+        field = synth.GaussianSum.draw(rng, 6)
+    P = synth.sample_ctrl(field, knots, degree, rng, 0.01)
+    model = mfa.Model(degree, nctrl, knots, P, storage=storage)
+    ref = orc.Model(degree, nctrl, knots, _stored(P, storage, orc))
+    return model, ref, P
+
+
+CASES = [((3, 3, 3), (13, 9, 11), (True, True, True)),
+         ((3, 3, 3), (21, 17, 19), (False, False, False)),
+         ((1, 1, 1), (7, 5, 6), (True, False, True)),
+         ((2, 2, 2), (10, 12, 8), (False, True, False)),
+         ((4, 4, 4), (9, 11, 10), (True, False, False)),
+         ((2, 3, 4), (8, 9, 12), (False, True, True)),
+         ((4, 1, 3), (6, 5, 7), (True, True, False))]
+
+
+@pytest.mark.parametrize("degree,nctrl,uniform", CASES)
+@pytest.mark.parametrize("storage", [1, 2, 3], ids=["f32", "f16", "bf16"])
+def test_decode_matches_oracle(mfa, orc, degree, nctrl, uniform, storage):
+    import torch
+    rng = np.random.default_rng(_seed(degree, nctrl, uniform, storage))
+    model, ref, P = _make(mfa, orc, rng, degree, nctrl, uniform, storage)
+    pts = _edge_points(ref.knots, rng, 5003)
+    val, grad = mfa.decode(model, torch.from_numpy(pts).cuda())
+    spans = mfa.locate_spans(model, torch.from_numpy(pts).cuda())
+    torch.cuda.synchronize()
+    v_ref, g_ref, s_ref = ref.decode(pts, spans=True)
+    np.testing.assert_array_equal(spans.cpu().numpy(), s_ref)
+    ev = value_error(val.cpu().numpy(), v_ref, ref.ctrl)
+    eg = grad_error(grad.cpu().numpy(), g_ref)
+    assert ev <= VALUE_TOL, ev
+    assert eg <= GRAD_TOL, eg
+    # values-only call gives the same values
+    val2, _ = mfa.decode(model, torch.from_numpy(pts).cuda(), want_grad=False)
+    np.testing.assert_array_equal(val2.cpu().numpy(), val.cpu().numpy())
+
+
+def test_decode_reduced_precision_total_error(mfa, orc):
+    """Error of FP16 / BF16 storage against the unrounded FP64 control points (reported)."""
+    import torch
+    rng = np.random.default_rng(5)
+    degree, nctrl = (3, 3, 3), (24, 20, 22)
+    knots = [synth.knots_nonuniform(n, 3, rng) for n in nctrl]
+    P = synth.sample_ctrl(synth.Turbulence.draw(rng, 64, 1.0, 8.0), knots, degree, rng, 0.0)
+    exact = orc.Model(degree, nctrl, knots, P)
+    pts = rng.uniform(0, 1, (20000, 3)).astype(np.float32)
+    v_ref, g_ref = exact.decode(pts)
+    out = {}
+    for storage, name in ((1, "f32"), (2, "f16"), (3, "bf16")):
+        m = mfa.Model(degree, nctrl, knots, P, storage=storage)
+        v, g = mfa.decode(m, torch.from_numpy(pts).cuda())
+        out[name] = (value_error(v.cpu().numpy(), v_ref, P), grad_error(g.cpu().numpy(), g_ref))
+    print("total error vs FP64 ctrl (value, gradient):", out)
+    assert out["f32"][0] <= VALUE_TOL and out["f32"][1] <= GRAD_TOL
+    assert out["f32"][0] <= out["f16"][0] <= out["bf16"][0]        # precision ordering
+
+
+def test_decode_empty_and_ragged(mfa, orc):
+    import torch
+    rng = np.random.default_rng(6)
+    model, ref, _ = _make(mfa, orc, rng, (3, 3, 3), (8, 8, 8), (True, True, True))
+    empty = torch.empty((0, 3), device="cuda")
+    v, g = mfa.decode(model, empty)
+    assert v.numel() == 0 and g.numel() == 0
+    for n in (1, 31, 33, 255, 257, 70001):
+        pts = rng.uniform(0, 1, (n, 3)).astype(np.float32)
+        v, g = mfa.decode(model, torch.from_numpy(pts).cuda())
+        vr, gr = ref.decode(pts)
+        assert value_error(v.cpu().numpy(), vr, ref.ctrl) <= VALUE_TOL
+
+
+def test_decode_full_size_128cube_2pow24(mfa, orc):
+    """The decode workload at full size: degree 3, 128^3 FP32 control points, 2^24
+    uniform points; every point checked against the oracle."""
+    import torch
+    wl = synth.config2(decode_n=1 << 24)
+    spec = wl.model
+    model = mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl)
+    ref = orc.Model.from_spec(spec)
+    pts = wl.decode_points
+    v, g = mfa.decode(model, torch.from_numpy(pts).cuda())
+    torch.cuda.synchronize()
+    vr, gr = ref.decode(pts)
+    ev, eg = value_error(v.cpu().numpy(), vr, ref.ctrl), grad_error(g.cpu().numpy(), gr)
+    print(f"decode 128^3 2^24: e_v={ev:.3e} e_g={eg:.3e}")
+    assert ev <= VALUE_TOL and eg <= GRAD_TOL
+
+
+# ----------------------------------------------------------------------------------------
+# rendering
+# ----------------------------------------------------------------------------------------
+
+def _render_both(mfa, orc, model, ref, job, pixels=None, vmin=math.nan, vmax=math.nan):
+    import torch
+    tf = mfa.transfer_fn(job.tf, shading=job.shading, ka=job.ka, kd=job.kd, ks=job.ks, shininess=job.shininess,
+                         ert_alpha=job.ert_alpha, vmin=vmin, vmax=vmax)
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    img = mfa.render(model, job.camera, tf, job.width, job.height, job.n_samples, samples_out=cnt)
+    torch.cuda.synchronize()
+    img = img.cpu().numpy().astype(np.float64)
+    rimg, rcount = orc.render(ref, job.camera, job.tf, job.width, job.height, job.n_samples, shading=job.shading,
+                              ka=job.ka, kd=job.kd, ks=job.ks, shininess=job.shininess, ert_alpha=job.ert_alpha,
+                              vmin=vmin, vmax=vmax, pixels=pixels)
+    gimg = img.reshape(-1, 4)[pixels] if pixels is not None else img
+    return gimg, rimg, int(cnt.item()), rcount
+
+
+def test_render_small_config_full_image(mfa, orc):
+    """Degree 3, 32^3 FP64 control points, ortho 256^2, 128 samples, no shading, ERT
+    0.99: every pixel against the oracle."""
+    wl = synth.config1()
+    spec = wl.model
+    model = mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl)
+    ref = orc.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl64.astype(np.float32).astype(np.float64))
+    g, r, gc, rc = _render_both(mfa, orc, model, ref, wl.render)
+    rmse = image_rmse(g, r)
+    print("config-1 RMSE per channel:", rmse, "max abs:", np.abs(g - r).max(), "samples gpu/oracle:", gc, rc)
+    assert np.all(rmse <= IMAGE_RMSE_TOL)
+    assert np.abs(g - r).max() <= 5e-3
+    assert abs(gc - rc) <= 1e-4 * rc
+    assert r[..., 3].max() > 0.5          # the image is not trivially empty
+
+
+RENDER_CASES = [
+    # degree, nctrl, uniform, camera, W, H, ns, shading
+    ((3, 3, 3), (16, 12, 14), (True, True, True), "persp", 37, 23, 96, True),
+    ((3, 3, 3), (20, 20, 20), (False, False, False), "persp", 64, 48, 200, True),
+    ((2, 3, 4), (10, 11, 12), (True, False, True), "ortho_oblique", 33, 41, 64, True),
+    ((1, 1, 1), (9, 9, 9), (True, True, True), "persp", 20, 20, 50, False),
+    ((4, 4, 4), (12, 10, 11), (False, True, False), "persp_inside", 24, 16, 80, True),
+]
+
+
+def _camera(kind, rng):
+    c = (0.5, 0.5, 0.5)
+    if kind == "persp":
+        d = synth.random_direction(rng)
+        return synth.camera_persp(np.array(c) + 2.2 * d, c, synth.view_up_for(d), 35.0)
+    if kind == "ortho_oblique":
+        return synth.camera_ortho((2.0, 1.4, 2.3), c, (0, 1, 0), 1.6)
+    return synth.camera_persp((0.45, 0.55, 0.6), (0.7, 0.2, 0.1), (0, 1, 0), 70.0)   # eye inside the box
+
+
+@pytest.mark.parametrize("degree,nctrl,uniform,cam,W,H,ns,shading", RENDER_CASES)
+def test_render_matches_oracle(mfa, orc, degree, nctrl, uniform, cam, W, H, ns, shading):
+    rng = np.random.default_rng(_seed(degree, nctrl, cam))
+    model, ref, _ = _make(mfa, orc, rng, degree, nctrl, uniform)
+    job = synth.RenderJob(_camera(cam, rng), W, H, ns, synth.ramp_tf(256, 0.08), shading)
+    g, r, gc, rc = _render_both(mfa, orc, model, ref, job)
+    rmse = image_rmse(g, r)
+    assert np.all(rmse <= IMAGE_RMSE_TOL), rmse
+    assert abs(gc - rc) <= max(2, 1e-3 * rc)
+    assert r[..., 3].max() > 0.05
+
+
+def test_render_full_size_persp_1024(mfa, orc):
+    """The render workload at full size (degree 3, 128^3 FP32, perspective 1024^2, 1024
+    samples, Phong): the whole frame on the GPU, 4096 seeded pixels plus two full rows
+    through the oracle."""
+    wl = synth.config2(with_points=False)
+    spec = wl.model
+    model = mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl)
+    ref = orc.Model.from_spec(spec)
+    rng = np.random.default_rng(99)
+    W, H = wl.render.width, wl.render.height
+    pix = np.concatenate([rng.choice(W * H, 4096, replace=False), np.arange(300 * W, 301 * W),
+                          np.arange(700 * W, 701 * W)])
+    g, r, gc, rc = _render_both(mfa, orc, model, ref, wl.render, pixels=pix)
+    rmse = image_rmse(g, r)
+    print("1024^2 RMSE per channel:", rmse, "max abs:", np.abs(g - r).max(), "gpu samples:", gc)
+    assert np.all(rmse <= IMAGE_RMSE_TOL)
+    assert r[:, 3].max() > 0.5
+
+
+def test_render_constant_density_closed_form(mfa, orc):
+    """Constant field and table: A = 1 - (1-a)^n, C = rgb A (no early termination), and
+    with termination the stop index k* = ceil(ln(1-alpha_T)/ln(1-a))."""
+    import torch
+    n = 6
+    model = mfa.Model((3, 3, 3), (n, n, n), None, np.full((n, n, n), 0.4))
+    cam = synth.camera_ortho((0.5, 0.5, 2.5), (0.5, 0.5, 0.5), (0, 1, 0), 1.0)
+    rgba = np.float32([0.25, 0.5, 0.75, 0.05]).astype(np.float64)
+    for ns, ert in ((64, 1.0), (128, 0.99)):
+        tf = mfa.transfer_fn(synth.constant_tf(rgba), ert_alpha=ert)
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        img = mfa.render(model, cam, tf, 16, 16, ns, samples_out=cnt).cpu().numpy()
+        k = ns if ert >= 1 else math.ceil(math.log(1 - ert) / math.log(1 - rgba[3]))
+        A = 1 - (1 - rgba[3]) ** k
+        np.testing.assert_allclose(img[..., 3], A, atol=2e-6)
+        np.testing.assert_allclose(img[..., :3], np.broadcast_to(rgba[:3] * A, (16, 16, 3)), atol=2e-6)
+        assert int(cnt.item()) == 256 * k
+
+
+def test_render_edge_cases(mfa, orc):
+    import torch
+    rng = np.random.default_rng(8)
+    model, ref, _ = _make(mfa, orc, rng, (3, 3, 3), (10, 10, 10), (True, True, True))
+    cam = synth.camera_persp((0.5, 0.5, 2.5), (0.5, 0.5, 0.5), (0, 1, 0), 30.0)
+    # a camera looking away: every ray misses, nothing is evaluated
+    away = synth.camera_persp((0.5, 0.5, 2.5), (0.5, 0.5, 5.0), (0, 1, 0), 30.0)
+    tf = mfa.transfer_fn(synth.ramp_tf(256, 0.1))
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    img = mfa.render(model, away, tf, 19, 7, 32, samples_out=cnt)
+    assert float(img.abs().max()) == 0.0 and int(cnt.item()) == 0
+    # 1x1 image, one sample, one-row table, no termination
+    for W, H, ns, table in ((1, 1, 1, synth.ramp_tf(256, 0.1)), (3, 2, 1, synth.constant_tf((1, 0, 0, 0.5), 1)),
+                            (5, 3, 7, synth.ramp_tf(2, 0.9))):
+        job = synth.RenderJob(cam, W, H, ns, table, True, ert_alpha=1.0)
+        g, r, gc, rc = _render_both(mfa, orc, model, ref, job)
+        np.testing.assert_allclose(g, r, atol=1e-4)
+        assert gc == rc
+    # rejected arguments leave the output untouched
+    out = torch.full((4, 4, 4), 7.0, device="cuda")
+    with pytest.raises(mfa.MfaError):
+        mfa.render(model, cam, tf, 4, 4, 0, out=out)
+    assert float(out.min()) == 7.0
