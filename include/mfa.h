@@ -143,7 +143,13 @@ typedef struct {
     unsigned long long* samples_out;  /* DEVICE counter or NULL: the number of samples
                                          evaluated (after box clipping and early
                                          termination) is ADDED to it */
-    int reserved[8];                  /* zero */
+    int variant;                      /* kernel variant: 0 = library default (2);
+                                         1 = span records cached in registers along the
+                                         ray, packed FP32x2 arithmetic; 2 = records cached,
+                                         scalar FP32; 3 = nothing cached, scalar FP32.
+                                         Variants differ only in FP32 summation order.
+                                         MFA_ERR_ARG outside 0..3. */
+    int reserved[7];                  /* zero */
 } mfa_render_opts;
 
 /*

@@ -47,7 +47,7 @@ class _TF(ctypes.Structure):
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("samples_out", c_void_p), ("reserved", c_int * 8)]
+    _fields_ = [("samples_out", c_void_p), ("variant", c_int), ("reserved", c_int * 7)]
 
 
 class _Info(ctypes.Structure):
@@ -229,7 +229,7 @@ class transfer_fn:
 
 
 def render(model: Model, cam, tf: transfer_fn, width: int, height: int, n_samples: int, out=None,
-           samples_out=None):
+           samples_out=None, variant: int = 0):
     """Premultiplied RGBA image (height, width, 4) FP32 on the current device.
     samples_out: optional 1-element int64 CUDA tensor to which the number of evaluated
     samples is added."""
@@ -240,6 +240,7 @@ def render(model: Model, cam, tf: transfer_fn, width: int, height: int, n_sample
         raise ValueError("out must be a contiguous (height, width, 4) FP32 CUDA tensor")
     c = cam if isinstance(cam, _Camera) else camera(cam)
     opts = _Opts()
+    opts.variant = int(variant)
     if samples_out is not None:
         if not (samples_out.is_cuda and samples_out.dtype == torch.int64):
             raise TypeError("samples_out must be an int64 CUDA tensor")

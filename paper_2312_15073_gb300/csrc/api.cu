@@ -302,6 +302,8 @@ int mfa_render_ex(const mfa_model* m, const mfa_camera* cam, const mfa_transfer_
     if (tf->n_entries < 1 || tf->n_entries > kTfMax || !tf->rgba)
         return fail(MFA_ERR_ARG, "transfer function needs 1..%d rows and a table", kTfMax);
     if (cam->projection != 0 && cam->projection != 1) return fail(MFA_ERR_ARG, "projection must be 0 or 1");
+    const int variant = opts ? opts->variant : 0;
+    if (variant < 0 || variant > 3) return fail(MFA_ERR_ARG, "render variant %d outside 0..3", variant);
     if (int rc = check_model_device(m)) return rc;
 
     // camera frame in FP64, handed to the kernel in FP32
@@ -368,7 +370,7 @@ int mfa_render_ex(const mfa_model* m, const mfa_camera* cam, const mfa_transfer_
     for (int i = 0; i < tf->n_entries; ++i)
         P.tf[i] = make_float4(tf->rgba[4 * i], tf->rgba[4 * i + 1], tf->rgba[4 * i + 2], tf->rgba[4 * i + 3]);
 
-    cudaError_t e = launch_render(m->dev, P, g_stream);
+    cudaError_t e = launch_render(m->dev, P, variant, g_stream);
     return e == cudaSuccess ? MFA_OK : cuda_fail(e, "render launch");
 }
 

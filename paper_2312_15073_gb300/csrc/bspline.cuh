@@ -1,6 +1,13 @@
 // bspline.cuh -- device building blocks of one MFA value+gradient query (Sec. III-B,
 // Sec. V-D.3): knot-span location per axis, basis values and derivatives on the span,
 // and the (p+1)^3 control-point contraction for the value and the three partials.
+//
+// Two arithmetic forms of the same computation:
+//   * scalar FP32 FMAs;
+//   * packed FP32x2 (`fma.rn.f32x2`, `mul.rn.f32x2` on sm_100+), which advance two
+//     basis functions, two support columns or two partial sums per instruction and so
+//     halve the issue slots the query needs.  Each lane of a packed op is an ordinary
+//     FP32 round-to-nearest FMA / multiply.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -10,6 +17,10 @@
 #include "mfa_internal.cuh"
 
 namespace mfa {
+
+// ----------------------------------------------------------------------------------------
+// knot spans
+// ----------------------------------------------------------------------------------------
 
 // Knot span of u (u already clamped to [0,1]): the largest s in [p, n-1] with
 // U[s] <= u.  kup holds the knots rounded up to FP32, so the FP32 comparisons below give
@@ -33,16 +44,50 @@ __device__ __forceinline__ int walk_span(const AxisDev& A, float u, int s)
     return s;
 }
 
-// The Q basis functions N_{s-p+r,p} on span s (zero for r > p) and their derivatives
-// with respect to the local coordinate t = (u - U_s)/h, by joint Horner evaluation of
-// the span's power-basis coefficients.  inv_h receives 1/h (d/du = inv_h d/dt).
+// ----------------------------------------------------------------------------------------
+// packed FP32x2 helpers
+// ----------------------------------------------------------------------------------------
+
+struct f2 {
+    unsigned long long v;
+};
+
+__device__ __forceinline__ f2 pk2(float a, float b)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(f2 x, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v)); }
+__device__ __forceinline__ float hsum2(f2 x)
+{
+    float a, b;
+    upk2(x, a, b);
+    return a + b;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+
+// ----------------------------------------------------------------------------------------
+// span records and basis functions
+// ----------------------------------------------------------------------------------------
+
+// A span record {U_s, 1/h, lo, hi, c[k][r]} copied into registers.
 template <int Q>
-__device__ __forceinline__ void span_basis(const AxisDev& A, int s, float u, float (&N)[Q], float (&D)[Q],
-                                           float& inv_h)
+__device__ __forceinline__ void load_record(const AxisDev& A, int s, float (&rec)[rec_stride(Q)])
 {
     constexpr int RS = rec_stride(Q);
     const float4* r4 = reinterpret_cast<const float4*>(A.rec + (s - A.p) * RS);
-    float rec[RS];
 #pragma unroll
     for (int v = 0; v < RS / 4; ++v) {
         float4 x = __ldg(r4 + v);
@@ -51,36 +96,87 @@ __device__ __forceinline__ void span_basis(const AxisDev& A, int s, float u, flo
         rec[4 * v + 2] = x.z;
         rec[4 * v + 3] = x.w;
     }
-    inv_h = rec[1];
-    const float t = (u - rec[0]) * inv_h;
+}
+
+// The Q basis functions N_{s-p+r,p} on the record's span (zero for r > p) and their
+// derivatives with respect to the local coordinate t = (u - U_s)/h, by joint Horner
+// evaluation of the power-basis coefficients (value b and derivative d together:
+// d <- d t + b, b <- b t + c_k).  d/du = (1/h) d/dt = rec[1] d/dt.
+template <int Q>
+__device__ __forceinline__ void record_basis(const float (&rec)[rec_stride(Q)], float u, float (&N)[Q], float (&D)[Q])
+{
+    constexpr int QP = qpair(Q);
+    const float t = (u - rec[0]) * rec[1];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const float* c = rec + 2 + i * Q;
-        float b = c[Q - 1], d = 0.0f;
+        float b = rec[kRecHead + (Q - 1) * QP + i], d = 0.0f;
 #pragma unroll
         for (int k = Q - 2; k >= 0; --k) {
             d = fmaf(d, t, b);
-            b = fmaf(b, t, c[k]);
+            b = fmaf(b, t, rec[kRecHead + k * QP + i]);
         }
         N[i] = b;
         D[i] = d;
     }
 }
 
-// One x-row of the support: Q consecutive control points as FP32.
-template <int Q, int STORAGE>
-__device__ __forceinline__ void load_row(const void* win, int idx, float (&row)[Q]);
+// Packed form: functions (2m, 2m+1) advance together; N2[m] = {N_2m, N_2m+1}, D2 likewise.
+template <int Q>
+__device__ __forceinline__ void record_basis2(const float (&rec)[rec_stride(Q)], float u, f2 (&N2)[qpair(Q) / 2],
+                                              f2 (&D2)[qpair(Q) / 2])
+{
+    constexpr int QP = qpair(Q);
+    const float t = (u - rec[0]) * rec[1];
+    const f2 t2 = pk2(t, t);
+#pragma unroll
+    for (int m = 0; m < QP / 2; ++m) {
+        f2 b = pk2(rec[kRecHead + (Q - 1) * QP + 2 * m], rec[kRecHead + (Q - 1) * QP + 2 * m + 1]);
+        f2 d = b;                                   // first step of d <- d t + b with d = 0
+        b = fma2(b, t2, pk2(rec[kRecHead + (Q - 2) * QP + 2 * m], rec[kRecHead + (Q - 2) * QP + 2 * m + 1]));
+#pragma unroll
+        for (int k = Q - 3; k >= 0; --k) {
+            d = fma2(d, t2, b);
+            b = fma2(b, t2, pk2(rec[kRecHead + k * QP + 2 * m], rec[kRecHead + k * QP + 2 * m + 1]));
+        }
+        N2[m] = b;
+        D2[m] = d;
+    }
+}
 
+// Loads span s's record and evaluates it at u; inv_h receives 1/h.
+template <int Q>
+__device__ __forceinline__ void span_basis(const AxisDev& A, int s, float u, float (&N)[Q], float (&D)[Q],
+                                           float& inv_h)
+{
+    float rec[rec_stride(Q)];
+    load_record<Q>(A, s, rec);
+    inv_h = rec[1];
+    record_basis<Q>(rec, u, N, D);
+}
+
+// ----------------------------------------------------------------------------------------
+// control-point rows
+// ----------------------------------------------------------------------------------------
+
+// One x-row of the support: QP consecutive control points as FP32 (the entries past Q meet
+// zero basis values; they are always inside the zero-padded window array).
 template <int Q>
 struct RowF32 {
-    static __device__ __forceinline__ void load(const void* win, int idx, float (&row)[Q])
+    static __device__ __forceinline__ void load(const void* win, int idx, float (&row)[qpair(Q)])
     {
         const float4* W = static_cast<const float4*>(win);
         float4 v = __ldg(W + idx);
-        float tmp[4] = { v.x, v.y, v.z, v.w };
-#pragma unroll
-        for (int a = 0; a < Q && a < 4; ++a) row[a] = tmp[a];
-        if constexpr (Q == 5) row[4] = __ldg(reinterpret_cast<const float*>(W + idx + 4));
+        row[0] = v.x;
+        row[1] = v.y;
+        if constexpr (qpair(Q) >= 4) {
+            row[2] = v.z;
+            row[3] = v.w;
+        }
+        if constexpr (qpair(Q) == 6) {
+            float2 e = __ldg(reinterpret_cast<const float2*>(W + idx + 4));
+            row[4] = e.x;
+            row[5] = e.y;
+        }
     }
 };
 
@@ -96,17 +192,22 @@ struct Row16 {
             return __half22float2(h);
         }
     }
-    static __device__ __forceinline__ void load(const void* win, int idx, float (&row)[Q])
+    static __device__ __forceinline__ void load(const void* win, int idx, float (&row)[qpair(Q)])
     {
         const uint2* W = static_cast<const uint2*>(win);
         uint2 v = __ldg(W + idx);
-        float2 lo = cvt(v.x), hi = cvt(v.y);
-        float tmp[4] = { lo.x, lo.y, hi.x, hi.y };
-#pragma unroll
-        for (int a = 0; a < Q && a < 4; ++a) row[a] = tmp[a];
-        if constexpr (Q == 5) {
-            unsigned int b = __ldg(reinterpret_cast<const unsigned int*>(W + idx + 4));
-            row[4] = cvt(b).x;
+        float2 lo = cvt(v.x);
+        row[0] = lo.x;
+        row[1] = lo.y;
+        if constexpr (qpair(Q) >= 4) {
+            float2 hi = cvt(v.y);
+            row[2] = hi.x;
+            row[3] = hi.y;
+        }
+        if constexpr (qpair(Q) == 6) {
+            float2 e = cvt(__ldg(reinterpret_cast<const unsigned int*>(W + idx + 4)));
+            row[4] = e.x;
+            row[5] = e.y;
         }
     }
 };
@@ -117,9 +218,13 @@ template <int Q> struct RowLoader<Q, 1> : RowF32<Q> {};          // MFA_F32
 template <int Q> struct RowLoader<Q, 2> : Row16<Q, false> {};    // MFA_F16
 template <int Q> struct RowLoader<Q, 3> : Row16<Q, true> {};     // MFA_BF16
 
+// ----------------------------------------------------------------------------------------
+// contraction
+// ----------------------------------------------------------------------------------------
+
 // Sum-factorised contraction over the Q^3 support starting at (i0, j0, k0):
 //   x-pass  A_jk = sum_i Nx_i P_ijk,  B_jk = sum_i Dx_i P_ijk          (2 Q^3 FMA)
-//   y-pass  C_k = sum_j Ny_j A_jk, Dk = sum_j Dy_j A_jk, E_k = sum_j Ny_j B_jk   (3 Q^2)
+//   y-pass  C_k = sum_j Ny_j A_jk, D_k = sum_j Dy_j A_jk, E_k = sum_j Ny_j B_jk   (3 Q^2)
 //   z-pass  f = sum_k Nz_k C_k, f_z = sum Dz_k C_k, f_y = sum Nz_k D_k, f_x = sum Nz_k E_k
 // Returns {f, df/dtx, df/dty, df/dtz} (derivatives in the local span coordinates).
 template <int Q, int STORAGE>
@@ -135,7 +240,7 @@ __device__ __forceinline__ float4 contract(const ModelDev& M, int i0, int j0, in
         float C = 0.0f, Dv = 0.0f, E = 0.0f;
 #pragma unroll
         for (int b = 0; b < Q; ++b) {
-            float row[Q];
+            float row[qpair(Q)];
             RowLoader<Q, STORAGE>::load(M.win, base + c * plane + b * M.nxp, row);
             float A = 0.0f, B = 0.0f;
 #pragma unroll
@@ -155,6 +260,72 @@ __device__ __forceinline__ float4 contract(const ModelDev& M, int i0, int j0, in
     return make_float4(f, fx, fy, fz);
 }
 
+// Packed form of the same contraction.  x-pass: each row is read as QP/2 column pairs,
+// A2 = sum_m Nx2[m] * row2[m] keeps two partial sums {even columns, odd columns}; the
+// y-pass accumulates those pairs against {Ny_j, Ny_j}; the two halves are added once per
+// z-layer.  Same products as the scalar form, summed in a different order.
+template <int Q, int STORAGE>
+__device__ __forceinline__ float4 contract2(const ModelDev& M, int i0, int j0, int k0, const f2 (&Nx2)[qpair(Q) / 2],
+                                            const f2 (&Dx2)[qpair(Q) / 2], const float (&Ny)[Q], const float (&Dy)[Q],
+                                            const float (&Nz)[Q], const float (&Dz)[Q])
+{
+    constexpr int NP = qpair(Q) / 2;
+    const int plane = M.nxp * M.nyp;
+    const int base = (k0 * M.nyp + j0) * M.nxp + i0;
+    f2 ny2[Q], dy2[Q];
+#pragma unroll
+    for (int b = 0; b < Q; ++b) {
+        ny2[b] = pk2(Ny[b], Ny[b]);
+        dy2[b] = pk2(Dy[b], Dy[b]);
+    }
+    float f = 0.0f, fx = 0.0f, fy = 0.0f, fz = 0.0f;
+#pragma unroll
+    for (int c = 0; c < Q; ++c) {
+        f2 CC, DD, EE;
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+            float row[qpair(Q)];
+            RowLoader<Q, STORAGE>::load(M.win, base + c * plane + b * M.nxp, row);
+            f2 A = mul2(Nx2[0], pk2(row[0], row[1]));
+            f2 B = mul2(Dx2[0], pk2(row[0], row[1]));
+#pragma unroll
+            for (int m = 1; m < NP; ++m) {
+                const f2 r = pk2(row[2 * m], row[2 * m + 1]);
+                A = fma2(Nx2[m], r, A);
+                B = fma2(Dx2[m], r, B);
+            }
+            if (b == 0) {
+                CC = mul2(ny2[0], A);
+                DD = mul2(dy2[0], A);
+                EE = mul2(ny2[0], B);
+            } else {
+                CC = fma2(ny2[b], A, CC);
+                DD = fma2(dy2[b], A, DD);
+                EE = fma2(ny2[b], B, EE);
+            }
+        }
+        const float C = hsum2(CC), Dv = hsum2(DD), E = hsum2(EE);
+        f = fmaf(Nz[c], C, f);
+        fz = fmaf(Dz[c], C, fz);
+        fy = fmaf(Nz[c], Dv, fy);
+        fx = fmaf(Nz[c], E, fx);
+    }
+    return make_float4(f, fx, fy, fz);
+}
+
+// Unpacks the first Q entries of a packed basis into scalars.
+template <int Q>
+__device__ __forceinline__ void unpack_basis(const f2 (&X2)[qpair(Q) / 2], float (&X)[Q])
+{
+#pragma unroll
+    for (int m = 0; m < qpair(Q) / 2; ++m) {
+        float a, b;
+        upk2(X2[m], a, b);
+        if (2 * m < Q) X[2 * m] = a;
+        if (2 * m + 1 < Q) X[2 * m + 1] = b;
+    }
+}
+
 // Full query at a clamped parameter point: value and world gradient (unit-cube domain,
 // so the chain-rule factor to world coordinates is 1; 1/h converts d/dt to d/du).
 template <int Q, int STORAGE>
@@ -169,6 +340,40 @@ __device__ __forceinline__ float4 query(const ModelDev& M, float u, float v, flo
     r.z *= hy;
     r.w *= hz;
     return r;
+}
+
+// Packed query from three records already in registers.
+template <int Q, int STORAGE>
+__device__ __forceinline__ float4 query2_rec(const ModelDev& M, const float (&rx)[rec_stride(Q)],
+                                             const float (&ry)[rec_stride(Q)], const float (&rz)[rec_stride(Q)],
+                                             float u, float v, float w, int i0, int j0, int k0)
+{
+    constexpr int NP = qpair(Q) / 2;
+    f2 Nx2[NP], Dx2[NP], Ny2[NP], Dy2[NP], Nz2[NP], Dz2[NP];
+    record_basis2<Q>(rx, u, Nx2, Dx2);
+    record_basis2<Q>(ry, v, Ny2, Dy2);
+    record_basis2<Q>(rz, w, Nz2, Dz2);
+    float Ny[Q], Dy[Q], Nz[Q], Dz[Q];
+    unpack_basis<Q>(Ny2, Ny);
+    unpack_basis<Q>(Dy2, Dy);
+    unpack_basis<Q>(Nz2, Nz);
+    unpack_basis<Q>(Dz2, Dz);
+    float4 r = contract2<Q, STORAGE>(M, i0, j0, k0, Nx2, Dx2, Ny, Dy, Nz, Dz);
+    r.y *= rx[1];
+    r.z *= ry[1];
+    r.w *= rz[1];
+    return r;
+}
+
+// Packed query that loads its three records.
+template <int Q, int STORAGE>
+__device__ __forceinline__ float4 query2(const ModelDev& M, float u, float v, float w, int sx, int sy, int sz)
+{
+    float rx[rec_stride(Q)], ry[rec_stride(Q)], rz[rec_stride(Q)];
+    load_record<Q>(M.ax[0], sx, rx);
+    load_record<Q>(M.ax[1], sy, ry);
+    load_record<Q>(M.ax[2], sz, rz);
+    return query2_rec<Q, STORAGE>(M, rx, ry, rz, u, v, w, sx - M.ax[0].p, sy - M.ax[1].p, sz - M.ax[2].p);
 }
 
 __device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.0f), 1.0f); }

@@ -9,9 +9,14 @@
 //   * per axis: kup[n+p+1]  the FP64 knots rounded UP to FP32, so that for an FP32
 //     coordinate u, (u >= kup[s]) is exactly (u >= U[s]) in real arithmetic;
 //     grid[G]  (G = 4 (n - p)) the span containing g / G, a starting guess for the span
-//     search; rec[(n-p) * RS(Q)]  one record per knot span: {U_s, 1/h, c[0..Q-1][0..Q-1]}
-//     with c[r][k] the power-basis coefficient of t^k of N_{s-p+r,p} on that span,
-//     t = (u - U_s)/h, h = U_{s+1} - U_s (computed in FP64, rounded to FP32).
+//     search; rec[(n-p) * RS(Q)]  one record per knot span: {U_s, 1/h, lo, hi, c[k][r]}
+//     with lo = kup[s], hi = kup[s+1] (+inf for the last span) -- an FP32 coordinate u
+//     lies in span s iff lo <= u < hi -- and c[k][r] (k = 0..Q-1, r = 0..QP-1, QP = Q
+//     rounded up to even) the power-basis
+//     coefficient of t^k of N_{s-p+r,p} on that span, t = (u - U_s)/h, h = U_{s+1} - U_s
+//     (computed in FP64, rounded to FP32; zero for r > p).  Power-major order puts the
+//     coefficients of functions r and r+1 side by side, so one 64-bit register pair feeds
+//     a packed FP32x2 FMA that advances two basis functions at once.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -24,8 +29,11 @@ constexpr int kMaxQ = kMaxDegree + 1;
 constexpr int kTfMax = 256;
 constexpr int kPad = 4;                 // zero padding added to every axis of the window array
 
-// floats per span record for Q = p_max + 1: {U_s, 1/h} + Q*Q coefficients, padded to float4
-__host__ __device__ constexpr int rec_stride(int q) { return ((2 + q * q) + 3) / 4 * 4; }
+// basis functions per axis rounded up to pairs, and floats per span record for
+// Q = p_max + 1: {U_s, 1/h, lo, hi} + Q*QP coefficients, padded to float4
+constexpr int kRecHead = 4;
+__host__ __device__ constexpr int qpair(int q) { return (q + 1) / 2 * 2; }
+__host__ __device__ constexpr int rec_stride(int q) { return ((kRecHead + q * qpair(q)) + 3) / 4 * 4; }
 
 struct AxisDev {
     const float* kup;   // n + p + 1 knots rounded up to FP32
@@ -75,6 +83,6 @@ cudaError_t launch_prep_stats(const void* win, int storage, int nx, int ny, int 
 cudaError_t launch_decode(const ModelDev& m, const float* pts, long long n, float* val, float* grad,
                           cudaStream_t stream);
 cudaError_t launch_spans(const ModelDev& m, const float* pts, long long n, int* spans, cudaStream_t stream);
-cudaError_t launch_render(const ModelDev& m, const RenderParams& rp, cudaStream_t stream);
+cudaError_t launch_render(const ModelDev& m, const RenderParams& rp, int variant, cudaStream_t stream);
 
 }  // namespace mfa

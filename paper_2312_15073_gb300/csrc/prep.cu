@@ -80,12 +80,15 @@ __global__ void k_span_records(const double* __restrict__ U, int n, int p, float
         for (int r = 0; r <= lev; ++r)
             for (int k = 0; k < Q; ++k) T[r][k] = Tn[r][k];
     }
+    constexpr int QP = qpair(Q);
     out[0] = __double2float_rn(Us);
     out[1] = h > 0.0 ? __double2float_rn(1.0 / h) : 0.0f;
-    for (int r = 0; r < Q; ++r)
-        for (int k = 0; k < Q; ++k)
-            out[2 + r * Q + k] = (r <= p) ? __double2float_rn(T[r][k]) : 0.0f;
-    for (int e = 2 + Q * Q; e < RS; ++e) out[e] = 0.0f;
+    out[2] = __double2float_ru(Us);
+    out[3] = s < n - 1 ? __double2float_ru(U[s + 1]) : INFINITY;
+    for (int k = 0; k < Q; ++k)
+        for (int r = 0; r < QP; ++r)
+            out[kRecHead + k * QP + r] = (r <= p && r < Q) ? __double2float_rn(T[r][k]) : 0.0f;
+    for (int e = kRecHead + Q * QP; e < RS; ++e) out[e] = 0.0f;
 }
 
 // ----------------------------------------------------------------------------------------

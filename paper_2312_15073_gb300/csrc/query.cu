@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(256) k_decode(ModelDev M, const float* __restr
         const int sx = locate_span(M.ax[0], u);
         const int sy = locate_span(M.ax[1], v);
         const int sz = locate_span(M.ax[2], w);
-        const float4 r = query<Q, STORAGE>(M, u, v, w, sx, sy, sz);
+        const float4 r = query2<Q, STORAGE>(M, u, v, w, sx, sy, sz);
         val[i] = r.x;
         if (grad) {
             grad[3 * i + 0] = r.y;

@@ -4,19 +4,63 @@
 //
 // Launch shape: one CTA of 128 threads per 16x8 pixel tile; each warp covers an 8x4
 // sub-tile so that its 32 rays are close together and their samples share knot spans
-// and control-point rows (broadcast loads in L1).  The hardware block scheduler hands
-// tiles to SMs as earlier ones finish, which balances the uneven ray lengths that early
-// termination creates.  The transfer-function table travels in the kernel parameters
-// and is copied into shared memory once per CTA.
+// and control-point rows.  The hardware block scheduler hands tiles to SMs as earlier
+// ones finish, which balances the uneven ray lengths that early termination creates.
+// The transfer-function table travels in the kernel parameters and is copied into
+// shared memory once per CTA.
+//
+// The query is L1-bandwidth bound when every sample reloads its span records (3 x 80 B
+// at degree 3) and its support rows (16 x 16 B): L1 returns 128 B per clock per SM to
+// the registers.  Along one ray each axis keeps the same knot span for several
+// consecutive samples, so each axis's span bounds and record stay in registers and only
+// the lanes whose span changed reload it.  With the loads thinned out the kernel is
+// bound by FP32 issue (about 285 FFMA of about 450 instructions per sample).
+//   variant 2 (default): records cached, scalar arithmetic
+//   variant 1:           records cached, packed FP32x2 arithmetic
+//   variant 3:           nothing cached, scalar arithmetic
+// Packed FP32x2 halves the FMA instructions issued but each one holds the FMA pipe for
+// two cycles, and pairing the y-pass adds lane work, so on GB300 it measures 2-6 % slower
+// than the scalar form on the 128^3 degree-3 frame (ncu: math-pipe-throttle stalls).
+// Variant 3 re-reads every record per sample and is L1 bound.
 #include "bspline.cuh"
 
 namespace mfa {
 namespace {
 
 constexpr int kTileW = 16, kTileH = 8, kThreads = kTileW * kTileH;
+// 4 resident CTAs per SM caps the kernel at 128 registers: the span records of three axes
+// stay in registers without spills and 16 warps per SM hide the L1 latency.  Measured on
+// the 128^3 degree-3 frame: cap 128 -> 6.33 ms, cap 168 (3 CTAs) -> 7.01 ms, cap 96 (5
+// CTAs, spills) -> 10.4 ms.
+constexpr int kMinBlocks = 4;
 
-template <int Q, int STORAGE>
-__global__ void __launch_bounds__(kThreads) k_render(ModelDev M, const __grid_constant__ RenderParams P)
+// Per-axis state of a ray: current span and its record (which carries the span's FP32
+// bounds [lo, hi) in rec[2], rec[3]: a coordinate u lies in the span iff lo <= u < hi).
+template <int Q>
+struct AxisCache {
+    int s;
+    float rec[rec_stride(Q)];
+};
+
+// Brings the cache to the span of u.  Along a ray the span moves by at most one step
+// between samples in the common case, so the next record is loaded directly and the
+// search only runs when u left that span too (or on the first sample).
+template <int Q>
+__device__ __forceinline__ void axis_update(const AxisDev& A, AxisCache<Q>& C, float u)
+{
+    if (C.s >= 0 && u >= C.rec[2] && u < C.rec[3]) return;
+    int s = C.s < 0 ? locate_span(A, u) : C.s + (u >= C.rec[3] ? 1 : -1);
+    load_record<Q>(A, s, C.rec);
+    if (u < C.rec[2] || u >= C.rec[3]) {
+        s = walk_span(A, u, s);
+        load_record<Q>(A, s, C.rec);
+    }
+    C.s = s;
+}
+
+// MODE = variant (see above); MINB = minimum resident CTAs per SM (register cap)
+template <int Q, int STORAGE, int MODE, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_render(ModelDev M, const __grid_constant__ RenderParams P)
 {
     __shared__ float4 tf[kTfMax];
     for (int i = threadIdx.x; i < P.tf_n; i += kThreads) tf[i] = P.tf[i];
@@ -69,16 +113,38 @@ __global__ void __launch_bounds__(kThreads) k_render(ModelDev M, const __grid_co
             const float dt = (t1 - t0) / static_cast<float>(P.n_samples);
             const float tscale = static_cast<float>(P.tf_n - 1);
             const float lx = -d[0], ly = -d[1], lz = -d[2];     // headlight: L = V = -d
+            AxisCache<Q> cx, cy, cz;
+            cx.s = cy.s = cz.s = -1;
             int sx_ = -1, sy_ = -1, sz_ = -1;
             for (int k = 0; k < P.n_samples; ++k) {
                 const float t = fmaf(static_cast<float>(k) + 0.5f, dt, t0);
                 const float u = clamp01(fmaf(t, d[0], o[0]));
                 const float v = clamp01(fmaf(t, d[1], o[1]));
                 const float w = clamp01(fmaf(t, d[2], o[2]));
-                sx_ = (k == 0) ? locate_span(M.ax[0], u) : walk_span(M.ax[0], u, sx_);
-                sy_ = (k == 0) ? locate_span(M.ax[1], v) : walk_span(M.ax[1], v, sy_);
-                sz_ = (k == 0) ? locate_span(M.ax[2], w) : walk_span(M.ax[2], w, sz_);
-                const float4 q = query<Q, STORAGE>(M, u, v, w, sx_, sy_, sz_);
+                float4 q;
+                if constexpr (MODE == 3) {
+                    sx_ = (k == 0) ? locate_span(M.ax[0], u) : walk_span(M.ax[0], u, sx_);
+                    sy_ = (k == 0) ? locate_span(M.ax[1], v) : walk_span(M.ax[1], v, sy_);
+                    sz_ = (k == 0) ? locate_span(M.ax[2], w) : walk_span(M.ax[2], w, sz_);
+                    q = query<Q, STORAGE>(M, u, v, w, sx_, sy_, sz_);
+                } else {
+                    axis_update<Q>(M.ax[0], cx, u);
+                    axis_update<Q>(M.ax[1], cy, v);
+                    axis_update<Q>(M.ax[2], cz, w);
+                    const int i0 = cx.s - M.ax[0].p, j0 = cy.s - M.ax[1].p, k0 = cz.s - M.ax[2].p;
+                    if constexpr (MODE == 1) {
+                        q = query2_rec<Q, STORAGE>(M, cx.rec, cy.rec, cz.rec, u, v, w, i0, j0, k0);
+                    } else {
+                        float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];
+                        record_basis<Q>(cx.rec, u, Nx, Dx);
+                        record_basis<Q>(cy.rec, v, Ny, Dy);
+                        record_basis<Q>(cz.rec, w, Nz, Dz);
+                        q = contract<Q, STORAGE>(M, i0, j0, k0, Nx, Dx, Ny, Dy, Nz, Dz);
+                        q.y *= cx.rec[1];
+                        q.z *= cy.rec[1];
+                        q.w *= cz.rec[1];
+                    }
+                }
                 ++count;
                 // ---- transfer function: linear interpolation between table rows
                 float tt = clamp01((q.x - P.vmin) * P.inv_range);
@@ -131,28 +197,39 @@ __global__ void __launch_bounds__(kThreads) k_render(ModelDev M, const __grid_co
     }
 }
 
-template <int Q>
-cudaError_t render_q(const ModelDev& m, const RenderParams& rp, cudaStream_t st)
+template <int Q, int STORAGE>
+cudaError_t render_qs(const ModelDev& m, const RenderParams& rp, int variant, cudaStream_t st)
 {
     dim3 grid((rp.width + kTileW - 1) / kTileW, (rp.height + kTileH - 1) / kTileH);
-    switch (m.storage) {
-    case 1: k_render<Q, 1><<<grid, kThreads, 0, st>>>(m, rp); break;
-    case 2: k_render<Q, 2><<<grid, kThreads, 0, st>>>(m, rp); break;
-    case 3: k_render<Q, 3><<<grid, kThreads, 0, st>>>(m, rp); break;
-    default: return cudaErrorInvalidValue;
+    switch (variant) {
+    case 0:
+    case 2: k_render<Q, STORAGE, 2, kMinBlocks><<<grid, kThreads, 0, st>>>(m, rp); break;
+    case 1: k_render<Q, STORAGE, 1, kMinBlocks><<<grid, kThreads, 0, st>>>(m, rp); break;
+    default: k_render<Q, STORAGE, 3, kMinBlocks><<<grid, kThreads, 0, st>>>(m, rp); break;
     }
     return cudaGetLastError();
 }
 
+template <int Q>
+cudaError_t render_q(const ModelDev& m, const RenderParams& rp, int variant, cudaStream_t st)
+{
+    switch (m.storage) {
+    case 1: return render_qs<Q, 1>(m, rp, variant, st);
+    case 2: return render_qs<Q, 2>(m, rp, variant, st);
+    case 3: return render_qs<Q, 3>(m, rp, variant, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace
 
-cudaError_t launch_render(const ModelDev& m, const RenderParams& rp, cudaStream_t stream)
+cudaError_t launch_render(const ModelDev& m, const RenderParams& rp, int variant, cudaStream_t stream)
 {
     switch (m.q) {
-    case 2: return render_q<2>(m, rp, stream);
-    case 3: return render_q<3>(m, rp, stream);
-    case 4: return render_q<4>(m, rp, stream);
-    case 5: return render_q<5>(m, rp, stream);
+    case 2: return render_q<2>(m, rp, variant, stream);
+    case 3: return render_q<3>(m, rp, variant, stream);
+    case 4: return render_q<4>(m, rp, variant, stream);
+    case 5: return render_q<5>(m, rp, variant, stream);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -282,3 +282,24 @@ def test_render_edge_cases(mfa, orc):
     with pytest.raises(mfa.MfaError):
         mfa.render(model, cam, tf, 4, 4, 0, out=out)
     assert float(out.min()) == 7.0
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("degree", [(3, 3, 3), (2, 3, 4), (4, 4, 4)])
+def test_render_variants_match_oracle(mfa, orc, variant, degree):
+    """Every kernel variant (support cached / records cached / nothing cached) against the
+    oracle, on a non-uniform model and a perspective view."""
+    import torch
+    rng = np.random.default_rng(_seed("variants", degree))
+    model, ref, _ = _make(mfa, orc, rng, degree, (14, 12, 13), (False, True, False))
+    cam = _camera("persp", rng)
+    job = synth.RenderJob(cam, 40, 24, 120, synth.ramp_tf(256, 0.08), True)
+    tf = mfa.transfer_fn(job.tf, shading=True)
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    img = mfa.render(model, cam, tf, job.width, job.height, job.n_samples, samples_out=cnt, variant=variant)
+    torch.cuda.synchronize()
+    rimg, rc = orc.render(ref, cam, job.tf, job.width, job.height, job.n_samples, shading=True)
+    rmse = image_rmse(img.cpu().numpy(), rimg)
+    assert np.all(rmse <= IMAGE_RMSE_TOL), rmse
+    assert abs(int(cnt.item()) - rc) <= max(2, 1e-3 * rc)
+    assert rimg[..., 3].max() > 0.05
