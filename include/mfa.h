@@ -149,7 +149,10 @@ typedef struct {
                                          scalar FP32; 3 = nothing cached, scalar FP32.
                                          Variants differ only in FP32 summation order.
                                          MFA_ERR_ARG outside 0..3. */
-    int reserved[7];                  /* zero */
+    int tile_shape;                   /* ray tile: 0 = 16x8 pixels per CTA with 8x4 per warp
+                                         (default), 1 = 32x4 / 8x4, 2 = 8x16 / 4x8,
+                                         3 = 16x8 / 16x2.  MFA_ERR_ARG outside 0..3. */
+    int reserved[6];                  /* zero */
 } mfa_render_opts;
 
 /*
@@ -168,6 +171,53 @@ int mfa_render(const mfa_model* model, const mfa_camera* camera, const mfa_trans
 /* mfa_render with options (opts may be NULL). */
 int mfa_render_ex(const mfa_model* model, const mfa_camera* camera, const mfa_transfer_fn* tf,
                   int width, int height, int n_samples, float* rgba_out, const mfa_render_opts* opts);
+
+/*
+ * Batched rendering: many images of many models in one persistent launch (the paper
+ * renders one partition per core, Sec. IV-A.4; on one GPU the unit of parallel work is a
+ * ray tile).  A request is one mfa_render call's worth of arguments.
+ */
+typedef struct {
+    const mfa_model* model;
+    mfa_camera camera;
+    const mfa_transfer_fn* tf;        /* its table is copied when the batch is submitted */
+    int width, height, n_samples;     /* as mfa_render */
+    float* rgba_out;                  /* DEVICE, height * width * 4 FP32 */
+    unsigned long long* samples_out;  /* DEVICE counter or NULL (samples evaluated are added) */
+} mfa_render_request;
+
+typedef struct mfa_batch mfa_batch;   /* reusable batch context; owns its work tables */
+
+/*
+ * Creates a batch context on the current device for up to max_requests (1..4096)
+ * requests per submission.  It owns two pinned host work tables and two device work
+ * tables (used alternately, so one submission can be in flight while the next is
+ * written) and the CUDA graphs it records: each submission is ONE graph launch made of
+ * the table upload and one persistent kernel per control-point storage type present.
+ * Inside the kernel, CTAs (SMs x resident CTAs) draw ray tiles of all requests from one
+ * device counter.  NULL on error.
+ */
+mfa_batch* mfa_batch_create(int max_requests);
+
+/* Ray-tile shape (as mfa_render_opts.tile_shape) and CTA count (0 = SMs x occupancy)
+ * for later submissions; chosen by the autotuner.  MFA_ERR_ARG on bad values. */
+int mfa_batch_configure(mfa_batch* batch, int tile_shape, int grid_ctas);
+
+/*
+ * Validates the n requests (every check of mfa_render; MFA_ERR_ARG names the first bad
+ * request and nothing is launched), writes the work table and launches the batch graph
+ * on the stream bound to the calling thread.  Asynchronous; the outputs are complete
+ * when that stream reaches this point.  Blocks only if the work table it is about to
+ * overwrite still belongs to a submission the GPU has not started (two in flight at
+ * most).  All models must live on the batch's device.  n = 0 is a no-op.
+ */
+int mfa_batch_render(mfa_batch* batch, const mfa_render_request* reqs, int n);
+
+/* Frees the context after the GPU has finished its submissions.  NULL is a no-op. */
+void mfa_batch_destroy(mfa_batch* batch);
+
+/* One-shot form: a thread-local batch context sized on demand, then mfa_batch_render. */
+int mfa_render_batch(const mfa_render_request* reqs, int n);
 
 /* Text of the last error on the calling thread ("" if none). */
 const char* mfa_last_error(void);

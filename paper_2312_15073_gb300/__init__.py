@@ -22,7 +22,7 @@ from ctypes import POINTER, c_double, c_float, c_int, c_longlong, c_size_t, c_ul
 import numpy as np
 
 __all__ = ["Model", "decode", "locate_spans", "render", "lib", "MFA_F64", "MFA_F32", "MFA_F16", "MFA_BF16",
-           "MfaError", "camera", "transfer_fn"]
+           "MfaError", "camera", "transfer_fn", "Request", "Batch", "render_batch"]
 
 MFA_F64, MFA_F32, MFA_F16, MFA_BF16 = 0, 1, 2, 3
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -47,7 +47,12 @@ class _TF(ctypes.Structure):
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("samples_out", c_void_p), ("variant", c_int), ("reserved", c_int * 7)]
+    _fields_ = [("samples_out", c_void_p), ("variant", c_int), ("tile_shape", c_int), ("reserved", c_int * 6)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("model", c_void_p), ("camera", _Camera), ("tf", c_void_p), ("width", c_int), ("height", c_int),
+                ("n_samples", c_int), ("rgba_out", c_void_p), ("samples_out", c_void_p)]
 
 
 class _Info(ctypes.Structure):
@@ -88,6 +93,16 @@ def lib():
         L.mfa_render_ex.restype = c_int
         L.mfa_render_ex.argtypes = [c_void_p, POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int, c_void_p,
                                     POINTER(_Opts)]
+        L.mfa_batch_create.restype = c_void_p
+        L.mfa_batch_create.argtypes = [c_int]
+        L.mfa_batch_configure.restype = c_int
+        L.mfa_batch_configure.argtypes = [c_void_p, c_int, c_int]
+        L.mfa_batch_render.restype = c_int
+        L.mfa_batch_render.argtypes = [c_void_p, c_void_p, c_int]
+        L.mfa_batch_destroy.restype = None
+        L.mfa_batch_destroy.argtypes = [c_void_p]
+        L.mfa_render_batch.restype = c_int
+        L.mfa_render_batch.argtypes = [c_void_p, c_int]
         _lib = L
     return _lib
 
@@ -229,7 +244,7 @@ class transfer_fn:
 
 
 def render(model: Model, cam, tf: transfer_fn, width: int, height: int, n_samples: int, out=None,
-           samples_out=None, variant: int = 0):
+           samples_out=None, variant: int = 0, tile_shape: int = 0):
     """Premultiplied RGBA image (height, width, 4) FP32 on the current device.
     samples_out: optional 1-element int64 CUDA tensor to which the number of evaluated
     samples is added."""
@@ -241,6 +256,7 @@ def render(model: Model, cam, tf: transfer_fn, width: int, height: int, n_sample
     c = cam if isinstance(cam, _Camera) else camera(cam)
     opts = _Opts()
     opts.variant = int(variant)
+    opts.tile_shape = int(tile_shape)
     if samples_out is not None:
         if not (samples_out.is_cuda and samples_out.dtype == torch.int64):
             raise TypeError("samples_out must be an int64 CUDA tensor")
@@ -249,3 +265,76 @@ def render(model: Model, cam, tf: transfer_fn, width: int, height: int, n_sample
     _check(lib().mfa_render_ex(model.handle, ctypes.byref(c), ctypes.byref(tf.struct), width, height, n_samples,
                                out.data_ptr(), ctypes.byref(opts)))
     return out
+
+
+class Request:
+    """One image of a batch: the arguments of one render() call."""
+
+    def __init__(self, model: Model, cam, tf: transfer_fn, width: int, height: int, n_samples: int, out=None,
+                 samples_out=None):
+        import torch
+        self.model, self.cam, self.tf = model, cam, tf
+        self.width, self.height, self.n_samples = int(width), int(height), int(n_samples)
+        self.out = out if out is not None else torch.empty((height, width, 4), device="cuda", dtype=torch.float32)
+        if not (self.out.is_cuda and self.out.dtype == torch.float32 and self.out.is_contiguous()
+                and self.out.numel() == height * width * 4):
+            raise ValueError("out must be a contiguous (height, width, 4) FP32 CUDA tensor")
+        self.samples_out = samples_out
+
+    def _struct(self) -> _Request:
+        r = _Request()
+        r.model = self.model.handle
+        r.camera = self.cam if isinstance(self.cam, _Camera) else camera(self.cam)
+        r.tf = ctypes.addressof(self.tf.struct)
+        r.width, r.height, r.n_samples = self.width, self.height, self.n_samples
+        r.rgba_out = self.out.data_ptr()
+        r.samples_out = self.samples_out.data_ptr() if self.samples_out is not None else None
+        return r
+
+
+def _request_array(requests):
+    arr = (_Request * len(requests))()
+    for i, q in enumerate(requests):
+        arr[i] = q._struct()
+    return arr
+
+
+class Batch:
+    """Reusable batch context (mfa_batch_*): each render() is one CUDA-graph launch of a
+    persistent kernel over the ray tiles of all requests."""
+
+    def __init__(self, max_requests: int):
+        import torch  # noqa: F401
+        h = lib().mfa_batch_create(int(max_requests))
+        if not h:
+            raise MfaError(-1, lib().mfa_last_error().decode())
+        self._h = h
+        self.max_requests = int(max_requests)
+
+    def configure(self, tile_shape: int = 0, grid_ctas: int = 0):
+        _check(lib().mfa_batch_configure(self._h, int(tile_shape), int(grid_ctas)))
+
+    def render(self, requests):
+        arr = _request_array(requests)
+        _bind_stream()
+        _check(lib().mfa_batch_render(self._h, ctypes.addressof(arr), len(requests)))
+        return [q.out for q in requests]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mfa_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def render_batch(requests):
+    """One-shot batched render (thread-local context)."""
+    arr = _request_array(requests)
+    _bind_stream()
+    _check(lib().mfa_render_batch(ctypes.addressof(arr), len(requests)))
+    return [q.out for q in requests]

@@ -1,5 +1,6 @@
 // api.cu -- the C ABI declared in include/mfa.h: argument checks, model ownership,
 // stream binding, error text, and the host-side set-up of each launch.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -8,26 +9,18 @@
 #include <vector>
 
 #include "../../include/mfa.h"
-#include "mfa_internal.cuh"
+#include "host.cuh"
 
 using namespace mfa;
 
-struct mfa_model {
-    int device = 0;
-    int degree[3] = { 0, 0, 0 };
-    int nctrl[3] = { 0, 0, 0 };
-    mfa_dtype storage = MFA_F32;
-    float vmin = 0.0f, vmax = 0.0f, maxabs = 0.0f;
-    size_t bytes = 0;
-    void* d_win = nullptr;      // window array
-    void* d_tables = nullptr;   // kup, grid and records of the three axes, one allocation
-    ModelDev dev{};
-};
+namespace mfa {
 
 namespace {
-
 thread_local std::string g_error;
 thread_local cudaStream_t g_stream = nullptr;
+}  // namespace
+
+cudaStream_t current_stream() { return g_stream; }
 
 int fail(int code, const char* fmt, ...)
 {
@@ -91,7 +84,86 @@ int check_model_device(const mfa_model* m)
     return MFA_OK;
 }
 
-}  // namespace
+// Validates one render call and fills the kernel's scalars and table.  Checks the model,
+// camera, transfer function, sizes and output; returns MFA_OK or an error code.
+int setup_render(const mfa_model* m, const mfa_camera* cam, const mfa_transfer_fn* tf, int width, int height,
+                 int n_samples, float* rgba_out, unsigned long long* samples_out, RenderScalars& S, float4* table)
+{
+    if (!m || !cam || !tf || !rgba_out) return fail(MFA_ERR_ARG, "model, camera, tf and rgba_out must be non-NULL");
+    if (width < 1 || width > 32768 || height < 1 || height > 32768)
+        return fail(MFA_ERR_ARG, "image size %dx%d outside 1..32768", width, height);
+    if (n_samples < 1 || n_samples > (1 << 20)) return fail(MFA_ERR_ARG, "n_samples = %d outside 1..2^20", n_samples);
+    if (tf->n_entries < 1 || tf->n_entries > kTfMax || !tf->rgba)
+        return fail(MFA_ERR_ARG, "transfer function needs 1..%d rows and a table", kTfMax);
+    if (cam->projection != 0 && cam->projection != 1) return fail(MFA_ERR_ARG, "projection must be 0 or 1");
+    if (int rc = check_model_device(m)) return rc;
+
+    // camera frame in FP64, handed to the kernel in FP32
+    double f[3], r[3], u[3];
+    for (int a = 0; a < 3; ++a) f[a] = cam->target[a] - cam->eye[a];
+    double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    if (!(fl > 0.0) || !std::isfinite(fl)) return fail(MFA_ERR_ARG, "camera eye and target coincide");
+    for (double& x : f) x /= fl;
+    r[0] = f[1] * cam->up[2] - f[2] * cam->up[1];
+    r[1] = f[2] * cam->up[0] - f[0] * cam->up[2];
+    r[2] = f[0] * cam->up[1] - f[1] * cam->up[0];
+    double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    double ul = std::sqrt(cam->up[0] * cam->up[0] + cam->up[1] * cam->up[1] + cam->up[2] * cam->up[2]);
+    if (!(rl > 1e-12 * ul) || !std::isfinite(rl)) return fail(MFA_ERR_ARG, "camera up is parallel to the view direction");
+    for (double& x : r) x /= rl;
+    u[0] = r[1] * f[2] - r[2] * f[1];
+    u[1] = r[2] * f[0] - r[0] * f[2];
+    u[2] = r[0] * f[1] - r[1] * f[0];
+    const double aspect = static_cast<double>(width) / height;
+    double sxs, sys;
+    if (cam->projection == 0) {
+        if (!(cam->ortho_height > 0.0) || !std::isfinite(cam->ortho_height))
+            return fail(MFA_ERR_ARG, "ortho_height must be > 0");
+        sys = 0.5 * cam->ortho_height;
+        sxs = sys * aspect;
+    } else {
+        if (!(cam->fov_y_deg > 0.0 && cam->fov_y_deg < 180.0)) return fail(MFA_ERR_ARG, "fov_y_deg outside (0,180)");
+        sys = std::tan(0.5 * cam->fov_y_deg * M_PI / 180.0);
+        sxs = sys * aspect;
+    }
+
+    std::memset(&S, 0, sizeof S);
+    for (int a = 0; a < 3; ++a) {
+        S.eye[a] = static_cast<float>(cam->eye[a]);
+        S.fwd[a] = static_cast<float>(f[a]);
+        S.rx[a] = static_cast<float>(r[a] * sxs);
+        S.uy[a] = static_cast<float>(u[a] * sys);
+    }
+    S.projection = cam->projection;
+    S.width = width;
+    S.height = height;
+    S.n_samples = n_samples;
+    S.inv_w = 1.0f / static_cast<float>(width);
+    S.inv_h = 1.0f / static_cast<float>(height);
+    const float vmin = std::isnan(tf->vmin) ? m->vmin : tf->vmin;
+    const float vmax = std::isnan(tf->vmax) ? m->vmax : tf->vmax;
+    S.vmin = vmin;
+    S.inv_range = vmax > vmin ? static_cast<float>(1.0 / (static_cast<double>(vmax) - vmin)) : 0.0f;
+    S.tf_n = tf->n_entries;
+    S.shading = tf->shading ? 1 : 0;
+    S.ka = tf->ka;
+    S.kd = tf->kd;
+    S.ks = tf->ks;
+    S.shininess = tf->shininess;
+    S.ert_alpha = tf->ert_alpha >= 1.0f ? INFINITY : tf->ert_alpha;
+    int spans = 0;
+    for (int a = 0; a < 3; ++a) spans = std::max(spans, m->nctrl[a] - m->degree[a]);
+    double scale = std::max(static_cast<double>(m->vmax) - m->vmin, static_cast<double>(m->maxabs));
+    double gt = 1e-6 * scale * spans;
+    S.gtiny2 = static_cast<float>(gt * gt);
+    S.samples_out = samples_out;
+    S.out = reinterpret_cast<float4*>(rgba_out);
+    for (int i = 0; i < tf->n_entries; ++i)
+        table[i] = make_float4(tf->rgba[4 * i], tf->rgba[4 * i + 1], tf->rgba[4 * i + 2], tf->rgba[4 * i + 3]);
+    return MFA_OK;
+}
+
+}  // namespace mfa
 
 extern "C" {
 
@@ -295,82 +367,15 @@ int mfa_locate_spans(const mfa_model* m, const float* pts, long long n, int* spa
 int mfa_render_ex(const mfa_model* m, const mfa_camera* cam, const mfa_transfer_fn* tf, int width, int height,
                   int n_samples, float* rgba_out, const mfa_render_opts* opts)
 {
-    if (!m || !cam || !tf || !rgba_out) return fail(MFA_ERR_ARG, "model, camera, tf and rgba_out must be non-NULL");
-    if (width < 1 || width > 32768 || height < 1 || height > 32768)
-        return fail(MFA_ERR_ARG, "image size %dx%d outside 1..32768", width, height);
-    if (n_samples < 1 || n_samples > (1 << 20)) return fail(MFA_ERR_ARG, "n_samples = %d outside 1..2^20", n_samples);
-    if (tf->n_entries < 1 || tf->n_entries > kTfMax || !tf->rgba)
-        return fail(MFA_ERR_ARG, "transfer function needs 1..%d rows and a table", kTfMax);
-    if (cam->projection != 0 && cam->projection != 1) return fail(MFA_ERR_ARG, "projection must be 0 or 1");
     const int variant = opts ? opts->variant : 0;
+    const int shape = opts ? opts->tile_shape : 0;
     if (variant < 0 || variant > 3) return fail(MFA_ERR_ARG, "render variant %d outside 0..3", variant);
-    if (int rc = check_model_device(m)) return rc;
-
-    // camera frame in FP64, handed to the kernel in FP32
-    double f[3], r[3], u[3];
-    for (int a = 0; a < 3; ++a) f[a] = cam->target[a] - cam->eye[a];
-    double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
-    if (!(fl > 0.0) || !std::isfinite(fl)) return fail(MFA_ERR_ARG, "camera eye and target coincide");
-    for (double& x : f) x /= fl;
-    r[0] = f[1] * cam->up[2] - f[2] * cam->up[1];
-    r[1] = f[2] * cam->up[0] - f[0] * cam->up[2];
-    r[2] = f[0] * cam->up[1] - f[1] * cam->up[0];
-    double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-    double ul = std::sqrt(cam->up[0] * cam->up[0] + cam->up[1] * cam->up[1] + cam->up[2] * cam->up[2]);
-    if (!(rl > 1e-12 * ul) || !std::isfinite(rl)) return fail(MFA_ERR_ARG, "camera up is parallel to the view direction");
-    for (double& x : r) x /= rl;
-    u[0] = r[1] * f[2] - r[2] * f[1];
-    u[1] = r[2] * f[0] - r[0] * f[2];
-    u[2] = r[0] * f[1] - r[1] * f[0];
-    const double aspect = static_cast<double>(width) / height;
-    double sxs, sys;
-    if (cam->projection == 0) {
-        if (!(cam->ortho_height > 0.0) || !std::isfinite(cam->ortho_height))
-            return fail(MFA_ERR_ARG, "ortho_height must be > 0");
-        sys = 0.5 * cam->ortho_height;
-        sxs = sys * aspect;
-    } else {
-        if (!(cam->fov_y_deg > 0.0 && cam->fov_y_deg < 180.0)) return fail(MFA_ERR_ARG, "fov_y_deg outside (0,180)");
-        sys = std::tan(0.5 * cam->fov_y_deg * M_PI / 180.0);
-        sxs = sys * aspect;
-    }
-
+    if (shape < 0 || shape >= kTileShapes) return fail(MFA_ERR_ARG, "tile_shape %d outside 0..%d", shape, kTileShapes - 1);
     RenderParams P;
-    std::memset(&P, 0, sizeof P);
-    for (int a = 0; a < 3; ++a) {
-        P.eye[a] = static_cast<float>(cam->eye[a]);
-        P.fwd[a] = static_cast<float>(f[a]);
-        P.rx[a] = static_cast<float>(r[a] * sxs);
-        P.uy[a] = static_cast<float>(u[a] * sys);
-    }
-    P.projection = cam->projection;
-    P.width = width;
-    P.height = height;
-    P.n_samples = n_samples;
-    P.inv_w = 1.0f / static_cast<float>(width);
-    P.inv_h = 1.0f / static_cast<float>(height);
-    const float vmin = std::isnan(tf->vmin) ? m->vmin : tf->vmin;
-    const float vmax = std::isnan(tf->vmax) ? m->vmax : tf->vmax;
-    P.vmin = vmin;
-    P.inv_range = vmax > vmin ? static_cast<float>(1.0 / (static_cast<double>(vmax) - vmin)) : 0.0f;
-    P.tf_n = tf->n_entries;
-    P.shading = tf->shading ? 1 : 0;
-    P.ka = tf->ka;
-    P.kd = tf->kd;
-    P.ks = tf->ks;
-    P.shininess = tf->shininess;
-    P.ert_alpha = tf->ert_alpha >= 1.0f ? INFINITY : tf->ert_alpha;
-    int spans = 0;
-    for (int a = 0; a < 3; ++a) spans = std::max(spans, m->nctrl[a] - m->degree[a]);
-    double scale = std::max(static_cast<double>(m->vmax) - m->vmin, static_cast<double>(m->maxabs));
-    double gt = 1e-6 * scale * spans;
-    P.gtiny2 = static_cast<float>(gt * gt);
-    P.samples_out = opts ? opts->samples_out : nullptr;
-    P.out = reinterpret_cast<float4*>(rgba_out);
-    for (int i = 0; i < tf->n_entries; ++i)
-        P.tf[i] = make_float4(tf->rgba[4 * i], tf->rgba[4 * i + 1], tf->rgba[4 * i + 2], tf->rgba[4 * i + 3]);
-
-    cudaError_t e = launch_render(m->dev, P, variant, g_stream);
+    if (int rc = setup_render(m, cam, tf, width, height, n_samples, rgba_out, opts ? opts->samples_out : nullptr, P.s,
+                              P.tf))
+        return rc;
+    cudaError_t e = launch_render(m->dev, P, variant, shape, g_stream);
     return e == cudaSuccess ? MFA_OK : cuda_fail(e, "render launch");
 }
 

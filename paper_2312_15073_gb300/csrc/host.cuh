@@ -1,0 +1,39 @@
+// host.cuh -- host-side pieces shared by the C-ABI translation units (api.cu, batch.cu):
+// the model object, error reporting, the calling thread's stream and the validation of
+// one render call.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/mfa.h"
+#include "mfa_internal.cuh"
+
+// The opaque model of the C ABI: host copies of its shape and statistics plus the device
+// tables the kernels read.
+struct mfa_model {
+    int device = 0;
+    int degree[3] = { 0, 0, 0 };
+    int nctrl[3] = { 0, 0, 0 };
+    mfa_dtype storage = MFA_F32;
+    float vmin = 0.0f, vmax = 0.0f, maxabs = 0.0f;
+    size_t bytes = 0;
+    void* d_win = nullptr;      // window array
+    void* d_tables = nullptr;   // kup, grid and records of the three axes, one allocation
+    mfa::ModelDev dev{};
+};
+
+namespace mfa {
+
+// Records the error text for mfa_last_error() on the calling thread; returns code.
+int fail(int code, const char* fmt, ...);
+// Same for a CUDA error (MFA_ERR_NOMEM for allocation failures, else MFA_ERR_CUDA).
+int cuda_fail(cudaError_t e, const char* what);
+// Stream bound with mfa_set_stream on the calling thread.
+cudaStream_t current_stream();
+// MFA_OK if the model lives on the current device.
+int check_model_device(const mfa_model* m);
+// Validates one render call and fills the kernel's scalars and table (tf_n rows).
+int setup_render(const mfa_model* m, const mfa_camera* cam, const mfa_transfer_fn* tf, int width, int height,
+                 int n_samples, float* rgba_out, unsigned long long* samples_out, RenderScalars& S, float4* table);
+
+}  // namespace mfa

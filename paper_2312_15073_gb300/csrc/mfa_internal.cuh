@@ -52,8 +52,8 @@ struct ModelDev {
     int storage;        // mfa_dtype of the window values
 };
 
-// Render parameters passed by value as kernel arguments (about 4.3 KB with the table).
-struct RenderParams {
+// Per-image render parameters (camera frame, image size, transfer-function scalars).
+struct RenderScalars {
     float eye[3];       // ray origin (perspective) / view centre (orthographic)
     float fwd[3];       // unit view direction
     float rx[3];        // image-plane step for sx in [-1,1]: right * half-width (ortho) or
@@ -66,12 +66,40 @@ struct RenderParams {
     int tf_n;           // table rows
     int shading;
     float ka, kd, ks, shininess;
-    float ert_alpha;    // >= 1: no early termination
+    float ert_alpha;    // +inf: no early termination
     float gtiny2;       // squared gradient-norm threshold for an undefined normal
     unsigned long long* samples_out;   // optional device counter
     float4* out;        // height * width premultiplied RGBA
+};
+
+// Single-image launch: the scalars and the table travel as kernel arguments (about 4.3 KB).
+struct RenderParams {
+    RenderScalars s;
     float4 tf[kTfMax];  // non-premultiplied RGBA rows
 };
+
+// One request of a batched launch, in the device work table.
+struct BatchItem {
+    ModelDev m;
+    RenderScalars s;
+    const float4* tf;   // device copy of the request's table (tf_n rows)
+    int tile_begin;     // index of the request's first ray tile in the batch
+    int tiles_x;        // ray tiles per image row
+    int pad[2];
+};
+
+// Device work table of a batch: kBatchGroups heads (one per degree class x storage type)
+// at its start, then the items of every group back to back, then the requests'
+// transfer-function rows.  A head holds the tile counter its group's persistent CTAs draw
+// from, the group's item count and ray-tile count, and where its items start.
+struct BatchHead {
+    int next_tile;
+    int n_items;
+    int total_tiles;
+    int items_offset;   // bytes from the start of the table
+};
+constexpr int kBatchGroups = 12;          // (storage F32/F16/BF16) x (Q = 2..5)
+constexpr int kBatchItemsOffset = 256;    // heads occupy the first 256 bytes
 
 // launchers (defined in the .cu files), all asynchronous on `stream`
 cudaError_t launch_prep_axis(const double* d_knots, int n, int p, int q, float* kup, float* rec, int* grid,
@@ -83,6 +111,18 @@ cudaError_t launch_prep_stats(const void* win, int storage, int nx, int ny, int 
 cudaError_t launch_decode(const ModelDev& m, const float* pts, long long n, float* val, float* grad,
                           cudaStream_t stream);
 cudaError_t launch_spans(const ModelDev& m, const float* pts, long long n, int* spans, cudaStream_t stream);
-cudaError_t launch_render(const ModelDev& m, const RenderParams& rp, int variant, cudaStream_t stream);
+cudaError_t launch_render(const ModelDev& m, const RenderParams& rp, int variant, int shape, cudaStream_t stream);
+// The persistent batched render kernel for models of one degree class q and one storage
+// type: arguments (BatchHead* table, int group, int tile_shape).  Launch with `threads`
+// threads per CTA and about SMs x blocks_per_sm CTAs.
+struct BatchKernel {
+    const void* fn;
+    int blocks_per_sm;
+    int threads;
+};
+BatchKernel render_batch_kernel(int q, int storage);
+// Pixel size of ray-tile shape `shape` (0..kTileShapes-1); -1 if out of range.
+int render_tile_dims(int shape, int* tw, int* th);
+constexpr int kTileShapes = 4;
 
 }  // namespace mfa

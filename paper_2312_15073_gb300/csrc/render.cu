@@ -2,12 +2,16 @@
 // query per sample, 1-D transfer function and Phong shading (Sec. IV-B), front-to-back
 // over compositing with early ray termination, one 16-byte store per pixel.
 //
-// Launch shape: one CTA of 128 threads per 16x8 pixel tile; each warp covers an 8x4
-// sub-tile so that its 32 rays are close together and their samples share knot spans
-// and control-point rows.  The hardware block scheduler hands tiles to SMs as earlier
-// ones finish, which balances the uneven ray lengths that early termination creates.
-// The transfer-function table travels in the kernel parameters and is copied into
-// shared memory once per CTA.
+// Work decomposition: CTAs of 128 threads each render one ray tile; the 32 lanes of a warp
+// cover a compact block of pixels (8x4 by default) so that their samples share knot spans
+// and control-point rows.  Two launch forms share the per-pixel code:
+//   * k_render: one image, one CTA per tile, the hardware block scheduler hands tiles to
+//     SMs as earlier ones finish (balancing the uneven ray lengths early termination
+//     creates); scalars and the transfer-function table travel as kernel arguments.
+//   * k_render_batch: many images of many models in one persistent launch.  Each CTA
+//     draws tile indices from a device counter in the work table until the batch is
+//     exhausted, loads the tile's request (model, camera, table) into shared memory when
+//     it changes, and dispatches on the model's degree.
 //
 // The query is L1-bandwidth bound when every sample reloads its span records (3 x 80 B
 // at degree 3) and its support rows (16 x 16 B): L1 returns 128 B per clock per SM to
@@ -27,12 +31,33 @@
 namespace mfa {
 namespace {
 
-constexpr int kTileW = 16, kTileH = 8, kThreads = kTileW * kTileH;
+constexpr int kThreads = 128;
 // 4 resident CTAs per SM caps the kernel at 128 registers: the span records of three axes
 // stay in registers without spills and 16 warps per SM hide the L1 latency.  Measured on
 // the 128^3 degree-3 frame: cap 128 -> 6.33 ms, cap 168 (3 CTAs) -> 7.01 ms, cap 96 (5
 // CTAs, spills) -> 10.4 ms.
 constexpr int kMinBlocks = 4;
+
+// Ray-tile shapes (CTA tile, warp tile).  Shape 0 is the default; the autotuner picks one
+// per workload.
+struct TileShape {
+    int tw, th;   // pixels per CTA tile
+    int ww, wh;   // pixels per warp tile (ww * wh = 32)
+};
+__host__ __device__ constexpr TileShape tile_shape(int s)
+{
+    return s == 1 ? TileShape{ 32, 4, 8, 4 } : s == 2 ? TileShape{ 8, 16, 4, 8 } : s == 3 ? TileShape{ 16, 8, 16, 2 }
+                                                                                         : TileShape{ 16, 8, 8, 4 };
+}
+
+// pixel of thread `tid` in tile (tx, ty)
+__device__ __forceinline__ void tile_pixel(const TileShape& T, int tx, int ty, int tid, int& col, int& row)
+{
+    const int warp = tid >> 5, lane = tid & 31;
+    const int wpr = T.tw / T.ww;   // warps per tile row
+    col = tx * T.tw + (warp % wpr) * T.ww + lane % T.ww;
+    row = ty * T.th + (warp / wpr) * T.wh + lane / T.ww;
+}
 
 // Per-axis state of a ray: current span and its record (which carries the span's FP32
 // bounds [lo, hi) in rec[2], rec[3]: a coordinate u lies in the span iff lo <= u < hi).
@@ -58,179 +83,301 @@ __device__ __forceinline__ void axis_update(const AxisDev& A, AxisCache<Q>& C, f
     C.s = s;
 }
 
-// MODE = variant (see above); MINB = minimum resident CTAs per SM (register cap)
-template <int Q, int STORAGE, int MODE, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) k_render(ModelDev M, const __grid_constant__ RenderParams P)
+// The whole ray of pixel (col, row): premultiplied RGBA; `count` += samples evaluated.
+// MODE = variant (see above).
+template <int Q, int STORAGE, int MODE>
+__device__ __forceinline__ float4 march(const ModelDev& M, const RenderScalars& P, const float4* __restrict__ tf,
+                                        int col, int row, unsigned long long& count)
 {
-    __shared__ float4 tf[kTfMax];
-    for (int i = threadIdx.x; i < P.tf_n; i += kThreads) tf[i] = P.tf[i];
-    __syncthreads();
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int col = blockIdx.x * kTileW + (warp & 1) * 8 + (lane & 7);
-    const int row = blockIdx.y * kTileH + (warp >> 1) * 4 + (lane >> 3);
-    unsigned long long count = 0;
-
-    if (col < P.width && row < P.height) {
-        // ---- ray through the pixel centre (row 0 at the top)
-        const float sx = fmaf(static_cast<float>(2 * col + 1), P.inv_w, -1.0f);
-        const float sy = fmaf(static_cast<float>(-(2 * row + 1)), P.inv_h, 1.0f);
-        float o[3], d[3];
-        if (P.projection == 0) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                o[a] = fmaf(sy, P.uy[a], fmaf(sx, P.rx[a], P.eye[a]));
-                d[a] = P.fwd[a];
-            }
-        } else {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                o[a] = P.eye[a];
-                d[a] = fmaf(sy, P.uy[a], fmaf(sx, P.rx[a], P.fwd[a]));
-            }
-            const float inv = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            d[0] *= inv;
-            d[1] *= inv;
-            d[2] *= inv;
-        }
-        // ---- slab clip against [0,1]^3, t >= 0
-        float t0 = 0.0f, t1 = INFINITY;
-        bool hit = true;
+    // ---- ray through the pixel centre (row 0 at the top)
+    const float sx = fmaf(static_cast<float>(2 * col + 1), P.inv_w, -1.0f);
+    const float sy = fmaf(static_cast<float>(-(2 * row + 1)), P.inv_h, 1.0f);
+    float o[3], d[3];
+    if (P.projection == 0) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            if (d[a] != 0.0f) {
-                const float inv = 1.0f / d[a];
-                float ta = -o[a] * inv, tb = (1.0f - o[a]) * inv;
-                if (ta > tb) { const float t = ta; ta = tb; tb = t; }
-                t0 = fmaxf(t0, ta);
-                t1 = fminf(t1, tb);
-            } else if (o[a] < 0.0f || o[a] > 1.0f) {
-                hit = false;
-            }
+            o[a] = fmaf(sy, P.uy[a], fmaf(sx, P.rx[a], P.eye[a]));
+            d[a] = P.fwd[a];
         }
-        float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);   // premultiplied rgb, alpha
-        if (hit && t0 < t1) {
-            const float dt = (t1 - t0) / static_cast<float>(P.n_samples);
-            const float tscale = static_cast<float>(P.tf_n - 1);
-            const float lx = -d[0], ly = -d[1], lz = -d[2];     // headlight: L = V = -d
-            AxisCache<Q> cx, cy, cz;
-            cx.s = cy.s = cz.s = -1;
-            int sx_ = -1, sy_ = -1, sz_ = -1;
-            for (int k = 0; k < P.n_samples; ++k) {
-                const float t = fmaf(static_cast<float>(k) + 0.5f, dt, t0);
-                const float u = clamp01(fmaf(t, d[0], o[0]));
-                const float v = clamp01(fmaf(t, d[1], o[1]));
-                const float w = clamp01(fmaf(t, d[2], o[2]));
-                float4 q;
-                if constexpr (MODE == 3) {
-                    sx_ = (k == 0) ? locate_span(M.ax[0], u) : walk_span(M.ax[0], u, sx_);
-                    sy_ = (k == 0) ? locate_span(M.ax[1], v) : walk_span(M.ax[1], v, sy_);
-                    sz_ = (k == 0) ? locate_span(M.ax[2], w) : walk_span(M.ax[2], w, sz_);
-                    q = query<Q, STORAGE>(M, u, v, w, sx_, sy_, sz_);
-                } else {
-                    axis_update<Q>(M.ax[0], cx, u);
-                    axis_update<Q>(M.ax[1], cy, v);
-                    axis_update<Q>(M.ax[2], cz, w);
-                    const int i0 = cx.s - M.ax[0].p, j0 = cy.s - M.ax[1].p, k0 = cz.s - M.ax[2].p;
-                    if constexpr (MODE == 1) {
-                        q = query2_rec<Q, STORAGE>(M, cx.rec, cy.rec, cz.rec, u, v, w, i0, j0, k0);
-                    } else {
-                        float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];
-                        record_basis<Q>(cx.rec, u, Nx, Dx);
-                        record_basis<Q>(cy.rec, v, Ny, Dy);
-                        record_basis<Q>(cz.rec, w, Nz, Dz);
-                        q = contract<Q, STORAGE>(M, i0, j0, k0, Nx, Dx, Ny, Dy, Nz, Dz);
-                        q.y *= cx.rec[1];
-                        q.z *= cy.rec[1];
-                        q.w *= cz.rec[1];
-                    }
-                }
-                ++count;
-                // ---- transfer function: linear interpolation between table rows
-                float tt = clamp01((q.x - P.vmin) * P.inv_range);
-                float4 c;
-                if (P.tf_n > 1) {
-                    const float xx = tt * tscale;
-                    const int i0 = min(static_cast<int>(xx), P.tf_n - 2);
-                    const float wt = xx - static_cast<float>(i0);
-                    const float4 c0 = tf[i0], c1 = tf[i0 + 1];
-                    c.x = fmaf(wt, c1.x - c0.x, c0.x);
-                    c.y = fmaf(wt, c1.y - c0.y, c0.y);
-                    c.z = fmaf(wt, c1.z - c0.z, c0.z);
-                    c.w = fmaf(wt, c1.w - c0.w, c0.w);
-                } else {
-                    c = tf[0];
-                }
-                // ---- Phong with a headlight, two-sided
-                if (P.shading) {
-                    const float g2 = q.y * q.y + q.z * q.z + q.w * q.w;
-                    float factor, spec = 0.0f;
-                    if (g2 <= P.gtiny2) {
-                        factor = P.ka + P.kd;
-                    } else {
-                        const float ndl = fabsf(q.y * lx + q.z * ly + q.w * lz) * rsqrtf(g2);
-                        const float rv = 2.0f * ndl * ndl - 1.0f;     // R.V with V = L
-                        spec = rv > 0.0f ? __powf(rv, P.shininess) : 0.0f;
-                        factor = fmaf(P.kd, ndl, P.ka);
-                    }
-                    c.x = clamp01(fmaf(c.x, factor, P.ks * spec));
-                    c.y = clamp01(fmaf(c.y, factor, P.ks * spec));
-                    c.z = clamp01(fmaf(c.z, factor, P.ks * spec));
-                }
-                // ---- front-to-back over
-                const float wgt = (1.0f - acc.w) * c.w;
-                acc.x = fmaf(wgt, c.x, acc.x);
-                acc.y = fmaf(wgt, c.y, acc.y);
-                acc.z = fmaf(wgt, c.z, acc.z);
-                acc.w += wgt;
-                if (acc.w >= P.ert_alpha) break;
-            }
-        }
-        P.out[static_cast<long long>(row) * P.width + col] = acc;
-    }
-
-    if (P.samples_out) {
-        unsigned long long c = count;
+    } else {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
-        if (lane == 0 && c) atomicAdd(P.samples_out, c);
+        for (int a = 0; a < 3; ++a) {
+            o[a] = P.eye[a];
+            d[a] = fmaf(sy, P.uy[a], fmaf(sx, P.rx[a], P.fwd[a]));
+        }
+        const float inv = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        d[0] *= inv;
+        d[1] *= inv;
+        d[2] *= inv;
     }
+    // ---- slab clip against [0,1]^3, t >= 0
+    float t0 = 0.0f, t1 = INFINITY;
+    bool hit = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] != 0.0f) {
+            const float inv = 1.0f / d[a];
+            float ta = -o[a] * inv, tb = (1.0f - o[a]) * inv;
+            if (ta > tb) {
+                const float t = ta;
+                ta = tb;
+                tb = t;
+            }
+            t0 = fmaxf(t0, ta);
+            t1 = fminf(t1, tb);
+        } else if (o[a] < 0.0f || o[a] > 1.0f) {
+            hit = false;
+        }
+    }
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);   // premultiplied rgb, alpha
+    if (!hit || !(t0 < t1)) return acc;
+
+    const int ns = P.n_samples, tf_n = P.tf_n, shading = P.shading;
+    const float vmin = P.vmin, inv_range = P.inv_range, ert = P.ert_alpha, gtiny2 = P.gtiny2;
+    const float ka = P.ka, kd = P.kd, ks = P.ks, shin = P.shininess;
+    const float dt = (t1 - t0) / static_cast<float>(ns);
+    const float tscale = static_cast<float>(tf_n - 1);
+    const float lx = -d[0], ly = -d[1], lz = -d[2];     // headlight: L = V = -d
+    AxisCache<Q> cx, cy, cz;
+    cx.s = cy.s = cz.s = -1;
+    int sx_ = -1, sy_ = -1, sz_ = -1;
+    for (int k = 0; k < ns; ++k) {
+        const float t = fmaf(static_cast<float>(k) + 0.5f, dt, t0);
+        const float u = clamp01(fmaf(t, d[0], o[0]));
+        const float v = clamp01(fmaf(t, d[1], o[1]));
+        const float w = clamp01(fmaf(t, d[2], o[2]));
+        float4 q;
+        if constexpr (MODE == 3) {
+            sx_ = (k == 0) ? locate_span(M.ax[0], u) : walk_span(M.ax[0], u, sx_);
+            sy_ = (k == 0) ? locate_span(M.ax[1], v) : walk_span(M.ax[1], v, sy_);
+            sz_ = (k == 0) ? locate_span(M.ax[2], w) : walk_span(M.ax[2], w, sz_);
+            q = query<Q, STORAGE>(M, u, v, w, sx_, sy_, sz_);
+        } else {
+            axis_update<Q>(M.ax[0], cx, u);
+            axis_update<Q>(M.ax[1], cy, v);
+            axis_update<Q>(M.ax[2], cz, w);
+            const int i0 = cx.s - M.ax[0].p, j0 = cy.s - M.ax[1].p, k0 = cz.s - M.ax[2].p;
+            if constexpr (MODE == 1) {
+                q = query2_rec<Q, STORAGE>(M, cx.rec, cy.rec, cz.rec, u, v, w, i0, j0, k0);
+            } else {
+                float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];
+                record_basis<Q>(cx.rec, u, Nx, Dx);
+                record_basis<Q>(cy.rec, v, Ny, Dy);
+                record_basis<Q>(cz.rec, w, Nz, Dz);
+                q = contract<Q, STORAGE>(M, i0, j0, k0, Nx, Dx, Ny, Dy, Nz, Dz);
+                q.y *= cx.rec[1];
+                q.z *= cy.rec[1];
+                q.w *= cz.rec[1];
+            }
+        }
+        ++count;
+        // ---- transfer function: linear interpolation between table rows
+        const float tt = clamp01((q.x - vmin) * inv_range);
+        float4 c;
+        if (tf_n > 1) {
+            const float xx = tt * tscale;
+            const int i0 = min(static_cast<int>(xx), tf_n - 2);
+            const float wt = xx - static_cast<float>(i0);
+            const float4 c0 = tf[i0], c1 = tf[i0 + 1];
+            c.x = fmaf(wt, c1.x - c0.x, c0.x);
+            c.y = fmaf(wt, c1.y - c0.y, c0.y);
+            c.z = fmaf(wt, c1.z - c0.z, c0.z);
+            c.w = fmaf(wt, c1.w - c0.w, c0.w);
+        } else {
+            c = tf[0];
+        }
+        // ---- Phong with a headlight, two-sided
+        if (shading) {
+            const float g2 = q.y * q.y + q.z * q.z + q.w * q.w;
+            float factor, spec = 0.0f;
+            if (g2 <= gtiny2) {
+                factor = ka + kd;
+            } else {
+                const float ndl = fabsf(q.y * lx + q.z * ly + q.w * lz) * rsqrtf(g2);
+                const float rv = 2.0f * ndl * ndl - 1.0f;     // R.V with V = L
+                spec = rv > 0.0f ? __powf(rv, shin) : 0.0f;
+                factor = fmaf(kd, ndl, ka);
+            }
+            c.x = clamp01(fmaf(c.x, factor, ks * spec));
+            c.y = clamp01(fmaf(c.y, factor, ks * spec));
+            c.z = clamp01(fmaf(c.z, factor, ks * spec));
+        }
+        // ---- front-to-back over
+        const float wgt = (1.0f - acc.w) * c.w;
+        acc.x = fmaf(wgt, c.x, acc.x);
+        acc.y = fmaf(wgt, c.y, acc.y);
+        acc.z = fmaf(wgt, c.z, acc.z);
+        acc.w += wgt;
+        if (acc.w >= ert) break;
+    }
+    return acc;
+}
+
+__device__ __forceinline__ void add_count(unsigned long long* dst, unsigned long long count)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) count += __shfl_xor_sync(0xFFFFFFFFu, count, o);
+    if ((threadIdx.x & 31) == 0 && count) atomicAdd(dst, count);
+}
+
+// ----------------------------------------------------------------------------------------
+// one image
+// ----------------------------------------------------------------------------------------
+
+template <int Q, int STORAGE, int MODE>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_render(ModelDev M, const __grid_constant__ RenderParams P,
+                                                                 int shape)
+{
+    __shared__ float4 tf[kTfMax];
+    for (int i = threadIdx.x; i < P.s.tf_n; i += kThreads) tf[i] = P.tf[i];
+    __syncthreads();
+
+    int col, row;
+    tile_pixel(tile_shape(shape), blockIdx.x, blockIdx.y, threadIdx.x, col, row);
+    unsigned long long count = 0;
+    if (col < P.s.width && row < P.s.height) {
+        const float4 acc = march<Q, STORAGE, MODE>(M, P.s, tf, col, row, count);
+        P.s.out[static_cast<long long>(row) * P.s.width + col] = acc;
+    }
+    if (P.s.samples_out) add_count(P.s.samples_out, count);
 }
 
 template <int Q, int STORAGE>
-cudaError_t render_qs(const ModelDev& m, const RenderParams& rp, int variant, cudaStream_t st)
+cudaError_t render_qs(const ModelDev& m, const RenderParams& rp, int variant, int shape, cudaStream_t st)
 {
-    dim3 grid((rp.width + kTileW - 1) / kTileW, (rp.height + kTileH - 1) / kTileH);
+    const TileShape T = tile_shape(shape);
+    dim3 grid((rp.s.width + T.tw - 1) / T.tw, (rp.s.height + T.th - 1) / T.th);
     switch (variant) {
     case 0:
-    case 2: k_render<Q, STORAGE, 2, kMinBlocks><<<grid, kThreads, 0, st>>>(m, rp); break;
-    case 1: k_render<Q, STORAGE, 1, kMinBlocks><<<grid, kThreads, 0, st>>>(m, rp); break;
-    default: k_render<Q, STORAGE, 3, kMinBlocks><<<grid, kThreads, 0, st>>>(m, rp); break;
+    case 2: k_render<Q, STORAGE, 2><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
+    case 1: k_render<Q, STORAGE, 1><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
+    default: k_render<Q, STORAGE, 3><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
     }
     return cudaGetLastError();
 }
 
 template <int Q>
-cudaError_t render_q(const ModelDev& m, const RenderParams& rp, int variant, cudaStream_t st)
+cudaError_t render_q(const ModelDev& m, const RenderParams& rp, int variant, int shape, cudaStream_t st)
 {
     switch (m.storage) {
-    case 1: return render_qs<Q, 1>(m, rp, variant, st);
-    case 2: return render_qs<Q, 2>(m, rp, variant, st);
-    case 3: return render_qs<Q, 3>(m, rp, variant, st);
+    case 1: return render_qs<Q, 1>(m, rp, variant, shape, st);
+    case 2: return render_qs<Q, 2>(m, rp, variant, shape, st);
+    case 3: return render_qs<Q, 3>(m, rp, variant, shape, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
+// ----------------------------------------------------------------------------------------
+// persistent batch
+// ----------------------------------------------------------------------------------------
+
+// Persistent CTAs over the requests of one (degree, storage) group: draw a tile, find its
+// request (tiles of one request are contiguous, so the previous request is checked
+// first), stage the request and its table in shared memory when it changes, render,
+// repeat until the counter passes the group's last tile.  One kernel per group keeps each
+// degree's register allocation free of the others'.
+template <int Q, int STORAGE>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_batch(BatchHead* __restrict__ table, int group,
+                                                                       int shape)
+{
+    __shared__ BatchItem item;
+    __shared__ float4 tf[kTfMax];
+    __shared__ int s_tile, s_idx;
+    BatchHead* head = table + group;
+    const BatchItem* items =
+        reinterpret_cast<const BatchItem*>(reinterpret_cast<const char*>(table) + head->items_offset);
+    const int n_items = head->n_items, total = head->total_tiles;
+    const TileShape T = tile_shape(shape);
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int t = atomicAdd(&head->next_tile, 1);
+            int i = cur < 0 ? 0 : cur;
+            if (t < total) {
+                if (!(items[i].tile_begin <= t && (i + 1 >= n_items || t < items[i + 1].tile_begin))) {
+                    int lo = 0, hi = n_items - 1;      // largest i with tile_begin <= t
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) / 2;
+                        if (items[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+                    }
+                    i = lo;
+                }
+            }
+            s_tile = t;
+            s_idx = i;
+        }
+        __syncthreads();
+        const int t = s_tile, i = s_idx;
+        if (t >= total) break;
+        if (i != cur) {
+            const int* src = reinterpret_cast<const int*>(items + i);
+            int* dst = reinterpret_cast<int*>(&item);
+            for (int e = threadIdx.x; e < static_cast<int>(sizeof(BatchItem) / sizeof(int)); e += kThreads) dst[e] = src[e];
+            __syncthreads();
+            for (int e = threadIdx.x; e < item.s.tf_n; e += kThreads) tf[e] = item.tf[e];
+            cur = i;
+            __syncthreads();
+        }
+        const int local = t - item.tile_begin;
+        const int tx = local % item.tiles_x, ty = local / item.tiles_x;
+        int col, row;
+        tile_pixel(T, tx, ty, threadIdx.x, col, row);
+        unsigned long long count = 0;
+        if (col < item.s.width && row < item.s.height) {
+            const float4 acc = march<Q, STORAGE, 2>(item.m, item.s, tf, col, row, count);
+            item.s.out[static_cast<long long>(row) * item.s.width + col] = acc;
+        }
+        if (item.s.samples_out) add_count(item.s.samples_out, count);
+        __syncthreads();   // s_tile / s_idx / item are rewritten next round
+    }
+}
+
+template <int Q, int STORAGE>
+BatchKernel batch_kernel_qs()
+{
+    BatchKernel k;
+    k.fn = reinterpret_cast<const void*>(&k_render_batch<Q, STORAGE>);
+    int blocks = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_render_batch<Q, STORAGE>, kThreads, 0);
+    k.blocks_per_sm = blocks > 0 ? blocks : 1;
+    k.threads = kThreads;
+    return k;
+}
+
+template <int Q>
+BatchKernel batch_kernel_q(int storage)
+{
+    return storage == 1 ? batch_kernel_qs<Q, 1>() : storage == 2 ? batch_kernel_qs<Q, 2>() : batch_kernel_qs<Q, 3>();
+}
+
 }  // namespace
 
-cudaError_t launch_render(const ModelDev& m, const RenderParams& rp, int variant, cudaStream_t stream)
+int render_tile_dims(int shape, int* tw, int* th)
+{
+    if (shape < 0 || shape >= kTileShapes) return -1;
+    *tw = tile_shape(shape).tw;
+    *th = tile_shape(shape).th;
+    return 0;
+}
+
+cudaError_t launch_render(const ModelDev& m, const RenderParams& rp, int variant, int shape, cudaStream_t stream)
 {
     switch (m.q) {
-    case 2: return render_q<2>(m, rp, variant, stream);
-    case 3: return render_q<3>(m, rp, variant, stream);
-    case 4: return render_q<4>(m, rp, variant, stream);
-    case 5: return render_q<5>(m, rp, variant, stream);
+    case 2: return render_q<2>(m, rp, variant, shape, stream);
+    case 3: return render_q<3>(m, rp, variant, shape, stream);
+    case 4: return render_q<4>(m, rp, variant, shape, stream);
+    case 5: return render_q<5>(m, rp, variant, shape, stream);
     default: return cudaErrorInvalidValue;
+    }
+}
+
+BatchKernel render_batch_kernel(int q, int storage)
+{
+    switch (q) {
+    case 2: return batch_kernel_q<2>(storage);
+    case 3: return batch_kernel_q<3>(storage);
+    case 4: return batch_kernel_q<4>(storage);
+    default: return batch_kernel_q<5>(storage);
     }
 }
 

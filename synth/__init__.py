@@ -124,7 +124,7 @@ class Turbulence:
 
     @staticmethod
     def draw(rng: np.random.Generator, m: int = 256, kmin: float = 1.0, kmax: float = 64.0) -> "Turbulence":
-        """Draws directions (2m normals... as 3m normals), magnitudes (m), phases (m)."""
+        """Draws directions (3m normals), magnitudes (m), phases (m)."""
         w = rng.normal(size=(m, 3))
         w /= np.linalg.norm(w, axis=1, keepdims=True)
         kap = np.exp(rng.uniform(math.log(kmin), math.log(kmax), size=m))
@@ -316,3 +316,70 @@ def config3(dtype_in=np.float64, nctrl=(512, 512, 256), decode_n: int = 1 << 22,
 def ctrl_minmax(P: np.ndarray):
     P = np.asarray(P, dtype=np.float64)
     return float(P.min()), float(P.max())
+
+
+def config4(size_scale: float = 1.0, rng_draws: bool = True) -> list:
+    """Batched workload: 16 models, per-axis control-point counts log-uniform integers in
+    [32, 256] (times size_scale), degrees cycling 2, 3, 4, uniform knots for even models
+    and non-uniform (1:4) for odd ones, FP32, Gaussian-sum fields (16 Gaussians + noise).
+    Each model gets one request: square image of side drawn from {256, 384, 512, 768,
+    1024}, 256..1024 samples per ray, Phong, ramp a_max 0.05, seeded perspective view.
+    Returns a list of (ModelSpec, RenderJob)."""
+    rng = rng_for(4)
+    out = []
+    for i in range(16):
+        p = (2, 3, 4)[i % 3]
+        n = tuple(max(p + 1, int(round(size_scale * math.exp(rng.uniform(math.log(32), math.log(256))))))
+                  for _ in range(3))
+        if i % 2 == 0:
+            knots = [knots_uniform(n[a], p) for a in range(3)]
+        else:
+            knots = [knots_nonuniform(n[a], p, rng) for a in range(3)]
+        m = gaussian_model(rng, (p, p, p), n, 16, noise=0.01, knots=knots, dtype=np.float32)
+        side = int(rng.choice([256, 384, 512, 768, 1024]))
+        ns = int(rng.integers(256, 1025))
+        d = random_direction(rng)
+        c = np.array([0.5, 0.5, 0.5])
+        cam = camera_persp(c + 2.5 * d, c, view_up_for(d), 30.0)
+        out.append((m, RenderJob(cam, side, side, ns, ramp_tf(256, 0.05), shading=True)))
+    return out
+
+
+SERVE_SIZES = [(128, 128, 128), (192, 192, 192), (256, 256, 256), (320, 320, 320), (384, 384, 384),
+               (512, 384, 256), (512, 512, 192), (512, 512, 256)]
+
+
+def config5_models(size_scale: float = 1.0) -> list:
+    """Serving workload models: 8 resident degree-3 models of the listed sizes (times
+    size_scale), turbulence (even index) and Gaussian-sum (odd) fields alternating,
+    stored as FP16 control points.  Returns ModelSpecs with FP64 control points."""
+    rng = rng_for(5)
+    out = []
+    for i, n in enumerate(SERVE_SIZES):
+        n = tuple(max(4, int(round(size_scale * x))) for x in n)
+        knots = [knots_uniform(n[a], 3) for a in range(3)]
+        if i % 2 == 0:
+            out.append(turbulence_model(rng, (3, 3, 3), n, knots, 64, 0.0, dtype=np.float64))
+        else:
+            out.append(gaussian_model(rng, (3, 3, 3), n, 32, noise=0.01, knots=knots, dtype=np.float64))
+    return out
+
+
+def config5_requests(rate_hz: float, duration_s: float, n_models: int = 8, seed_offset: int = 0,
+                     sides=(512, 1024, 1536, 2048), ns_range=(512, 2048)):
+    """Poisson request stream: arrival times (exponential gaps at rate_hz), a model index,
+    a square image side from `sides`, samples per ray uniform in ns_range, and an orbit
+    camera that advances along a seeded path per model.  Returns a list of dicts."""
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 5 + 1000 * (1 + seed_offset)))
+    t, out = 0.0, []
+    phase = rng.uniform(0, 2 * math.pi, size=n_models)
+    elev = rng.uniform(-0.5, 0.5, size=n_models)
+    while True:
+        t += rng.exponential(1.0 / rate_hz)
+        if t >= duration_s:
+            break
+        m = int(rng.integers(0, n_models))
+        phase[m] += 0.05
+        out.append(dict(t=t, model=m, side=int(rng.choice(sides)), n_samples=int(rng.integers(ns_range[0], ns_range[1] + 1)),
+                        camera=orbit_camera((0.5, 0.5, 0.5), 2.5, float(phase[m]), float(elev[m]), 30.0)))
+    return out
