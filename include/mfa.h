@@ -219,6 +219,25 @@ void mfa_batch_destroy(mfa_batch* batch);
 /* One-shot form: a thread-local batch context sized on demand, then mfa_batch_render. */
 int mfa_render_batch(const mfa_render_request* reqs, int n);
 
+/*
+ * Allocation-free batched render (the paper has no counterpart; this is a deployment
+ * variant of mfa_render_batch).  For callers that cannot call cudaMalloc -- for example a
+ * process whose memory pool already holds the whole device, or a render loop that must
+ * not take the allocator's implicit synchronisation -- this call renders up to 32
+ * requests with the same persistent kernels as mfa_batch_render but keeps the work table
+ * in a fixed 176 KiB array inside the library's device image instead of allocating one.
+ * Every GPU that loads the library holds that array until the process exits.
+ *   reqs, n  as mfa_batch_render; n in 0..32, MFA_ERR_ARG beyond (nothing launched).
+ * Asynchronous on the bound stream; it makes no allocation (no cudaMalloc, cudaFree or
+ * cudaMallocHost).  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture.  All calls share the one array, which keeps the previous call's contents
+ * (each call rewrites everything the kernels read, tile counters included): calls whose
+ * work overlaps on the GPU -- on different streams, or from different threads -- race and
+ * must be serialised by the caller.
+ */
+int mfa_render_batch_static(const mfa_render_request* reqs, int n);
+
 /* Text of the last error on the calling thread ("" if none). */
 const char* mfa_last_error(void);
 

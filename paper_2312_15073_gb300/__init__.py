@@ -22,7 +22,7 @@ from ctypes import POINTER, c_double, c_float, c_int, c_longlong, c_size_t, c_ul
 import numpy as np
 
 __all__ = ["Model", "decode", "locate_spans", "render", "lib", "MFA_F64", "MFA_F32", "MFA_F16", "MFA_BF16",
-           "MfaError", "camera", "transfer_fn", "Request", "Batch", "render_batch"]
+           "MfaError", "camera", "transfer_fn", "Request", "Batch", "render_batch", "render_batch_static"]
 
 MFA_F64, MFA_F32, MFA_F16, MFA_BF16 = 0, 1, 2, 3
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -103,6 +103,8 @@ def lib():
         L.mfa_batch_destroy.argtypes = [c_void_p]
         L.mfa_render_batch.restype = c_int
         L.mfa_render_batch.argtypes = [c_void_p, c_int]
+        L.mfa_render_batch_static.restype = c_int
+        L.mfa_render_batch_static.argtypes = [c_void_p, c_int]
         _lib = L
     return _lib
 
@@ -337,4 +339,13 @@ def render_batch(requests):
     arr = _request_array(requests)
     _bind_stream()
     _check(lib().mfa_render_batch(ctypes.addressof(arr), len(requests)))
+    return [q.out for q in requests]
+
+
+def render_batch_static(requests):
+    """Batched render that allocates nothing (mfa_render_batch_static): at most 32
+    requests; the work table lives in a fixed array in the library's device memory."""
+    arr = _request_array(requests)
+    _bind_stream()
+    _check(lib().mfa_render_batch_static(ctypes.addressof(arr), len(requests)))
     return [q.out for q in requests]
