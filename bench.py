@@ -380,6 +380,12 @@ def run_ours(args):
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
     }
+    if ws == 1 and not args.no_serve:
+        line["serving"] = dict(run_serve(mfa, rates=args.serve_rates, duration=args.serve_duration),
+                               note="Poisson requests (sides 512..2048, 512..2048 samples) on 8 resident degree-3 "
+                                    "models; served = FP16 control points, up to 8 requests in flight on priority "
+                                    "streams; plain = FP32 control points, one request at a time in arrival order; "
+                                    "latency from scheduled arrival to completion")
     if ws == 1 and not args.no_cpu_baseline:
         r_rate, d_rate, info = oracle_rates(wl, budget_s=args.cpu_budget)
         cpu_step_s = samples_per_frame / r_rate + n_pts / d_rate
@@ -396,6 +402,84 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------------------------------------
+# serving: Poisson camera-view requests, served FP16 path vs plain single-request FP32 path
+# ------------------------------------------------------------------------------------------
+
+def serve_models(mfa, size_scale=1.0):
+    """The 8 serving models twice: FP16 storage (served path) and FP32 (plain path)."""
+    import synth
+    specs = synth.config5_models(size_scale)
+    f16 = [mfa.Model(s.degree, s.nctrl, s.knots, s.ctrl64, storage=mfa.MFA_F16) for s in specs]
+    f32 = [mfa.Model(s.degree, s.nctrl, s.knots, s.ctrl64, storage=mfa.MFA_F32) for s in specs]
+    return specs, f16, f32
+
+
+def serve_stream(mfa, server, models, tf, stream):
+    """Submits the stream at its arrival times (a client thread sleeping until each one),
+    waits for every ticket; returns (latencies ms, completed, rejected, wall seconds)."""
+    import threading
+    t0 = mfa.server_now() + 0.05
+    tickets, rejected = [], 0
+    lock = threading.Lock()
+
+    def client():
+        nonlocal rejected
+        for r in stream:
+            delay = t0 + r["t"] - mfa.server_now()
+            if delay > 0:
+                time.sleep(delay)
+            try:
+                tk = server.submit(models[r["model"]], r["camera"], tf, r["side"], r["side"], r["n_samples"],
+                                   arrival_time=t0 + r["t"])
+                with lock:
+                    tickets.append(tk)
+            except mfa.MfaError:
+                rejected += 1
+
+    th = threading.Thread(target=client)
+    th.start()
+    lat = []
+    done = 0
+    while th.is_alive() or done < len(tickets):
+        with lock:
+            pending = tickets[done:]
+        for tk in pending:
+            lat.append(server.wait(tk, 600000.0))
+            server.release(tk)
+            done += 1
+        if not pending:
+            time.sleep(0.002)
+    th.join()
+    wall = mfa.server_now() - t0
+    return lat, done, rejected, wall
+
+
+def run_serve(mfa, rates, duration, size_scale=1.0, max_slots=8):
+    import synth
+    specs, f16, f32 = serve_models(mfa, size_scale)
+    tf = mfa.transfer_fn(synth.ramp_tf(256, 0.05), shading=True)
+    budget = 2 << 30
+    out = {"models": [list(s.nctrl) for s in specs], "hbm_budget_bytes": budget, "rates": {}}
+
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(math.ceil(q * len(v))) - 1)] if v else None
+
+    for rate in rates:
+        stream = synth.config5_requests(rate, duration)
+        row = {"requests": len(stream)}
+        for name, models, cfg in (("served_f16", f16, dict(max_slots=max_slots, priority_levels=4)),
+                                  ("plain_f32", f32, dict(max_slots=1, priority_levels=1))):
+            srv = mfa.Server(hbm_budget_bytes=budget, max_queue=4096, **cfg)
+            lat, done, rej, wall = serve_stream(mfa, srv, models, tf, stream)
+            srv.close()
+            row[name] = {"frames_per_s": done / wall if wall > 0 else None, "p50_ms": pct(lat, 0.5),
+                         "p99_ms": pct(lat, 0.99), "completed": done, "rejected": rej, "wall_s": wall}
+        out["rates"][str(rate)] = row
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -404,6 +488,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving comparison")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[20.0, 50.0], help="request rates (1/s)")
+    ap.add_argument("--serve-duration", type=float, default=6.0, help="seconds of arrivals per rate")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)      # at least three untimed warm-up steps
     if args.impl == "reference":

@@ -187,6 +187,7 @@ typedef struct {
 } mfa_render_request;
 
 typedef struct mfa_batch mfa_batch;   /* reusable batch context; owns its work tables */
+typedef struct mfa_server mfa_server; /* render server; owns its output arena */
 
 /*
  * Creates a batch context on the current device for up to max_requests (1..4096)
@@ -218,6 +219,68 @@ void mfa_batch_destroy(mfa_batch* batch);
 
 /* One-shot form: a thread-local batch context sized on demand, then mfa_batch_render. */
 int mfa_render_batch(const mfa_render_request* reqs, int n);
+
+/*
+ * Serving (the paper's input-latency concern, Sec. IV-B and Sec. V-C, on one GPU): a server
+ * keeps client-created models resident, takes camera-view requests of any image size,
+ * admits them in arrival order while a slot is free and the output image fits in its HBM
+ * arena (hbm_budget_bytes, allocated once at creation), and launches each admitted request
+ * at once on a stream whose priority rises as the request's work (pixels x samples)
+ * falls, so requests join the GPU while others are running and small views overtake large
+ * ones on the SMs that free up.  A server thread does the admitting; completions are
+ * stamped by host callbacks on the request streams.  No call waits without a bound.
+ */
+typedef struct {
+    size_t hbm_budget_bytes;   /* arena for output images (>= 4096) */
+    int max_slots;             /* requests on the GPU at once, 1..4096 */
+    int max_queue;             /* waiting requests before submit answers MFA_ERR_BUSY, >= 1 */
+    int priority_levels;       /* streams of distinct priority, 1..8 (1 = one FIFO stream) */
+    int variant, tile_shape;   /* render kernel choice (as mfa_render_opts) */
+} mfa_server_config;
+
+typedef struct {
+    const mfa_model* model;           /* resident; must outlive the request */
+    mfa_camera camera;
+    const mfa_transfer_fn* tf;        /* copied at submit */
+    int width, height, n_samples;
+    double arrival_time_s;            /* mfa_server_now() clock; <= 0 means the submit time */
+} mfa_serve_request;
+
+typedef struct {
+    long long submitted, completed, failed, rejected_busy, cancelled;
+    long long peak_in_flight, peak_arena_bytes;
+    long long in_flight, queued, arena_bytes_in_use;
+} mfa_server_stats;
+
+enum { MFA_TICKET_QUEUED = 0, MFA_TICKET_RUNNING = 1, MFA_TICKET_DONE = 2, MFA_TICKET_FAILED = 3 };
+
+/* Seconds on the monotonic clock the server stamps latencies with. */
+double mfa_server_now(void);
+/* Creates a server on the current device (allocates the arena, the streams and the
+ * server thread).  NULL on error. */
+mfa_server* mfa_server_create(const mfa_server_config* cfg);
+/* Queues a request; *ticket identifies it.  MFA_ERR_NOMEM if its image (width*height*16
+ * bytes) can never fit the budget, MFA_ERR_BUSY if max_queue requests are waiting,
+ * MFA_ERR_ARG on bad arguments; nothing is queued on error. */
+int mfa_server_submit(mfa_server* server, const mfa_serve_request* req, long long* ticket);
+/* State of a ticket (MFA_TICKET_*) and, once done, its latency from arrival to
+ * completion in ms (-1 before). */
+int mfa_server_poll(mfa_server* server, long long ticket, int* state, double* latency_ms);
+/* Waits up to timeout_ms for the ticket; MFA_ERR_TIMEOUT if it is still queued or
+ * running then.  *latency_ms as in mfa_server_poll. */
+int mfa_server_wait(mfa_server* server, long long ticket, double timeout_ms, double* latency_ms);
+/* DEVICE pointer to a done ticket's premultiplied RGBA image (height * width * 4 FP32),
+ * valid until mfa_server_release.  MFA_ERR_BUSY if the ticket is not done. */
+int mfa_server_result(mfa_server* server, long long ticket, const float** rgba);
+/* Copies a done ticket's image (width*height*16 bytes) to dst (device or host memory,
+ * dst_bytes large enough) asynchronously on the calling thread's bound stream. */
+int mfa_server_copy_result(mfa_server* server, long long ticket, void* dst, size_t dst_bytes);
+/* Returns a done ticket's image memory to the arena (or cancels a queued ticket).
+ * MFA_ERR_BUSY while the ticket is on the GPU. */
+int mfa_server_release(mfa_server* server, long long ticket);
+int mfa_server_get_stats(mfa_server* server, mfa_server_stats* stats);
+/* Stops the server thread, waits for requests on the GPU, frees everything. */
+void mfa_server_destroy(mfa_server* server);
 
 /*
  * Allocation-free batched render (the paper has no counterpart; this is a deployment

@@ -22,7 +22,7 @@ from ctypes import POINTER, c_double, c_float, c_int, c_longlong, c_size_t, c_ul
 import numpy as np
 
 __all__ = ["Model", "decode", "locate_spans", "render", "lib", "MFA_F64", "MFA_F32", "MFA_F16", "MFA_BF16",
-           "MfaError", "camera", "transfer_fn", "Request", "Batch", "render_batch", "render_batch_static"]
+           "MfaError", "camera", "transfer_fn", "Request", "Batch", "render_batch", "render_batch_static", "Server", "server_now"]
 
 MFA_F64, MFA_F32, MFA_F16, MFA_BF16 = 0, 1, 2, 3
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -53,6 +53,22 @@ class _Opts(ctypes.Structure):
 class _Request(ctypes.Structure):
     _fields_ = [("model", c_void_p), ("camera", _Camera), ("tf", c_void_p), ("width", c_int), ("height", c_int),
                 ("n_samples", c_int), ("rgba_out", c_void_p), ("samples_out", c_void_p)]
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", c_size_t), ("max_slots", c_int), ("max_queue", c_int),
+                ("priority_levels", c_int), ("variant", c_int), ("tile_shape", c_int)]
+
+
+class _ServeRequest(ctypes.Structure):
+    _fields_ = [("model", c_void_p), ("camera", _Camera), ("tf", c_void_p), ("width", c_int), ("height", c_int),
+                ("n_samples", c_int), ("arrival_time_s", c_double)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [(n, c_longlong) for n in ("submitted", "completed", "failed", "rejected_busy", "cancelled",
+                                          "peak_in_flight", "peak_arena_bytes", "in_flight", "queued",
+                                          "arena_bytes_in_use")]
 
 
 class _Info(ctypes.Structure):
@@ -103,6 +119,26 @@ def lib():
         L.mfa_batch_destroy.argtypes = [c_void_p]
         L.mfa_render_batch.restype = c_int
         L.mfa_render_batch.argtypes = [c_void_p, c_int]
+        L.mfa_server_now.restype = c_double
+        L.mfa_server_now.argtypes = []
+        L.mfa_server_create.restype = c_void_p
+        L.mfa_server_create.argtypes = [POINTER(_ServerConfig)]
+        L.mfa_server_submit.restype = c_int
+        L.mfa_server_submit.argtypes = [c_void_p, POINTER(_ServeRequest), POINTER(c_longlong)]
+        L.mfa_server_poll.restype = c_int
+        L.mfa_server_poll.argtypes = [c_void_p, c_longlong, POINTER(c_int), POINTER(c_double)]
+        L.mfa_server_wait.restype = c_int
+        L.mfa_server_wait.argtypes = [c_void_p, c_longlong, c_double, POINTER(c_double)]
+        L.mfa_server_result.restype = c_int
+        L.mfa_server_result.argtypes = [c_void_p, c_longlong, POINTER(c_void_p)]
+        L.mfa_server_copy_result.restype = c_int
+        L.mfa_server_copy_result.argtypes = [c_void_p, c_longlong, c_void_p, c_size_t]
+        L.mfa_server_release.restype = c_int
+        L.mfa_server_release.argtypes = [c_void_p, c_longlong]
+        L.mfa_server_get_stats.restype = c_int
+        L.mfa_server_get_stats.argtypes = [c_void_p, POINTER(_ServerStats)]
+        L.mfa_server_destroy.restype = None
+        L.mfa_server_destroy.argtypes = [c_void_p]
         L.mfa_render_batch_static.restype = c_int
         L.mfa_render_batch_static.argtypes = [c_void_p, c_int]
         _lib = L
@@ -349,3 +385,80 @@ def render_batch_static(requests):
     _bind_stream()
     _check(lib().mfa_render_batch_static(ctypes.addressof(arr), len(requests)))
     return [q.out for q in requests]
+
+
+TICKET_QUEUED, TICKET_RUNNING, TICKET_DONE, TICKET_FAILED = 0, 1, 2, 3
+
+
+def server_now() -> float:
+    """The monotonic clock (seconds) the server stamps arrivals and completions with."""
+    return lib().mfa_server_now()
+
+
+class Server:
+    """Render server (mfa_server_*): resident models, requests admitted by an HBM budget
+    and launched on priority streams as slots free up."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 16, max_queue: int = 4096, priority_levels: int = 4,
+                 variant: int = 0, tile_shape: int = 0):
+        import torch  # noqa: F401
+        cfg = _ServerConfig(int(hbm_budget_bytes), int(max_slots), int(max_queue), int(priority_levels), int(variant),
+                            int(tile_shape))
+        h = lib().mfa_server_create(ctypes.byref(cfg))
+        if not h:
+            raise MfaError(-1, lib().mfa_last_error().decode())
+        self._h = h
+        self._keep = {}
+
+    def submit(self, model: Model, cam, tf: transfer_fn, width: int, height: int, n_samples: int,
+               arrival_time: float = 0.0) -> int:
+        r = _ServeRequest()
+        r.model = model.handle
+        r.camera = cam if isinstance(cam, _Camera) else camera(cam)
+        r.tf = ctypes.addressof(tf.struct)
+        r.width, r.height, r.n_samples = int(width), int(height), int(n_samples)
+        r.arrival_time_s = float(arrival_time)
+        t = c_longlong()
+        _check(lib().mfa_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        self._keep[t.value] = (width, height)
+        return t.value
+
+    def poll(self, ticket: int):
+        st, lat = c_int(), c_double()
+        _check(lib().mfa_server_poll(self._h, ticket, ctypes.byref(st), ctypes.byref(lat)))
+        return st.value, lat.value
+
+    def wait(self, ticket: int, timeout_ms: float = 60000.0) -> float:
+        lat = c_double()
+        _check(lib().mfa_server_wait(self._h, ticket, float(timeout_ms), ctypes.byref(lat)))
+        return lat.value
+
+    def result(self, ticket: int, out=None):
+        """Copies the done ticket's image into a (H, W, 4) FP32 CUDA tensor."""
+        import torch
+        w, h = self._keep[ticket]
+        if out is None:
+            out = torch.empty((h, w, 4), device="cuda", dtype=torch.float32)
+        _bind_stream()
+        _check(lib().mfa_server_copy_result(self._h, ticket, out.data_ptr(), out.numel() * 4))
+        return out
+
+    def release(self, ticket: int):
+        _check(lib().mfa_server_release(self._h, ticket))
+        self._keep.pop(ticket, None)
+
+    def stats(self) -> dict:
+        s = _ServerStats()
+        _check(lib().mfa_server_get_stats(self._h, ctypes.byref(s)))
+        return {n: getattr(s, n) for n, _ in _ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mfa_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,423 @@
+// server.cu -- render serving: resident models, camera-view requests admitted by an HBM
+// budget, continuously joined onto the running work, p50/p99 latency (the mfa_server_*
+// calls of include/mfa.h).
+//
+// The paper's concern is input latency: every view or transfer-function change re-runs
+// the pipeline (Sec. IV-B, Sec. V-C).  A server thread owns a queue of submitted requests.
+// A request is admitted when a slot is free and its output image fits in the HBM arena
+// (one device allocation of the budget, sub-allocated on the host); it is then launched
+// at once as a one-CTA-per-tile render on a stream whose priority grows as the request's
+// work (pixels x samples) shrinks.  Requests therefore join the GPU while others run: the
+// block scheduler hands freed SMs to the highest-priority pending tiles, so a small view
+// overtakes a large one already on the device instead of queueing behind it.  Completion
+// is stamped by a host callback on the request's stream; latency runs from the request's
+// arrival time (given by the client, or the submit time) to that stamp.  No device-side
+// wait is involved anywhere; every host wait has a timeout.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "host.cuh"
+
+using namespace mfa;
+
+namespace {
+
+double now_s()
+{
+    using namespace std::chrono;
+    return duration_cast<duration<double>>(steady_clock::now().time_since_epoch()).count();
+}
+
+// First-fit sub-allocator over one device range; host bookkeeping only.
+class Arena {
+public:
+    void init(char* base, size_t bytes)
+    {
+        base_ = base;
+        free_.clear();
+        free_[0] = bytes;
+        used_ = 0;
+    }
+    // offset of a block of `bytes` (256-aligned), or -1
+    long long alloc(size_t bytes)
+    {
+        bytes = (bytes + 255) / 256 * 256;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                const size_t off = it->first, len = it->second;
+                free_.erase(it);
+                if (len > bytes) free_[off + bytes] = len - bytes;
+                used_ += bytes;
+                sizes_[off] = bytes;
+                return static_cast<long long>(off);
+            }
+        }
+        return -1;
+    }
+    void release(size_t off)
+    {
+        auto s = sizes_.find(off);
+        if (s == sizes_.end()) return;
+        size_t len = s->second;
+        sizes_.erase(s);
+        used_ -= len;
+        auto next = free_.lower_bound(off);
+        if (next != free_.end() && off + len == next->first) {
+            len += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == off) {
+                prev->second += len;
+                return;
+            }
+        }
+        free_[off] = len;
+    }
+    char* base() const { return base_; }
+    size_t used() const { return used_; }
+
+private:
+    char* base_ = nullptr;
+    std::map<size_t, size_t> free_;    // offset -> length
+    std::map<size_t, size_t> sizes_;   // live offset -> length
+    size_t used_ = 0;
+};
+
+enum TicketState { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3, kCancelled = 4 };
+
+struct Ticket {
+    long long id = 0;
+    int state = kQueued;
+    const mfa_model* model = nullptr;
+    mfa_camera camera{};
+    mfa_transfer_fn tf{};
+    std::vector<float> table;            // the request's own copy of the TF rows
+    int width = 0, height = 0, n_samples = 0;
+    size_t bytes = 0;
+    long long offset = -1;               // arena offset of the image once admitted
+    double t_arrival = 0, t_admit = 0, t_done = 0;
+    int stream = 0;
+    mfa_server* server = nullptr;
+    int error = 0;
+};
+
+}  // namespace
+
+struct mfa_server {
+    mfa_server_config cfg{};
+    int device = 0;
+    void* arena_mem = nullptr;
+    Arena arena;
+    std::vector<cudaStream_t> streams;   // index 0 = highest priority
+    std::mutex mu;
+    std::condition_variable cv;          // wakes the scheduler
+    std::condition_variable done_cv;     // wakes waiters
+    std::deque<Ticket*> queue;
+    std::unordered_map<long long, Ticket*> tickets;
+    std::vector<Ticket*> cancelled_keep;   // released while queued; freed at destroy
+    long long next_id = 1;
+    int in_flight = 0;
+    bool stop = false;
+    std::thread worker;
+    mfa_server_stats stats{};
+};
+
+namespace {
+
+void CUDART_CB on_done(void* arg)
+{
+    Ticket* t = static_cast<Ticket*>(arg);
+    mfa_server* s = t->server;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        t->t_done = now_s();
+        t->state = kDone;
+        --s->in_flight;
+        ++s->stats.completed;
+    }
+    s->cv.notify_all();
+    s->done_cv.notify_all();
+}
+
+// Stream for a request: more work -> lower priority (index), log4 buckets.
+int stream_for(const mfa_server* s, const Ticket* t)
+{
+    const double work = static_cast<double>(t->width) * t->height * t->n_samples;
+    int lvl = 0;
+    for (double w = 1 << 26; w < work && lvl + 1 < static_cast<int>(s->streams.size()); w *= 4.0) ++lvl;
+    return lvl;
+}
+
+// Launches one admitted request (called with the mutex NOT held).
+int launch(mfa_server* s, Ticket* t)
+{
+    cudaSetDevice(s->device);
+    t->tf.rgba = t->table.data();
+    mfa_render_opts opts;
+    std::memset(&opts, 0, sizeof opts);
+    opts.variant = s->cfg.variant;
+    opts.tile_shape = s->cfg.tile_shape;
+    cudaStream_t st = s->streams[t->stream];
+    mfa_set_stream(st);
+    int rc = mfa_render_ex(t->model, &t->camera, &t->tf, t->width, t->height, t->n_samples,
+                           reinterpret_cast<float*>(s->arena.base() + t->offset), &opts);
+    if (rc == MFA_OK) {
+        cudaError_t e = cudaLaunchHostFunc(st, on_done, t);
+        if (e != cudaSuccess) rc = cuda_fail(e, "completion callback");
+    }
+    return rc;
+}
+
+void worker_main(mfa_server* s)
+{
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (!s->stop) {
+        // admit in arrival order while a slot and arena memory are free
+        std::vector<Ticket*> admitted;
+        while (!s->queue.empty() && s->in_flight < s->cfg.max_slots) {
+            Ticket* t = s->queue.front();
+            if (t->state == kCancelled) {
+                s->queue.pop_front();
+                continue;
+            }
+            const long long off = s->arena.alloc(t->bytes);
+            if (off < 0) break;   // wait for memory
+            s->queue.pop_front();
+            t->offset = off;
+            t->state = kRunning;
+            t->t_admit = now_s();
+            t->stream = stream_for(s, t);
+            ++s->in_flight;
+            s->stats.peak_in_flight = std::max<long long>(s->stats.peak_in_flight, s->in_flight);
+            s->stats.peak_arena_bytes = std::max<long long>(s->stats.peak_arena_bytes, static_cast<long long>(s->arena.used()));
+            admitted.push_back(t);
+        }
+        if (!admitted.empty()) {
+            lk.unlock();
+            for (Ticket* t : admitted) {
+                const int rc = launch(s, t);
+                if (rc != MFA_OK) {
+                    std::lock_guard<std::mutex> g(s->mu);
+                    t->state = kFailed;
+                    t->error = rc;
+                    t->t_done = now_s();
+                    --s->in_flight;
+                    ++s->stats.failed;
+                }
+            }
+            lk.lock();
+            s->done_cv.notify_all();
+            continue;
+        }
+        s->cv.wait_for(lk, std::chrono::milliseconds(50));
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+double mfa_server_now(void) { return now_s(); }
+
+mfa_server* mfa_server_create(const mfa_server_config* cfg)
+{
+    if (!cfg) return fail(MFA_ERR_ARG, "config is NULL"), nullptr;
+    if (cfg->hbm_budget_bytes < 4096) return fail(MFA_ERR_ARG, "hbm_budget_bytes must be >= 4096"), nullptr;
+    if (cfg->max_slots < 1 || cfg->max_slots > 4096) return fail(MFA_ERR_ARG, "max_slots outside 1..4096"), nullptr;
+    if (cfg->max_queue < 1) return fail(MFA_ERR_ARG, "max_queue must be >= 1"), nullptr;
+    if (cfg->priority_levels < 1 || cfg->priority_levels > 8) return fail(MFA_ERR_ARG, "priority_levels outside 1..8"), nullptr;
+    if (cfg->variant < 0 || cfg->variant > 3 || cfg->tile_shape < 0 || cfg->tile_shape >= kTileShapes)
+        return fail(MFA_ERR_ARG, "variant or tile_shape out of range"), nullptr;
+    mfa_server* s = new mfa_server();
+    s->cfg = *cfg;
+    cudaGetDevice(&s->device);
+    cudaError_t e = cudaMalloc(&s->arena_mem, cfg->hbm_budget_bytes);
+    if (e != cudaSuccess) {
+        cuda_fail(e, "server arena");
+        delete s;
+        return nullptr;
+    }
+    s->arena.init(static_cast<char*>(s->arena_mem), cfg->hbm_budget_bytes);
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    const int span = least - greatest;   // greatest is the most negative (highest) priority
+    for (int l = 0; l < cfg->priority_levels; ++l) {
+        const int prio = cfg->priority_levels == 1 ? least : greatest + (span * l) / (cfg->priority_levels - 1);
+        cudaStream_t st;
+        cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio);
+        s->streams.push_back(st);
+    }
+    s->worker = std::thread(worker_main, s);
+    return s;
+}
+
+int mfa_server_submit(mfa_server* s, const mfa_serve_request* req, long long* ticket)
+{
+    if (!s || !req || !ticket) return fail(MFA_ERR_ARG, "server, request and ticket must be non-NULL");
+    if (!req->model || !req->tf || !req->tf->rgba) return fail(MFA_ERR_ARG, "request needs a model and a table");
+    if (req->width < 1 || req->width > 32768 || req->height < 1 || req->height > 32768 || req->n_samples < 1 ||
+        req->n_samples > (1 << 20) || req->tf->n_entries < 1 || req->tf->n_entries > kTfMax)
+        return fail(MFA_ERR_ARG, "request size, samples or table out of range");
+    if (req->model->device != s->device) return fail(MFA_ERR_ARG, "model lives on another device");
+    const size_t bytes = static_cast<size_t>(req->width) * req->height * 16;
+    if (bytes > s->cfg.hbm_budget_bytes)
+        return fail(MFA_ERR_NOMEM, "image of %zu bytes exceeds the HBM budget of %zu bytes", bytes,
+                    s->cfg.hbm_budget_bytes);
+    Ticket* t = new Ticket();
+    t->model = req->model;
+    t->camera = req->camera;
+    t->tf = *req->tf;
+    t->table.assign(req->tf->rgba, req->tf->rgba + 4 * req->tf->n_entries);
+    t->width = req->width;
+    t->height = req->height;
+    t->n_samples = req->n_samples;
+    t->bytes = bytes;
+    t->server = s;
+    t->t_arrival = req->arrival_time_s > 0 ? req->arrival_time_s : now_s();
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        if (static_cast<int>(s->queue.size()) >= s->cfg.max_queue) {
+            ++s->stats.rejected_busy;
+            delete t;
+            return fail(MFA_ERR_BUSY, "queue full (%d requests waiting)", s->cfg.max_queue);
+        }
+        t->id = s->next_id++;
+        s->tickets[t->id] = t;
+        s->queue.push_back(t);
+        ++s->stats.submitted;
+        *ticket = t->id;
+    }
+    s->cv.notify_all();
+    return MFA_OK;
+}
+
+int mfa_server_poll(mfa_server* s, long long ticket, int* state, double* latency_ms)
+{
+    if (!s) return fail(MFA_ERR_ARG, "server is NULL");
+    std::lock_guard<std::mutex> g(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) return fail(MFA_ERR_ARG, "unknown ticket %lld", ticket);
+    Ticket* t = it->second;
+    if (state) *state = t->state;
+    if (latency_ms) *latency_ms = t->state == kDone ? 1e3 * (t->t_done - t->t_arrival) : -1.0;
+    return t->state == kFailed ? t->error : MFA_OK;
+}
+
+int mfa_server_wait(mfa_server* s, long long ticket, double timeout_ms, double* latency_ms)
+{
+    if (!s) return fail(MFA_ERR_ARG, "server is NULL");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) return fail(MFA_ERR_ARG, "unknown ticket %lld", ticket);
+    Ticket* t = it->second;
+    const auto until = std::chrono::steady_clock::now() +
+                       std::chrono::microseconds(static_cast<long long>(std::max(0.0, timeout_ms) * 1e3));
+    while (t->state == kQueued || t->state == kRunning) {
+        if (s->done_cv.wait_until(lk, until) == std::cv_status::timeout &&
+            (t->state == kQueued || t->state == kRunning))
+            return fail(MFA_ERR_TIMEOUT, "ticket %lld not done after %.3f ms", ticket, timeout_ms);
+    }
+    if (latency_ms) *latency_ms = t->state == kDone ? 1e3 * (t->t_done - t->t_arrival) : -1.0;
+    if (t->state == kFailed) return fail(t->error, "ticket %lld failed", ticket);
+    if (t->state == kCancelled) return fail(MFA_ERR_ARG, "ticket %lld was cancelled", ticket);
+    return MFA_OK;
+}
+
+int mfa_server_result(mfa_server* s, long long ticket, const float** rgba)
+{
+    if (!s || !rgba) return fail(MFA_ERR_ARG, "server and rgba must be non-NULL");
+    std::lock_guard<std::mutex> g(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) return fail(MFA_ERR_ARG, "unknown ticket %lld", ticket);
+    if (it->second->state != kDone) return fail(MFA_ERR_BUSY, "ticket %lld not done", ticket);
+    *rgba = reinterpret_cast<const float*>(s->arena.base() + it->second->offset);
+    return MFA_OK;
+}
+
+int mfa_server_copy_result(mfa_server* s, long long ticket, void* dst, size_t dst_bytes)
+{
+    if (!s || !dst) return fail(MFA_ERR_ARG, "server and dst must be non-NULL");
+    const float* src = nullptr;
+    size_t bytes = 0;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        auto it = s->tickets.find(ticket);
+        if (it == s->tickets.end()) return fail(MFA_ERR_ARG, "unknown ticket %lld", ticket);
+        if (it->second->state != kDone) return fail(MFA_ERR_BUSY, "ticket %lld not done", ticket);
+        src = reinterpret_cast<const float*>(s->arena.base() + it->second->offset);
+        bytes = it->second->bytes;
+    }
+    if (dst_bytes < bytes) return fail(MFA_ERR_ARG, "destination holds %zu bytes, the image needs %zu", dst_bytes, bytes);
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, current_stream());
+    return e == cudaSuccess ? MFA_OK : cuda_fail(e, "copy result");
+}
+
+int mfa_server_release(mfa_server* s, long long ticket)
+{
+    if (!s) return fail(MFA_ERR_ARG, "server is NULL");
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        auto it = s->tickets.find(ticket);
+        if (it == s->tickets.end()) return fail(MFA_ERR_ARG, "unknown ticket %lld", ticket);
+        Ticket* t = it->second;
+        if (t->state == kRunning) return fail(MFA_ERR_BUSY, "ticket %lld still running", ticket);
+        if (t->state == kQueued) {
+            t->state = kCancelled;   // the scheduler drops it from the queue
+            ++s->stats.cancelled;
+            s->tickets.erase(it);
+            // the queue still points at it: leave it to the scheduler, which skips cancelled
+            // tickets; the ticket object is freed at destroy
+            s->cancelled_keep.push_back(t);
+            return MFA_OK;
+        }
+        if (t->offset >= 0) s->arena.release(static_cast<size_t>(t->offset));
+        s->tickets.erase(it);
+        delete t;
+    }
+    s->cv.notify_all();
+    return MFA_OK;
+}
+
+int mfa_server_get_stats(mfa_server* s, mfa_server_stats* out)
+{
+    if (!s || !out) return fail(MFA_ERR_ARG, "server and out must be non-NULL");
+    std::lock_guard<std::mutex> g(s->mu);
+    *out = s->stats;
+    out->in_flight = s->in_flight;
+    out->queued = static_cast<long long>(s->queue.size());
+    out->arena_bytes_in_use = static_cast<long long>(s->arena.used());
+    return MFA_OK;
+}
+
+void mfa_server_destroy(mfa_server* s)
+{
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        s->stop = true;
+    }
+    s->cv.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    cudaSetDevice(s->device);
+    for (cudaStream_t st : s->streams) {
+        cudaStreamSynchronize(st);   // callbacks of launched requests have run after this
+        cudaStreamDestroy(st);
+    }
+    for (auto& kv : s->tickets) delete kv.second;
+    for (Ticket* t : s->cancelled_keep) delete t;
+    cudaFree(s->arena_mem);
+    delete s;
+}
+
+}  // extern "C"
