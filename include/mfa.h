@@ -152,7 +152,10 @@ typedef struct {
     int tile_shape;                   /* ray tile: 0 = 16x8 pixels per CTA with 8x4 per warp
                                          (default), 1 = 32x4 / 8x4, 2 = 8x16 / 4x8,
                                          3 = 16x8 / 16x2.  MFA_ERR_ARG outside 0..3. */
-    int reserved[6];                  /* zero */
+    int use_tuned;                    /* nonzero: take variant and tile_shape from the
+                                         autotuner's choice for this workload class when
+                                         there is one (mfa_tune_render) */
+    int reserved[5];                  /* zero */
 } mfa_render_opts;
 
 /*
@@ -221,6 +224,34 @@ void mfa_batch_destroy(mfa_batch* batch);
 int mfa_render_batch(const mfa_render_request* reqs, int n);
 
 /*
+ * Autotuner (no counterpart in the paper: it picks this implementation's launch shape).
+ * A workload class is (degree class p_max + 1, storage type, image pixels in powers of 4,
+ * samples per ray in powers of 2, uniform or other knots).
+ */
+typedef struct {
+    int variant;      /* as mfa_render_opts.variant */
+    int tile_shape;   /* as mfa_render_opts.tile_shape */
+    float ms;         /* measured time per launch */
+} mfa_tune_result;
+
+/* Times every variant x tile-shape candidate on this render (one warm-up plus `reps`
+ * launches each, CUDA events on the bound stream; synchronises it), stores the fastest as
+ * the choice for the workload's class and returns it in *best; `all` (may be NULL)
+ * receives up to max_all measured candidates, *n_all their count.  rgba_out is
+ * overwritten.  Any render argument error is returned as by mfa_render. */
+int mfa_tune_render(const mfa_model* model, const mfa_camera* camera, const mfa_transfer_fn* tf, int width,
+                    int height, int n_samples, float* rgba_out, int reps, mfa_tune_result* best,
+                    mfa_tune_result* all, int max_all, int* n_all);
+/* Times each tile shape for this batch submission and configures the batch with the
+ * fastest (*best).  Synchronises the bound stream. */
+int mfa_tune_batch(mfa_batch* batch, const mfa_render_request* reqs, int n, int reps, mfa_tune_result* best);
+/* The stored choice for a workload's class; MFA_ERR_ARG if there is none. */
+int mfa_tune_lookup(const mfa_model* model, int width, int height, int n_samples, mfa_tune_result* out);
+/* Writes / reads the stored choices (one text line per class). */
+int mfa_tune_save(const char* path);
+int mfa_tune_load(const char* path);
+
+/*
  * Serving (the paper's input-latency concern, Sec. IV-B and Sec. V-C, on one GPU): a server
  * keeps client-created models resident, takes camera-view requests of any image size,
  * admits them in arrival order while a slot is free and the output image fits in its HBM
@@ -236,6 +267,7 @@ typedef struct {
     int max_queue;             /* waiting requests before submit answers MFA_ERR_BUSY, >= 1 */
     int priority_levels;       /* streams of distinct priority, 1..8 (1 = one FIFO stream) */
     int variant, tile_shape;   /* render kernel choice (as mfa_render_opts) */
+    int use_tuned;             /* nonzero: the autotuner's choice per request class when known */
 } mfa_server_config;
 
 typedef struct {

@@ -22,7 +22,7 @@ from ctypes import POINTER, c_double, c_float, c_int, c_longlong, c_size_t, c_ul
 import numpy as np
 
 __all__ = ["Model", "decode", "locate_spans", "render", "lib", "MFA_F64", "MFA_F32", "MFA_F16", "MFA_BF16",
-           "MfaError", "camera", "transfer_fn", "Request", "Batch", "render_batch", "render_batch_static", "Server", "server_now"]
+           "MfaError", "camera", "transfer_fn", "Request", "Batch", "render_batch", "render_batch_static", "Server", "server_now", "tune_render", "tune_batch", "tune_save", "tune_load"]
 
 MFA_F64, MFA_F32, MFA_F16, MFA_BF16 = 0, 1, 2, 3
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -47,7 +47,12 @@ class _TF(ctypes.Structure):
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("samples_out", c_void_p), ("variant", c_int), ("tile_shape", c_int), ("reserved", c_int * 6)]
+    _fields_ = [("samples_out", c_void_p), ("variant", c_int), ("tile_shape", c_int), ("use_tuned", c_int),
+                ("reserved", c_int * 5)]
+
+
+class _TuneResult(ctypes.Structure):
+    _fields_ = [("variant", c_int), ("tile_shape", c_int), ("ms", c_float)]
 
 
 class _Request(ctypes.Structure):
@@ -57,7 +62,7 @@ class _Request(ctypes.Structure):
 
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", c_size_t), ("max_slots", c_int), ("max_queue", c_int),
-                ("priority_levels", c_int), ("variant", c_int), ("tile_shape", c_int)]
+                ("priority_levels", c_int), ("variant", c_int), ("tile_shape", c_int), ("use_tuned", c_int)]
 
 
 class _ServeRequest(ctypes.Structure):
@@ -139,6 +144,17 @@ def lib():
         L.mfa_server_get_stats.argtypes = [c_void_p, POINTER(_ServerStats)]
         L.mfa_server_destroy.restype = None
         L.mfa_server_destroy.argtypes = [c_void_p]
+        L.mfa_tune_render.restype = c_int
+        L.mfa_tune_render.argtypes = [c_void_p, POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int, c_void_p, c_int,
+                                      POINTER(_TuneResult), c_void_p, c_int, POINTER(c_int)]
+        L.mfa_tune_batch.restype = c_int
+        L.mfa_tune_batch.argtypes = [c_void_p, c_void_p, c_int, c_int, POINTER(_TuneResult)]
+        L.mfa_tune_lookup.restype = c_int
+        L.mfa_tune_lookup.argtypes = [c_void_p, c_int, c_int, c_int, POINTER(_TuneResult)]
+        L.mfa_tune_save.restype = c_int
+        L.mfa_tune_save.argtypes = [ctypes.c_char_p]
+        L.mfa_tune_load.restype = c_int
+        L.mfa_tune_load.argtypes = [ctypes.c_char_p]
         L.mfa_render_batch_static.restype = c_int
         L.mfa_render_batch_static.argtypes = [c_void_p, c_int]
         _lib = L
@@ -282,7 +298,7 @@ class transfer_fn:
 
 
 def render(model: Model, cam, tf: transfer_fn, width: int, height: int, n_samples: int, out=None,
-           samples_out=None, variant: int = 0, tile_shape: int = 0):
+           samples_out=None, variant: int = 0, tile_shape: int = 0, use_tuned: bool = False):
     """Premultiplied RGBA image (height, width, 4) FP32 on the current device.
     samples_out: optional 1-element int64 CUDA tensor to which the number of evaluated
     samples is added."""
@@ -295,6 +311,7 @@ def render(model: Model, cam, tf: transfer_fn, width: int, height: int, n_sample
     opts = _Opts()
     opts.variant = int(variant)
     opts.tile_shape = int(tile_shape)
+    opts.use_tuned = 1 if use_tuned else 0
     if samples_out is not None:
         if not (samples_out.is_cuda and samples_out.dtype == torch.int64):
             raise TypeError("samples_out must be an int64 CUDA tensor")
@@ -400,10 +417,10 @@ class Server:
     and launched on priority streams as slots free up."""
 
     def __init__(self, hbm_budget_bytes: int, max_slots: int = 16, max_queue: int = 4096, priority_levels: int = 4,
-                 variant: int = 0, tile_shape: int = 0):
+                 variant: int = 0, tile_shape: int = 0, use_tuned: bool = False):
         import torch  # noqa: F401
         cfg = _ServerConfig(int(hbm_budget_bytes), int(max_slots), int(max_queue), int(priority_levels), int(variant),
-                            int(tile_shape))
+                            int(tile_shape), 1 if use_tuned else 0)
         h = lib().mfa_server_create(ctypes.byref(cfg))
         if not h:
             raise MfaError(-1, lib().mfa_last_error().decode())
@@ -462,3 +479,35 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def tune_render(model: Model, cam, tf: transfer_fn, width: int, height: int, n_samples: int, reps: int = 3):
+    """Autotunes (variant, tile shape) for this render's workload class; returns
+    (best dict, list of all measured candidates)."""
+    import torch
+    out = torch.empty((height, width, 4), device="cuda", dtype=torch.float32)
+    best = _TuneResult()
+    allr = (_TuneResult * 32)()
+    n = c_int()
+    c = cam if isinstance(cam, _Camera) else camera(cam)
+    _bind_stream()
+    _check(lib().mfa_tune_render(model.handle, ctypes.byref(c), ctypes.byref(tf.struct), width, height, n_samples,
+                                 out.data_ptr(), reps, ctypes.byref(best), ctypes.addressof(allr), 32, ctypes.byref(n)))
+    conv = lambda r: dict(variant=r.variant, tile_shape=r.tile_shape, ms=r.ms)
+    return conv(best), [conv(allr[i]) for i in range(n.value)]
+
+
+def tune_batch(batch: "Batch", requests, reps: int = 2) -> dict:
+    arr = _request_array(requests)
+    best = _TuneResult()
+    _bind_stream()
+    _check(lib().mfa_tune_batch(batch._h, ctypes.addressof(arr), len(requests), reps, ctypes.byref(best)))
+    return dict(variant=best.variant, tile_shape=best.tile_shape, ms=best.ms)
+
+
+def tune_save(path: str):
+    _check(lib().mfa_tune_save(path.encode()))
+
+
+def tune_load(path: str):
+    _check(lib().mfa_tune_load(path.encode()))

@@ -206,15 +206,16 @@ mfa_model* mfa_model_create_ex(const int degree[3], const int nctrl[3], const do
 
     // knot vectors (host, FP64): caller's or clamped uniform
     std::vector<double> U[3];
+    bool uniform = true;
     for (int a = 0; a < 3; ++a) {
         const int n = nctrl[a], p = degree[a], m = n + p + 1;
         U[a].resize(m);
+        for (int i = 0; i < m; ++i)
+            U[a][i] = i <= p ? 0.0 : (i >= n ? 1.0 : static_cast<double>(i - p) / static_cast<double>(n - p));
         if (knots && knots[a]) {
+            if (std::memcmp(U[a].data(), knots[a], sizeof(double) * m) != 0) uniform = false;
             std::memcpy(U[a].data(), knots[a], sizeof(double) * m);
             if (!check_knots(U[a].data(), n, p, a)) return nullptr;
-        } else {
-            for (int i = 0; i < m; ++i)
-                U[a][i] = i <= p ? 0.0 : (i >= n ? 1.0 : static_cast<double>(i - p) / static_cast<double>(n - p));
         }
     }
 
@@ -225,6 +226,7 @@ mfa_model* mfa_model_create_ex(const int degree[3], const int nctrl[3], const do
         M->nctrl[a] = nctrl[a];
     }
     M->storage = storage;
+    M->uniform = uniform;
     const int Q = qmax;
     cudaStream_t st = g_stream;
 
@@ -367,10 +369,11 @@ int mfa_locate_spans(const mfa_model* m, const float* pts, long long n, int* spa
 int mfa_render_ex(const mfa_model* m, const mfa_camera* cam, const mfa_transfer_fn* tf, int width, int height,
                   int n_samples, float* rgba_out, const mfa_render_opts* opts)
 {
-    const int variant = opts ? opts->variant : 0;
-    const int shape = opts ? opts->tile_shape : 0;
+    int variant = opts ? opts->variant : 0;
+    int shape = opts ? opts->tile_shape : 0;
     if (variant < 0 || variant > 3) return fail(MFA_ERR_ARG, "render variant %d outside 0..3", variant);
     if (shape < 0 || shape >= kTileShapes) return fail(MFA_ERR_ARG, "tile_shape %d outside 0..%d", shape, kTileShapes - 1);
+    if (opts && opts->use_tuned && m) tuned_lookup(m, width, height, n_samples, &variant, &shape);
     RenderParams P;
     if (int rc = setup_render(m, cam, tf, width, height, n_samples, rgba_out, opts ? opts->samples_out : nullptr, P.s,
                               P.tf))

@@ -17,6 +17,7 @@ struct mfa_model {
     mfa_dtype storage = MFA_F32;
     float vmin = 0.0f, vmax = 0.0f, maxabs = 0.0f;
     size_t bytes = 0;
+    bool uniform = true;        // every axis has clamped uniform knots
     void* d_win = nullptr;      // window array
     void* d_tables = nullptr;   // kup, grid and records of the three axes, one allocation
     mfa::ModelDev dev{};
@@ -32,6 +33,8 @@ int cuda_fail(cudaError_t e, const char* what);
 cudaStream_t current_stream();
 // MFA_OK if the model lives on the current device.
 int check_model_device(const mfa_model* m);
+// Cached autotuner choice for this workload class, if any.
+bool tuned_lookup(const mfa_model* m, int w, int h, int ns, int* variant, int* shape);
 // Validates one render call and fills the kernel's scalars and table (tf_n rows).
 int setup_render(const mfa_model* m, const mfa_camera* cam, const mfa_transfer_fn* tf, int width, int height,
                  int n_samples, float* rgba_out, unsigned long long* samples_out, RenderScalars& S, float4* table);

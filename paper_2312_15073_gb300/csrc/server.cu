@@ -167,6 +167,7 @@ int launch(mfa_server* s, Ticket* t)
     std::memset(&opts, 0, sizeof opts);
     opts.variant = s->cfg.variant;
     opts.tile_shape = s->cfg.tile_shape;
+    opts.use_tuned = s->cfg.use_tuned;
     cudaStream_t st = s->streams[t->stream];
     mfa_set_stream(st);
     int rc = mfa_render_ex(t->model, &t->camera, &t->tf, t->width, t->height, t->n_samples,

@@ -136,3 +136,32 @@ def test_batch_grid_override_and_validation(mfa, orc):
     assert all(float(q.out.min()) == 3.0 for q in reqs[:2])
     with pytest.raises(mfa.MfaError):
         mfa.Batch(8).render(reqs + reqs)                 # more than the capacity
+
+
+def test_autotuner_render_and_batch(mfa, orc, tmp_path):
+    """The tuner measures every variant x tile shape, its choice is looked up by workload
+    class (use_tuned), and a tuned render equals the explicit render of that choice."""
+    import torch
+    models = _models(mfa, orc)
+    rng = np.random.default_rng(9)
+    reqs, jobs = _requests(mfa, models, rng)
+    m, ref, cam, table, tf, W, H, ns = jobs[0]
+    best, allr = mfa.tune_render(m, cam, tf, W, H, ns, reps=2)
+    assert len(allr) == 12 and all(r["ms"] > 0 for r in allr)
+    assert best["ms"] == min(r["ms"] for r in allr)
+    a = mfa.render(m, cam, tf, W, H, ns, use_tuned=True)
+    b = mfa.render(m, cam, tf, W, H, ns, variant=best["variant"], tile_shape=best["tile_shape"])
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    path = str(tmp_path / "tune.txt")
+    mfa.tune_save(path)
+    mfa.tune_load(path)
+    batch = mfa.Batch(16)
+    bb = mfa.tune_batch(batch, reqs, reps=1)
+    assert 0 <= bb["tile_shape"] < 4 and bb["ms"] > 0
+    for q in reqs:
+        q.out.fill_(-1)
+    batch.render(reqs)
+    torch.cuda.synchronize()
+    for q, (m, ref, cam, table, tf, W, H, ns) in zip(reqs, jobs):
+        assert torch.equal(q.out, mfa.render(m, cam, tf, W, H, ns))
