@@ -143,12 +143,13 @@ typedef struct {
     unsigned long long* samples_out;  /* DEVICE counter or NULL: the number of samples
                                          evaluated (after box clipping and early
                                          termination) is ADDED to it */
-    int variant;                      /* kernel variant: 0 = library default (2);
+    int variant;                      /* kernel variant: 0 = library default (4);
                                          1 = span records cached in registers along the
                                          ray, packed FP32x2 arithmetic; 2 = records cached,
-                                         scalar FP32; 3 = nothing cached, scalar FP32.
-                                         Variants differ only in FP32 summation order.
-                                         MFA_ERR_ARG outside 0..3. */
+                                         scalar FP32; 3 = nothing cached, scalar FP32;
+                                         4 = as 2, software-pipelined over samples.
+                                         Variants differ only in FP32 rounding order.
+                                         MFA_ERR_ARG outside 0..4. */
     int tile_shape;                   /* ray tile: 0 = 16x8 pixels per CTA with 8x4 per warp
                                          (default), 1 = 32x4 / 8x4, 2 = 8x16 / 4x8,
                                          3 = 16x8 / 16x2.  MFA_ERR_ARG outside 0..3. */

@@ -65,7 +65,7 @@ int mfa_tune_render(const mfa_model* m, const mfa_camera* cam, const mfa_transfe
     if (e != cudaSuccess) return cuda_fail(e, "tuner events");
     mfa_tune_result top{ 0, 0, INFINITY };
     int count = 0, rc = MFA_OK;
-    for (int variant = 1; variant <= 3 && rc == MFA_OK; ++variant) {
+    for (int variant = 1; variant <= 4 && rc == MFA_OK; ++variant) {
         for (int shape = 0; shape < kTileShapes && rc == MFA_OK; ++shape) {
             mfa_render_opts o{};
             o.variant = variant;
@@ -106,7 +106,7 @@ int mfa_tune_batch(mfa_batch* batch, const mfa_render_request* reqs, int n, int 
     cudaError_t e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&b);
     if (e != cudaSuccess) return cuda_fail(e, "tuner events");
-    mfa_tune_result top{ 2, 0, INFINITY };
+    mfa_tune_result top{ 4, 0, INFINITY };
     int rc = MFA_OK;
     for (int shape = 0; shape < kTileShapes && rc == MFA_OK; ++shape) {
         if ((rc = mfa_batch_configure(batch, shape, 0)) != MFA_OK) break;
@@ -120,7 +120,7 @@ int mfa_tune_batch(mfa_batch* batch, const mfa_render_request* reqs, int n, int 
         }
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, a, b);
-        if (ms / reps < top.ms) top = mfa_tune_result{ 2, shape, ms / reps };
+        if (ms / reps < top.ms) top = mfa_tune_result{ 4, shape, ms / reps };
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
@@ -167,7 +167,7 @@ int mfa_tune_load(const char* path)
         int q, s, pb, sb, u, v, t;
         float ms;
         if (std::sscanf(line, "%d %d %d %d %d %d %d %f", &q, &s, &pb, &sb, &u, &v, &t, &ms) != 8) continue;
-        if (v < 1 || v > 3 || t < 0 || t >= kTileShapes) continue;
+        if (v < 1 || v > 4 || t < 0 || t >= kTileShapes) continue;
         g_cache[Key(q, s, pb, sb, u)] = mfa_tune_result{ v, t, ms };
         ++loaded;
     }
