@@ -145,6 +145,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate_replicas(total_s: float, units: float, dist, device: str):
+    """Whole-job numbers of N independent replicas: the slowest rank's time and the sum
+    of the work every rank did (the only collective; it is not in the data path)."""
+    import torch
+    t = torch.tensor([total_s], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -333,11 +344,7 @@ def run_ours(args):
     units = samples + args.steps * n_pts
     total_s = sum(step_ms) / 1e3
     if dist:
-        t = torch.tensor([total_s, float(units)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-        total_s, units = float(tmax[0]), float(t[1])
+        total_s, units = aggregate_replicas(total_s, units, dist, "cuda")
     value = units / total_s
 
     # end to end through the public API with host buffers (pinned), copies inside the region

@@ -147,9 +147,11 @@ typedef struct {
                                          1 = span records cached in registers along the
                                          ray, packed FP32x2 arithmetic; 2 = records cached,
                                          scalar FP32; 3 = nothing cached, scalar FP32;
-                                         4 = as 2, software-pipelined over samples.
-                                         Variants differ only in FP32 rounding order.
-                                         MFA_ERR_ARG outside 0..4. */
+                                         4 = as 2, software-pipelined over samples;
+                                         5 = control-point bricks staged per warp in shared
+                                         memory as FP32 (degree <= 3 on every axis; otherwise
+                                         4).  Variants differ only in FP32 rounding order.
+                                         MFA_ERR_ARG outside 0..5. */
     int tile_shape;                   /* ray tile: 0 = 16x8 pixels per CTA with 8x4 per warp
                                          (default), 1 = 32x4 / 8x4, 2 = 8x16 / 4x8,
                                          3 = 16x8 / 16x2.  MFA_ERR_ARG outside 0..3. */
@@ -227,7 +229,8 @@ int mfa_render_batch(const mfa_render_request* reqs, int n);
 /*
  * Autotuner (no counterpart in the paper: it picks this implementation's launch shape).
  * A workload class is (degree class p_max + 1, storage type, image pixels in powers of 4,
- * samples per ray in powers of 2, uniform or other knots).
+ * samples per ray in powers of 2, uniform or other knots, largest control-point count per
+ * axis in powers of 2).
  */
 typedef struct {
     int variant;      /* as mfa_render_opts.variant */

@@ -371,7 +371,7 @@ int mfa_render_ex(const mfa_model* m, const mfa_camera* cam, const mfa_transfer_
 {
     int variant = opts ? opts->variant : 0;
     int shape = opts ? opts->tile_shape : 0;
-    if (variant < 0 || variant > 4) return fail(MFA_ERR_ARG, "render variant %d outside 0..4", variant);
+    if (variant < 0 || variant > 5) return fail(MFA_ERR_ARG, "render variant %d outside 0..5", variant);
     if (shape < 0 || shape >= kTileShapes) return fail(MFA_ERR_ARG, "tile_shape %d outside 0..%d", shape, kTileShapes - 1);
     if (opts && opts->use_tuned && m) tuned_lookup(m, width, height, n_samples, &variant, &shape);
     RenderParams P;

@@ -365,6 +365,243 @@ __device__ __forceinline__ float4 march_pipelined(const ModelDev& M, const Rende
     return acc;
 }
 
+// ----------------------------------------------------------------------------------------
+// variant 5: control-point bricks in shared memory, per warp
+// ----------------------------------------------------------------------------------------
+//
+// The 32 rays of a warp march through the same region of the model.  The march is cut
+// into segments of S sample indices; for each segment the warp computes the bounding box
+// of its rays' sample positions (positions are monotone in the sample index, so the
+// segment's end points bound it), turns the box into a range of knot spans per axis, and
+// copies the control-point windows that range needs into a kBrick^3 brick of shared
+// memory -- converted to FP32 once, whatever the storage type.  Every sample of the
+// segment then reads its 16 support rows from the brick at fixed offsets (no per-sample
+// conversion, no 64-bit address arithmetic).  S adapts so the range fits the brick (halved
+// when it does not, doubled back after a segment that fits); a segment of one sample that
+// still does not fit is evaluated from global memory.
+constexpr int kBrick = 8;
+constexpr int kBrickFloats4 = kBrick * kBrick * kBrick;   // 8 KB per warp
+constexpr int kSegMax = 64;
+
+template <int STORAGE>
+__device__ __forceinline__ float4 window_f32(const void* win, long long idx)
+{
+    if constexpr (STORAGE == 1) {
+        return __ldg(static_cast<const float4*>(win) + idx);
+    } else {
+        const uint2 v = __ldg(static_cast<const uint2*>(win) + idx);
+        const float2 lo = Row16<4, STORAGE == 3>::cvt(v.x), hi = Row16<4, STORAGE == 3>::cvt(v.y);
+        return make_float4(lo.x, lo.y, hi.x, hi.y);
+    }
+}
+
+// Sum-factorised contraction over a support held in a shared-memory brick (rows at fixed
+// offsets from `b0`); same arithmetic order as contract().
+template <int Q>
+__device__ __forceinline__ float4 contract_brick(const float4* __restrict__ b0, const float (&Nx)[Q], const float (&Dx)[Q],
+                                                 const float (&Ny)[Q], const float (&Dy)[Q], const float (&Nz)[Q],
+                                                 const float (&Dz)[Q])
+{
+    float f = 0.0f, fx = 0.0f, fy = 0.0f, fz = 0.0f;
+#pragma unroll
+    for (int c = 0; c < Q; ++c) {
+        float C = 0.0f, Dv = 0.0f, E = 0.0f;
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+            const float4 r4 = b0[(c * kBrick + b) * kBrick];
+            const float row[4] = { r4.x, r4.y, r4.z, r4.w };
+            float A = 0.0f, B = 0.0f;
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                A = fmaf(Nx[a], row[a], A);
+                B = fmaf(Dx[a], row[a], B);
+            }
+            C = fmaf(Ny[b], A, C);
+            Dv = fmaf(Dy[b], A, Dv);
+            E = fmaf(Ny[b], B, E);
+        }
+        f = fmaf(Nz[c], C, f);
+        fz = fmaf(Dz[c], C, fz);
+        fy = fmaf(Nz[c], Dv, fy);
+        fx = fmaf(Nz[c], E, fx);
+    }
+    return make_float4(f, fx, fy, fz);
+}
+
+// Warp-collective: every lane of the warp calls it (valid = false for lanes without a pixel).
+template <int Q, int STORAGE>
+__device__ __forceinline__ float4 march_bricked(const ModelDev& M, const RenderScalars& P, const float4* __restrict__ tf,
+                                                int col, int row, bool valid, unsigned long long& count,
+                                                float4* __restrict__ brick)
+{
+    static_assert(Q <= 4, "bricks hold 4-wide windows");
+    const unsigned kFull = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    const float sx = fmaf(static_cast<float>(2 * col + 1), P.inv_w, -1.0f);
+    const float sy = fmaf(static_cast<float>(-(2 * row + 1)), P.inv_h, 1.0f);
+    float o[3], d[3];
+    if (P.projection == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            o[a] = fmaf(sy, P.uy[a], fmaf(sx, P.rx[a], P.eye[a]));
+            d[a] = P.fwd[a];
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            o[a] = P.eye[a];
+            d[a] = fmaf(sy, P.uy[a], fmaf(sx, P.rx[a], P.fwd[a]));
+        }
+        const float inv = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        d[0] *= inv;
+        d[1] *= inv;
+        d[2] *= inv;
+    }
+    float t0 = 0.0f, t1 = INFINITY;
+    bool hit = valid;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] != 0.0f) {
+            const float inv = 1.0f / d[a];
+            float ta = -o[a] * inv, tb = (1.0f - o[a]) * inv;
+            if (ta > tb) {
+                const float t = ta;
+                ta = tb;
+                tb = t;
+            }
+            t0 = fmaxf(t0, ta);
+            t1 = fminf(t1, tb);
+        } else if (o[a] < 0.0f || o[a] > 1.0f) {
+            hit = false;
+        }
+    }
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    bool live = hit && t0 < t1;
+
+    const int ns = P.n_samples;
+    const float ert = P.ert_alpha;
+    const float dt = live ? (t1 - t0) / static_cast<float>(ns) : 0.0f;
+    ShadeParams S;
+    S.vmin = P.vmin;
+    S.inv_range = P.inv_range;
+    S.tscale = static_cast<float>(P.tf_n - 1);
+    S.tf_last = max(P.tf_n - 2, 0);
+    S.shading = P.shading;
+    S.ka = P.ka;
+    S.kd = P.kd;
+    S.ks = P.ks;
+    S.shin = P.shininess;
+    S.gtiny2 = P.gtiny2;
+    S.lx = -d[0];
+    S.ly = -d[1];
+    S.lz = -d[2];
+    AxisCache<Q> cx, cy, cz;
+    cx.s = cy.s = cz.s = -1;
+    const int nxp = M.nxp, nyp = M.nyp;
+
+    auto pos = [&](int k, float (&u)[3]) {
+        const float t = fmaf(static_cast<float>(k) + 0.5f, dt, t0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u[a] = clamp01(fmaf(t, d[a], o[a]));
+    };
+
+    int k_lo = 0, seg = 16;
+    while (__any_sync(kFull, live) && k_lo < ns) {
+        const int kb = min(k_lo + seg, ns) - 1;
+        float lo[3] = { 2.0f, 2.0f, 2.0f }, hi[3] = { -1.0f, -1.0f, -1.0f };
+        if (live) {
+            float pa[3], pb[3];
+            pos(k_lo, pa);
+            pos(kb, pb);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = fminf(pa[a], pb[a]);
+                hi[a] = fmaxf(pa[a], pb[a]);
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = fminf(lo[a], __shfl_xor_sync(kFull, lo[a], off));
+                hi[a] = fmaxf(hi[a], __shfl_xor_sync(kFull, hi[a], off));
+            }
+        }
+        // knot spans of the box corners: lanes 0..2 the low corner, lanes 3..5 the high one
+        int sv = 0;
+        if (lane < 6) {
+            const int a = lane % 3;
+            const float u = lane < 3 ? (a == 0 ? lo[0] : a == 1 ? lo[1] : lo[2]) : (a == 0 ? hi[0] : a == 1 ? hi[1] : hi[2]);
+            sv = locate_span(M.ax[a], clamp01(u));
+        }
+        int org[3], ext[3];
+        bool fits = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int slo = __shfl_sync(kFull, sv, a), shi = __shfl_sync(kFull, sv, a + 3);
+            org[a] = slo - M.ax[a].p;
+            ext[a] = shi - slo + Q;
+            fits = fits && ext[a] <= kBrick;
+        }
+        if (!fits && seg > 1) {
+            seg >>= 1;   // retry this segment with fewer samples
+            continue;
+        }
+        if (fits) {
+            const int total = ext[0] * ext[1] * ext[2];
+            for (int e = lane; e < total; e += 32) {
+                const int ex = e % ext[0], r = e / ext[0];
+                const int ey = r % ext[1], ez = r / ext[1];
+                const long long gidx =
+                    (static_cast<long long>(org[2] + ez) * nyp + (org[1] + ey)) * nxp + (org[0] + ex);
+                brick[(ez * kBrick + ey) * kBrick + ex] = window_f32<STORAGE>(M.win, gidx);
+            }
+            __syncwarp();
+        }
+        if (live) {
+            for (int k = k_lo; k <= kb; ++k) {
+                float u[3];
+                pos(k, u);
+                axis_update<Q>(M.ax[0], cx, u[0]);
+                axis_update<Q>(M.ax[1], cy, u[1]);
+                axis_update<Q>(M.ax[2], cz, u[2]);
+                float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];
+                record_basis<Q>(cx.rec, u[0], Nx, Dx);
+                record_basis<Q>(cy.rec, u[1], Ny, Dy);
+                record_basis<Q>(cz.rec, u[2], Nz, Dz);
+                float4 q;
+                if (fits) {
+                    const int rx = min(max(cx.s - M.ax[0].p - org[0], 0), kBrick - Q);
+                    const int ry = min(max(cy.s - M.ax[1].p - org[1], 0), kBrick - Q);
+                    const int rz = min(max(cz.s - M.ax[2].p - org[2], 0), kBrick - Q);
+                    q = contract_brick<Q>(brick + (rz * kBrick + ry) * kBrick + rx, Nx, Dx, Ny, Dy, Nz, Dz);
+                } else {
+                    q = contract<Q, STORAGE>(M, cx.s - M.ax[0].p, cy.s - M.ax[1].p, cz.s - M.ax[2].p, Nx, Dx, Ny, Dy,
+                                             Nz, Dz);
+                }
+                q.y *= cx.rec[1];
+                q.z *= cy.rec[1];
+                q.w *= cz.rec[1];
+                const float4 c = sample_colour(tf, S, q);
+                const float wgt = (1.0f - acc.w) * c.w;
+                acc.x = fmaf(wgt, c.x, acc.x);
+                acc.y = fmaf(wgt, c.y, acc.y);
+                acc.z = fmaf(wgt, c.z, acc.z);
+                acc.w += wgt;
+                ++count;
+                if (acc.w >= ert) {
+                    live = false;
+                    break;
+                }
+            }
+        }
+        __syncwarp();   // the brick is rewritten by the next segment
+        k_lo = kb + 1;
+        if (fits) seg = min(seg * 2, kSegMax);
+    }
+    return acc;
+}
+
 __device__ __forceinline__ void add_count(unsigned long long* dst, unsigned long long count)
 {
 #pragma unroll
@@ -388,7 +625,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_render(ModelDev M, con
     int col, row;
     tile_pixel(tile_shape(shape), blockIdx.x, blockIdx.y, threadIdx.x, col, row);
     unsigned long long count = 0;
-    if (col < P.s.width && row < P.s.height) {
+    if constexpr (MODE == 5) {
+        __shared__ float4 bricks[kThreads / 32][kBrickFloats4];
+        const bool valid = col < P.s.width && row < P.s.height;
+        const float4 acc = march_bricked<(Q <= 4 ? Q : 4), STORAGE>(M, P.s, tf, valid ? col : 0, valid ? row : 0, valid,
+                                                                    count, bricks[threadIdx.x >> 5]);
+        if (valid) P.s.out[static_cast<long long>(row) * P.s.width + col] = acc;
+    } else if (col < P.s.width && row < P.s.height) {
         float4 acc;
         if constexpr (MODE == 4)
             acc = march_pipelined<Q, STORAGE>(M, P.s, tf, col, row, count);
@@ -409,6 +652,13 @@ cudaError_t render_qs(const ModelDev& m, const RenderParams& rp, int variant, in
     case 1: k_render<Q, STORAGE, 1><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
     case 0:
     case 4: k_render<Q, STORAGE, 4><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
+    case 5:
+        if constexpr (Q <= 4) {
+            k_render<Q, STORAGE, 5><<<grid, kThreads, 0, st>>>(m, rp, shape);
+        } else {
+            k_render<Q, STORAGE, 4><<<grid, kThreads, 0, st>>>(m, rp, shape);   // bricks hold 4-wide rows
+        }
+        break;
     default: k_render<Q, STORAGE, 3><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
     }
     return cudaGetLastError();

@@ -3,10 +3,12 @@
 // (the mfa_tune_* calls of include/mfa.h).
 //
 // A workload class is (degree class Q, storage type, image pixels in powers of 4, samples
-// per ray in powers of 2, knot layout uniform or not): the relative speed of the
-// candidates depends on how many samples a ray spends per knot span and on how coherent
-// a warp's rays are, both of which these capture.  Timing uses CUDA events on the calling
+// per ray in powers of 2, knot layout uniform or not, largest control-point count per axis
+// in powers of 2): the relative speed of the candidates depends on how many samples a ray
+// spends per knot span and how many knot spans a warp's rays cover (shared-memory bricks
+// win when both are small), which these capture.  Timing uses CUDA events on the calling
 // thread's stream around `reps` launches after one warm-up launch.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <map>
@@ -19,7 +21,7 @@ using namespace mfa;
 
 namespace {
 
-using Key = std::tuple<int, int, int, int, int>;
+using Key = std::tuple<int, int, int, int, int, int>;
 
 std::mutex g_mu;
 std::map<Key, mfa_tune_result> g_cache;
@@ -30,8 +32,9 @@ Key key_of(const mfa_model* m, int w, int h, int ns)
 {
     // uniform knots <=> every axis's first interior knot sits at 1/(n-p) (the library builds
     // them that way when the caller passes NULL); other layouts share one class
+    const int nmax = std::max(m->nctrl[0], std::max(m->nctrl[1], m->nctrl[2]));
     return Key(m->dev.q, static_cast<int>(m->storage), log_bucket(static_cast<double>(w) * h, 4.0),
-               log_bucket(ns, 2.0), m->uniform ? 1 : 0);
+               log_bucket(ns, 2.0), m->uniform ? 1 : 0, log_bucket(nmax, 2.0));
 }
 
 }  // namespace
@@ -65,7 +68,7 @@ int mfa_tune_render(const mfa_model* m, const mfa_camera* cam, const mfa_transfe
     if (e != cudaSuccess) return cuda_fail(e, "tuner events");
     mfa_tune_result top{ 0, 0, INFINITY };
     int count = 0, rc = MFA_OK;
-    for (int variant = 1; variant <= 4 && rc == MFA_OK; ++variant) {
+    for (int variant = 1; variant <= 5 && rc == MFA_OK; ++variant) {
         for (int shape = 0; shape < kTileShapes && rc == MFA_OK; ++shape) {
             mfa_render_opts o{};
             o.variant = variant;
@@ -145,11 +148,11 @@ int mfa_tune_save(const char* path)
     FILE* f = std::fopen(path, "w");
     if (!f) return fail(MFA_ERR_ARG, "cannot write %s", path);
     std::lock_guard<std::mutex> g(g_mu);
-    std::fprintf(f, "# q storage pixel_bucket sample_bucket uniform variant tile_shape ms\n");
+    std::fprintf(f, "# q storage pixel_bucket sample_bucket uniform size_bucket variant tile_shape ms\n");
     for (const auto& kv : g_cache)
-        std::fprintf(f, "%d %d %d %d %d %d %d %.6f\n", std::get<0>(kv.first), std::get<1>(kv.first),
-                     std::get<2>(kv.first), std::get<3>(kv.first), std::get<4>(kv.first), kv.second.variant,
-                     kv.second.tile_shape, kv.second.ms);
+        std::fprintf(f, "%d %d %d %d %d %d %d %d %.6f\n", std::get<0>(kv.first), std::get<1>(kv.first),
+                     std::get<2>(kv.first), std::get<3>(kv.first), std::get<4>(kv.first), std::get<5>(kv.first),
+                     kv.second.variant, kv.second.tile_shape, kv.second.ms);
     std::fclose(f);
     return MFA_OK;
 }
@@ -164,11 +167,11 @@ int mfa_tune_load(const char* path)
     std::lock_guard<std::mutex> g(g_mu);
     while (std::fgets(line, sizeof line, f)) {
         if (line[0] == '#') continue;
-        int q, s, pb, sb, u, v, t;
+        int q, s, pb, sb, u, nb, v, t;
         float ms;
-        if (std::sscanf(line, "%d %d %d %d %d %d %d %f", &q, &s, &pb, &sb, &u, &v, &t, &ms) != 8) continue;
-        if (v < 1 || v > 4 || t < 0 || t >= kTileShapes) continue;
-        g_cache[Key(q, s, pb, sb, u)] = mfa_tune_result{ v, t, ms };
+        if (std::sscanf(line, "%d %d %d %d %d %d %d %d %f", &q, &s, &pb, &sb, &u, &nb, &v, &t, &ms) != 9) continue;
+        if (v < 1 || v > 5 || t < 0 || t >= kTileShapes) continue;
+        g_cache[Key(q, s, pb, sb, u, nb)] = mfa_tune_result{ v, t, ms };
         ++loaded;
     }
     std::fclose(f);

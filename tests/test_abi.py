@@ -97,8 +97,8 @@ def test_tune_cache_file_errors(libmfa, tmp_path):
     assert libmfa.mfa_tune_load(str(bad).encode()) == -1
     assert libmfa.mfa_tune_load(str(tmp_path / "missing.txt").encode()) == -1
     ok = tmp_path / "ok.txt"
-    ok.write_text("4 1 10 10 1 2 3 1.5\n4 1 10 10 1 9 3 1.5\n")      # second line: bad variant, skipped
+    ok.write_text("4 1 10 10 1 7 2 3 1.5\n4 1 10 10 1 7 9 3 1.5\n")      # second line: bad variant, skipped
     assert libmfa.mfa_tune_load(str(ok).encode()) == 0
     out = tmp_path / "out.txt"
     assert libmfa.mfa_tune_save(str(out).encode()) == 0
-    assert "4 1 10 10 1 2 3" in out.read_text()
+    assert "4 1 10 10 1 7 2 3" in out.read_text()

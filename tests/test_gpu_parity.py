@@ -284,7 +284,7 @@ def test_render_edge_cases(mfa, orc):
     assert float(out.min()) == 7.0
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("degree", [(3, 3, 3), (2, 3, 4), (4, 4, 4)])
 def test_render_variants_match_oracle(mfa, orc, variant, degree):
     """Every kernel variant (support cached / records cached / nothing cached) against the
