@@ -60,7 +60,8 @@ typedef struct mfa_model mfa_model;   /* opaque; owns all of its device memory *
  *   knots      knots[d] is a HOST array of nctrl[d] + degree[d] + 1 FP64 values,
  *              non-decreasing, clamped (the first degree+1 equal 0, the last degree+1
  *              equal 1).  knots == NULL or knots[d] == NULL selects the clamped uniform
- *              vector (interior knots i / (nctrl - degree)).
+ *              vector (interior knots i / (nctrl - degree)); knots within 1e-12 of it
+ *              count as uniform (mfa_model_info.cardinal).
  *   ctrl       HOST array of nctrl[0]*nctrl[1]*nctrl[2] values of type `dtype`,
  *              [n_z][n_y][n_x], x fastest.  Copied; the caller keeps ownership.
  *   dtype      type of ctrl.  Storage is FP32 for F64/F32 input, FP16 for F16, BF16 for
@@ -91,6 +92,9 @@ typedef struct {
     float vmin, vmax;          /* min / max of the stored control points */
     size_t device_bytes;       /* device memory the model holds */
     int device;                /* CUDA ordinal the model lives on */
+    int cardinal;              /* 1: uniform knots and one degree on all three axes, so
+                                  decode and render take the cardinal path (interior
+                                  spans share one basis; render variant 6) */
 } mfa_model_info;
 
 /* Fills *info.  MFA_ERR_ARG on NULL arguments. */
@@ -143,15 +147,19 @@ typedef struct {
     unsigned long long* samples_out;  /* DEVICE counter or NULL: the number of samples
                                          evaluated (after box clipping and early
                                          termination) is ADDED to it */
-    int variant;                      /* kernel variant: 0 = library default (4);
+    int variant;                      /* kernel variant: 0 = library default (6 for a
+                                         cardinal model, see mfa_model_info, else 4);
                                          1 = span records cached in registers along the
                                          ray, packed FP32x2 arithmetic; 2 = records cached,
                                          scalar FP32; 3 = nothing cached, scalar FP32;
                                          4 = as 2, software-pipelined over samples;
                                          5 = control-point bricks staged per warp in shared
                                          memory as FP32 (degree <= 3 on every axis; otherwise
-                                         4).  Variants differ only in FP32 rounding order.
-                                         MFA_ERR_ARG outside 0..5. */
+                                         4); 6 = uniform knots: interior spans evaluate
+                                         the one cardinal basis without span records
+                                         (cardinal models only; otherwise 4).  Variants
+                                         differ only in FP32 rounding order.
+                                         MFA_ERR_ARG outside 0..6. */
     int tile_shape;                   /* ray tile: 0 = 16x8 pixels per CTA with 8x4 per warp
                                          (default), 1 = 32x4 / 8x4, 2 = 8x16 / 4x8,
                                          3 = 16x8 / 16x2.  MFA_ERR_ARG outside 0..3. */

@@ -78,7 +78,7 @@ class _ServerStats(ctypes.Structure):
 
 class _Info(ctypes.Structure):
     _fields_ = [("degree", c_int * 3), ("nctrl", c_int * 3), ("storage", c_int), ("vmin", c_float),
-                ("vmax", c_float), ("device_bytes", c_size_t), ("device", c_int)]
+                ("vmax", c_float), ("device_bytes", c_size_t), ("device", c_int), ("cardinal", c_int)]
 
 
 _lib = None
@@ -219,7 +219,7 @@ class Model:
         i = _Info()
         _check(lib().mfa_model_get_info(self._h, ctypes.byref(i)))
         return dict(degree=tuple(i.degree), nctrl=tuple(i.nctrl), storage=i.storage, vmin=i.vmin, vmax=i.vmax,
-                    device_bytes=i.device_bytes, device=i.device)
+                    device_bytes=i.device_bytes, device=i.device, cardinal=bool(i.cardinal))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -204,7 +204,9 @@ mfa_model* mfa_model_create_ex(const int degree[3], const int nctrl[3], const do
     if (nxp * nyp * nzp >= (1LL << 31))
         return fail(MFA_ERR_UNSUPPORTED, "model too large: (nx+4)(ny+4)(nz+4) must stay below 2^31"), nullptr;
 
-    // knot vectors (host, FP64): caller's or clamped uniform
+    // knot vectors (host, FP64): caller's or clamped uniform.  Caller's knots within 1e-12
+    // of the clamped uniform ones count as uniform: the basis they give differs from the
+    // cardinal one far below FP32 resolution.
     std::vector<double> U[3];
     bool uniform = true;
     for (int a = 0; a < 3; ++a) {
@@ -213,7 +215,8 @@ mfa_model* mfa_model_create_ex(const int degree[3], const int nctrl[3], const do
         for (int i = 0; i < m; ++i)
             U[a][i] = i <= p ? 0.0 : (i >= n ? 1.0 : static_cast<double>(i - p) / static_cast<double>(n - p));
         if (knots && knots[a]) {
-            if (std::memcmp(U[a].data(), knots[a], sizeof(double) * m) != 0) uniform = false;
+            for (int i = 0; i < m; ++i)
+                if (!(std::fabs(knots[a][i] - U[a][i]) <= 1e-12)) uniform = false;
             std::memcpy(U[a].data(), knots[a], sizeof(double) * m);
             if (!check_knots(U[a].data(), n, p, a)) return nullptr;
         }
@@ -318,6 +321,7 @@ mfa_model* mfa_model_create_ex(const int degree[3], const int nctrl[3], const do
     M->dev.nzp = static_cast<int>(nzp);
     M->dev.q = Q;
     M->dev.storage = storage;
+    M->dev.cardinal = uniform && degree[0] == Q - 1 && degree[1] == Q - 1 && degree[2] == Q - 1 ? 1 : 0;
     M->bytes = tab + win_bytes;
     return M;
 }
@@ -341,6 +345,7 @@ int mfa_model_get_info(const mfa_model* m, mfa_model_info* info)
     info->vmax = m->vmax;
     info->device_bytes = m->bytes;
     info->device = m->device;
+    info->cardinal = m->dev.cardinal;
     return MFA_OK;
 }
 
@@ -371,7 +376,7 @@ int mfa_render_ex(const mfa_model* m, const mfa_camera* cam, const mfa_transfer_
 {
     int variant = opts ? opts->variant : 0;
     int shape = opts ? opts->tile_shape : 0;
-    if (variant < 0 || variant > 5) return fail(MFA_ERR_ARG, "render variant %d outside 0..5", variant);
+    if (variant < 0 || variant > 6) return fail(MFA_ERR_ARG, "render variant %d outside 0..6", variant);
     if (shape < 0 || shape >= kTileShapes) return fail(MFA_ERR_ARG, "tile_shape %d outside 0..%d", shape, kTileShapes - 1);
     if (opts && opts->use_tuned && m) tuned_lookup(m, width, height, n_samples, &variant, &shape);
     RenderParams P;

@@ -21,8 +21,6 @@ using namespace mfa;
 
 namespace {
 
-int group_of(int storage, int q) { return (storage - 1) * 4 + (q - 2); }
-
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct GraphEntry {
@@ -75,7 +73,7 @@ cudaError_t build_graph(mfa_batch* b, mfa_batch::Slot& s, int mask, GraphEntry* 
                                  cudaMemcpyHostToDevice);
     for (int g = 0; g < kBatchGroups && e == cudaSuccess; ++g) {
         if (!(mask & (1 << g))) continue;
-        const BatchKernel k = render_batch_kernel(g % 4 + 2, g / 4 + 1);
+        const BatchKernel k = render_batch_kernel(batch_group_q(g), batch_group_storage(g), batch_group_cardinal(g));
         void* table = s.d_table;
         int group = g, shape = b->shape;
         void* args[] = { &table, &group, &shape };
@@ -187,7 +185,7 @@ int mfa_batch_render(mfa_batch* b, const mfa_render_request* reqs, int n)
             fail(rc, "request %d: %s", r, mfa_last_error());
             return rc;
         }
-        const int g = group_of(q.model->storage, q.model->dev.q);
+        const int g = batch_group(q.model->dev.q, q.model->storage, q.model->dev.cardinal);
         it.m = q.model->dev;
         it.tiles_x = (q.width + tw - 1) / tw;
         const long long nt = static_cast<long long>(it.tiles_x) * ((q.height + th - 1) / th);

@@ -99,14 +99,14 @@ __device__ __forceinline__ void load_record(const AxisDev& A, int s, float (&rec
 }
 
 // The Q basis functions N_{s-p+r,p} on the record's span (zero for r > p) and their
-// derivatives with respect to the local coordinate t = (u - U_s)/h, by joint Horner
+// derivatives with respect to the local coordinate t = (u - U_s)/h (record_basis_t takes t,
+// record_basis takes u), by joint Horner
 // evaluation of the power-basis coefficients (value b and derivative d together:
 // d <- d t + b, b <- b t + c_k).  d/du = (1/h) d/dt = rec[1] d/dt.
 template <int Q>
-__device__ __forceinline__ void record_basis(const float (&rec)[rec_stride(Q)], float u, float (&N)[Q], float (&D)[Q])
+__device__ __forceinline__ void record_basis_t(const float (&rec)[rec_stride(Q)], float t, float (&N)[Q], float (&D)[Q])
 {
     constexpr int QP = qpair(Q);
-    const float t = (u - rec[0]) * rec[1];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         float b = rec[kRecHead + (Q - 1) * QP + i], d = 0.0f;
@@ -118,6 +118,12 @@ __device__ __forceinline__ void record_basis(const float (&rec)[rec_stride(Q)], 
         N[i] = b;
         D[i] = d;
     }
+}
+
+template <int Q>
+__device__ __forceinline__ void record_basis(const float (&rec)[rec_stride(Q)], float u, float (&N)[Q], float (&D)[Q])
+{
+    record_basis_t<Q>(rec, (u - rec[0]) * rec[1], N, D);
 }
 
 // Packed form: functions (2m, 2m+1) advance together; N2[m] = {N_2m, N_2m+1}, D2 likewise.
@@ -152,6 +158,67 @@ __device__ __forceinline__ void span_basis(const AxisDev& A, int s, float u, flo
     load_record<Q>(A, s, rec);
     inv_h = rec[1];
     record_basis<Q>(rec, u, N, D);
+}
+
+// ----------------------------------------------------------------------------------------
+// uniform knots: the cardinal basis
+// ----------------------------------------------------------------------------------------
+//
+// With uniform knot spacing h, the Cox-de Boor recursion (Sec. III-B) has integer knot
+// differences in units of h.  On one span, with local coordinate t in [0,1), the degree-k
+// functions r = 0..k that are non-zero there satisfy
+//   N^k_r = ((t + k - r) N^{k-1}_{r-1} + (r + 1 - t) N^{k-1}_r) / k,   N^0_0 = 1,
+// (out-of-range terms zero) and dN^p_r/dt = N^{p-1}_{r-1} - N^{p-1}_r.  cardinal_basis
+// returns the scaled values M = p! N^p and G = (p-1)! dN^p/dt, which drops every division
+// from the triangle; the contraction's results are scaled back once per sample by
+// kValScale and kGradScale.  This holds on every span whose 2p surrounding knots are all
+// uniform, i.e. all spans but the p-1 at each end of a clamped knot vector.
+__host__ __device__ constexpr float factorial(int k) { return k <= 1 ? 1.0f : k * factorial(k - 1); }
+template <int Q>
+struct Cardinal {
+    static constexpr int p = Q - 1;
+    static constexpr float kBasisScale = factorial(p);        // M = kBasisScale N
+    static constexpr float kDerivScale = factorial(p - 1);    // G = kDerivScale dN/dt
+    static constexpr float kValScale = 1.0f / (factorial(p) * factorial(p) * factorial(p));
+    static constexpr float kGradScale = 1.0f / (factorial(p - 1) * factorial(p) * factorial(p));
+};
+
+template <int Q>
+__device__ __forceinline__ void cardinal_basis(float t, float (&M)[Q], float (&G)[Q])
+{
+    const float s = 1.0f - t;
+    if constexpr (Q == 4) {
+        // p = 3 written out: M = {s^3, 3t^3 - 6t^2 + 4, 3s^3 - 6s^2 + 4, t^3},
+        // G = differences of the quadratic level {s^2, 1 + 2ts, t^2}
+        const float t2 = t * t, s2 = s * s;
+        M[0] = s2 * s;
+        M[1] = fmaf(t2, fmaf(3.0f, t, -6.0f), 4.0f);
+        M[2] = fmaf(s2, fmaf(3.0f, s, -6.0f), 4.0f);
+        M[3] = t2 * t;
+        G[0] = -s2;
+        G[1] = t * fmaf(3.0f, t, -4.0f);
+        G[2] = s * fmaf(3.0f, t, 1.0f);
+        G[3] = t2;
+    } else {
+        float L[Q];   // level k of the triangle, scaled by k!
+        L[0] = 1.0f;
+#pragma unroll
+        for (int k = 1; k < Q; ++k) {
+            if (k == Q - 1) {
+                G[0] = -L[0];
+#pragma unroll
+                for (int r = 1; r < k; ++r) G[r] = L[r - 1] - L[r];
+                G[k] = L[k - 1];
+            }
+            L[k] = t * L[k - 1];
+#pragma unroll
+            for (int r = k - 1; r >= 1; --r)
+                L[r] = fmaf(t + static_cast<float>(k - r), L[r - 1], (static_cast<float>(r + 1) - t) * L[r]);
+            L[0] = s * L[0];
+        }
+#pragma unroll
+        for (int r = 0; r < Q; ++r) M[r] = L[r];
+    }
 }
 
 // ----------------------------------------------------------------------------------------
@@ -222,18 +289,18 @@ template <int Q> struct RowLoader<Q, 3> : Row16<Q, true> {};     // MFA_BF16
 // contraction
 // ----------------------------------------------------------------------------------------
 
-// Sum-factorised contraction over the Q^3 support starting at (i0, j0, k0):
+// Sum-factorised contraction over the Q^3 support whose first row is window entry `base`
+// (= (k0 nyp + j0) nxp + i0 for the support origin (i0, j0, k0)):
 //   x-pass  A_jk = sum_i Nx_i P_ijk,  B_jk = sum_i Dx_i P_ijk          (2 Q^3 FMA)
 //   y-pass  C_k = sum_j Ny_j A_jk, D_k = sum_j Dy_j A_jk, E_k = sum_j Ny_j B_jk   (3 Q^2)
 //   z-pass  f = sum_k Nz_k C_k, f_z = sum Dz_k C_k, f_y = sum Nz_k D_k, f_x = sum Nz_k E_k
 // Returns {f, df/dtx, df/dty, df/dtz} (derivatives in the local span coordinates).
 template <int Q, int STORAGE>
-__device__ __forceinline__ float4 contract(const ModelDev& M, int i0, int j0, int k0, const float (&Nx)[Q],
-                                           const float (&Dx)[Q], const float (&Ny)[Q], const float (&Dy)[Q],
-                                           const float (&Nz)[Q], const float (&Dz)[Q])
+__device__ __forceinline__ float4 contract_at(const ModelDev& M, int base, const float (&Nx)[Q], const float (&Dx)[Q],
+                                              const float (&Ny)[Q], const float (&Dy)[Q], const float (&Nz)[Q],
+                                              const float (&Dz)[Q])
 {
     const int plane = M.nxp * M.nyp;
-    const int base = (k0 * M.nyp + j0) * M.nxp + i0;
     float f = 0.0f, fx = 0.0f, fy = 0.0f, fz = 0.0f;
 #pragma unroll
     for (int c = 0; c < Q; ++c) {
@@ -258,6 +325,15 @@ __device__ __forceinline__ float4 contract(const ModelDev& M, int i0, int j0, in
         fx = fmaf(Nz[c], E, fx);
     }
     return make_float4(f, fx, fy, fz);
+}
+
+// Same, from the support's origin (i0, j0, k0) in the window array.
+template <int Q, int STORAGE>
+__device__ __forceinline__ float4 contract(const ModelDev& M, int i0, int j0, int k0, const float (&Nx)[Q],
+                                           const float (&Dx)[Q], const float (&Ny)[Q], const float (&Dy)[Q],
+                                           const float (&Nz)[Q], const float (&Dz)[Q])
+{
+    return contract_at<Q, STORAGE>(M, (k0 * M.nyp + j0) * M.nxp + i0, Nx, Dx, Ny, Dy, Nz, Dz);
 }
 
 // Packed form of the same contraction.  x-pass: each row is read as QP/2 column pairs,
@@ -374,6 +450,71 @@ __device__ __forceinline__ float4 query2(const ModelDev& M, float u, float v, fl
     load_record<Q>(M.ax[1], sy, ry);
     load_record<Q>(M.ax[2], sz, rz);
     return query2_rec<Q, STORAGE>(M, rx, ry, rz, u, v, w, sx - M.ax[0].p, sy - M.ax[1].p, sz - M.ax[2].p);
+}
+
+// ----------------------------------------------------------------------------------------
+// queries on the cardinal path (ModelDev::cardinal: uniform knots, degree Q-1 on every axis)
+// ----------------------------------------------------------------------------------------
+//
+// Coordinates are taken in span units x = (n - p) u: the span is j = floor(x), clamped to
+// 0..n-p-1, and its local coordinate is t = x - j (exact in FP32 for x >= 0).  Spans at
+// least p-1 from both ends use cardinal_basis; the p-1 end spans on each side, whose
+// functions see the repeated end knots, evaluate their record at the same t (uniform
+// spacing makes the record's local coordinate equal to x - j) and rescale to M, G.
+struct CardAxis {
+    float jf;    // span index as a float: t = x - jf
+    int j;       // span index, 0..n-p-1
+    bool edge;   // one of the p-1 end spans: evaluate from its record
+};
+
+__device__ __forceinline__ void card_update(const AxisDev& A, CardAxis& C, float x)
+{
+    const int m = A.n - A.p;
+    const int j = min(max(__float2int_rd(x), 0), m - 1);   // positions just outside the box clamp
+    C.j = j;
+    C.jf = static_cast<float>(j);
+    C.edge = j < A.p - 1 || j > m - A.p;
+}
+
+// Scaled basis (M = p! N, G = (p-1)! dN/dt) on the axis's current span.
+template <int Q>
+__device__ __forceinline__ void card_basis(const AxisDev& A, const CardAxis& C, float t, float (&N)[Q], float (&D)[Q])
+{
+    if (C.edge) {
+        float rec[rec_stride(Q)];
+        load_record<Q>(A, C.j + A.p, rec);
+        record_basis_t<Q>(rec, t, N, D);   // uniform spacing: the record's t is x - j too
+#pragma unroll
+        for (int r = 0; r < Q; ++r) {
+            N[r] *= Cardinal<Q>::kBasisScale;
+            D[r] *= Cardinal<Q>::kDerivScale;
+        }
+    } else {
+        cardinal_basis<Q>(t, N, D);
+    }
+}
+
+// Value and parameter-space gradient at a clamped point on the cardinal path.
+template <int Q, int STORAGE>
+__device__ __forceinline__ float4 query_cardinal(const ModelDev& M, float u, float v, float w)
+{
+    const float x = u * static_cast<float>(M.ax[0].n - M.ax[0].p);
+    const float y = v * static_cast<float>(M.ax[1].n - M.ax[1].p);
+    const float z = w * static_cast<float>(M.ax[2].n - M.ax[2].p);
+    CardAxis cx, cy, cz;
+    card_update(M.ax[0], cx, x);
+    card_update(M.ax[1], cy, y);
+    card_update(M.ax[2], cz, z);
+    float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];
+    card_basis<Q>(M.ax[0], cx, x - cx.jf, Nx, Dx);
+    card_basis<Q>(M.ax[1], cy, y - cy.jf, Ny, Dy);
+    card_basis<Q>(M.ax[2], cz, z - cz.jf, Nz, Dz);
+    float4 r = contract_at<Q, STORAGE>(M, (cz.j * M.nyp + cy.j) * M.nxp + cx.j, Nx, Dx, Ny, Dy, Nz, Dz);
+    r.x *= Cardinal<Q>::kValScale;
+    r.y *= static_cast<float>(M.ax[0].n - M.ax[0].p) * Cardinal<Q>::kGradScale;
+    r.z *= static_cast<float>(M.ax[1].n - M.ax[1].p) * Cardinal<Q>::kGradScale;
+    r.w *= static_cast<float>(M.ax[2].n - M.ax[2].p) * Cardinal<Q>::kGradScale;
+    return r;
 }
 
 __device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.0f), 1.0f); }

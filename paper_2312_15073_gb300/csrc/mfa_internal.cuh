@@ -50,6 +50,8 @@ struct ModelDev {
     int nxp, nyp, nzp;  // padded sizes n + kPad
     int q;              // Q = max degree + 1 (kernel template parameter)
     int storage;        // mfa_dtype of the window values
+    int cardinal;       // 1: uniform knots and degree Q-1 on all three axes, so interior
+                        // spans share the cardinal basis (render variant 6 applies)
 };
 
 // Per-image render parameters (camera frame, image size, transfer-function scalars).
@@ -98,8 +100,17 @@ struct BatchHead {
     int total_tiles;
     int items_offset;   // bytes from the start of the table
 };
-constexpr int kBatchGroups = 12;          // (storage F32/F16/BF16) x (Q = 2..5)
-constexpr int kBatchItemsOffset = 256;    // heads occupy the first 256 bytes
+// Groups: (record / cardinal path) x (storage F32/F16/BF16) x (Q = 2..5).
+constexpr int kBatchGroups = 24;
+constexpr int kBatchItemsOffset = 512;    // heads occupy the first 512 bytes
+static_assert(kBatchGroups * sizeof(BatchHead) <= kBatchItemsOffset, "batch heads overflow");
+__host__ __device__ constexpr int batch_group(int q, int storage, int cardinal)
+{
+    return (cardinal * 3 + (storage - 1)) * 4 + (q - 2);
+}
+__host__ __device__ constexpr int batch_group_q(int g) { return g % 4 + 2; }
+__host__ __device__ constexpr int batch_group_storage(int g) { return g / 4 % 3 + 1; }
+__host__ __device__ constexpr int batch_group_cardinal(int g) { return g / 12; }
 
 // launchers (defined in the .cu files), all asynchronous on `stream`
 cudaError_t launch_prep_axis(const double* d_knots, int n, int p, int q, float* kup, float* rec, int* grid,
@@ -112,15 +123,15 @@ cudaError_t launch_decode(const ModelDev& m, const float* pts, long long n, floa
                           cudaStream_t stream);
 cudaError_t launch_spans(const ModelDev& m, const float* pts, long long n, int* spans, cudaStream_t stream);
 cudaError_t launch_render(const ModelDev& m, const RenderParams& rp, int variant, int shape, cudaStream_t stream);
-// The persistent batched render kernel for models of one degree class q and one storage
-// type: arguments (BatchHead* table, int group, int tile_shape).  Launch with `threads`
-// threads per CTA and about SMs x blocks_per_sm CTAs.
+// The persistent batched render kernel for models of one degree class q, one storage type
+// and one path (cardinal or record): arguments (BatchHead* table, int group, int
+// tile_shape).  Launch with `threads` threads per CTA and about SMs x blocks_per_sm CTAs.
 struct BatchKernel {
     const void* fn;
     int blocks_per_sm;
     int threads;
 };
-BatchKernel render_batch_kernel(int q, int storage);
+BatchKernel render_batch_kernel(int q, int storage, int cardinal);
 // Pixel size of ray-tile shape `shape` (0..kTileShapes-1); -1 if out of range.
 int render_tile_dims(int shape, int* tw, int* th);
 constexpr int kTileShapes = 4;

@@ -49,8 +49,6 @@ cudaError_t static_table(int dev, void** out)
     return cudaSuccess;
 }
 
-int group_of(int storage, int q) { return (storage - 1) * 4 + (q - 2); }
-
 }  // namespace
 
 extern "C" int mfa_render_batch_static(const mfa_render_request* reqs, int n)
@@ -79,7 +77,7 @@ extern "C" int mfa_render_batch_static(const mfa_render_request* reqs, int n)
         }
         int tw, th;
         render_tile_dims(0, &tw, &th);
-        const int g = group_of(q.model->storage, q.model->dev.q);
+        const int g = batch_group(q.model->dev.q, q.model->storage, q.model->dev.cardinal);
         ++count[g];
         tiles[g] += static_cast<long long>((q.width + tw - 1) / tw) * ((q.height + th - 1) / th);
         if (tiles[g] > (1LL << 30)) return fail(MFA_ERR_ARG, "batch too large: more than 2^30 ray tiles");
@@ -116,7 +114,7 @@ extern "C" int mfa_render_batch_static(const mfa_render_request* reqs, int n)
         setup_render(q.model, &q.camera, q.tf, q.width, q.height, q.n_samples, q.rgba_out, q.samples_out, it.s, rows);
         int tw, th;
         render_tile_dims(0, &tw, &th);
-        const int g = group_of(q.model->storage, q.model->dev.q);
+        const int g = batch_group(q.model->dev.q, q.model->storage, q.model->dev.cardinal);
         it.m = q.model->dev;
         it.tiles_x = (q.width + tw - 1) / tw;
         it.tile_begin = static_cast<int>(next_tile[g]);
@@ -134,7 +132,7 @@ extern "C" int mfa_render_batch_static(const mfa_render_request* reqs, int n)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     for (int g = 0; g < kBatchGroups; ++g) {
         if (!count[g]) continue;
-        const BatchKernel k = render_batch_kernel(g % 4 + 2, g / 4 + 1);
+        const BatchKernel k = render_batch_kernel(batch_group_q(g), batch_group_storage(g), batch_group_cardinal(g));
         BatchHead* tp = static_cast<BatchHead*>(table);
         int group = g, shape = 0;
         void* args[] = { &tp, &group, &shape };

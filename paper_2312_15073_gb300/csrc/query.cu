@@ -2,16 +2,19 @@
 // Fig. 8 in Sec. V-D.3) and the knot-span search on its own.
 //
 // One thread per point, grid-stride.  Per point: clamp to [0,1], locate the three spans,
-// evaluate the span-local basis and derivatives, contract the (p+1)^3 support.  Points
-// are read as three scalar FP32 loads (12 B, coalesced across the warp), values and
-// gradients written as scalar stores; for random points the control-point gathers hit
-// L2 (the window array of a 128^3 FP32 model is 32 MiB).
+// evaluate the span-local basis and derivatives, contract the (p+1)^3 support.  Models with
+// uniform knots and one degree take the cardinal path (span = floor((n-p) u), interior
+// spans without records).  Points are read as three scalar FP32 loads (12 B, coalesced
+// across the warp), values and gradients written as scalar stores; for random points the
+// control-point gathers hit L2 (the window array of a 128^3 FP32 model is 32 MiB).
 #include "bspline.cuh"
 
 namespace mfa {
 namespace {
 
-template <int Q, int STORAGE>
+// CARD: the model is on the cardinal path (uniform knots, degree Q-1 on every axis), so the
+// span is floor((n - p) u) and interior spans need no record.
+template <int Q, int STORAGE, bool CARD>
 __global__ void __launch_bounds__(256) k_decode(ModelDev M, const float* __restrict__ pts, long long n,
                                                 float* __restrict__ val, float* __restrict__ grad)
 {
@@ -20,10 +23,15 @@ __global__ void __launch_bounds__(256) k_decode(ModelDev M, const float* __restr
         const float u = clamp01(__ldg(pts + 3 * i + 0));
         const float v = clamp01(__ldg(pts + 3 * i + 1));
         const float w = clamp01(__ldg(pts + 3 * i + 2));
-        const int sx = locate_span(M.ax[0], u);
-        const int sy = locate_span(M.ax[1], v);
-        const int sz = locate_span(M.ax[2], w);
-        const float4 r = query2<Q, STORAGE>(M, u, v, w, sx, sy, sz);
+        float4 r;
+        if constexpr (CARD) {
+            r = query_cardinal<Q, STORAGE>(M, u, v, w);
+        } else {
+            const int sx = locate_span(M.ax[0], u);
+            const int sy = locate_span(M.ax[1], v);
+            const int sz = locate_span(M.ax[2], w);
+            r = query2<Q, STORAGE>(M, u, v, w, sx, sy, sz);
+        }
         val[i] = r.x;
         if (grad) {
             grad[3 * i + 0] = r.y;
@@ -53,17 +61,23 @@ int grid_for(long long n, int threads)
     return static_cast<int>(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
-template <int Q>
-cudaError_t decode_q(const ModelDev& m, const float* pts, long long n, float* val, float* grad, cudaStream_t st)
+template <int Q, bool CARD>
+cudaError_t decode_qc(const ModelDev& m, const float* pts, long long n, float* val, float* grad, cudaStream_t st)
 {
     const int blocks = grid_for(n, 256);
     switch (m.storage) {
-    case 1: k_decode<Q, 1><<<blocks, 256, 0, st>>>(m, pts, n, val, grad); break;
-    case 2: k_decode<Q, 2><<<blocks, 256, 0, st>>>(m, pts, n, val, grad); break;
-    case 3: k_decode<Q, 3><<<blocks, 256, 0, st>>>(m, pts, n, val, grad); break;
+    case 1: k_decode<Q, 1, CARD><<<blocks, 256, 0, st>>>(m, pts, n, val, grad); break;
+    case 2: k_decode<Q, 2, CARD><<<blocks, 256, 0, st>>>(m, pts, n, val, grad); break;
+    case 3: k_decode<Q, 3, CARD><<<blocks, 256, 0, st>>>(m, pts, n, val, grad); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+template <int Q>
+cudaError_t decode_q(const ModelDev& m, const float* pts, long long n, float* val, float* grad, cudaStream_t st)
+{
+    return m.cardinal ? decode_qc<Q, true>(m, pts, n, val, grad, st) : decode_qc<Q, false>(m, pts, n, val, grad, st);
 }
 
 }  // namespace

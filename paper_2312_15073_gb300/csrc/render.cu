@@ -19,11 +19,16 @@
 // consecutive samples, so each axis's span bounds and record stay in registers and only
 // the lanes whose span changed reload it.  With the loads thinned out the kernel is
 // bound by FP32 issue (about 285 FFMA of about 450 instructions per sample).
-//   variant 4 (default): records cached, scalar arithmetic, software-pipelined (the query
+//   variant 6:           uniform knots and one degree (the cardinal path): interior spans
+//                        share one basis, computed from t without a record; the state per
+//                        axis is the span index; software-pipelined like 4
+//   variant 4:           records cached, scalar arithmetic, software-pipelined (the query
 //                        of sample k+1 interleaves with the colour/compositing of sample k)
 //   variant 2:           records cached, scalar arithmetic
 //   variant 1:           records cached, packed FP32x2 arithmetic
 //   variant 3:           nothing cached, scalar arithmetic
+//   variant 5:           per-warp control-point bricks in shared memory (below)
+// The default (variant 0) is 6 where the cardinal path applies, else 4.
 // Variant 4 measures 2 % faster than 2 (6.13 vs 6.28 ms per 1024^2 frame).
 // Packed FP32x2 halves the FMA instructions issued but each one holds the FMA pipe for
 // two cycles, and pairing the y-pass adds lane work, so on GB300 it measures 2-6 % slower
@@ -40,6 +45,8 @@ constexpr int kThreads = 128;
 // the 128^3 degree-3 frame: cap 128 -> 6.33 ms, cap 168 (3 CTAs) -> 7.01 ms, cap 96 (5
 // CTAs, spills) -> 10.4 ms.
 constexpr int kMinBlocks = 4;
+// The cardinal path (variant 6) holds no span records, so more CTAs fit per SM.
+constexpr int kMinBlocksCardinal = 5;
 
 // Ray-tile shapes (CTA tile, warp tile).  Shape 0 is the default; the autotuner picks one
 // per workload.
@@ -60,6 +67,53 @@ __device__ __forceinline__ void tile_pixel(const TileShape& T, int tx, int ty, i
     const int wpr = T.tw / T.ww;   // warps per tile row
     col = tx * T.tw + (warp % wpr) * T.ww + lane % T.ww;
     row = ty * T.th + (warp / wpr) * T.wh + lane / T.ww;
+}
+
+// Ray through the centre of pixel (col, row) (row 0 at the top): origin o, unit direction
+// d, and its parameter interval [t0, t1] inside [0,1]^3 (slab clip, t >= 0).  False when
+// the ray misses the box.
+__device__ __forceinline__ bool ray_box(const RenderScalars& P, int col, int row, float (&o)[3], float (&d)[3],
+                                        float& t0, float& t1)
+{
+    const float sx = fmaf(static_cast<float>(2 * col + 1), P.inv_w, -1.0f);
+    const float sy = fmaf(static_cast<float>(-(2 * row + 1)), P.inv_h, 1.0f);
+    if (P.projection == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            o[a] = fmaf(sy, P.uy[a], fmaf(sx, P.rx[a], P.eye[a]));
+            d[a] = P.fwd[a];
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            o[a] = P.eye[a];
+            d[a] = fmaf(sy, P.uy[a], fmaf(sx, P.rx[a], P.fwd[a]));
+        }
+        const float inv = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        d[0] *= inv;
+        d[1] *= inv;
+        d[2] *= inv;
+    }
+    t0 = 0.0f;
+    t1 = INFINITY;
+    bool hit = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] != 0.0f) {
+            const float inv = 1.0f / d[a];
+            float ta = -o[a] * inv, tb = (1.0f - o[a]) * inv;
+            if (ta > tb) {
+                const float t = ta;
+                ta = tb;
+                tb = t;
+            }
+            t0 = fmaxf(t0, ta);
+            t1 = fminf(t1, tb);
+        } else if (o[a] < 0.0f || o[a] > 1.0f) {
+            hit = false;
+        }
+    }
+    return hit && t0 < t1;
 }
 
 // Per-axis state of a ray: current span and its record (which carries the span's FP32
@@ -92,48 +146,9 @@ template <int Q, int STORAGE, int MODE>
 __device__ __forceinline__ float4 march(const ModelDev& M, const RenderScalars& P, const float4* __restrict__ tf,
                                         int col, int row, unsigned long long& count)
 {
-    // ---- ray through the pixel centre (row 0 at the top)
-    const float sx = fmaf(static_cast<float>(2 * col + 1), P.inv_w, -1.0f);
-    const float sy = fmaf(static_cast<float>(-(2 * row + 1)), P.inv_h, 1.0f);
-    float o[3], d[3];
-    if (P.projection == 0) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            o[a] = fmaf(sy, P.uy[a], fmaf(sx, P.rx[a], P.eye[a]));
-            d[a] = P.fwd[a];
-        }
-    } else {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            o[a] = P.eye[a];
-            d[a] = fmaf(sy, P.uy[a], fmaf(sx, P.rx[a], P.fwd[a]));
-        }
-        const float inv = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        d[0] *= inv;
-        d[1] *= inv;
-        d[2] *= inv;
-    }
-    // ---- slab clip against [0,1]^3, t >= 0
-    float t0 = 0.0f, t1 = INFINITY;
-    bool hit = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (d[a] != 0.0f) {
-            const float inv = 1.0f / d[a];
-            float ta = -o[a] * inv, tb = (1.0f - o[a]) * inv;
-            if (ta > tb) {
-                const float t = ta;
-                ta = tb;
-                tb = t;
-            }
-            t0 = fmaxf(t0, ta);
-            t1 = fminf(t1, tb);
-        } else if (o[a] < 0.0f || o[a] > 1.0f) {
-            hit = false;
-        }
-    }
+    float o[3], d[3], t0, t1;
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);   // premultiplied rgb, alpha
-    if (!hit || !(t0 < t1)) return acc;
+    if (!ray_box(P, col, row, o, d, t0, t1)) return acc;
 
     const int ns = P.n_samples, tf_n = P.tf_n, shading = P.shading;
     const float vmin = P.vmin, inv_range = P.inv_range, ert = P.ert_alpha, gtiny2 = P.gtiny2;
@@ -224,6 +239,25 @@ struct ShadeParams {
     int tf_last, shading;
 };
 
+__device__ __forceinline__ ShadeParams shade_params(const RenderScalars& P, const float (&d)[3])
+{
+    ShadeParams S;
+    S.vmin = P.vmin;
+    S.inv_range = P.inv_range;
+    S.tscale = static_cast<float>(P.tf_n - 1);
+    S.tf_last = max(P.tf_n - 2, 0);
+    S.shading = P.shading;
+    S.ka = P.ka;
+    S.kd = P.kd;
+    S.ks = P.ks;
+    S.shin = P.shininess;
+    S.gtiny2 = P.gtiny2;
+    S.lx = -d[0];
+    S.ly = -d[1];
+    S.lz = -d[2];
+    return S;
+}
+
 __device__ __forceinline__ float4 sample_colour(const float4* __restrict__ tf, const ShadeParams& S, const float4 q)
 {
     const float tt = clamp01((q.x - S.vmin) * S.inv_range);
@@ -263,64 +297,14 @@ __device__ __forceinline__ float4 march_pipelined(const ModelDev& M, const Rende
                                                   const float4* __restrict__ tf, int col, int row,
                                                   unsigned long long& count)
 {
-    const float sx = fmaf(static_cast<float>(2 * col + 1), P.inv_w, -1.0f);
-    const float sy = fmaf(static_cast<float>(-(2 * row + 1)), P.inv_h, 1.0f);
-    float o[3], d[3];
-    if (P.projection == 0) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            o[a] = fmaf(sy, P.uy[a], fmaf(sx, P.rx[a], P.eye[a]));
-            d[a] = P.fwd[a];
-        }
-    } else {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            o[a] = P.eye[a];
-            d[a] = fmaf(sy, P.uy[a], fmaf(sx, P.rx[a], P.fwd[a]));
-        }
-        const float inv = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        d[0] *= inv;
-        d[1] *= inv;
-        d[2] *= inv;
-    }
-    float t0 = 0.0f, t1 = INFINITY;
-    bool hit = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (d[a] != 0.0f) {
-            const float inv = 1.0f / d[a];
-            float ta = -o[a] * inv, tb = (1.0f - o[a]) * inv;
-            if (ta > tb) {
-                const float t = ta;
-                ta = tb;
-                tb = t;
-            }
-            t0 = fmaxf(t0, ta);
-            t1 = fminf(t1, tb);
-        } else if (o[a] < 0.0f || o[a] > 1.0f) {
-            hit = false;
-        }
-    }
+    float o[3], d[3], t0, t1;
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (!hit || !(t0 < t1)) return acc;
+    if (!ray_box(P, col, row, o, d, t0, t1)) return acc;
 
     const int ns = P.n_samples;
     const float ert = P.ert_alpha;
     const float dt = (t1 - t0) / static_cast<float>(ns);
-    ShadeParams S;
-    S.vmin = P.vmin;
-    S.inv_range = P.inv_range;
-    S.tscale = static_cast<float>(P.tf_n - 1);
-    S.tf_last = max(P.tf_n - 2, 0);
-    S.shading = P.shading;
-    S.ka = P.ka;
-    S.kd = P.kd;
-    S.ks = P.ks;
-    S.shin = P.shininess;
-    S.gtiny2 = P.gtiny2;
-    S.lx = -d[0];
-    S.ly = -d[1];
-    S.lz = -d[2];
+    const ShadeParams S = shade_params(P, d);
     AxisCache<Q> cx, cy, cz;
     cx.s = cy.s = cz.s = -1;
 
@@ -346,6 +330,100 @@ __device__ __forceinline__ float4 march_pipelined(const ModelDev& M, const Rende
         q.y *= cx.rec[1];
         q.z *= cy.rec[1];
         q.w *= cz.rec[1];
+        return q;
+    };
+
+    float4 q = query_at(0);
+    for (int k = 0; k < ns; ++k) {
+        const float4 qn = query_at(min(k + 1, ns - 1));
+        const float4 c = sample_colour(tf, S, q);
+        const float wgt = (1.0f - acc.w) * c.w;
+        acc.x = fmaf(wgt, c.x, acc.x);
+        acc.y = fmaf(wgt, c.y, acc.y);
+        acc.z = fmaf(wgt, c.z, acc.z);
+        acc.w += wgt;
+        ++count;
+        if (acc.w >= ert) break;
+        q = qn;
+    }
+    return acc;
+}
+
+// ----------------------------------------------------------------------------------------
+// variant 6: uniform knots (cardinal basis)
+// ----------------------------------------------------------------------------------------
+//
+// For a model with clamped uniform knots and degree Q-1 on all three axes (ModelDev::
+// cardinal), every span but the p-1 at each end of an axis carries the same basis
+// polynomials (cardinal_basis).  The ray is marched in span units x = (n - p) u, so the
+// span is j = floor(x) and its local coordinate t = x - j; the per-axis state is the span
+// index alone (no record in registers), and the support's first window entry is kept
+// until a span changes.  The end spans, whose functions see the repeated end knots, read
+// their record from global memory (L1-resident, a few hundred bytes per axis) for each
+// sample.  Software-pipelined like variant 4.
+template <int Q, int STORAGE>
+__device__ __forceinline__ float4 march_cardinal(const ModelDev& M, const RenderScalars& P,
+                                                 const float4* __restrict__ tf, int col, int row,
+                                                 unsigned long long& count)
+{
+    float o[3], d[3], t0, t1;
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (!ray_box(P, col, row, o, d, t0, t1)) return acc;
+
+    const int ns = P.n_samples;
+    const float ert = P.ert_alpha;
+    const float dt = (t1 - t0) / static_cast<float>(ns);
+    const ShadeParams S = shade_params(P, d);
+    float om[3], dm[3], gs[3];   // ray in span units, gradient scale per axis
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float m = static_cast<float>(M.ax[a].n - M.ax[a].p);
+        om[a] = o[a] * m;
+        dm[a] = d[a] * m;
+        gs[a] = m * Cardinal<Q>::kGradScale;
+    }
+    CardAxis cx{ -INFINITY, 0, false }, cy{ -INFINITY, 0, false }, cz{ -INFINITY, 0, false };
+    int base = 0;
+
+    auto query_at = [&](int k) -> float4 {
+        const float t = fmaf(static_cast<float>(k) + 0.5f, dt, t0);
+        const float x = fmaf(t, dm[0], om[0]);
+        const float y = fmaf(t, dm[1], om[1]);
+        const float z = fmaf(t, dm[2], om[2]);
+        float tx = x - cx.jf, ty = y - cy.jf, tz = z - cz.jf;
+        const bool ox = !(tx >= 0.0f && tx < 1.0f);
+        const bool oy = !(ty >= 0.0f && ty < 1.0f);
+        const bool oz = !(tz >= 0.0f && tz < 1.0f);
+        if (ox | oy | oz) {
+            if (ox) {
+                card_update(M.ax[0], cx, x);
+                tx = x - cx.jf;
+            }
+            if (oy) {
+                card_update(M.ax[1], cy, y);
+                ty = y - cy.jf;
+            }
+            if (oz) {
+                card_update(M.ax[2], cz, z);
+                tz = z - cz.jf;
+            }
+            base = (cz.j * M.nyp + cy.j) * M.nxp + cx.j;
+        }
+        float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];
+        if (cx.edge | cy.edge | cz.edge) {
+            card_basis<Q>(M.ax[0], cx, tx, Nx, Dx);
+            card_basis<Q>(M.ax[1], cy, ty, Ny, Dy);
+            card_basis<Q>(M.ax[2], cz, tz, Nz, Dz);
+        } else {
+            cardinal_basis<Q>(tx, Nx, Dx);
+            cardinal_basis<Q>(ty, Ny, Dy);
+            cardinal_basis<Q>(tz, Nz, Dz);
+        }
+        float4 q = contract_at<Q, STORAGE>(M, base, Nx, Dx, Ny, Dy, Nz, Dz);
+        q.x *= Cardinal<Q>::kValScale;
+        q.y *= gs[0];
+        q.z *= gs[1];
+        q.w *= gs[2];
         return q;
     };
 
@@ -437,64 +515,14 @@ __device__ __forceinline__ float4 march_bricked(const ModelDev& M, const RenderS
     static_assert(Q <= 4, "bricks hold 4-wide windows");
     const unsigned kFull = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
-    const float sx = fmaf(static_cast<float>(2 * col + 1), P.inv_w, -1.0f);
-    const float sy = fmaf(static_cast<float>(-(2 * row + 1)), P.inv_h, 1.0f);
-    float o[3], d[3];
-    if (P.projection == 0) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            o[a] = fmaf(sy, P.uy[a], fmaf(sx, P.rx[a], P.eye[a]));
-            d[a] = P.fwd[a];
-        }
-    } else {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            o[a] = P.eye[a];
-            d[a] = fmaf(sy, P.uy[a], fmaf(sx, P.rx[a], P.fwd[a]));
-        }
-        const float inv = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        d[0] *= inv;
-        d[1] *= inv;
-        d[2] *= inv;
-    }
-    float t0 = 0.0f, t1 = INFINITY;
-    bool hit = valid;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (d[a] != 0.0f) {
-            const float inv = 1.0f / d[a];
-            float ta = -o[a] * inv, tb = (1.0f - o[a]) * inv;
-            if (ta > tb) {
-                const float t = ta;
-                ta = tb;
-                tb = t;
-            }
-            t0 = fmaxf(t0, ta);
-            t1 = fminf(t1, tb);
-        } else if (o[a] < 0.0f || o[a] > 1.0f) {
-            hit = false;
-        }
-    }
+    float o[3], d[3], t0, t1;
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    bool live = hit && t0 < t1;
+    bool live = ray_box(P, col, row, o, d, t0, t1) && valid;
 
     const int ns = P.n_samples;
     const float ert = P.ert_alpha;
     const float dt = live ? (t1 - t0) / static_cast<float>(ns) : 0.0f;
-    ShadeParams S;
-    S.vmin = P.vmin;
-    S.inv_range = P.inv_range;
-    S.tscale = static_cast<float>(P.tf_n - 1);
-    S.tf_last = max(P.tf_n - 2, 0);
-    S.shading = P.shading;
-    S.ka = P.ka;
-    S.kd = P.kd;
-    S.ks = P.ks;
-    S.shin = P.shininess;
-    S.gtiny2 = P.gtiny2;
-    S.lx = -d[0];
-    S.ly = -d[1];
-    S.lz = -d[2];
+    const ShadeParams S = shade_params(P, d);
     AxisCache<Q> cx, cy, cz;
     cx.s = cy.s = cz.s = -1;
     const int nxp = M.nxp, nyp = M.nyp;
@@ -614,8 +642,8 @@ __device__ __forceinline__ void add_count(unsigned long long* dst, unsigned long
 // ----------------------------------------------------------------------------------------
 
 template <int Q, int STORAGE, int MODE>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_render(ModelDev M, const __grid_constant__ RenderParams P,
-                                                                 int shape)
+__global__ void __launch_bounds__(kThreads, MODE == 6 ? kMinBlocksCardinal : kMinBlocks)
+    k_render(ModelDev M, const __grid_constant__ RenderParams P, int shape)
 {
     __shared__ float4 tf[kTfMax + 1];
     for (int i = threadIdx.x; i < P.s.tf_n; i += kThreads) tf[i] = P.tf[i];
@@ -635,6 +663,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_render(ModelDev M, con
         float4 acc;
         if constexpr (MODE == 4)
             acc = march_pipelined<Q, STORAGE>(M, P.s, tf, col, row, count);
+        else if constexpr (MODE == 6)
+            acc = march_cardinal<Q, STORAGE>(M, P.s, tf, col, row, count);
         else
             acc = march<Q, STORAGE, MODE>(M, P.s, tf, col, row, count);
         P.s.out[static_cast<long long>(row) * P.s.width + col] = acc;
@@ -650,7 +680,13 @@ cudaError_t render_qs(const ModelDev& m, const RenderParams& rp, int variant, in
     switch (variant) {
     case 2: k_render<Q, STORAGE, 2><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
     case 1: k_render<Q, STORAGE, 1><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
-    case 0:
+    case 0:   // default: the cardinal path where it applies, else variant 4
+    case 6:
+        if (m.cardinal)
+            k_render<Q, STORAGE, 6><<<grid, kThreads, 0, st>>>(m, rp, shape);
+        else
+            k_render<Q, STORAGE, 4><<<grid, kThreads, 0, st>>>(m, rp, shape);
+        break;
     case 4: k_render<Q, STORAGE, 4><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
     case 5:
         if constexpr (Q <= 4) {
@@ -683,10 +719,10 @@ cudaError_t render_q(const ModelDev& m, const RenderParams& rp, int variant, int
 // request (tiles of one request are contiguous, so the previous request is checked
 // first), stage the request and its table in shared memory when it changes, render,
 // repeat until the counter passes the group's last tile.  One kernel per group keeps each
-// degree's register allocation free of the others'.
-template <int Q, int STORAGE>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_batch(BatchHead* __restrict__ table, int group,
-                                                                       int shape)
+// degree's (and each path's) register allocation free of the others'.
+template <int Q, int STORAGE, bool CARD>
+__global__ void __launch_bounds__(kThreads, CARD ? kMinBlocksCardinal : kMinBlocks)
+    k_render_batch(BatchHead* __restrict__ table, int group, int shape)
 {
     __shared__ BatchItem item;
     __shared__ float4 tf[kTfMax + 1];
@@ -733,7 +769,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_batch(BatchHead
         tile_pixel(T, tx, ty, threadIdx.x, col, row);
         unsigned long long count = 0;
         if (col < item.s.width && row < item.s.height) {
-            const float4 acc = march_pipelined<Q, STORAGE>(item.m, item.s, tf, col, row, count);
+            float4 acc;
+            if constexpr (CARD)
+                acc = march_cardinal<Q, STORAGE>(item.m, item.s, tf, col, row, count);
+            else
+                acc = march_pipelined<Q, STORAGE>(item.m, item.s, tf, col, row, count);
             item.s.out[static_cast<long long>(row) * item.s.width + col] = acc;
         }
         if (item.s.samples_out) add_count(item.s.samples_out, count);
@@ -741,22 +781,30 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_batch(BatchHead
     }
 }
 
-template <int Q, int STORAGE>
+template <int Q, int STORAGE, bool CARD>
 BatchKernel batch_kernel_qs()
 {
     BatchKernel k;
-    k.fn = reinterpret_cast<const void*>(&k_render_batch<Q, STORAGE>);
+    k.fn = reinterpret_cast<const void*>(&k_render_batch<Q, STORAGE, CARD>);
     int blocks = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_render_batch<Q, STORAGE>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_render_batch<Q, STORAGE, CARD>, kThreads, 0);
     k.blocks_per_sm = blocks > 0 ? blocks : 1;
     k.threads = kThreads;
     return k;
 }
 
-template <int Q>
-BatchKernel batch_kernel_q(int storage)
+template <int Q, bool CARD>
+BatchKernel batch_kernel_qc(int storage)
 {
-    return storage == 1 ? batch_kernel_qs<Q, 1>() : storage == 2 ? batch_kernel_qs<Q, 2>() : batch_kernel_qs<Q, 3>();
+    return storage == 1   ? batch_kernel_qs<Q, 1, CARD>()
+           : storage == 2 ? batch_kernel_qs<Q, 2, CARD>()
+                          : batch_kernel_qs<Q, 3, CARD>();
+}
+
+template <int Q>
+BatchKernel batch_kernel_q(int storage, int cardinal)
+{
+    return cardinal ? batch_kernel_qc<Q, true>(storage) : batch_kernel_qc<Q, false>(storage);
 }
 
 }  // namespace
@@ -780,13 +828,13 @@ cudaError_t launch_render(const ModelDev& m, const RenderParams& rp, int variant
     }
 }
 
-BatchKernel render_batch_kernel(int q, int storage)
+BatchKernel render_batch_kernel(int q, int storage, int cardinal)
 {
     switch (q) {
-    case 2: return batch_kernel_q<2>(storage);
-    case 3: return batch_kernel_q<3>(storage);
-    case 4: return batch_kernel_q<4>(storage);
-    default: return batch_kernel_q<5>(storage);
+    case 2: return batch_kernel_q<2>(storage, cardinal);
+    case 3: return batch_kernel_q<3>(storage, cardinal);
+    case 4: return batch_kernel_q<4>(storage, cardinal);
+    default: return batch_kernel_q<5>(storage, cardinal);
     }
 }
 

@@ -79,7 +79,13 @@ CASES = [((3, 3, 3), (13, 9, 11), (True, True, True)),
          ((2, 2, 2), (10, 12, 8), (False, True, False)),
          ((4, 4, 4), (9, 11, 10), (True, False, False)),
          ((2, 3, 4), (8, 9, 12), (False, True, True)),
-         ((4, 1, 3), (6, 5, 7), (True, True, False))]
+         ((4, 1, 3), (6, 5, 7), (True, True, False)),
+         # uniform knots, one degree: the cardinal path, including models with no interior
+         # span (n - p < 2p - 1) and a single span (n = p + 1)
+         ((1, 1, 1), (5, 4, 6), (True, True, True)),
+         ((2, 2, 2), (3, 7, 12), (True, True, True)),
+         ((3, 3, 3), (4, 6, 40), (True, True, True)),
+         ((4, 4, 4), (5, 9, 16), (True, True, True))]
 
 
 @pytest.mark.parametrize("degree,nctrl,uniform", CASES)
@@ -206,6 +212,8 @@ def _camera(kind, rng):
         return synth.camera_persp(np.array(c) + 2.2 * d, c, synth.view_up_for(d), 35.0)
     if kind == "ortho_oblique":
         return synth.camera_ortho((2.0, 1.4, 2.3), c, (0, 1, 0), 1.6)
+    if kind == "ortho_axis":     # rays along -z: two direction components are zero
+        return synth.camera_ortho((0.5, 0.5, 2.5), c, (0, 1, 0), 1.2)
     return synth.camera_persp((0.45, 0.55, 0.6), (0.7, 0.2, 0.1), (0, 1, 0), 70.0)   # eye inside the box
 
 
@@ -284,7 +292,7 @@ def test_render_edge_cases(mfa, orc):
     assert float(out.min()) == 7.0
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("degree", [(3, 3, 3), (2, 3, 4), (4, 4, 4)])
 def test_render_variants_match_oracle(mfa, orc, variant, degree):
     """Every kernel variant (support cached / records cached / nothing cached) against the
@@ -303,3 +311,62 @@ def test_render_variants_match_oracle(mfa, orc, variant, degree):
     assert np.all(rmse <= IMAGE_RMSE_TOL), rmse
     assert abs(int(cnt.item()) - rc) <= max(2, 1e-3 * rc)
     assert rimg[..., 3].max() > 0.05
+
+
+CARDINAL_CASES = [
+    ((1, 1, 1), (9, 7, 8), "persp"),
+    ((2, 2, 2), (3, 7, 12), "ortho_axis"),
+    ((3, 3, 3), (4, 6, 40), "persp_inside"),
+    ((3, 3, 3), (24, 20, 28), "persp"),
+    ((3, 3, 3), (33, 17, 9), "ortho_axis"),
+    ((4, 4, 4), (5, 9, 16), "ortho_oblique"),
+    ((4, 4, 4), (18, 14, 12), "persp"),
+]
+
+
+@pytest.mark.parametrize("storage", [1, 2, 3], ids=["f32", "f16", "bf16"])
+@pytest.mark.parametrize("degree,nctrl,cam", CARDINAL_CASES)
+def test_render_cardinal_matches_oracle(mfa, orc, degree, nctrl, cam, storage):
+    """Variant 6 (uniform knots: interior spans on the cardinal basis, the p-1 end spans of
+    each axis from their records) against the oracle, including models with no interior
+    span, axis-aligned rays whose positions sit on knots, and an eye inside the box; and
+    against the record path (variant 4) on the same model."""
+    import torch
+    rng = np.random.default_rng(_seed("cardinal", degree, nctrl, cam, storage))
+    model, ref, _ = _make(mfa, orc, rng, degree, nctrl, (True, True, True), storage)
+    assert model.info()["cardinal"]
+    camera = _camera(cam, rng)
+    job = synth.RenderJob(camera, 40, 28, 150, synth.ramp_tf(256, 0.08), True)
+    tf = mfa.transfer_fn(job.tf, shading=True)
+    imgs, counts = {}, {}
+    for variant in (6, 4, 0):
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        imgs[variant] = mfa.render(model, camera, tf, job.width, job.height, job.n_samples, samples_out=cnt,
+                                   variant=variant).cpu().numpy()
+        counts[variant] = int(cnt.item())
+    np.testing.assert_array_equal(imgs[0], imgs[6])          # the default on a cardinal model
+    rimg, rc = orc.render(ref, camera, job.tf, job.width, job.height, job.n_samples, shading=True)
+    rmse = image_rmse(imgs[6], rimg)
+    assert np.all(rmse <= IMAGE_RMSE_TOL), rmse
+    assert abs(counts[6] - rc) <= max(2, 1e-3 * rc)
+    assert rimg[..., 3].max() > 0.05
+    assert np.abs(imgs[6] - imgs[4]).max() <= 2e-3
+
+
+def test_cardinal_flag(mfa, orc):
+    """Which models take the cardinal path: uniform knots (within 1e-12) and one degree."""
+    rng = np.random.default_rng(31)
+    P = rng.standard_normal((9, 8, 7))
+    n = (7, 8, 9)
+    uni = [synth.knots_uniform(n[a], 3) for a in range(3)]
+    assert mfa.Model((3, 3, 3), n, None, P).info()["cardinal"]
+    assert mfa.Model((3, 3, 3), n, uni, P).info()["cardinal"]
+    near = [k.copy() for k in uni]
+    near[1][5] += 1e-13
+    assert mfa.Model((3, 3, 3), n, near, P).info()["cardinal"]
+    off = [k.copy() for k in uni]
+    off[1][5] += 1e-7
+    assert not mfa.Model((3, 3, 3), n, off, P).info()["cardinal"]
+    assert not mfa.Model((2, 3, 3), n, None, P).info()["cardinal"]
+    nonu = [synth.knots_nonuniform(n[a], 3, rng) for a in range(3)]
+    assert not mfa.Model((3, 3, 3), n, nonu, P).info()["cardinal"]
