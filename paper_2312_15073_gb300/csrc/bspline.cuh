@@ -2,12 +2,11 @@
 // Sec. V-D.3): knot-span location per axis, basis values and derivatives on the span,
 // and the (p+1)^3 control-point contraction for the value and the three partials.
 //
-// Two arithmetic forms of the same computation:
-//   * scalar FP32 FMAs;
-//   * packed FP32x2 (`fma.rn.f32x2`, `mul.rn.f32x2` on sm_100+), which advance two
-//     basis functions, two support columns or two partial sums per instruction and so
-//     halve the issue slots the query needs.  Each lane of a packed op is an ordinary
-//     FP32 round-to-nearest FMA / multiply.
+// Arithmetic is FP32 throughout.  The contraction's x- and y-passes use packed FP32x2
+// instructions (`fma.rn.f32x2`, `mul.rn.f32x2` on sm_100+) over pairs of support rows,
+// which the row-pair window layout delivers as ready operands; this halves the issue
+// slots of the dominant loop.  Each lane of a packed op is an ordinary FP32
+// round-to-nearest FMA / multiply.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -222,33 +221,33 @@ __device__ __forceinline__ void cardinal_basis(float t, float (&M)[Q], float (&G
 }
 
 // ----------------------------------------------------------------------------------------
-// control-point rows
+// control-point row pairs
 // ----------------------------------------------------------------------------------------
 
-// One x-row of the support: QP consecutive control points as FP32 (the entries past Q meet
-// zero basis values; they are always inside the zero-padded window array).
+// One window entry (k, j, i) as QP column pairs: pr[a] = {P[k][j][i+a], P[k][j+1][i+a]}
+// (two support rows side by side, the layout of a packed FP32x2 operand).  Entries past Q
+// meet zero basis values; they are always inside the zero-padded window array.  FP32: one
+// 256-bit load (a 16-byte one for Q = 2; Q = 5 adds 16 bytes of entry i + 4).
 template <int Q>
-struct RowF32 {
-    static __device__ __forceinline__ void load(const void* win, int idx, float (&row)[qpair(Q)])
+struct PairF32 {
+    static __device__ __forceinline__ void load(const void* win, int idx, f2 (&pr)[qpair(Q)])
     {
-        const float4* W = static_cast<const float4*>(win);
-        float4 v = __ldg(W + idx);
-        row[0] = v.x;
-        row[1] = v.y;
-        if constexpr (qpair(Q) >= 4) {
-            row[2] = v.z;
-            row[3] = v.w;
+        const float* e = static_cast<const float*>(win) + 8LL * idx;
+        if constexpr (qpair(Q) == 2) {
+            asm("ld.global.nc.v2.b64 {%0, %1}, [%2];" : "=l"(pr[0].v), "=l"(pr[1].v) : "l"(e));
+        } else {
+            asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
+                : "=l"(pr[0].v), "=l"(pr[1].v), "=l"(pr[2].v), "=l"(pr[3].v)
+                : "l"(e));
         }
-        if constexpr (qpair(Q) == 6) {
-            float2 e = __ldg(reinterpret_cast<const float2*>(W + idx + 4));
-            row[4] = e.x;
-            row[5] = e.y;
-        }
+        if constexpr (qpair(Q) == 6)
+            asm("ld.global.nc.v2.b64 {%0, %1}, [%2];" : "=l"(pr[4].v), "=l"(pr[5].v) : "l"(e + 32));
     }
 };
 
+// 16-bit storage: an entry is 16 bytes, one 32-bit word {row j, row j+1} per column.
 template <int Q, bool BF16>
-struct Row16 {
+struct Pair16 {
     static __device__ __forceinline__ float2 cvt(unsigned int bits)
     {
         if constexpr (BF16) {
@@ -259,31 +258,38 @@ struct Row16 {
             return __half22float2(h);
         }
     }
-    static __device__ __forceinline__ void load(const void* win, int idx, float (&row)[qpair(Q)])
+    static __device__ __forceinline__ f2 cvt2(unsigned int bits)
     {
-        const uint2* W = static_cast<const uint2*>(win);
-        uint2 v = __ldg(W + idx);
-        float2 lo = cvt(v.x);
-        row[0] = lo.x;
-        row[1] = lo.y;
-        if constexpr (qpair(Q) >= 4) {
-            float2 hi = cvt(v.y);
-            row[2] = hi.x;
-            row[3] = hi.y;
+        const float2 x = cvt(bits);
+        return pk2(x.x, x.y);
+    }
+    static __device__ __forceinline__ void load(const void* win, int idx, f2 (&pr)[qpair(Q)])
+    {
+        const unsigned short* e = static_cast<const unsigned short*>(win) + 8LL * idx;
+        if constexpr (qpair(Q) == 2) {
+            const uint2 w = __ldg(reinterpret_cast<const uint2*>(e));
+            pr[0] = cvt2(w.x);
+            pr[1] = cvt2(w.y);
+        } else {
+            const uint4 w = __ldg(reinterpret_cast<const uint4*>(e));
+            pr[0] = cvt2(w.x);
+            pr[1] = cvt2(w.y);
+            pr[2] = cvt2(w.z);
+            pr[3] = cvt2(w.w);
         }
         if constexpr (qpair(Q) == 6) {
-            float2 e = cvt(__ldg(reinterpret_cast<const unsigned int*>(W + idx + 4)));
-            row[4] = e.x;
-            row[5] = e.y;
+            const uint2 w = __ldg(reinterpret_cast<const uint2*>(e + 32));
+            pr[4] = cvt2(w.x);
+            pr[5] = cvt2(w.y);
         }
     }
 };
 
 template <int Q, int STORAGE>
-struct RowLoader;
-template <int Q> struct RowLoader<Q, 1> : RowF32<Q> {};          // MFA_F32
-template <int Q> struct RowLoader<Q, 2> : Row16<Q, false> {};    // MFA_F16
-template <int Q> struct RowLoader<Q, 3> : Row16<Q, true> {};     // MFA_BF16
+struct PairLoader;
+template <int Q> struct PairLoader<Q, 1> : PairF32<Q> {};          // MFA_F32
+template <int Q> struct PairLoader<Q, 2> : Pair16<Q, false> {};    // MFA_F16
+template <int Q> struct PairLoader<Q, 3> : Pair16<Q, true> {};     // MFA_BF16
 
 // ----------------------------------------------------------------------------------------
 // contraction
@@ -295,89 +301,44 @@ template <int Q> struct RowLoader<Q, 3> : Row16<Q, true> {};     // MFA_BF16
 //   y-pass  C_k = sum_j Ny_j A_jk, D_k = sum_j Dy_j A_jk, E_k = sum_j Ny_j B_jk   (3 Q^2)
 //   z-pass  f = sum_k Nz_k C_k, f_z = sum Dz_k C_k, f_y = sum Nz_k D_k, f_x = sum Nz_k E_k
 // Returns {f, df/dtx, df/dty, df/dtz} (derivatives in the local span coordinates).
+//
+// The x- and y-passes run on packed FP32x2 values, two support rows (j, j+1) per
+// instruction: one row-pair entry gives {A_j, A_j+1} = sum_i {Nx_i, Nx_i} * pr[i] (and B
+// likewise), and the y-pass accumulates those pairs against {Ny_j, Ny_j+1}; the two halves
+// of each y sum are added once per z-layer.  nx, dx hold each basis value twice, ny, dy hold
+// the values of functions (2m, 2m+1) (zero past Q).  Each lane is an ordinary FP32 FMA;
+// the y sums add their even and odd terms separately before the final addition.
 template <int Q, int STORAGE>
-__device__ __forceinline__ float4 contract_at(const ModelDev& M, int base, const float (&Nx)[Q], const float (&Dx)[Q],
-                                              const float (&Ny)[Q], const float (&Dy)[Q], const float (&Nz)[Q],
-                                              const float (&Dz)[Q])
-{
-    const int plane = M.nxp * M.nyp;
-    float f = 0.0f, fx = 0.0f, fy = 0.0f, fz = 0.0f;
-#pragma unroll
-    for (int c = 0; c < Q; ++c) {
-        float C = 0.0f, Dv = 0.0f, E = 0.0f;
-#pragma unroll
-        for (int b = 0; b < Q; ++b) {
-            float row[qpair(Q)];
-            RowLoader<Q, STORAGE>::load(M.win, base + c * plane + b * M.nxp, row);
-            float A = 0.0f, B = 0.0f;
-#pragma unroll
-            for (int a = 0; a < Q; ++a) {
-                A = fmaf(Nx[a], row[a], A);
-                B = fmaf(Dx[a], row[a], B);
-            }
-            C = fmaf(Ny[b], A, C);
-            Dv = fmaf(Dy[b], A, Dv);
-            E = fmaf(Ny[b], B, E);
-        }
-        f = fmaf(Nz[c], C, f);
-        fz = fmaf(Dz[c], C, fz);
-        fy = fmaf(Nz[c], Dv, fy);
-        fx = fmaf(Nz[c], E, fx);
-    }
-    return make_float4(f, fx, fy, fz);
-}
-
-// Same, from the support's origin (i0, j0, k0) in the window array.
-template <int Q, int STORAGE>
-__device__ __forceinline__ float4 contract(const ModelDev& M, int i0, int j0, int k0, const float (&Nx)[Q],
-                                           const float (&Dx)[Q], const float (&Ny)[Q], const float (&Dy)[Q],
-                                           const float (&Nz)[Q], const float (&Dz)[Q])
-{
-    return contract_at<Q, STORAGE>(M, (k0 * M.nyp + j0) * M.nxp + i0, Nx, Dx, Ny, Dy, Nz, Dz);
-}
-
-// Packed form of the same contraction.  x-pass: each row is read as QP/2 column pairs,
-// A2 = sum_m Nx2[m] * row2[m] keeps two partial sums {even columns, odd columns}; the
-// y-pass accumulates those pairs against {Ny_j, Ny_j}; the two halves are added once per
-// z-layer.  Same products as the scalar form, summed in a different order.
-template <int Q, int STORAGE>
-__device__ __forceinline__ float4 contract2(const ModelDev& M, int i0, int j0, int k0, const f2 (&Nx2)[qpair(Q) / 2],
-                                            const f2 (&Dx2)[qpair(Q) / 2], const float (&Ny)[Q], const float (&Dy)[Q],
-                                            const float (&Nz)[Q], const float (&Dz)[Q])
+__device__ __forceinline__ float4 contract_pairs(const ModelDev& M, int base, const f2 (&nx)[Q], const f2 (&dx)[Q],
+                                                 const f2 (&ny)[qpair(Q) / 2], const f2 (&dy)[qpair(Q) / 2],
+                                                 const float (&Nz)[Q], const float (&Dz)[Q])
 {
     constexpr int NP = qpair(Q) / 2;
     const int plane = M.nxp * M.nyp;
-    const int base = (k0 * M.nyp + j0) * M.nxp + i0;
-    f2 ny2[Q], dy2[Q];
-#pragma unroll
-    for (int b = 0; b < Q; ++b) {
-        ny2[b] = pk2(Ny[b], Ny[b]);
-        dy2[b] = pk2(Dy[b], Dy[b]);
-    }
+    const int pair_step = 2 * M.nxp;
     float f = 0.0f, fx = 0.0f, fy = 0.0f, fz = 0.0f;
 #pragma unroll
     for (int c = 0; c < Q; ++c) {
         f2 CC, DD, EE;
 #pragma unroll
-        for (int b = 0; b < Q; ++b) {
-            float row[qpair(Q)];
-            RowLoader<Q, STORAGE>::load(M.win, base + c * plane + b * M.nxp, row);
-            f2 A = mul2(Nx2[0], pk2(row[0], row[1]));
-            f2 B = mul2(Dx2[0], pk2(row[0], row[1]));
+        for (int m = 0; m < NP; ++m) {
+            f2 pr[qpair(Q)];
+            PairLoader<Q, STORAGE>::load(M.win, base + c * plane + m * pair_step, pr);
+            f2 A = mul2(nx[0], pr[0]);
+            f2 B = mul2(dx[0], pr[0]);
 #pragma unroll
-            for (int m = 1; m < NP; ++m) {
-                const f2 r = pk2(row[2 * m], row[2 * m + 1]);
-                A = fma2(Nx2[m], r, A);
-                B = fma2(Dx2[m], r, B);
+            for (int a = 1; a < Q; ++a) {
+                A = fma2(nx[a], pr[a], A);
+                B = fma2(dx[a], pr[a], B);
             }
-            if (b == 0) {
-                CC = mul2(ny2[0], A);
-                DD = mul2(dy2[0], A);
-                EE = mul2(ny2[0], B);
+            if (m == 0) {
+                CC = mul2(ny[0], A);
+                DD = mul2(dy[0], A);
+                EE = mul2(ny[0], B);
             } else {
-                CC = fma2(ny2[b], A, CC);
-                DD = fma2(dy2[b], A, DD);
-                EE = fma2(ny2[b], B, EE);
+                CC = fma2(ny[m], A, CC);
+                DD = fma2(dy[m], A, DD);
+                EE = fma2(ny[m], B, EE);
             }
         }
         const float C = hsum2(CC), Dv = hsum2(DD), E = hsum2(EE);
@@ -389,17 +350,43 @@ __device__ __forceinline__ float4 contract2(const ModelDev& M, int i0, int j0, i
     return make_float4(f, fx, fy, fz);
 }
 
-// Unpacks the first Q entries of a packed basis into scalars.
+// {X_a, X_a} for every a
 template <int Q>
-__device__ __forceinline__ void unpack_basis(const f2 (&X2)[qpair(Q) / 2], float (&X)[Q])
+__device__ __forceinline__ void pack_dup(const float (&X)[Q], f2 (&X2)[Q])
 {
 #pragma unroll
-    for (int m = 0; m < qpair(Q) / 2; ++m) {
-        float a, b;
-        upk2(X2[m], a, b);
-        if (2 * m < Q) X[2 * m] = a;
-        if (2 * m + 1 < Q) X[2 * m + 1] = b;
-    }
+    for (int a = 0; a < Q; ++a) X2[a] = pk2(X[a], X[a]);
+}
+
+// {X_2m, X_2m+1} (zero past Q)
+template <int Q>
+__device__ __forceinline__ void pack_pairs(const float (&X)[Q], f2 (&X2)[qpair(Q) / 2])
+{
+#pragma unroll
+    for (int m = 0; m < qpair(Q) / 2; ++m) X2[m] = pk2(X[2 * m], 2 * m + 1 < Q ? X[2 * m + 1] : 0.0f);
+}
+
+// Contraction from scalar basis values.
+template <int Q, int STORAGE>
+__device__ __forceinline__ float4 contract_at(const ModelDev& M, int base, const float (&Nx)[Q], const float (&Dx)[Q],
+                                              const float (&Ny)[Q], const float (&Dy)[Q], const float (&Nz)[Q],
+                                              const float (&Dz)[Q])
+{
+    f2 nx[Q], dx[Q], ny[qpair(Q) / 2], dy[qpair(Q) / 2];
+    pack_dup<Q>(Nx, nx);
+    pack_dup<Q>(Dx, dx);
+    pack_pairs<Q>(Ny, ny);
+    pack_pairs<Q>(Dy, dy);
+    return contract_pairs<Q, STORAGE>(M, base, nx, dx, ny, dy, Nz, Dz);
+}
+
+// Same, from the support's origin (i0, j0, k0) in the window array.
+template <int Q, int STORAGE>
+__device__ __forceinline__ float4 contract(const ModelDev& M, int i0, int j0, int k0, const float (&Nx)[Q],
+                                           const float (&Dx)[Q], const float (&Ny)[Q], const float (&Dy)[Q],
+                                           const float (&Nz)[Q], const float (&Dz)[Q])
+{
+    return contract_at<Q, STORAGE>(M, (k0 * M.nyp + j0) * M.nxp + i0, Nx, Dx, Ny, Dy, Nz, Dz);
 }
 
 // Full query at a clamped parameter point: value and world gradient (unit-cube domain,
@@ -418,30 +405,29 @@ __device__ __forceinline__ float4 query(const ModelDev& M, float u, float v, flo
     return r;
 }
 
-// Packed query from three records already in registers.
+// Query from three records already in registers, the y basis evaluated directly as
+// function pairs (record_basis2) for the packed y-pass.
 template <int Q, int STORAGE>
 __device__ __forceinline__ float4 query2_rec(const ModelDev& M, const float (&rx)[rec_stride(Q)],
                                              const float (&ry)[rec_stride(Q)], const float (&rz)[rec_stride(Q)],
                                              float u, float v, float w, int i0, int j0, int k0)
 {
     constexpr int NP = qpair(Q) / 2;
-    f2 Nx2[NP], Dx2[NP], Ny2[NP], Dy2[NP], Nz2[NP], Dz2[NP];
-    record_basis2<Q>(rx, u, Nx2, Dx2);
-    record_basis2<Q>(ry, v, Ny2, Dy2);
-    record_basis2<Q>(rz, w, Nz2, Dz2);
-    float Ny[Q], Dy[Q], Nz[Q], Dz[Q];
-    unpack_basis<Q>(Ny2, Ny);
-    unpack_basis<Q>(Dy2, Dy);
-    unpack_basis<Q>(Nz2, Nz);
-    unpack_basis<Q>(Dz2, Dz);
-    float4 r = contract2<Q, STORAGE>(M, i0, j0, k0, Nx2, Dx2, Ny, Dy, Nz, Dz);
+    float Nx[Q], Dx[Q], Nz[Q], Dz[Q];
+    f2 nx[Q], dx[Q], ny[NP], dy[NP];
+    record_basis<Q>(rx, u, Nx, Dx);
+    record_basis2<Q>(ry, v, ny, dy);
+    record_basis<Q>(rz, w, Nz, Dz);
+    pack_dup<Q>(Nx, nx);
+    pack_dup<Q>(Dx, dx);
+    float4 r = contract_pairs<Q, STORAGE>(M, (k0 * M.nyp + j0) * M.nxp + i0, nx, dx, ny, dy, Nz, Dz);
     r.y *= rx[1];
     r.z *= ry[1];
     r.w *= rz[1];
     return r;
 }
 
-// Packed query that loads its three records.
+// Same, loading the three records.
 template <int Q, int STORAGE>
 __device__ __forceinline__ float4 query2(const ModelDev& M, float u, float v, float w, int sx, int sy, int sz)
 {

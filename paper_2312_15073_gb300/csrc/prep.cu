@@ -113,6 +113,7 @@ __device__ __forceinline__ unsigned short to16(double x, int storage)
     return __bfloat16_as_ushort(__double2bfloat16(x));
 }
 
+// The row-pair window array (layout in mfa_internal.cuh), one entry per thread.
 __global__ void k_window(const void* __restrict__ ctrl, int in_dtype, int storage, int nx, int ny, int nz,
                          void* __restrict__ win)
 {
@@ -124,22 +125,30 @@ __global__ void k_window(const void* __restrict__ ctrl, int in_dtype, int storag
         const long long jk = e / nxp;
         const int j = static_cast<int>(jk % nyp);
         const int k = static_cast<int>(jk / nyp);
-        double v[4];
+        double v[8];   // v[2a + r] = P[k][j + r][i + a]
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            const int ia = i + a;
-            v[a] = (ia < nx && j < ny && k < nz)
-                       ? load_in(ctrl, in_dtype, (static_cast<long long>(k) * ny + j) * nx + ia)
-                       : 0.0;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int ia = i + a, jr = j + r;
+                v[2 * a + r] = (ia < nx && jr < ny && k < nz)
+                                   ? load_in(ctrl, in_dtype, (static_cast<long long>(k) * ny + jr) * nx + ia)
+                                   : 0.0;
+            }
         }
         if (storage == 1) {
-            static_cast<float4*>(win)[e] = make_float4(__double2float_rn(v[0]), __double2float_rn(v[1]),
-                                                       __double2float_rn(v[2]), __double2float_rn(v[3]));
+            float4* w = static_cast<float4*>(win) + 2 * e;
+            w[0] = make_float4(__double2float_rn(v[0]), __double2float_rn(v[1]), __double2float_rn(v[2]),
+                               __double2float_rn(v[3]));
+            w[1] = make_float4(__double2float_rn(v[4]), __double2float_rn(v[5]), __double2float_rn(v[6]),
+                               __double2float_rn(v[7]));
         } else {
-            uint2 w;
-            w.x = static_cast<unsigned>(to16(v[0], storage)) | (static_cast<unsigned>(to16(v[1], storage)) << 16);
-            w.y = static_cast<unsigned>(to16(v[2], storage)) | (static_cast<unsigned>(to16(v[3], storage)) << 16);
-            static_cast<uint2*>(win)[e] = w;
+            unsigned int b[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+                b[a] = static_cast<unsigned>(to16(v[2 * a], storage)) |
+                       (static_cast<unsigned>(to16(v[2 * a + 1], storage)) << 16);
+            static_cast<uint4*>(win)[e] = make_uint4(b[0], b[1], b[2], b[3]);
         }
     }
 }
@@ -174,9 +183,9 @@ __global__ void k_stats(const void* __restrict__ win, int storage, int nx, int n
         const long long w = (static_cast<long long>(k) * nyp + j) * nxp + i;
         float v;
         if (storage == 1) {
-            v = static_cast<const float4*>(win)[w].x;
+            v = static_cast<const float*>(win)[8 * w];
         } else {
-            unsigned short b = static_cast<unsigned short>(static_cast<const uint2*>(win)[w].x & 0xFFFFu);
+            const unsigned short b = static_cast<const unsigned short*>(win)[8 * w];
             v = storage == 2 ? __half2float(__ushort_as_half(b)) : __bfloat162float(__ushort_as_bfloat16(b));
         }
         mn = fminf(mn, v);

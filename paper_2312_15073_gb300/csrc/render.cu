@@ -461,20 +461,24 @@ constexpr int kBrick = 8;
 constexpr int kBrickFloats4 = kBrick * kBrick * kBrick;   // 8 KB per warp
 constexpr int kSegMax = 64;
 
+// Row j of window entry idx, P[k][j][i..i+3], as FP32 (the even members of the entry's
+// column pairs).
 template <int STORAGE>
 __device__ __forceinline__ float4 window_f32(const void* win, long long idx)
 {
     if constexpr (STORAGE == 1) {
-        return __ldg(static_cast<const float4*>(win) + idx);
+        const float4* e = static_cast<const float4*>(win) + 2 * idx;
+        const float4 lo = __ldg(e), hi = __ldg(e + 1);
+        return make_float4(lo.x, lo.z, hi.x, hi.z);
     } else {
-        const uint2 v = __ldg(static_cast<const uint2*>(win) + idx);
-        const float2 lo = Row16<4, STORAGE == 3>::cvt(v.x), hi = Row16<4, STORAGE == 3>::cvt(v.y);
-        return make_float4(lo.x, lo.y, hi.x, hi.y);
+        const uint4 w = __ldg(static_cast<const uint4*>(win) + idx);
+        using P = Pair16<4, STORAGE == 3>;
+        return make_float4(P::cvt(w.x).x, P::cvt(w.y).x, P::cvt(w.z).x, P::cvt(w.w).x);
     }
 }
 
 // Sum-factorised contraction over a support held in a shared-memory brick (rows at fixed
-// offsets from `b0`); same arithmetic order as contract().
+// offsets from `b0`), in scalar FP32 (the y sums in natural order).
 template <int Q>
 __device__ __forceinline__ float4 contract_brick(const float4* __restrict__ b0, const float (&Nx)[Q], const float (&Dx)[Q],
                                                  const float (&Ny)[Q], const float (&Dy)[Q], const float (&Nz)[Q],
