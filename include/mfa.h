@@ -66,7 +66,7 @@ typedef struct mfa_model mfa_model;   /* opaque; owns all of its device memory *
  *              [n_z][n_y][n_x], x fastest.  Copied; the caller keeps ownership.
  *   dtype      type of ctrl.  Storage is FP32 for F64/F32 input, FP16 for F16, BF16 for
  *              BF16 (see mfa_model_create_ex to choose).
- * The padded row-pair window layout the kernels read takes about 32 bytes per control
+ * The padded layer-pair window layout the kernels read takes about 32 bytes per control
  * point (FP32 storage) or 16 bytes (FP16/BF16); the product of the padded sizes
  * (n_x+4)(n_y+4)(n_z+4) must stay below 2^31.
  * Synchronous: returns after the model is ready.  Returns NULL on error (reason in

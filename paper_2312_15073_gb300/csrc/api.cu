@@ -246,7 +246,7 @@ mfa_model* mfa_model_create_ex(const int degree[3], const int nctrl[3], const do
         off_rec[a] = tab;
         tab = align_up(tab + sizeof(float) * rec_stride(Q) * (n - p), 256);
     }
-    const size_t win_elem = storage == MFA_F32 ? 32 : 16;   // one row-pair entry
+    const size_t win_elem = storage == MFA_F32 ? 32 : 16;   // one layer-pair entry
     const size_t win_bytes = static_cast<size_t>(nxp * nyp * nzp) * win_elem;
     const size_t nctrl_total = static_cast<size_t>(nctrl[0]) * nctrl[1] * nctrl[2];
     const size_t in_bytes = nctrl_total * dtype_size(in_dtype);

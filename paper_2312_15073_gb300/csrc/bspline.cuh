@@ -2,10 +2,10 @@
 // Sec. V-D.3): knot-span location per axis, basis values and derivatives on the span,
 // and the (p+1)^3 control-point contraction for the value and the three partials.
 //
-// Arithmetic is FP32 throughout.  The contraction's x- and y-passes use packed FP32x2
-// instructions (`fma.rn.f32x2`, `mul.rn.f32x2` on sm_100+) over pairs of support rows,
-// which the row-pair window layout delivers as ready operands; this halves the issue
-// slots of the dominant loop.  Each lane of a packed op is an ordinary FP32
+// Arithmetic is FP32 throughout.  The contraction uses packed FP32x2 instructions
+// (`fma.rn.f32x2`, `mul.rn.f32x2` on sm_100+) over pairs of z-layers, which the layer-pair
+// window layout delivers as ready operands; this halves the issue slots of the dominant
+// loop.  Each lane of a packed op is an ordinary FP32
 // round-to-nearest FMA / multiply.
 #pragma once
 
@@ -221,13 +221,14 @@ __device__ __forceinline__ void cardinal_basis(float t, float (&M)[Q], float (&G
 }
 
 // ----------------------------------------------------------------------------------------
-// control-point row pairs
+// control-point layer pairs
 // ----------------------------------------------------------------------------------------
 
-// One window entry (k, j, i) as QP column pairs: pr[a] = {P[k][j][i+a], P[k][j+1][i+a]}
-// (two support rows side by side, the layout of a packed FP32x2 operand).  Entries past Q
-// meet zero basis values; they are always inside the zero-padded window array.  FP32: one
-// 256-bit load (a 16-byte one for Q = 2; Q = 5 adds 16 bytes of entry i + 4).
+// One window entry (k, j, i) as QP column pairs: pr[a] = {P[k][j][i+a], P[k+1][j][i+a]}
+// (the same row of two consecutive z-layers side by side, the layout of a packed FP32x2
+// operand).  Entries past Q meet zero basis values; they are always inside the
+// zero-padded window array.  FP32: one 256-bit load (a 16-byte one for Q = 2; Q = 5 adds
+// 16 bytes of entry i + 4).
 template <int Q>
 struct PairF32 {
     static __device__ __forceinline__ void load(const void* win, int idx, f2 (&pr)[qpair(Q)])
@@ -245,7 +246,7 @@ struct PairF32 {
     }
 };
 
-// 16-bit storage: an entry is 16 bytes, one 32-bit word {row j, row j+1} per column.
+// 16-bit storage: an entry is 16 bytes, one 32-bit word {layer k, layer k+1} per column.
 template <int Q, bool BF16>
 struct Pair16 {
     static __device__ __forceinline__ float2 cvt(unsigned int bits)
@@ -302,28 +303,28 @@ template <int Q> struct PairLoader<Q, 3> : Pair16<Q, true> {};     // MFA_BF16
 //   z-pass  f = sum_k Nz_k C_k, f_z = sum Dz_k C_k, f_y = sum Nz_k D_k, f_x = sum Nz_k E_k
 // Returns {f, df/dtx, df/dty, df/dtz} (derivatives in the local span coordinates).
 //
-// The x- and y-passes run on packed FP32x2 values, two support rows (j, j+1) per
-// instruction: one row-pair entry gives {A_j, A_j+1} = sum_i {Nx_i, Nx_i} * pr[i] (and B
-// likewise), and the y-pass accumulates those pairs against {Ny_j, Ny_j+1}; the two halves
-// of each y sum are added once per z-layer.  nx, dx hold each basis value twice, ny, dy hold
-// the values of functions (2m, 2m+1) (zero past Q).  Each lane is an ordinary FP32 FMA;
-// the y sums add their even and odd terms separately before the final addition.
+// All three passes run on packed FP32x2 values over pairs of z-layers (k, k+1): one
+// window entry gives {A_jk, A_j,k+1} = sum_i {Nx_i, Nx_i} * pr[i] (and B likewise), the
+// y-pass turns them into {C_k, C_k+1}, {D_k, D_k+1}, {E_k, E_k+1} with weights
+// {Ny_j, Ny_j}, and the z-pass accumulates those against {Nz_k, Nz_k+1}; the two halves of
+// each of the four results are added once at the end.  nx, dx, ny, dy hold each basis value
+// twice, nz, dz the values of functions (2m, 2m+1) (zero past Q).  Each lane is an ordinary
+// FP32 FMA; the z sums add their even and odd terms separately before the final addition.
 template <int Q, int STORAGE>
 __device__ __forceinline__ float4 contract_pairs(const ModelDev& M, int base, const f2 (&nx)[Q], const f2 (&dx)[Q],
-                                                 const f2 (&ny)[qpair(Q) / 2], const f2 (&dy)[qpair(Q) / 2],
-                                                 const float (&Nz)[Q], const float (&Dz)[Q])
+                                                 const f2 (&ny)[Q], const f2 (&dy)[Q], const f2 (&nz)[qpair(Q) / 2],
+                                                 const f2 (&dz)[qpair(Q) / 2])
 {
     constexpr int NP = qpair(Q) / 2;
-    const int plane = M.nxp * M.nyp;
-    const int pair_step = 2 * M.nxp;
-    float f = 0.0f, fx = 0.0f, fy = 0.0f, fz = 0.0f;
+    const int pair_step = 2 * M.nxp * M.nyp;
+    f2 F, FX, FY, FZ;
 #pragma unroll
-    for (int c = 0; c < Q; ++c) {
+    for (int m = 0; m < NP; ++m) {
         f2 CC, DD, EE;
 #pragma unroll
-        for (int m = 0; m < NP; ++m) {
+        for (int b = 0; b < Q; ++b) {
             f2 pr[qpair(Q)];
-            PairLoader<Q, STORAGE>::load(M.win, base + c * plane + m * pair_step, pr);
+            PairLoader<Q, STORAGE>::load(M.win, base + m * pair_step + b * M.nxp, pr);
             f2 A = mul2(nx[0], pr[0]);
             f2 B = mul2(dx[0], pr[0]);
 #pragma unroll
@@ -331,23 +332,29 @@ __device__ __forceinline__ float4 contract_pairs(const ModelDev& M, int base, co
                 A = fma2(nx[a], pr[a], A);
                 B = fma2(dx[a], pr[a], B);
             }
-            if (m == 0) {
+            if (b == 0) {
                 CC = mul2(ny[0], A);
                 DD = mul2(dy[0], A);
                 EE = mul2(ny[0], B);
             } else {
-                CC = fma2(ny[m], A, CC);
-                DD = fma2(dy[m], A, DD);
-                EE = fma2(ny[m], B, EE);
+                CC = fma2(ny[b], A, CC);
+                DD = fma2(dy[b], A, DD);
+                EE = fma2(ny[b], B, EE);
             }
         }
-        const float C = hsum2(CC), Dv = hsum2(DD), E = hsum2(EE);
-        f = fmaf(Nz[c], C, f);
-        fz = fmaf(Dz[c], C, fz);
-        fy = fmaf(Nz[c], Dv, fy);
-        fx = fmaf(Nz[c], E, fx);
+        if (m == 0) {
+            F = mul2(nz[0], CC);
+            FZ = mul2(dz[0], CC);
+            FY = mul2(nz[0], DD);
+            FX = mul2(nz[0], EE);
+        } else {
+            F = fma2(nz[m], CC, F);
+            FZ = fma2(dz[m], CC, FZ);
+            FY = fma2(nz[m], DD, FY);
+            FX = fma2(nz[m], EE, FX);
+        }
     }
-    return make_float4(f, fx, fy, fz);
+    return make_float4(hsum2(F), hsum2(FX), hsum2(FY), hsum2(FZ));
 }
 
 // {X_a, X_a} for every a
@@ -372,12 +379,14 @@ __device__ __forceinline__ float4 contract_at(const ModelDev& M, int base, const
                                               const float (&Ny)[Q], const float (&Dy)[Q], const float (&Nz)[Q],
                                               const float (&Dz)[Q])
 {
-    f2 nx[Q], dx[Q], ny[qpair(Q) / 2], dy[qpair(Q) / 2];
+    f2 nx[Q], dx[Q], ny[Q], dy[Q], nz[qpair(Q) / 2], dz[qpair(Q) / 2];
     pack_dup<Q>(Nx, nx);
     pack_dup<Q>(Dx, dx);
-    pack_pairs<Q>(Ny, ny);
-    pack_pairs<Q>(Dy, dy);
-    return contract_pairs<Q, STORAGE>(M, base, nx, dx, ny, dy, Nz, Dz);
+    pack_dup<Q>(Ny, ny);
+    pack_dup<Q>(Dy, dy);
+    pack_pairs<Q>(Nz, nz);
+    pack_pairs<Q>(Dz, dz);
+    return contract_pairs<Q, STORAGE>(M, base, nx, dx, ny, dy, nz, dz);
 }
 
 // Same, from the support's origin (i0, j0, k0) in the window array.
@@ -405,22 +414,24 @@ __device__ __forceinline__ float4 query(const ModelDev& M, float u, float v, flo
     return r;
 }
 
-// Query from three records already in registers, the y basis evaluated directly as
-// function pairs (record_basis2) for the packed y-pass.
+// Query from three records already in registers, the z basis evaluated directly as
+// function pairs (record_basis2) for the packed z-pass.
 template <int Q, int STORAGE>
 __device__ __forceinline__ float4 query2_rec(const ModelDev& M, const float (&rx)[rec_stride(Q)],
                                              const float (&ry)[rec_stride(Q)], const float (&rz)[rec_stride(Q)],
                                              float u, float v, float w, int i0, int j0, int k0)
 {
     constexpr int NP = qpair(Q) / 2;
-    float Nx[Q], Dx[Q], Nz[Q], Dz[Q];
-    f2 nx[Q], dx[Q], ny[NP], dy[NP];
+    float Nx[Q], Dx[Q], Ny[Q], Dy[Q];
+    f2 nx[Q], dx[Q], ny[Q], dy[Q], nz[NP], dz[NP];
     record_basis<Q>(rx, u, Nx, Dx);
-    record_basis2<Q>(ry, v, ny, dy);
-    record_basis<Q>(rz, w, Nz, Dz);
+    record_basis<Q>(ry, v, Ny, Dy);
+    record_basis2<Q>(rz, w, nz, dz);
     pack_dup<Q>(Nx, nx);
     pack_dup<Q>(Dx, dx);
-    float4 r = contract_pairs<Q, STORAGE>(M, (k0 * M.nyp + j0) * M.nxp + i0, nx, dx, ny, dy, Nz, Dz);
+    pack_dup<Q>(Ny, ny);
+    pack_dup<Q>(Dy, dy);
+    float4 r = contract_pairs<Q, STORAGE>(M, (k0 * M.nyp + j0) * M.nxp + i0, nx, dx, ny, dy, nz, dz);
     r.y *= rx[1];
     r.z *= ry[1];
     r.w *= rz[1];

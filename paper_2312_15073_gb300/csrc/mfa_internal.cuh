@@ -1,13 +1,13 @@
 // mfa_internal.cuh -- device-side model description shared by the libmfa translation units.
 //
 // Data layout in HBM (one model):
-//   * window array  W[(n_z+4)][(n_y+4)][(n_x+4)] of row-pair entries: entry (k, j, i)
-//     holds the eight control points P[k][j+r][i+a], a = 0..3, r = 0..1 (zero past the
-//     end), interleaved as {P[k][j][i+a], P[k][j+1][i+a]} column pairs: 32 bytes (FP32
-//     storage) or 16 bytes (FP16 / BF16).  One aligned 256-bit load then fetches two whole
-//     x-rows of a (p+1)^3 support for p <= 3 (plus 16 bytes for p = 4), and each column
-//     pair is a ready operand of a packed FP32x2 FMA that advances both rows.  Costs 8x
-//     the plain array.
+//   * window array  W[(n_z+4)][(n_y+4)][(n_x+4)] of layer-pair entries: entry (k, j, i)
+//     holds the eight control points P[k+r][j][i+a], a = 0..3, r = 0..1 (zero past the
+//     end), interleaved as {P[k][j][i+a], P[k+1][j][i+a]} column pairs: 32 bytes (FP32
+//     storage) or 16 bytes (FP16 / BF16).  One aligned 256-bit load then fetches the same
+//     x-row of two z-layers of a (p+1)^3 support for p <= 3 (plus 16 bytes for p = 4), and
+//     each column pair is a ready operand of a packed FP32x2 FMA that advances both
+//     layers.  Costs 8x the plain array.
 //   * per axis: kup[n+p+1]  the FP64 knots rounded UP to FP32, so that for an FP32
 //     coordinate u, (u >= kup[s]) is exactly (u >= U[s]) in real arithmetic;
 //     grid[G]  (G = 4 (n - p)) the span containing g / G, a starting guess for the span

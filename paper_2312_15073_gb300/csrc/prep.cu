@@ -113,7 +113,7 @@ __device__ __forceinline__ unsigned short to16(double x, int storage)
     return __bfloat16_as_ushort(__double2bfloat16(x));
 }
 
-// The row-pair window array (layout in mfa_internal.cuh), one entry per thread.
+// The layer-pair window array (layout in mfa_internal.cuh), one entry per thread.
 __global__ void k_window(const void* __restrict__ ctrl, int in_dtype, int storage, int nx, int ny, int nz,
                          void* __restrict__ win)
 {
@@ -125,14 +125,14 @@ __global__ void k_window(const void* __restrict__ ctrl, int in_dtype, int storag
         const long long jk = e / nxp;
         const int j = static_cast<int>(jk % nyp);
         const int k = static_cast<int>(jk / nyp);
-        double v[8];   // v[2a + r] = P[k][j + r][i + a]
+        double v[8];   // v[2a + r] = P[k + r][j][i + a]
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
-                const int ia = i + a, jr = j + r;
-                v[2 * a + r] = (ia < nx && jr < ny && k < nz)
-                                   ? load_in(ctrl, in_dtype, (static_cast<long long>(k) * ny + jr) * nx + ia)
+                const int ia = i + a, kr = k + r;
+                v[2 * a + r] = (ia < nx && j < ny && kr < nz)
+                                   ? load_in(ctrl, in_dtype, (static_cast<long long>(kr) * ny + j) * nx + ia)
                                    : 0.0;
             }
         }

@@ -45,8 +45,10 @@ constexpr int kThreads = 128;
 // the 128^3 degree-3 frame: cap 128 -> 6.33 ms, cap 168 (3 CTAs) -> 7.01 ms, cap 96 (5
 // CTAs, spills) -> 10.4 ms.
 constexpr int kMinBlocks = 4;
-// The cardinal path (variant 6) holds no span records, so more CTAs fit per SM.
-constexpr int kMinBlocksCardinal = 5;
+// The cardinal path (variant 6) holds no span records, so more CTAs fit per SM: 5 (102
+// registers) measures best with FP32 storage (5.12 ms on the 128^3 degree-3 1024^2 frame,
+// against 5.18 ms at 4 and 5.29 ms at 6), 4 with 16-bit storage (6.00 against 6.06 ms at 5).
+__host__ __device__ constexpr int card_min_blocks(int storage) { return storage == 1 ? 5 : 4; }
 
 // Ray-tile shapes (CTA tile, warp tile).  Shape 0 is the default; the autotuner picks one
 // per workload.
@@ -461,8 +463,8 @@ constexpr int kBrick = 8;
 constexpr int kBrickFloats4 = kBrick * kBrick * kBrick;   // 8 KB per warp
 constexpr int kSegMax = 64;
 
-// Row j of window entry idx, P[k][j][i..i+3], as FP32 (the even members of the entry's
-// column pairs).
+// Row (k, j) of window entry idx, P[k][j][i..i+3], as FP32 (the even members of the
+// entry's column pairs).
 template <int STORAGE>
 __device__ __forceinline__ float4 window_f32(const void* win, long long idx)
 {
@@ -646,7 +648,7 @@ __device__ __forceinline__ void add_count(unsigned long long* dst, unsigned long
 // ----------------------------------------------------------------------------------------
 
 template <int Q, int STORAGE, int MODE>
-__global__ void __launch_bounds__(kThreads, MODE == 6 ? kMinBlocksCardinal : kMinBlocks)
+__global__ void __launch_bounds__(kThreads, MODE == 6 ? card_min_blocks(STORAGE) : kMinBlocks)
     k_render(ModelDev M, const __grid_constant__ RenderParams P, int shape)
 {
     __shared__ float4 tf[kTfMax + 1];
@@ -725,7 +727,7 @@ cudaError_t render_q(const ModelDev& m, const RenderParams& rp, int variant, int
 // repeat until the counter passes the group's last tile.  One kernel per group keeps each
 // degree's (and each path's) register allocation free of the others'.
 template <int Q, int STORAGE, bool CARD>
-__global__ void __launch_bounds__(kThreads, CARD ? kMinBlocksCardinal : kMinBlocks)
+__global__ void __launch_bounds__(kThreads, CARD ? card_min_blocks(STORAGE) : kMinBlocks)
     k_render_batch(BatchHead* __restrict__ table, int group, int shape)
 {
     __shared__ BatchItem item;
