@@ -76,6 +76,12 @@ __device__ __forceinline__ f2 mul2(f2 a, f2 b)
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
     return d;
 }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
 
 // ----------------------------------------------------------------------------------------
 // span records and basis functions

@@ -45,10 +45,10 @@ constexpr int kThreads = 128;
 // the 128^3 degree-3 frame: cap 128 -> 6.33 ms, cap 168 (3 CTAs) -> 7.01 ms, cap 96 (5
 // CTAs, spills) -> 10.4 ms.
 constexpr int kMinBlocks = 4;
-// The cardinal path (variant 6) holds no span records, so more CTAs fit per SM: 5 (102
-// registers) measures best with FP32 storage (5.12 ms on the 128^3 degree-3 1024^2 frame,
-// against 5.18 ms at 4 and 5.29 ms at 6), 4 with 16-bit storage (6.00 against 6.06 ms at 5).
-__host__ __device__ constexpr int card_min_blocks(int storage) { return storage == 1 ? 5 : 4; }
+// The cardinal path (variant 6) holds no span records and would fit more CTAs per SM, but
+// with the packed layer-pair contraction 4 CTAs (128 registers) still measures best on the
+// 128^3 degree-3 1024^2 frame: FP32 4.87 ms against 5.05 ms at 5 CTAs (96 registers, with
+// spills), FP16 5.74 against 5.73 ms.
 
 // Ray-tile shapes (CTA tile, warp tile).  Shape 0 is the default; the autotuner picks one
 // per workload.
@@ -267,11 +267,12 @@ __device__ __forceinline__ float4 sample_colour(const float4* __restrict__ tf, c
     const int i0 = min(static_cast<int>(xx), S.tf_last);
     const float wt = xx - static_cast<float>(i0);
     const float4 c0 = tf[i0], c1 = tf[i0 + 1];
+    // c = c0 + wt (c1 - c0), two channels per packed instruction
+    const f2 w2 = pk2(wt, wt), rg0 = pk2(c0.x, c0.y), ba0 = pk2(c0.z, c0.w);
+    const f2 rg = fma2(w2, sub2(pk2(c1.x, c1.y), rg0), rg0), ba = fma2(w2, sub2(pk2(c1.z, c1.w), ba0), ba0);
     float4 c;
-    c.x = fmaf(wt, c1.x - c0.x, c0.x);
-    c.y = fmaf(wt, c1.y - c0.y, c0.y);
-    c.z = fmaf(wt, c1.z - c0.z, c0.z);
-    c.w = fmaf(wt, c1.w - c0.w, c0.w);
+    upk2(rg, c.x, c.y);
+    upk2(ba, c.z, c.w);
     const float g2 = q.y * q.y + q.z * q.z + q.w * q.w;
     const bool flat = g2 <= S.gtiny2;
     const float ndl = fabsf(q.y * S.lx + q.z * S.ly + q.w * S.lz) * rsqrtf(flat ? 1.0f : g2);
@@ -430,7 +431,8 @@ __device__ __forceinline__ float4 march_cardinal(const ModelDev& M, const Render
     };
 
     float4 q = query_at(0);
-    for (int k = 0; k < ns; ++k) {
+    int k = 0;   // samples composited
+    while (k < ns) {
         const float4 qn = query_at(min(k + 1, ns - 1));
         const float4 c = sample_colour(tf, S, q);
         const float wgt = (1.0f - acc.w) * c.w;
@@ -438,10 +440,11 @@ __device__ __forceinline__ float4 march_cardinal(const ModelDev& M, const Render
         acc.y = fmaf(wgt, c.y, acc.y);
         acc.z = fmaf(wgt, c.z, acc.z);
         acc.w += wgt;
-        ++count;
+        ++k;
         if (acc.w >= ert) break;
         q = qn;
     }
+    count += static_cast<unsigned>(k);
     return acc;
 }
 
@@ -648,8 +651,8 @@ __device__ __forceinline__ void add_count(unsigned long long* dst, unsigned long
 // ----------------------------------------------------------------------------------------
 
 template <int Q, int STORAGE, int MODE>
-__global__ void __launch_bounds__(kThreads, MODE == 6 ? card_min_blocks(STORAGE) : kMinBlocks)
-    k_render(ModelDev M, const __grid_constant__ RenderParams P, int shape)
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_render(ModelDev M, const __grid_constant__ RenderParams P,
+                                                                 int shape)
 {
     __shared__ float4 tf[kTfMax + 1];
     for (int i = threadIdx.x; i < P.s.tf_n; i += kThreads) tf[i] = P.tf[i];
@@ -727,8 +730,8 @@ cudaError_t render_q(const ModelDev& m, const RenderParams& rp, int variant, int
 // repeat until the counter passes the group's last tile.  One kernel per group keeps each
 // degree's (and each path's) register allocation free of the others'.
 template <int Q, int STORAGE, bool CARD>
-__global__ void __launch_bounds__(kThreads, CARD ? card_min_blocks(STORAGE) : kMinBlocks)
-    k_render_batch(BatchHead* __restrict__ table, int group, int shape)
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_batch(BatchHead* __restrict__ table, int group,
+                                                                       int shape)
 {
     __shared__ BatchItem item;
     __shared__ float4 tf[kTfMax + 1];
