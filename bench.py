@@ -60,8 +60,8 @@ RENDER_EXTRA_FLOPS = 40
 # DRAM bytes (read + write) of one k_render launch on this workload, from the ncu capture
 # summarised in profiles/k_render_p3_128cube_persp1024_ns1024.md, valid only for the kernel
 # sources it was taken on (their SHA-256 is checked at run time; any change -> null).
-RENDER_TRAFFIC = {"src_sha256": "be1cd4da798960dfc6539f63210bd23774d026c0d6e7fa07cea4c16b81e5e0f3",
-                  "bytes_per_launch": 8994048}
+RENDER_TRAFFIC = {"src_sha256": "5512bb9d31aaa0112cb8d691f46bed0fd1e9f2f6c1dca82a8bf22b7564a25f24",
+                  "bytes_per_launch": 16107520}
 KERNEL_SOURCES = ["paper_2312_15073_gb300/csrc/render.cu", "paper_2312_15073_gb300/csrc/bspline.cuh",
                   "paper_2312_15073_gb300/csrc/mfa_internal.cuh"]
 
@@ -412,7 +412,7 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": "k_render", "achieved": achieved_tflops, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops, "traffic": render_traffic(),
                      "traffic_note": "DRAM bytes per launch from ncu (model and image stay in L2; "
-                                     "algorithmic bytes: 35 MiB model window + 16 MiB image)",
+                                     "algorithmic bytes: 70 MiB layer-pair model window + 16 MiB image)",
                      "tuned": tuned,
                      "flops_per_sample": flops_sample,
                      "flops_note": "algorithmic count (sum-factorised contraction + span-local Cox-de Boor "

@@ -8,32 +8,29 @@
 //   * k_render: one image, one CTA per tile, the hardware block scheduler hands tiles to
 //     SMs as earlier ones finish (balancing the uneven ray lengths early termination
 //     creates); scalars and the transfer-function table travel as kernel arguments.
-//   * k_render_batch: many images of many models in one persistent launch.  Each CTA
-//     draws tile indices from a device counter in the work table until the batch is
-//     exhausted, loads the tile's request (model, camera, table) into shared memory when
-//     it changes, and dispatches on the model's degree.
+//   * k_render_batch: many images of many models in persistent launches, one kernel per
+//     (degree class, storage type, cardinal or record path) group.  Each CTA draws tile
+//     indices from its group's device counter in the work table until the group is
+//     exhausted, and loads the tile's request (model, camera, table) into shared memory
+//     when it changes.
 //
-// The query is L1-bandwidth bound when every sample reloads its span records (3 x 80 B
-// at degree 3) and its support rows (16 x 16 B): L1 returns 128 B per clock per SM to
-// the registers.  Along one ray each axis keeps the same knot span for several
-// consecutive samples, so each axis's span bounds and record stay in registers and only
-// the lanes whose span changed reload it.  With the loads thinned out the kernel is
-// bound by FP32 issue (about 285 FFMA of about 450 instructions per sample).
-//   variant 6:           uniform knots and one degree (the cardinal path): interior spans
-//                        share one basis, computed from t without a record; the state per
-//                        axis is the span index; software-pipelined like 4
-//   variant 4:           records cached, scalar arithmetic, software-pipelined (the query
-//                        of sample k+1 interleaves with the colour/compositing of sample k)
-//   variant 2:           records cached, scalar arithmetic
-//   variant 1:           records cached, packed FP32x2 arithmetic
-//   variant 3:           nothing cached, scalar arithmetic
-//   variant 5:           per-warp control-point bricks in shared memory (below)
-// The default (variant 0) is 6 where the cardinal path applies, else 4.
-// Variant 4 measures 2 % faster than 2 (6.13 vs 6.28 ms per 1024^2 frame).
-// Packed FP32x2 halves the FMA instructions issued but each one holds the FMA pipe for
-// two cycles, and pairing the y-pass adds lane work, so on GB300 it measures 2-6 % slower
-// than the scalar form on the 128^3 degree-3 frame (ncu: math-pipe-throttle stalls).
-// Variant 3 re-reads every record per sample and is L1 bound.
+// Per sample the kernel is bound by FP32 issue and the FMA pipe once the loads are thinned
+// out: along one ray each axis keeps the same knot span for several consecutive samples,
+// so the per-axis span state stays in registers and only the lanes whose span changed
+// reload anything, and the (p+1)^3 contraction runs on packed FP32x2 instructions fed
+// directly by the layer-pair window layout (bspline.cuh).  Variants (one contraction):
+//   variant 6:  uniform knots and one degree (the cardinal path): interior spans share one
+//               basis, computed from t without a record; the state per axis is the span
+//               index; software-pipelined like 4
+//   variant 4:  span records cached in registers, software-pipelined (the query of sample
+//               k+1 interleaves with the colour and compositing of sample k)
+//   variant 2:  records cached
+//   variant 1:  records cached, the z basis evaluated directly as function pairs
+//   variant 3:  nothing cached (records re-read per sample)
+//   variant 5:  per-warp control-point bricks in shared memory (below)
+// The default (variant 0) is 6 where the cardinal path applies, else 4.  ncu launch times
+// on the 128^3 degree-3 FP32 frame (1024^2, 1024 samples, Phong): 6: 4.9 ms, 4: 5.6, 1: 5.7,
+// 2: 5.8, 5: 6.9, 3: 7.6.
 #include "bspline.cuh"
 
 namespace mfa {
