@@ -353,7 +353,9 @@ def run_ours(args):
         total_s, units = aggregate_replicas(total_s, units, dist, "cuda")
     value = units / total_s
 
-    # end to end through the public API with host buffers (pinned), copies inside the region
+    # end to end through the C ABI's host-buffer calls (page-locked host memory, the library
+    # stages the copies): the render and the decode of a step are enqueued on two streams
+    # and overlap; copies in and out are inside the timed region
     pts_h = torch.from_numpy(wl.decode_points).pin_memory()
     img_h = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
     val_h = torch.empty(n_pts, dtype=torch.float32).pin_memory()
@@ -361,17 +363,19 @@ def run_ours(args):
     e2e_steps = max(2, min(args.steps, 5))
     e2e_ms = []
     cnt_e = torch.zeros(1, dtype=torch.int64, device="cuda")
+    side = torch.cuda.Stream()
     for k in range(e2e_steps + 1):
         flush.zero_()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        pts_d.copy_(pts_h, non_blocking=True)
-        mfa.render(model, job.camera, tf, W, H, NS, out=img_d, samples_out=cnt_e, **kernel)
-        mfa.decode(model, pts_d, val_d, grad_d)
-        img_h.copy_(img_d, non_blocking=True)
-        val_h.copy_(val_d, non_blocking=True)
-        grad_h.copy_(grad_d, non_blocking=True)
+        side.wait_event(a)
+        mfa.render_host(model, job.camera, tf, W, H, NS, out=img_h, samples_out=cnt_e, sync=False, **kernel)
+        with torch.cuda.stream(side):
+            mfa.decode_host(model, pts_h, val_h, grad_h, sync=False)
+        joined = torch.cuda.Event()
+        joined.record(side)
+        stream.wait_event(joined)
         b.record(stream)
         b.synchronize()
         if k > 0:                                          # first pass warms the copy engines
@@ -422,7 +426,9 @@ def run_ours(args):
                      "peak_at_median_clock": (SMS * FP32_LANES * 2 * clk["sm_mhz"] * 1e6 / 1e12)
                      if clk["sm_mhz"] else None},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": statistics.mean(e2e_ms)},
+                "ms_per_step": statistics.mean(e2e_ms),
+                "path": "mfa_render_host + mfa_decode_host (page-locked host buffers, library-staged "
+                        "copies), enqueued on two streams so that they overlap"},
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
     }

@@ -187,6 +187,27 @@ int mfa_render_ex(const mfa_model* model, const mfa_camera* camera, const mfa_tr
                   int width, int height, int n_samples, float* rgba_out, const mfa_render_opts* opts);
 
 /*
+ * Host-buffer forms of mfa_decode and mfa_render_ex: the same queries (Sec. III-B, the
+ * query of Fig. 8 in Sec. V-D.3) and the same ray casting (Sec. IV-A.4), for data in HOST
+ * memory.
+ *   mfa_decode_host: pts HOST n * 3 FP32, val HOST n FP32, grad HOST n * 3 FP32 or NULL;
+ *   mfa_render_host: rgba_out HOST [height][width][4] FP32; opts as mfa_render_ex (may be
+ *   NULL; its samples_out, if set, is still a DEVICE counter).
+ * The library stages the data through device memory of its own (a per-device pool kept
+ * cached between calls) and, for decode, pipelines copy-in, kernel and copy-out over
+ * chunks of 2^21 points on helper streams of the calling thread.  Both calls are
+ * asynchronous on the bound stream, like cudaMemcpyAsync: they return once the work is
+ * enqueued, and the host buffers must stay valid -- inputs unchanged, outputs unread --
+ * until that stream has been synchronised.  Page-locked host buffers let the copies run
+ * beside the kernels; pageable ones work, with serialised copies.  Argument errors are
+ * reported as by mfa_decode / mfa_render_ex before any work is enqueued; n = 0 is a no-op.
+ * The caller keeps ownership of every buffer.
+ */
+int mfa_decode_host(const mfa_model* model, const float* pts, long long n, float* val, float* grad);
+int mfa_render_host(const mfa_model* model, const mfa_camera* camera, const mfa_transfer_fn* tf,
+                    int width, int height, int n_samples, float* rgba_out, const mfa_render_opts* opts);
+
+/*
  * Batched rendering: many images of many models in one persistent launch (the paper
  * renders one partition per core, Sec. IV-A.4; on one GPU the unit of parallel work is a
  * ray tile).  A request is one mfa_render call's worth of arguments.

@@ -114,6 +114,11 @@ def lib():
         L.mfa_render_ex.restype = c_int
         L.mfa_render_ex.argtypes = [c_void_p, POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int, c_void_p,
                                     POINTER(_Opts)]
+        L.mfa_decode_host.restype = c_int
+        L.mfa_decode_host.argtypes = [c_void_p, c_void_p, c_longlong, c_void_p, c_void_p]
+        L.mfa_render_host.restype = c_int
+        L.mfa_render_host.argtypes = [c_void_p, POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int, c_void_p,
+                                      POINTER(_Opts)]
         L.mfa_batch_create.restype = c_void_p
         L.mfa_batch_create.argtypes = [c_int]
         L.mfa_batch_configure.restype = c_int
@@ -319,6 +324,62 @@ def render(model: Model, cam, tf: transfer_fn, width: int, height: int, n_sample
     _bind_stream()
     _check(lib().mfa_render_ex(model.handle, ctypes.byref(c), ctypes.byref(tf.struct), width, height, n_samples,
                                out.data_ptr(), ctypes.byref(opts)))
+    return out
+
+
+def _host_ptr(t, shape_tail, name):
+    import torch
+    if t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous FP32 CPU tensor")
+    if shape_tail is not None and tuple(t.shape[1:]) != shape_tail:
+        raise ValueError(f"{name} must have shape (n, {shape_tail[0]})")
+    return t.data_ptr()
+
+
+def decode_host(model: Model, pts, val=None, grad=None, want_grad: bool = True, sync: bool = True):
+    """decode() for HOST data: pts (n, 3) FP32 CPU tensor (page-locked for overlapped copies);
+    returns CPU tensors val (n,) and grad (n, 3) (allocated page-locked if not given).  The
+    library stages and pipelines the copies; with sync=False the call only enqueues the work
+    on the current stream, which must be synchronised before the outputs are read."""
+    import torch
+    n = pts.shape[0]
+    pin = pts.is_pinned()
+    if val is None:
+        val = torch.empty(n, dtype=torch.float32, pin_memory=pin)
+    if grad is None and want_grad:
+        grad = torch.empty((n, 3), dtype=torch.float32, pin_memory=pin)
+    _bind_stream()
+    _check(lib().mfa_decode_host(model.handle, _host_ptr(pts, (3,), "pts"), n, _host_ptr(val, None, "val"),
+                                 _host_ptr(grad, (3,), "grad") if grad is not None else None))
+    if sync:
+        torch.cuda.current_stream().synchronize()
+    return val, grad
+
+
+def render_host(model: Model, cam, tf: transfer_fn, width: int, height: int, n_samples: int, out=None,
+                samples_out=None, variant: int = 0, tile_shape: int = 0, use_tuned: bool = False, sync: bool = True):
+    """render() into a HOST image: out (height, width, 4) FP32 CPU tensor (allocated
+    page-locked if not given).  With sync=False the call only enqueues the work on the
+    current stream, which must be synchronised before the image is read."""
+    import torch
+    if out is None:
+        out = torch.empty((height, width, 4), dtype=torch.float32, pin_memory=True)
+    if out.numel() != height * width * 4:
+        raise ValueError("out must hold (height, width, 4) FP32 values")
+    c = cam if isinstance(cam, _Camera) else camera(cam)
+    opts = _Opts()
+    opts.variant = int(variant)
+    opts.tile_shape = int(tile_shape)
+    opts.use_tuned = 1 if use_tuned else 0
+    if samples_out is not None:
+        if not (samples_out.is_cuda and samples_out.dtype == torch.int64):
+            raise TypeError("samples_out must be an int64 CUDA tensor")
+        opts.samples_out = samples_out.data_ptr()
+    _bind_stream()
+    _check(lib().mfa_render_host(model.handle, ctypes.byref(c), ctypes.byref(tf.struct), width, height, n_samples,
+                                 _host_ptr(out, None, "out"), ctypes.byref(opts)))
+    if sync:
+        torch.cuda.current_stream().synchronize()
     return out
 
 

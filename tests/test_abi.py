@@ -58,6 +58,11 @@ def test_host_side_argument_checks(libmfa):
     cam = mfa.camera(dict(projection=0, eye=(0, 0, 2), target=(0, 0, 0), up=(0, 1, 0), ortho_height=1.0))
     tf = mfa.transfer_fn(np.zeros((4, 4)))
     assert L.mfa_render(None, ctypes.byref(cam), ctypes.byref(tf.struct), 8, 8, 8, None) == -1
+    # host-buffer forms check the same way, before any device work
+    assert L.mfa_decode_host(None, None, 10, None, None) == -1
+    assert L.mfa_decode_host(None, None, -3, None, None) == -1
+    assert L.mfa_render_host(None, ctypes.byref(cam), ctypes.byref(tf.struct), 8, 8, 8, None, None) == -1
+    assert "NULL" in L.mfa_last_error().decode()
     # model creation rejects bad degrees, counts and knots before any device work
     deg = (ctypes.c_int * 3)(3, 3, 5)
     nc = (ctypes.c_int * 3)(8, 8, 8)
