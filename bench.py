@@ -56,6 +56,9 @@ def query_flops(p: int) -> int:
 
 
 RENDER_EXTRA_FLOPS = 40
+# window bytes a degree-p FP32 query gathers: ceil(q/2) layer pairs x q rows x one entry
+# (16 bytes at p = 1, 32 at p = 2, 3, 32 + 16 at p = 4)
+DECODE_WINDOW_BYTES = {1: 1 * 2 * 16, 2: 2 * 3 * 32, 3: 2 * 4 * 32, 4: 3 * 5 * 48}
 
 # DRAM bytes (read + write) of one k_render launch on this workload, from the ncu capture
 # summarised in profiles/k_render_p3_128cube_persp1024_ns1024.md, valid only for the kernel
@@ -212,7 +215,20 @@ def oracle_rates(wl, budget_s: float, seed: int = 7):
     t = time.perf_counter()
     ref.decode(pts, nthreads=threads)
     td = time.perf_counter() - t
-    info = dict(pixels=npx, render_samples=ns1, render_s=t1, decode_points=len(pts), decode_s=td, threads=threads)
+    # the same on one core, on a smaller sample (about 15 % of the budget)
+    npx1 = max(64, min(W * H, int(0.1 * budget_s * rate0 / threads / max(1.0, ns1 / npx))))
+    pix1 = rng.choice(W * H, npx1, replace=False)
+    t = time.perf_counter()
+    _, ns_1 = oracle.render(ref, job.camera, job.tf, W, H, job.n_samples, shading=job.shading, ka=job.ka, kd=job.kd,
+                            ks=job.ks, shininess=job.shininess, ert_alpha=job.ert_alpha, pixels=pix1, nthreads=1)
+    t_1 = time.perf_counter() - t
+    pts1 = pts[:max(1024, len(pts) // threads // 4)]
+    t = time.perf_counter()
+    ref.decode(pts1, nthreads=1)
+    td_1 = time.perf_counter() - t
+    info = dict(pixels=npx, render_samples=ns1, render_s=t1, decode_points=len(pts), decode_s=td, threads=threads,
+                one_core=dict(pixels=npx1, render_samples=ns_1, render_s=t_1, decode_points=len(pts1), decode_s=td_1,
+                              render_rate=ns_1 / t_1, decode_rate=len(pts1) / td_1))
     return ns1 / t1, len(pts) / td, info
 
 
@@ -305,6 +321,9 @@ def run_ours(args):
     img_d = torch.empty((H, W, 4), device="cuda")
     cnt_d = torch.zeros(1, dtype=torch.int64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    # measured denominators beside the derived FP32 peak (calibration kernels, untimed)
+    peaks = mfa.measure_peaks()
 
     # the autotuner picks the kernel variant and ray-tile shape for this workload class
     # (outside the timed region); the timed renders then use its choice, unless the command
@@ -424,7 +443,18 @@ def run_ours(args):
                                    "cardinal path executes 42 instead of 126 basis flops per sample",
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
                      "peak_at_median_clock": (SMS * FP32_LANES * 2 * clk["sm_mhz"] * 1e6 / 1e12)
-                     if clk["sm_mhz"] else None},
+                     if clk["sm_mhz"] else None,
+                     "measured_fma": {"tflops": peaks["fp32_tflops"], "fp32x2_tflops": peaks["fp32x2_tflops"],
+                                      "clock_mhz": peaks["fma_clock_mhz"],
+                                      "frac": achieved_tflops / peaks["fp32_tflops"],
+                                      "note": "chip-wide FFMA / packed FFMA2 calibration kernels in this run"}},
+        "decode_l2": {"bytes_per_query": DECODE_WINDOW_BYTES[spec.degree[0]],
+                      "achieved_gbs": DECODE_WINDOW_BYTES[spec.degree[0]] * n_pts / (statistics.mean(decode_ms) / 1e3) / 1e9,
+                      "l2_gather_peak_gbs": peaks["l2_gather_gbs"],
+                      "frac": DECODE_WINDOW_BYTES[spec.degree[0]] * n_pts / (statistics.mean(decode_ms) / 1e3) / 1e9
+                      / peaks["l2_gather_gbs"],
+                      "note": "decode reads its support as random 32-byte window entries (8 at degree 3, FP32); "
+                              "peak = random 32-byte gathers from an L2-resident buffer"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.mean(e2e_ms),
                 "path": "mfa_render_host + mfa_decode_host (page-locked host buffers, library-staged "
@@ -443,12 +473,18 @@ def run_ours(args):
     if ws == 1 and not args.no_cpu_baseline:
         r_rate, d_rate, info = oracle_rates(wl, budget_s=args.cpu_budget)
         cpu_step_s = samples_per_frame / r_rate + n_pts / d_rate
+        o1 = info["one_core"]
+        one_step_s = samples_per_frame / o1["render_rate"] + n_pts / o1["decode_rate"]
         line["cpu_baseline"] = {
             "value": (samples_per_frame + n_pts) / cpu_step_s, "unit": UNIT, "cores": info["threads"],
             "kind": "oracle",
             "sample": (f"FP64 oracle: {info['pixels']} seeded pixels of the frame ({info['render_samples']} samples, "
                        f"{info['render_s']:.1f} s) + {info['decode_points']} decode points ({info['decode_s']:.1f} s); "
                        "step time extrapolated from the two rates"),
+            "one_core": {"value": (samples_per_frame + n_pts) / one_step_s, "unit": UNIT, "cores": 1,
+                         "sample": (f"{o1['pixels']} seeded pixels ({o1['render_samples']} samples, "
+                                    f"{o1['render_s']:.1f} s) + {o1['decode_points']} decode points "
+                                    f"({o1['decode_s']:.1f} s) on one thread")},
         }
     print(json.dumps(line), flush=True)
     if dist:

@@ -366,6 +366,23 @@ void mfa_server_destroy(mfa_server* server);
  */
 int mfa_render_batch_static(const mfa_render_request* reqs, int n);
 
+/*
+ * Calibration for the roofline denominators (no counterpart in the paper: measurement
+ * infrastructure).  Runs, on the current device and the bound stream, a chip-wide FP32
+ * FMA kernel (scalar and packed FP32x2 forms) and a kernel of random 32-byte gathers from
+ * a 32 MiB buffer held in L2, each timed with CUDA events after a warm-up launch, and
+ * synchronises the stream.  Allocates and frees about 45 MB of device memory.
+ * MFA_ERR_ARG on NULL; MFA_ERR_CUDA / MFA_ERR_NOMEM on a failed CUDA call.
+ */
+typedef struct {
+    double fp32_tflops;     /* scalar FFMA rate, 2 flops per FMA */
+    double fp32x2_tflops;   /* packed fma.rn.f32x2 rate, 4 flops per instruction */
+    double l2_gather_gbs;   /* bytes of random 32-byte entries served per second */
+    double fma_clock_mhz;   /* fp32_tflops / (SMs x 128 lanes x 2 flops) */
+    int sm_count;
+} mfa_peaks;
+int mfa_measure_peaks(mfa_peaks* out);
+
 /* Text of the last error on the calling thread ("" if none). */
 const char* mfa_last_error(void);
 

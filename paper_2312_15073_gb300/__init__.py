@@ -76,6 +76,11 @@ class _ServerStats(ctypes.Structure):
                                           "arena_bytes_in_use")]
 
 
+class _Peaks(ctypes.Structure):
+    _fields_ = [("fp32_tflops", ctypes.c_double), ("fp32x2_tflops", ctypes.c_double),
+                ("l2_gather_gbs", ctypes.c_double), ("fma_clock_mhz", ctypes.c_double), ("sm_count", c_int)]
+
+
 class _Info(ctypes.Structure):
     _fields_ = [("degree", c_int * 3), ("nctrl", c_int * 3), ("storage", c_int), ("vmin", c_float),
                 ("vmax", c_float), ("device_bytes", c_size_t), ("device", c_int), ("cardinal", c_int)]
@@ -114,6 +119,8 @@ def lib():
         L.mfa_render_ex.restype = c_int
         L.mfa_render_ex.argtypes = [c_void_p, POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int, c_void_p,
                                     POINTER(_Opts)]
+        L.mfa_measure_peaks.restype = c_int
+        L.mfa_measure_peaks.argtypes = [POINTER(_Peaks)]
         L.mfa_decode_host.restype = c_int
         L.mfa_decode_host.argtypes = [c_void_p, c_void_p, c_longlong, c_void_p, c_void_p]
         L.mfa_render_host.restype = c_int
@@ -325,6 +332,16 @@ def render(model: Model, cam, tf: transfer_fn, width: int, height: int, n_sample
     _check(lib().mfa_render_ex(model.handle, ctypes.byref(c), ctypes.byref(tf.struct), width, height, n_samples,
                                out.data_ptr(), ctypes.byref(opts)))
     return out
+
+
+def measure_peaks() -> dict:
+    """Calibration kernels for the roofline denominators on the current device: FP32 FMA
+    rate (scalar and packed FP32x2) and the L2 rate of random 32-byte gathers."""
+    p = _Peaks()
+    _bind_stream()
+    _check(lib().mfa_measure_peaks(ctypes.byref(p)))
+    return dict(fp32_tflops=p.fp32_tflops, fp32x2_tflops=p.fp32x2_tflops, l2_gather_gbs=p.l2_gather_gbs,
+                fma_clock_mhz=p.fma_clock_mhz, sm_count=p.sm_count)
 
 
 def _host_ptr(t, shape_tail, name):
