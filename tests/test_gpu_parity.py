@@ -370,3 +370,33 @@ def test_cardinal_flag(mfa, orc):
     assert not mfa.Model((2, 3, 3), n, None, P).info()["cardinal"]
     nonu = [synth.knots_nonuniform(n[a], 3, rng) for a in range(3)]
     assert not mfa.Model((3, 3, 3), n, nonu, P).info()["cardinal"]
+
+
+def _random_config(seed):
+    rng = np.random.default_rng(seed)
+    degree = tuple(int(d) for d in rng.integers(1, 5, 3)) if rng.random() < 0.5 else (int(rng.integers(1, 5)),) * 3
+    nctrl = tuple(int(degree[a] + 1 + rng.integers(0, 36)) for a in range(3))
+    uniform = tuple(bool(u) for u in rng.random(3) < 0.6)
+    storage = int(rng.integers(1, 4))
+    return rng, degree, nctrl, uniform, storage
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_random_models_against_oracle(mfa, orc, seed):
+    """Seeded random models -- degrees 1-4 (mixed per axis or not), 2 to 40 control points
+    per axis, uniform and non-uniform knots per axis, every storage type -- decoded at random
+    and edge points and rendered from a random perspective view, against the oracle on the
+    same stored control points."""
+    import torch
+    rng, degree, nctrl, uniform, storage = _random_config(1000 + seed)
+    model, ref, _ = _make(mfa, orc, rng, degree, nctrl, uniform, storage)
+    pts = _edge_points(ref.knots, rng, 3000)
+    val, grad = mfa.decode(model, torch.from_numpy(pts).cuda())
+    v_ref, g_ref = ref.decode(pts)
+    assert value_error(val.cpu().numpy(), v_ref, ref.ctrl) <= VALUE_TOL
+    assert grad_error(grad.cpu().numpy(), g_ref) <= GRAD_TOL
+    cam = _camera("persp", rng)
+    job = synth.RenderJob(cam, 29, 21, int(rng.integers(16, 200)), synth.ramp_tf(256, 0.1), bool(seed % 2))
+    g, r, gc, rc = _render_both(mfa, orc, model, ref, job)
+    assert np.all(image_rmse(g, r) <= IMAGE_RMSE_TOL), (degree, nctrl, uniform, storage)
+    assert abs(gc - rc) <= max(2, 1e-3 * rc)
