@@ -90,6 +90,12 @@ def _load():
         lib.orc_render.restype = c_longlong
         lib.orc_render.argtypes = [POINTER(_Model), POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int,
                                    c_void_p, c_longlong, c_void_p, c_int]
+        lib.orc_render_segments.restype = c_longlong
+        lib.orc_render_segments.argtypes = [POINTER(_Model), POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int,
+                                            c_void_p, c_void_p, c_longlong, c_void_p, c_int]
+        lib.orc_block_range.restype = None
+        lib.orc_block_range.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_double, c_int,
+                                        POINTER(c_int), POINTER(c_int)]
         _lib = lib
     return _lib
 
@@ -251,6 +257,49 @@ def render(model: Model, cam: dict, tf_rgba, width: int, height: int, n_samples:
     ns = _load().orc_render(ctypes.byref(model._s), ctypes.byref(cam_s), ctypes.byref(tf), width, height,
                             n_samples, pix_ptr, npix, _ptr(out), nthreads or default_threads())
     return out, int(ns)
+
+
+def render_segments(model: Model, cam: dict, tf_rgba, width: int, height: int, n_samples: int, blocks, *,
+                    shading: bool = False, ka=0.3, kd=0.6, ks=0.3, shininess=32.0, ert_alpha=0.99,
+                    vmin=math.nan, vmax=math.nan, pixels=None, nthreads: int | None = None):
+    """render() with the volume split into blocks[0] x blocks[1] x blocks[2] equal blocks,
+    each rendering its segment of every ray (early termination per segment), the partial
+    images merged with over nearest segment first.  Returns (rgba, samples evaluated)."""
+    tf_rgba = np.ascontiguousarray(tf_rgba, dtype=np.float32).reshape(-1, 4)
+    tf = _TF()
+    tf.n_entries = tf_rgba.shape[0]
+    tf.rgba = _ptr(tf_rgba)
+    tf.vmin = vmin
+    tf.vmax = vmax
+    tf.shading = 1 if shading else 0
+    tf.ka, tf.kd, tf.ks, tf.shininess = ka, kd, ks, shininess
+    tf.ert_alpha = ert_alpha
+    cam_s = _camera(cam)
+    g = np.ascontiguousarray(blocks, dtype=np.int32)
+    if pixels is None:
+        out = np.zeros((height, width, 4))
+        npix, pix_ptr = width * height, None
+    else:
+        pixels = np.ascontiguousarray(pixels, dtype=np.int64)
+        out = np.zeros((len(pixels), 4))
+        npix, pix_ptr = len(pixels), _ptr(pixels)
+    ns = _load().orc_render_segments(ctypes.byref(model._s), ctypes.byref(cam_s), ctypes.byref(tf), width, height,
+                                     n_samples, _ptr(g), pix_ptr, npix, _ptr(out), nthreads or default_threads())
+    if ns < 0:
+        raise ValueError("blocks must be >= 1 per axis and at most 512 in total")
+    return out, int(ns)
+
+
+def block_range(blocks, block, o, d, t0: float, dt: float, n_samples: int):
+    """Sample index range [kb, ke) that block `block` of the blocks grid renders on the ray
+    (o, d) whose samples sit at t0 + (k + 1/2) dt."""
+    g = np.ascontiguousarray(blocks, dtype=np.int32)
+    bi = np.ascontiguousarray(block, dtype=np.int32)
+    o, d = _f64(o), _f64(d)
+    kb, ke = c_int(), c_int()
+    _load().orc_block_range(_ptr(g), _ptr(bi), _ptr(o), _ptr(d), float(t0), float(dt), int(n_samples),
+                            ctypes.byref(kb), ctypes.byref(ke))
+    return kb.value, ke.value
 
 
 # ------------------------------------------------------------------------------------------

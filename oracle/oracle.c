@@ -388,6 +388,34 @@ static void tf_lookup(const orc_tf* tf, double f, double c[4])
 
 static double clamp01(double x) { return x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x); }
 
+/* Colour of the sample at ray parameter t (transfer function, then Phong if enabled). */
+static void orc_sample_colour(const orc_model* m, const orc_tf* tf, const double o[3], const double d[3],
+                          double t, double gtiny, double c[4])
+{
+    double x[3] = { o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2] };
+    double q[4];
+    orc_eval(m, x, q, NULL);
+    tf_lookup(tf, q[0], c);
+    if (tf->shading) {
+        double g[3] = { q[1], q[2], q[3] };
+        double gn = sqrt(dot3(g, g));
+        double factor, spec = 0.0;
+        if (gn <= gtiny) {
+            factor = tf->ka + tf->kd;
+        } else {
+            double n[3] = { g[0] / gn, g[1] / gn, g[2] / gn };
+            double L[3] = { -d[0], -d[1], -d[2] };
+            double ndl = dot3(n, L);
+            if (ndl < 0.0) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; ndl = -ndl; }
+            double R[3] = { 2.0 * ndl * n[0] - L[0], 2.0 * ndl * n[1] - L[1], 2.0 * ndl * n[2] - L[2] };
+            double rv = dot3(R, L);   /* V = L for a headlight */
+            spec = rv > 0.0 ? pow(rv, tf->shininess) : 0.0;
+            factor = tf->ka + tf->kd * ndl;
+        }
+        for (int ch = 0; ch < 3; ++ch) c[ch] = clamp01(c[ch] * factor + tf->ks * spec);
+    }
+}
+
 /* One pixel: returns premultiplied RGBA and the number of samples evaluated. */
 static long long orc_render_pixel(const orc_model* m, const orc_camera* cam, const orc_tf* tf,
                                   int W, int H, int ns, int col, int row, double gtiny, double rgba[4])
@@ -400,31 +428,9 @@ static long long orc_render_pixel(const orc_model* m, const orc_camera* cam, con
     double C[3] = { 0.0, 0.0, 0.0 }, A = 0.0;
     long long count = 0;
     for (int k = 0; k < ns; ++k) {
-        double t = t0 + (k + 0.5) * dt;
-        double x[3] = { o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2] };
-        double q[4];
-        orc_eval(m, x, q, NULL);
-        ++count;
         double c[4];
-        tf_lookup(tf, q[0], c);
-        if (tf->shading) {
-            double g[3] = { q[1], q[2], q[3] };
-            double gn = sqrt(dot3(g, g));
-            double factor, spec = 0.0;
-            if (gn <= gtiny) {
-                factor = tf->ka + tf->kd;
-            } else {
-                double n[3] = { g[0] / gn, g[1] / gn, g[2] / gn };
-                double L[3] = { -d[0], -d[1], -d[2] };
-                double ndl = dot3(n, L);
-                if (ndl < 0.0) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; ndl = -ndl; }
-                double R[3] = { 2.0 * ndl * n[0] - L[0], 2.0 * ndl * n[1] - L[1], 2.0 * ndl * n[2] - L[2] };
-                double rv = dot3(R, L);   /* V = L for a headlight */
-                spec = rv > 0.0 ? pow(rv, tf->shininess) : 0.0;
-                factor = tf->ka + tf->kd * ndl;
-            }
-            for (int ch = 0; ch < 3; ++ch) c[ch] = clamp01(c[ch] * factor + tf->ks * spec);
-        }
+        orc_sample_colour(m, tf, o, d, t0 + (k + 0.5) * dt, gtiny, c);
+        ++count;
         double a = c[3];
         for (int ch = 0; ch < 3; ++ch) C[ch] += (1.0 - A) * a * c[ch];
         A += (1.0 - A) * a;
@@ -451,9 +457,9 @@ static void orc_render_body(void* vctx, long long b, long long e, long long* cou
 
 /* Renders the pixels listed in pix (indices row*W + col), or all W*H pixels when pix is
  * NULL, into out (npix * 4 doubles).  Returns the number of samples evaluated. */
-long long orc_render(const orc_model* m, const orc_camera* cam, const orc_tf* tf_in,
-                     int W, int H, int ns, const long long* pix, long long npix,
-                     double* out, int nthreads)
+/* The transfer function with vmin/vmax filled in from the control points where NaN, and
+ * the gradient-norm threshold below which the normal is undefined. */
+static void orc_prepare_tf(const orc_model* m, const orc_tf* tf_in, orc_tf* tf_out, double* gtiny_out)
 {
     const long long total = (long long)m->n[0] * m->n[1] * m->n[2];
     double pmin = m->P[0], pmax = m->P[0];
@@ -469,8 +475,145 @@ long long orc_render(const orc_model* m, const orc_camera* cam, const orc_tf* tf
     double scale = pmax - pmin;
     if (fabs(pmax) > scale) scale = fabs(pmax);
     if (fabs(pmin) > scale) scale = fabs(pmin);
-    double gtiny = 1e-6 * scale * spans;
+    *tf_out = tf;
+    *gtiny_out = 1e-6 * scale * spans;
+}
+
+long long orc_render(const orc_model* m, const orc_camera* cam, const orc_tf* tf_in,
+                     int W, int H, int ns, const long long* pix, long long npix,
+                     double* out, int nthreads)
+{
+    orc_tf tf;
+    double gtiny;
+    orc_prepare_tf(m, tf_in, &tf, &gtiny);
     if (!pix) npix = (long long)W * H;
     orc_render_ctx ctx = { m, cam, &tf, W, H, ns, pix, gtiny, out };
     return orc_parallel(npix, 16, nthreads, orc_render_body, &ctx);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Object-space decomposition (Sec. IV-A.1, IV-A.4, IV-A.5)                              */
+/* ------------------------------------------------------------------------------------ */
+/*
+ * The volume is split into g[0] x g[1] x g[2] equal blocks of the unit box (block
+ * (i, j, k) covers [i/g0, (i+1)/g0] x [j/g1, (j+1)/g1] x [k/g2, (k+1)/g2]).  Each block
+ * renders, for every ray, the segment of the ray's samples that lies in it -- front to
+ * back, with early termination on the segment's own accumulated alpha -- into a partial
+ * image, and the partial images are combined per pixel with the over operation in front-
+ * to-back order of the segments (the associativity of over, Sec. IV-A.5).  Sample k of a
+ * ray stays where the single-pass render puts it, t_k = t0 + (k + 1/2) dt.  The split
+ * between two neighbouring blocks is the sample index
+ *     K(t_b) = clamp(ceil((t_b - t0)/dt - 1/2), 0, n_s),
+ * t_b the ray parameter at their common plane, so the blocks' index ranges partition
+ * 0..n_s-1 (a block face on the box boundary gives 0 or n_s; a ray parallel to an axis's
+ * planes stays in the slab holding its origin, the top slab keeping the coordinate 1).
+ */
+#define ORC_MAX_BLOCKS 512
+
+static int orc_split_index(double tb, double t0, double dt, int ns)
+{
+    double k = ceil((tb - t0) / dt - 0.5);
+    if (!(k >= 0.0)) return 0;
+    if (k > ns) return ns;
+    return (int)k;
+}
+
+/* Sample index range [*kb, *ke) of block bi on the ray (o, d) with samples t0 + (k+1/2) dt. */
+void orc_block_range(const int g[3], const int bi[3], const double o[3], const double d[3], double t0, double dt,
+                     int ns, int* kb, int* ke)
+{
+    int lo_k = 0, hi_k = ns;
+    for (int a = 0; a < 3; ++a) {
+        const double lo = (double)bi[a] / g[a], hi = (double)(bi[a] + 1) / g[a];
+        int k_in, k_out;
+        if (d[a] > 0.0) {
+            k_in = bi[a] == 0 ? 0 : orc_split_index((lo - o[a]) / d[a], t0, dt, ns);
+            k_out = bi[a] == g[a] - 1 ? ns : orc_split_index((hi - o[a]) / d[a], t0, dt, ns);
+        } else if (d[a] < 0.0) {
+            k_in = bi[a] == g[a] - 1 ? 0 : orc_split_index((hi - o[a]) / d[a], t0, dt, ns);
+            k_out = bi[a] == 0 ? ns : orc_split_index((lo - o[a]) / d[a], t0, dt, ns);
+        } else {
+            const int inside = (o[a] >= lo && o[a] < hi) || (bi[a] == g[a] - 1 && o[a] == hi);
+            k_in = inside ? 0 : ns;
+            k_out = inside ? ns : 0;
+        }
+        if (k_in > lo_k) lo_k = k_in;
+        if (k_out < hi_k) hi_k = k_out;
+    }
+    *kb = lo_k;
+    *ke = hi_k;
+}
+
+static long long orc_render_pixel_segments(const orc_model* m, const orc_camera* cam, const orc_tf* tf, int W,
+                                           int H, int ns, const int g[3], int col, int row, double gtiny,
+                                           double rgba[4])
+{
+    double o[3], d[3], t0, t1;
+    rgba[0] = rgba[1] = rgba[2] = rgba[3] = 0.0;
+    orc_ray(cam, W, H, col, row, o, d);
+    if (!orc_clip_unit_box(o, d, &t0, &t1)) return 0;
+    const double dt = (t1 - t0) / ns;
+    const int nb = g[0] * g[1] * g[2];
+    int kb[ORC_MAX_BLOCKS], ke[ORC_MAX_BLOCKS], done[ORC_MAX_BLOCKS];
+    double part[ORC_MAX_BLOCKS][4];
+    long long count = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int bi[3] = { b % g[0], (b / g[0]) % g[1], b / (g[0] * g[1]) };
+        orc_block_range(g, bi, o, d, t0, dt, ns, &kb[b], &ke[b]);
+        done[b] = kb[b] >= ke[b];
+        double C[3] = { 0.0, 0.0, 0.0 }, A = 0.0;
+        for (int k = kb[b]; k < ke[b]; ++k) {   /* the block's segment, front to back */
+            double c[4];
+            orc_sample_colour(m, tf, o, d, t0 + (k + 0.5) * dt, gtiny, c);
+            ++count;
+            double a = c[3];
+            for (int ch = 0; ch < 3; ++ch) C[ch] += (1.0 - A) * a * c[ch];
+            A += (1.0 - A) * a;
+            if (tf->ert_alpha < 1.0 && A >= tf->ert_alpha) break;
+        }
+        part[b][0] = C[0]; part[b][1] = C[1]; part[b][2] = C[2]; part[b][3] = A;
+    }
+    /* over of the partial images, nearest segment first */
+    double C[3] = { 0.0, 0.0, 0.0 }, A = 0.0;
+    for (;;) {
+        int next = -1;
+        for (int b = 0; b < nb; ++b)
+            if (!done[b] && (next < 0 || kb[b] < kb[next])) next = b;
+        if (next < 0) break;
+        done[next] = 1;
+        for (int ch = 0; ch < 3; ++ch) C[ch] += (1.0 - A) * part[next][ch];
+        A += (1.0 - A) * part[next][3];
+    }
+    rgba[0] = C[0]; rgba[1] = C[1]; rgba[2] = C[2]; rgba[3] = A;
+    return count;
+}
+
+typedef struct {
+    const orc_model* m; const orc_camera* cam; const orc_tf* tf;
+    int W, H, ns; const int* g; const long long* pix; double gtiny; double* out;
+} orc_segments_ctx;
+
+static void orc_segments_body(void* vctx, long long b, long long e, long long* counter)
+{
+    orc_segments_ctx* c = (orc_segments_ctx*)vctx;
+    for (long long i = b; i < e; ++i) {
+        long long p = c->pix ? c->pix[i] : i;
+        int col = (int)(p % c->W), row = (int)(p / c->W);
+        *counter += orc_render_pixel_segments(c->m, c->cam, c->tf, c->W, c->H, c->ns, c->g, col, row, c->gtiny,
+                                              &c->out[4 * i]);
+    }
+}
+
+/* orc_render with the volume split into g[0] x g[1] x g[2] blocks (at most 512) rendered
+ * as separate segments and merged with over.  Returns the samples evaluated, -1 on a bad g. */
+long long orc_render_segments(const orc_model* m, const orc_camera* cam, const orc_tf* tf_in, int W, int H, int ns,
+                              const int g[3], const long long* pix, long long npix, double* out, int nthreads)
+{
+    if (g[0] < 1 || g[1] < 1 || g[2] < 1 || (long long)g[0] * g[1] * g[2] > ORC_MAX_BLOCKS) return -1;
+    orc_tf tf;
+    double gtiny;
+    orc_prepare_tf(m, tf_in, &tf, &gtiny);
+    if (!pix) npix = (long long)W * H;
+    orc_segments_ctx ctx = { m, cam, &tf, W, H, ns, g, pix, gtiny, out };
+    return orc_parallel(npix, 16, nthreads, orc_segments_body, &ctx);
 }
