@@ -464,6 +464,7 @@ def run_ours(args):
     }
     if ws == 1:
         line["precision"] = storage_throughput(mfa, torch, spec, job, tf)
+        line["segments"] = segments_throughput(mfa, torch, model, job, tf, render_s)
     if ws == 1 and not args.no_serve:
         line["serving"] = dict(run_serve(mfa, rates=args.serve_rates, duration=args.serve_duration),
                                note="Poisson requests (sides 512..2048, 512..2048 samples) on 8 resident degree-3 "
@@ -490,6 +491,29 @@ def run_ours(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def segments_throughput(mfa, torch, model, job, tf, single_s, frames=5):
+    """The same frame with the object-space decomposition (blocks render their ray segments
+    into partial images, merged with over): time per frame and samples evaluated, beside
+    the single-pass render."""
+    out = {"single_pass_ms": 1e3 * single_s}
+    W, H, NS = job.width, job.height, job.n_samples
+    img = torch.empty((H, W, 4), device="cuda")
+    for g in ((2, 2, 2), (4, 4, 4)):
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        mfa.render_segments(model, job.camera, tf, W, H, NS, g, out=img)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(frames):
+            mfa.render_segments(model, job.camera, tf, W, H, NS, g, out=img, samples_out=cnt)
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b) / frames
+        out["x".join(str(x) for x in g)] = {"ms_per_frame": ms, "samples_per_frame": int(cnt.item()) / frames,
+                                            "samples_per_s": int(cnt.item()) / frames / (ms / 1e3)}
+    return out
 
 
 def storage_throughput(mfa, torch, spec, job, tf, frames=5):

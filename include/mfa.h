@@ -187,6 +187,24 @@ int mfa_render_ex(const mfa_model* model, const mfa_camera* camera, const mfa_tr
                   int width, int height, int n_samples, float* rgba_out, const mfa_render_opts* opts);
 
 /*
+ * The render with the paper's object-space decomposition (Sec. IV-A.1 partitioning into
+ * blocks, Sec. IV-A.4 MFA-VV of each block into a partial image, Sec. IV-A.5 compositing of
+ * the partial images with the associative over), on one GPU.  The unit box is split into
+ * blocks[0] x blocks[1] x blocks[2] equal blocks (1..64 in total).  Every ray keeps the
+ * samples of mfa_render; block b renders those of them inside it -- front to back, early
+ * termination on the segment's own alpha -- and the partial images are merged per pixel,
+ * nearest segment first, into rgba_out (DEVICE, as mfa_render).  With ert_alpha >= 1 the
+ * image equals mfa_render's up to FP32 rounding order; with termination each segment may
+ * add what lies behind the single-pass stopping point, at most 1 - ert_alpha per channel.
+ * opts as mfa_render_ex (may be NULL; variant 0, 4 or 6 only).  Partial images
+ * (16 bytes x pixels x blocks) come from the library's staging pool; asynchronous on the
+ * bound stream.  MFA_ERR_ARG on a bad block grid, otherwise errors as mfa_render_ex.
+ */
+int mfa_render_segments(const mfa_model* model, const mfa_camera* camera, const mfa_transfer_fn* tf, int width,
+                        int height, int n_samples, const int blocks[3], float* rgba_out,
+                        const mfa_render_opts* opts);
+
+/*
  * Host-buffer forms of mfa_decode and mfa_render_ex: the same queries (Sec. III-B, the
  * query of Fig. 8 in Sec. V-D.3) and the same ray casting (Sec. IV-A.4), for data in HOST
  * memory.

@@ -119,6 +119,9 @@ def lib():
         L.mfa_render_ex.restype = c_int
         L.mfa_render_ex.argtypes = [c_void_p, POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int, c_void_p,
                                     POINTER(_Opts)]
+        L.mfa_render_segments.restype = c_int
+        L.mfa_render_segments.argtypes = [c_void_p, POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int, c_void_p,
+                                          c_void_p, POINTER(_Opts)]
         L.mfa_measure_peaks.restype = c_int
         L.mfa_measure_peaks.argtypes = [POINTER(_Peaks)]
         L.mfa_decode_host.restype = c_int
@@ -397,6 +400,31 @@ def render_host(model: Model, cam, tf: transfer_fn, width: int, height: int, n_s
                                  _host_ptr(out, None, "out"), ctypes.byref(opts)))
     if sync:
         torch.cuda.current_stream().synchronize()
+    return out
+
+
+def render_segments(model: Model, cam, tf: transfer_fn, width: int, height: int, n_samples: int, blocks, out=None,
+                    samples_out=None, variant: int = 0, tile_shape: int = 0):
+    """render() with the object-space decomposition: the box split into blocks[0] x
+    blocks[1] x blocks[2] blocks, each rendering its ray segments into a partial image,
+    merged with over nearest segment first."""
+    import torch
+    if out is None:
+        out = torch.empty((height, width, 4), device="cuda", dtype=torch.float32)
+    if not (out.is_cuda and out.dtype == torch.float32 and out.is_contiguous() and out.numel() == height * width * 4):
+        raise ValueError("out must be a contiguous (height, width, 4) FP32 CUDA tensor")
+    c = cam if isinstance(cam, _Camera) else camera(cam)
+    g = (c_int * 3)(*[int(b) for b in blocks])
+    opts = _Opts()
+    opts.variant = int(variant)
+    opts.tile_shape = int(tile_shape)
+    if samples_out is not None:
+        if not (samples_out.is_cuda and samples_out.dtype == torch.int64):
+            raise TypeError("samples_out must be an int64 CUDA tensor")
+        opts.samples_out = samples_out.data_ptr()
+    _bind_stream()
+    _check(lib().mfa_render_segments(model.handle, ctypes.byref(c), ctypes.byref(tf.struct), width, height, n_samples,
+                                     ctypes.byref(g), out.data_ptr(), ctypes.byref(opts)))
     return out
 
 

@@ -35,6 +35,9 @@ cudaStream_t current_stream();
 int check_model_device(const mfa_model* m);
 // Cached autotuner choice for this workload class, if any.
 bool tuned_lookup(const mfa_model* m, int w, int h, int ns, int* variant, int* shape);
+// The library's device staging pool on device `dev` (created on first use, memory kept
+// cached between calls; allocate and free with the stream-ordered pool calls).
+cudaError_t staging_pool(int dev, cudaMemPool_t* out);
 // Validates one render call and fills the kernel's scalars and table (tf_n rows).
 int setup_render(const mfa_model* m, const mfa_camera* cam, const mfa_transfer_fn* tf, int width, int height,
                  int n_samples, float* rgba_out, unsigned long long* samples_out, RenderScalars& S, float4* table);

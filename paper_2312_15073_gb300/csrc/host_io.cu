@@ -28,9 +28,13 @@ constexpr int kMaxDevices = 64;
 std::mutex g_pool_mu;
 cudaMemPool_t g_pool[kMaxDevices] = {};
 
-// The library's staging pool on `dev` (created on first use; freed memory stays cached).
+}  // namespace
+
+namespace mfa {
+
 cudaError_t staging_pool(int dev, cudaMemPool_t* out)
 {
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> g(g_pool_mu);
     if (!g_pool[dev]) {
         cudaMemPoolProps props = {};
@@ -51,6 +55,10 @@ cudaError_t staging_pool(int dev, cudaMemPool_t* out)
     *out = g_pool[dev];
     return cudaSuccess;
 }
+
+}  // namespace mfa
+
+namespace {
 
 // Helper streams and an event ring of the calling thread, for one device.
 struct IoStreams {

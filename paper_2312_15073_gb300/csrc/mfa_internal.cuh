@@ -125,6 +125,12 @@ cudaError_t launch_decode(const ModelDev& m, const float* pts, long long n, floa
                           cudaStream_t stream);
 cudaError_t launch_spans(const ModelDev& m, const float* pts, long long n, int* spans, cudaStream_t stream);
 cudaError_t launch_render(const ModelDev& m, const RenderParams& rp, int variant, int shape, cudaStream_t stream);
+// Object-space decomposition into g[0] x g[1] x g[2] blocks (at most 64): every block's ray
+// segments into partial[block][height][width] (the variant picks the cardinal path unless
+// it is 4), then their over-merge into s.out.
+cudaError_t launch_render_segments(const ModelDev& m, const RenderParams& rp, int variant, int shape, const int g[3],
+                                   float4* partial, cudaStream_t stream);
+cudaError_t launch_merge_segments(const RenderScalars& s, const int g[3], const float4* partial, cudaStream_t stream);
 // The persistent batched render kernel for models of one degree class q, one storage type
 // and one path (cardinal or record): arguments (BatchHead* table, int group, int
 // tile_shape).  Launch with `threads` threads per CTA and about SMs x blocks_per_sm CTAs.

@@ -287,15 +287,66 @@ __device__ __forceinline__ float4 sample_colour(const float4* __restrict__ tf, c
     return c;
 }
 
+// One block of the object-space decomposition (mfa_render_segments): the block grid and
+// this block's index per axis.  Block (i, j, k) covers [i/g0, (i+1)/g0] x [j/g1, (j+1)/g1]
+// x [k/g2, (k+1)/g2] of the unit box.
+struct SegBlock {
+    int g[3];
+    int bi[3];
+};
+
+// The split between two neighbouring blocks along a ray: the first sample index at or past
+// their common plane (ray parameter tb), clamped to 0..ns.
+__device__ __forceinline__ int split_index(float tb, float t0, float dt, int ns)
+{
+    const float k = ceilf((tb - t0) / dt - 0.5f);
+    return !(k >= 0.0f) ? 0 : (k > static_cast<float>(ns) ? ns : static_cast<int>(k));
+}
+
+// Sample index range [kb, ke) of block B on the ray (o, d) whose samples sit at
+// t0 + (k + 1/2) dt.  Neighbouring blocks evaluate the same expression for their common
+// plane, so the ranges of all blocks partition 0..ns-1; a face on the box boundary gives 0
+// or ns, and a ray parallel to an axis's planes stays in the slab holding its origin (the
+// top slab keeps the coordinate 1).
+__device__ __forceinline__ void block_range(const SegBlock& B, const float (&o)[3], const float (&d)[3], float t0,
+                                            float dt, int ns, int& kb, int& ke)
+{
+    int lo_k = 0, hi_k = ns;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float gf = static_cast<float>(B.g[a]);
+        const float lo = static_cast<float>(B.bi[a]) / gf, hi = static_cast<float>(B.bi[a] + 1) / gf;
+        const bool first = B.bi[a] == 0, last = B.bi[a] == B.g[a] - 1;
+        int k_in, k_out;
+        if (d[a] > 0.0f) {
+            k_in = first ? 0 : split_index((lo - o[a]) / d[a], t0, dt, ns);
+            k_out = last ? ns : split_index((hi - o[a]) / d[a], t0, dt, ns);
+        } else if (d[a] < 0.0f) {
+            k_in = last ? 0 : split_index((hi - o[a]) / d[a], t0, dt, ns);
+            k_out = first ? ns : split_index((lo - o[a]) / d[a], t0, dt, ns);
+        } else {
+            const bool inside = (o[a] >= lo && o[a] < hi) || (last && o[a] == hi);
+            k_in = inside ? 0 : ns;
+            k_out = inside ? ns : 0;
+        }
+        lo_k = max(lo_k, k_in);
+        hi_k = min(hi_k, k_out);
+    }
+    kb = lo_k;
+    ke = hi_k;
+}
+
 // Software-pipelined ray march (variant 4): the query of sample k+1 is issued before the
 // colour and compositing of sample k, so the two independent chains interleave in one
 // basic block and the transfer-function / shading / compositing latency of one sample
 // hides behind the contraction of the next.  The three span checks share one branch.
 // The last iteration queries the final sample a second time (its result is not used).
-template <int Q, int STORAGE>
+// SEG: march only the samples of one block of the object-space decomposition (seg), with
+// early termination on the segment's own alpha.
+template <int Q, int STORAGE, bool SEG = false>
 __device__ __forceinline__ float4 march_pipelined(const ModelDev& M, const RenderScalars& P,
                                                   const float4* __restrict__ tf, int col, int row,
-                                                  unsigned long long& count)
+                                                  unsigned long long& count, const SegBlock* seg = nullptr)
 {
     float o[3], d[3], t0, t1;
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -304,6 +355,11 @@ __device__ __forceinline__ float4 march_pipelined(const ModelDev& M, const Rende
     const int ns = P.n_samples;
     const float ert = P.ert_alpha;
     const float dt = (t1 - t0) / static_cast<float>(ns);
+    int kb = 0, ke = ns;
+    if constexpr (SEG) {
+        block_range(*seg, o, d, t0, dt, ns, kb, ke);
+        if (kb >= ke) return acc;
+    }
     const ShadeParams S = shade_params(P, d);
     AxisCache<Q> cx, cy, cz;
     cx.s = cy.s = cz.s = -1;
@@ -333,9 +389,9 @@ __device__ __forceinline__ float4 march_pipelined(const ModelDev& M, const Rende
         return q;
     };
 
-    float4 q = query_at(0);
-    for (int k = 0; k < ns; ++k) {
-        const float4 qn = query_at(min(k + 1, ns - 1));
+    float4 q = query_at(kb);
+    for (int k = kb; k < ke; ++k) {
+        const float4 qn = query_at(min(k + 1, ke - 1));
         const float4 c = sample_colour(tf, S, q);
         const float wgt = (1.0f - acc.w) * c.w;
         acc.x = fmaf(wgt, c.x, acc.x);
@@ -361,10 +417,10 @@ __device__ __forceinline__ float4 march_pipelined(const ModelDev& M, const Rende
 // until a span changes.  The end spans, whose functions see the repeated end knots, read
 // their record from global memory (L1-resident, a few hundred bytes per axis) for each
 // sample.  Software-pipelined like variant 4.
-template <int Q, int STORAGE>
+template <int Q, int STORAGE, bool SEG = false>
 __device__ __forceinline__ float4 march_cardinal(const ModelDev& M, const RenderScalars& P,
                                                  const float4* __restrict__ tf, int col, int row,
-                                                 unsigned long long& count)
+                                                 unsigned long long& count, const SegBlock* seg = nullptr)
 {
     float o[3], d[3], t0, t1;
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -373,6 +429,11 @@ __device__ __forceinline__ float4 march_cardinal(const ModelDev& M, const Render
     const int ns = P.n_samples;
     const float ert = P.ert_alpha;
     const float dt = (t1 - t0) / static_cast<float>(ns);
+    int kb = 0, ke = ns;
+    if constexpr (SEG) {
+        block_range(*seg, o, d, t0, dt, ns, kb, ke);
+        if (kb >= ke) return acc;
+    }
     const ShadeParams S = shade_params(P, d);
     float om[3], dm[3], gs[3];   // ray in span units, gradient scale per axis
 #pragma unroll
@@ -427,10 +488,10 @@ __device__ __forceinline__ float4 march_cardinal(const ModelDev& M, const Render
         return q;
     };
 
-    float4 q = query_at(0);
-    int k = 0;   // samples composited
-    while (k < ns) {
-        const float4 qn = query_at(min(k + 1, ns - 1));
+    float4 q = query_at(kb);
+    int k = kb;   // next sample to composite
+    while (k < ke) {
+        const float4 qn = query_at(min(k + 1, ke - 1));
         const float4 c = sample_colour(tf, S, q);
         const float wgt = (1.0f - acc.w) * c.w;
         acc.x = fmaf(wgt, c.x, acc.x);
@@ -441,7 +502,7 @@ __device__ __forceinline__ float4 march_cardinal(const ModelDev& M, const Render
         if (acc.w >= ert) break;
         q = qn;
     }
-    count += static_cast<unsigned>(k);
+    count += static_cast<unsigned>(k - kb);
     return acc;
 }
 
@@ -718,6 +779,125 @@ cudaError_t render_q(const ModelDev& m, const RenderParams& rp, int variant, int
 }
 
 // ----------------------------------------------------------------------------------------
+// object-space decomposition: block segments and their over-merge
+// ----------------------------------------------------------------------------------------
+//
+// The paper renders each partitioned block on its own node into a partial image and
+// merges the partial images with the associative over (Sec. IV-A.1, IV-A.4, IV-A.5).  On
+// one GPU the blocks are the z index of the launch grid: CTA (tile, b) renders, for every
+// pixel of its tile, the samples of that pixel's ray that lie in block b (block_range),
+// front to back with early termination on the segment's own alpha, into partial image b.
+// The merge then composites, per pixel, the non-empty segments nearest first.
+
+constexpr int kMaxSegBlocks = 64;
+
+template <int Q, int STORAGE, int MODE>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+    k_render_segments(ModelDev M, const __grid_constant__ RenderParams P, int shape, int gx, int gy, int gz,
+                      float4* __restrict__ partial)
+{
+    __shared__ float4 tf[kTfMax + 1];
+    for (int i = threadIdx.x; i < P.s.tf_n; i += kThreads) tf[i] = P.tf[i];
+    if (threadIdx.x == 0 && P.s.tf_n == 1) tf[1] = P.tf[0];   // the branch-free lerp reads row 1
+    __syncthreads();
+
+    int col, row;
+    tile_pixel(tile_shape(shape), blockIdx.x, blockIdx.y, threadIdx.x, col, row);
+    const int b = blockIdx.z;
+    SegBlock B;
+    B.g[0] = gx;
+    B.g[1] = gy;
+    B.g[2] = gz;
+    B.bi[0] = b % gx;
+    B.bi[1] = (b / gx) % gy;
+    B.bi[2] = b / (gx * gy);
+    unsigned long long count = 0;
+    if (col < P.s.width && row < P.s.height) {
+        float4 acc;
+        if constexpr (MODE == 6)
+            acc = march_cardinal<Q, STORAGE, true>(M, P.s, tf, col, row, count, &B);
+        else
+            acc = march_pipelined<Q, STORAGE, true>(M, P.s, tf, col, row, count, &B);
+        const long long npix = static_cast<long long>(P.s.width) * P.s.height;
+        partial[b * npix + static_cast<long long>(row) * P.s.width + col] = acc;
+    }
+    if (P.s.samples_out) add_count(P.s.samples_out, count);
+}
+
+// One thread per pixel: the non-empty segments of the pixel's ray, ordered by their first
+// sample, composited with over into the output image.
+__global__ void __launch_bounds__(256) k_merge_segments(const __grid_constant__ RenderScalars S, int gx, int gy,
+                                                        int gz, const float4* __restrict__ partial)
+{
+    const int col = blockIdx.x * 16 + (threadIdx.x & 15), row = blockIdx.y * 16 + (threadIdx.x >> 4);
+    if (col >= S.width || row >= S.height) return;
+    const long long npix = static_cast<long long>(S.width) * S.height;
+    const long long pix = static_cast<long long>(row) * S.width + col;
+    float o[3], d[3], t0, t1;
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (ray_box(S, col, row, o, d, t0, t1)) {
+        const int ns = S.n_samples;
+        const float dt = (t1 - t0) / static_cast<float>(ns);
+        int first[kMaxSegBlocks], blk[kMaxSegBlocks], n = 0;
+        SegBlock B;
+        B.g[0] = gx;
+        B.g[1] = gy;
+        B.g[2] = gz;
+        const int nb = gx * gy * gz;
+        for (int b = 0; b < nb; ++b) {
+            B.bi[0] = b % gx;
+            B.bi[1] = (b / gx) % gy;
+            B.bi[2] = b / (gx * gy);
+            int kb, ke;
+            block_range(B, o, d, t0, dt, ns, kb, ke);
+            if (kb >= ke) continue;
+            int i = n++;   // insertion by first sample index (segments are disjoint)
+            while (i > 0 && first[i - 1] > kb) {
+                first[i] = first[i - 1];
+                blk[i] = blk[i - 1];
+                --i;
+            }
+            first[i] = kb;
+            blk[i] = b;
+        }
+        for (int i = 0; i < n; ++i) {
+            const float4 p = partial[blk[i] * npix + pix];
+            const float tr = 1.0f - acc.w;
+            acc.x = fmaf(tr, p.x, acc.x);
+            acc.y = fmaf(tr, p.y, acc.y);
+            acc.z = fmaf(tr, p.z, acc.z);
+            acc.w = fmaf(tr, p.w, acc.w);
+        }
+    }
+    S.out[pix] = acc;
+}
+
+template <int Q, int STORAGE>
+cudaError_t segments_qs(const ModelDev& m, const RenderParams& rp, bool cardinal, int shape, const int g[3],
+                        float4* partial, cudaStream_t st)
+{
+    const TileShape T = tile_shape(shape);
+    dim3 grid((rp.s.width + T.tw - 1) / T.tw, (rp.s.height + T.th - 1) / T.th, g[0] * g[1] * g[2]);
+    if (cardinal)
+        k_render_segments<Q, STORAGE, 6><<<grid, kThreads, 0, st>>>(m, rp, shape, g[0], g[1], g[2], partial);
+    else
+        k_render_segments<Q, STORAGE, 4><<<grid, kThreads, 0, st>>>(m, rp, shape, g[0], g[1], g[2], partial);
+    return cudaGetLastError();
+}
+
+template <int Q>
+cudaError_t segments_q(const ModelDev& m, const RenderParams& rp, bool cardinal, int shape, const int g[3],
+                       float4* partial, cudaStream_t st)
+{
+    switch (m.storage) {
+    case 1: return segments_qs<Q, 1>(m, rp, cardinal, shape, g, partial, st);
+    case 2: return segments_qs<Q, 2>(m, rp, cardinal, shape, g, partial, st);
+    case 3: return segments_qs<Q, 3>(m, rp, cardinal, shape, g, partial, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// ----------------------------------------------------------------------------------------
 // persistent batch
 // ----------------------------------------------------------------------------------------
 
@@ -832,6 +1012,28 @@ cudaError_t launch_render(const ModelDev& m, const RenderParams& rp, int variant
     case 5: return render_q<5>(m, rp, variant, shape, stream);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_render_segments(const ModelDev& m, const RenderParams& rp, int variant, int shape, const int g[3],
+                                   float4* partial, cudaStream_t stream)
+{
+    if (g[0] * g[1] * g[2] > kMaxSegBlocks) return cudaErrorInvalidValue;
+    const bool cardinal = m.cardinal && variant != 4;
+    switch (m.q) {
+    case 2: return segments_q<2>(m, rp, cardinal, shape, g, partial, stream);
+    case 3: return segments_q<3>(m, rp, cardinal, shape, g, partial, stream);
+    case 4: return segments_q<4>(m, rp, cardinal, shape, g, partial, stream);
+    case 5: return segments_q<5>(m, rp, cardinal, shape, g, partial, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_merge_segments(const RenderScalars& s, const int g[3], const float4* partial, cudaStream_t stream)
+{
+    if (g[0] * g[1] * g[2] > kMaxSegBlocks) return cudaErrorInvalidValue;
+    dim3 grid((s.width + 15) / 16, (s.height + 15) / 16);
+    k_merge_segments<<<grid, 256, 0, stream>>>(s, g[0], g[1], g[2], partial);
+    return cudaGetLastError();
 }
 
 BatchKernel render_batch_kernel(int q, int storage, int cardinal)

@@ -63,6 +63,13 @@ def test_host_side_argument_checks(libmfa):
     assert L.mfa_decode_host(None, None, -3, None, None) == -1
     assert L.mfa_render_host(None, ctypes.byref(cam), ctypes.byref(tf.struct), 8, 8, 8, None, None) == -1
     assert "NULL" in L.mfa_last_error().decode()
+    assert L.mfa_render_segments(None, ctypes.byref(cam), ctypes.byref(tf.struct), 8, 8, 8, None, None, None) == -1
+    assert "blocks" in L.mfa_last_error().decode()
+    g = (ctypes.c_int * 3)(2, 0, 1)
+    assert L.mfa_render_segments(None, ctypes.byref(cam), ctypes.byref(tf.struct), 8, 8, 8, g, None, None) == -1
+    g = (ctypes.c_int * 3)(8, 8, 2)
+    assert L.mfa_render_segments(None, ctypes.byref(cam), ctypes.byref(tf.struct), 8, 8, 8, g, None, None) == -1
+    assert "at most 64" in L.mfa_last_error().decode()
     # model creation rejects bad degrees, counts and knots before any device work
     deg = (ctypes.c_int * 3)(3, 3, 5)
     nc = (ctypes.c_int * 3)(8, 8, 8)
