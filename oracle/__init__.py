@@ -93,6 +93,9 @@ def _load():
         lib.orc_render_segments.restype = c_longlong
         lib.orc_render_segments.argtypes = [POINTER(_Model), POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int,
                                             c_void_p, c_void_p, c_longlong, c_void_p, c_int]
+        lib.orc_render_iso.restype = c_longlong
+        lib.orc_render_iso.argtypes = [POINTER(_Model), POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int, c_double,
+                                       c_void_p, c_longlong, c_void_p, c_void_p, c_int]
         lib.orc_block_range.restype = None
         lib.orc_block_range.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_double, c_int,
                                         POINTER(c_int), POINTER(c_int)]
@@ -288,6 +291,37 @@ def render_segments(model: Model, cam: dict, tf_rgba, width: int, height: int, n
     if ns < 0:
         raise ValueError("blocks must be >= 1 per axis and at most 512 in total")
     return out, int(ns)
+
+
+def render_iso(model: Model, cam: dict, tf_rgba, width: int, height: int, n_samples: int, iso: float, *,
+               shading: bool = True, ka=0.3, kd=0.6, ks=0.3, shininess=32.0, vmin=math.nan, vmax=math.nan,
+               pixels=None, nthreads: int | None = None):
+    """Isosurface f = iso: first crossing along each ray's samples, refined by bracketed
+    Newton steps, shaded opaque.  Returns (rgba, depth, queries): rgba (H, W, 4) or
+    (len(pixels), 4), depth the hit parameter t (+inf on a miss)."""
+    tf_rgba = np.ascontiguousarray(tf_rgba, dtype=np.float32).reshape(-1, 4)
+    tf = _TF()
+    tf.n_entries = tf_rgba.shape[0]
+    tf.rgba = _ptr(tf_rgba)
+    tf.vmin = vmin
+    tf.vmax = vmax
+    tf.shading = 1 if shading else 0
+    tf.ka, tf.kd, tf.ks, tf.shininess = ka, kd, ks, shininess
+    tf.ert_alpha = 1.0
+    cam_s = _camera(cam)
+    if pixels is None:
+        out = np.zeros((height, width, 4))
+        depth = np.zeros((height, width))
+        npix, pix_ptr = width * height, None
+    else:
+        pixels = np.ascontiguousarray(pixels, dtype=np.int64)
+        out = np.zeros((len(pixels), 4))
+        depth = np.zeros(len(pixels))
+        npix, pix_ptr = len(pixels), _ptr(pixels)
+    nq = _load().orc_render_iso(ctypes.byref(model._s), ctypes.byref(cam_s), ctypes.byref(tf), width, height,
+                                n_samples, float(iso), pix_ptr, npix, _ptr(out), _ptr(depth),
+                                nthreads or default_threads())
+    return out, depth, int(nq)
 
 
 def block_range(blocks, block, o, d, t0: float, dt: float, n_samples: int):

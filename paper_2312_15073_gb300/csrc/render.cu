@@ -31,7 +31,7 @@
 // The default (variant 0) is 6 where the cardinal path applies, else 4.  ncu launch times
 // on the 128^3 degree-3 FP32 frame (1024^2, 1024 samples, Phong): 6: 4.9 ms, 4: 5.6, 1: 5.7,
 // 2: 5.8, 5: 6.9, 3: 7.6.
-#include "bspline.cuh"
+#include "raycast.cuh"
 
 namespace mfa {
 namespace {
@@ -46,98 +46,6 @@ constexpr int kMinBlocks = 4;
 // with the packed layer-pair contraction 4 CTAs (128 registers) still measures best on the
 // 128^3 degree-3 1024^2 frame: FP32 4.87 ms against 5.05 ms at 5 CTAs (96 registers, with
 // spills), FP16 5.74 against 5.73 ms.
-
-// Ray-tile shapes (CTA tile, warp tile).  Shape 0 is the default; the autotuner picks one
-// per workload.
-struct TileShape {
-    int tw, th;   // pixels per CTA tile
-    int ww, wh;   // pixels per warp tile (ww * wh = 32)
-};
-__host__ __device__ constexpr TileShape tile_shape(int s)
-{
-    return s == 1 ? TileShape{ 32, 4, 8, 4 } : s == 2 ? TileShape{ 8, 16, 4, 8 } : s == 3 ? TileShape{ 16, 8, 16, 2 }
-                                                                                         : TileShape{ 16, 8, 8, 4 };
-}
-
-// pixel of thread `tid` in tile (tx, ty)
-__device__ __forceinline__ void tile_pixel(const TileShape& T, int tx, int ty, int tid, int& col, int& row)
-{
-    const int warp = tid >> 5, lane = tid & 31;
-    const int wpr = T.tw / T.ww;   // warps per tile row
-    col = tx * T.tw + (warp % wpr) * T.ww + lane % T.ww;
-    row = ty * T.th + (warp / wpr) * T.wh + lane / T.ww;
-}
-
-// Ray through the centre of pixel (col, row) (row 0 at the top): origin o, unit direction
-// d, and its parameter interval [t0, t1] inside [0,1]^3 (slab clip, t >= 0).  False when
-// the ray misses the box.
-__device__ __forceinline__ bool ray_box(const RenderScalars& P, int col, int row, float (&o)[3], float (&d)[3],
-                                        float& t0, float& t1)
-{
-    const float sx = fmaf(static_cast<float>(2 * col + 1), P.inv_w, -1.0f);
-    const float sy = fmaf(static_cast<float>(-(2 * row + 1)), P.inv_h, 1.0f);
-    if (P.projection == 0) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            o[a] = fmaf(sy, P.uy[a], fmaf(sx, P.rx[a], P.eye[a]));
-            d[a] = P.fwd[a];
-        }
-    } else {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            o[a] = P.eye[a];
-            d[a] = fmaf(sy, P.uy[a], fmaf(sx, P.rx[a], P.fwd[a]));
-        }
-        const float inv = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        d[0] *= inv;
-        d[1] *= inv;
-        d[2] *= inv;
-    }
-    t0 = 0.0f;
-    t1 = INFINITY;
-    bool hit = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (d[a] != 0.0f) {
-            const float inv = 1.0f / d[a];
-            float ta = -o[a] * inv, tb = (1.0f - o[a]) * inv;
-            if (ta > tb) {
-                const float t = ta;
-                ta = tb;
-                tb = t;
-            }
-            t0 = fmaxf(t0, ta);
-            t1 = fminf(t1, tb);
-        } else if (o[a] < 0.0f || o[a] > 1.0f) {
-            hit = false;
-        }
-    }
-    return hit && t0 < t1;
-}
-
-// Per-axis state of a ray: current span and its record (which carries the span's FP32
-// bounds [lo, hi) in rec[2], rec[3]: a coordinate u lies in the span iff lo <= u < hi).
-template <int Q>
-struct AxisCache {
-    int s;
-    float rec[rec_stride(Q)];
-};
-
-// Brings the cache to the span of u.  Along a ray the span moves by at most one step
-// between samples in the common case, so the next record is loaded directly and the
-// search only runs when u left that span too (or on the first sample).
-template <int Q>
-__device__ __forceinline__ void axis_update(const AxisDev& A, AxisCache<Q>& C, float u)
-{
-    if (C.s >= 0 && u >= C.rec[2] && u < C.rec[3]) return;
-    int s = C.s < 0 ? locate_span(A, u) : C.s + (u >= C.rec[3] ? 1 : -1);
-    load_record<Q>(A, s, C.rec);
-    if (u < C.rec[2] || u >= C.rec[3]) {
-        s = walk_span(A, u, s);
-        load_record<Q>(A, s, C.rec);
-    }
-    C.s = s;
-}
 
 // The whole ray of pixel (col, row): premultiplied RGBA; `count` += samples evaluated.
 // MODE = variant (see above).
@@ -227,282 +135,6 @@ __device__ __forceinline__ float4 march(const ModelDev& M, const RenderScalars& 
         acc.w += wgt;
         if (acc.w >= ert) break;
     }
-    return acc;
-}
-
-// Colour of one sample, without branches: transfer-function lerp (the table has at least
-// two rows in shared memory; a one-row table is duplicated) and, when `shading`, Phong
-// with a headlight.  Same arithmetic as the per-sample code of march().
-struct ShadeParams {
-    float vmin, inv_range, tscale, ka, kd, ks, shin, gtiny2, lx, ly, lz;
-    int tf_last, shading;
-};
-
-__device__ __forceinline__ ShadeParams shade_params(const RenderScalars& P, const float (&d)[3])
-{
-    ShadeParams S;
-    S.vmin = P.vmin;
-    S.inv_range = P.inv_range;
-    S.tscale = static_cast<float>(P.tf_n - 1);
-    S.tf_last = max(P.tf_n - 2, 0);
-    S.shading = P.shading;
-    S.ka = P.ka;
-    S.kd = P.kd;
-    S.ks = P.ks;
-    S.shin = P.shininess;
-    S.gtiny2 = P.gtiny2;
-    S.lx = -d[0];
-    S.ly = -d[1];
-    S.lz = -d[2];
-    return S;
-}
-
-__device__ __forceinline__ float4 sample_colour(const float4* __restrict__ tf, const ShadeParams& S, const float4 q)
-{
-    const float tt = clamp01((q.x - S.vmin) * S.inv_range);
-    const float xx = tt * S.tscale;
-    const int i0 = min(static_cast<int>(xx), S.tf_last);
-    const float wt = xx - static_cast<float>(i0);
-    const float4 c0 = tf[i0], c1 = tf[i0 + 1];
-    // c = c0 + wt (c1 - c0), two channels per packed instruction
-    const f2 w2 = pk2(wt, wt), rg0 = pk2(c0.x, c0.y), ba0 = pk2(c0.z, c0.w);
-    const f2 rg = fma2(w2, sub2(pk2(c1.x, c1.y), rg0), rg0), ba = fma2(w2, sub2(pk2(c1.z, c1.w), ba0), ba0);
-    float4 c;
-    upk2(rg, c.x, c.y);
-    upk2(ba, c.z, c.w);
-    const float g2 = q.y * q.y + q.z * q.z + q.w * q.w;
-    const bool flat = g2 <= S.gtiny2;
-    const float ndl = fabsf(q.y * S.lx + q.z * S.ly + q.w * S.lz) * rsqrtf(flat ? 1.0f : g2);
-    const float rv = 2.0f * ndl * ndl - 1.0f;   // R.V with V = L
-    float spec = rv > 0.0f ? __powf(rv, S.shin) : 0.0f;
-    float factor = fmaf(S.kd, ndl, S.ka);
-    factor = flat ? S.ka + S.kd : factor;
-    spec = flat ? 0.0f : spec;
-    const float ksp = S.ks * spec;
-    if (S.shading) {
-        c.x = clamp01(fmaf(c.x, factor, ksp));
-        c.y = clamp01(fmaf(c.y, factor, ksp));
-        c.z = clamp01(fmaf(c.z, factor, ksp));
-    }
-    return c;
-}
-
-// One block of the object-space decomposition (mfa_render_segments): the block grid and
-// this block's index per axis.  Block (i, j, k) covers [i/g0, (i+1)/g0] x [j/g1, (j+1)/g1]
-// x [k/g2, (k+1)/g2] of the unit box.
-struct SegBlock {
-    int g[3];
-    int bi[3];
-};
-
-// The split between two neighbouring blocks along a ray: the first sample index at or past
-// their common plane (ray parameter tb), clamped to 0..ns.
-__device__ __forceinline__ int split_index(float tb, float t0, float dt, int ns)
-{
-    const float k = ceilf((tb - t0) / dt - 0.5f);
-    return !(k >= 0.0f) ? 0 : (k > static_cast<float>(ns) ? ns : static_cast<int>(k));
-}
-
-// Sample index range [kb, ke) of block B on the ray (o, d) whose samples sit at
-// t0 + (k + 1/2) dt.  Neighbouring blocks evaluate the same expression for their common
-// plane, so the ranges of all blocks partition 0..ns-1; a face on the box boundary gives 0
-// or ns, and a ray parallel to an axis's planes stays in the slab holding its origin (the
-// top slab keeps the coordinate 1).
-__device__ __forceinline__ void block_range(const SegBlock& B, const float (&o)[3], const float (&d)[3], float t0,
-                                            float dt, int ns, int& kb, int& ke)
-{
-    int lo_k = 0, hi_k = ns;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float gf = static_cast<float>(B.g[a]);
-        const float lo = static_cast<float>(B.bi[a]) / gf, hi = static_cast<float>(B.bi[a] + 1) / gf;
-        const bool first = B.bi[a] == 0, last = B.bi[a] == B.g[a] - 1;
-        int k_in, k_out;
-        if (d[a] > 0.0f) {
-            k_in = first ? 0 : split_index((lo - o[a]) / d[a], t0, dt, ns);
-            k_out = last ? ns : split_index((hi - o[a]) / d[a], t0, dt, ns);
-        } else if (d[a] < 0.0f) {
-            k_in = last ? 0 : split_index((hi - o[a]) / d[a], t0, dt, ns);
-            k_out = first ? ns : split_index((lo - o[a]) / d[a], t0, dt, ns);
-        } else {
-            const bool inside = (o[a] >= lo && o[a] < hi) || (last && o[a] == hi);
-            k_in = inside ? 0 : ns;
-            k_out = inside ? ns : 0;
-        }
-        lo_k = max(lo_k, k_in);
-        hi_k = min(hi_k, k_out);
-    }
-    kb = lo_k;
-    ke = hi_k;
-}
-
-// Software-pipelined ray march (variant 4): the query of sample k+1 is issued before the
-// colour and compositing of sample k, so the two independent chains interleave in one
-// basic block and the transfer-function / shading / compositing latency of one sample
-// hides behind the contraction of the next.  The three span checks share one branch.
-// The last iteration queries the final sample a second time (its result is not used).
-// SEG: march only the samples of one block of the object-space decomposition (seg), with
-// early termination on the segment's own alpha.
-template <int Q, int STORAGE, bool SEG = false>
-__device__ __forceinline__ float4 march_pipelined(const ModelDev& M, const RenderScalars& P,
-                                                  const float4* __restrict__ tf, int col, int row,
-                                                  unsigned long long& count, const SegBlock* seg = nullptr)
-{
-    float o[3], d[3], t0, t1;
-    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (!ray_box(P, col, row, o, d, t0, t1)) return acc;
-
-    const int ns = P.n_samples;
-    const float ert = P.ert_alpha;
-    const float dt = (t1 - t0) / static_cast<float>(ns);
-    int kb = 0, ke = ns;
-    if constexpr (SEG) {
-        block_range(*seg, o, d, t0, dt, ns, kb, ke);
-        if (kb >= ke) return acc;
-    }
-    const ShadeParams S = shade_params(P, d);
-    AxisCache<Q> cx, cy, cz;
-    cx.s = cy.s = cz.s = -1;
-
-    auto query_at = [&](int k) -> float4 {
-        const float t = fmaf(static_cast<float>(k) + 0.5f, dt, t0);
-        const float u = clamp01(fmaf(t, d[0], o[0]));
-        const float v = clamp01(fmaf(t, d[1], o[1]));
-        const float w = clamp01(fmaf(t, d[2], o[2]));
-        const bool ox = !(cx.s >= 0 && u >= cx.rec[2] && u < cx.rec[3]);
-        const bool oy = !(cy.s >= 0 && v >= cy.rec[2] && v < cy.rec[3]);
-        const bool oz = !(cz.s >= 0 && w >= cz.rec[2] && w < cz.rec[3]);
-        if (ox | oy | oz) {
-            if (ox) axis_update<Q>(M.ax[0], cx, u);
-            if (oy) axis_update<Q>(M.ax[1], cy, v);
-            if (oz) axis_update<Q>(M.ax[2], cz, w);
-        }
-        float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];
-        record_basis<Q>(cx.rec, u, Nx, Dx);
-        record_basis<Q>(cy.rec, v, Ny, Dy);
-        record_basis<Q>(cz.rec, w, Nz, Dz);
-        float4 q = contract<Q, STORAGE>(M, cx.s - M.ax[0].p, cy.s - M.ax[1].p, cz.s - M.ax[2].p, Nx, Dx, Ny, Dy,
-                                        Nz, Dz);
-        q.y *= cx.rec[1];
-        q.z *= cy.rec[1];
-        q.w *= cz.rec[1];
-        return q;
-    };
-
-    float4 q = query_at(kb);
-    for (int k = kb; k < ke; ++k) {
-        const float4 qn = query_at(min(k + 1, ke - 1));
-        const float4 c = sample_colour(tf, S, q);
-        const float wgt = (1.0f - acc.w) * c.w;
-        acc.x = fmaf(wgt, c.x, acc.x);
-        acc.y = fmaf(wgt, c.y, acc.y);
-        acc.z = fmaf(wgt, c.z, acc.z);
-        acc.w += wgt;
-        ++count;
-        if (acc.w >= ert) break;
-        q = qn;
-    }
-    return acc;
-}
-
-// ----------------------------------------------------------------------------------------
-// variant 6: uniform knots (cardinal basis)
-// ----------------------------------------------------------------------------------------
-//
-// For a model with clamped uniform knots and degree Q-1 on all three axes (ModelDev::
-// cardinal), every span but the p-1 at each end of an axis carries the same basis
-// polynomials (cardinal_basis).  The ray is marched in span units x = (n - p) u, so the
-// span is j = floor(x) and its local coordinate t = x - j; the per-axis state is the span
-// index alone (no record in registers), and the support's first window entry is kept
-// until a span changes.  The end spans, whose functions see the repeated end knots, read
-// their record from global memory (L1-resident, a few hundred bytes per axis) for each
-// sample.  Software-pipelined like variant 4.
-template <int Q, int STORAGE, bool SEG = false>
-__device__ __forceinline__ float4 march_cardinal(const ModelDev& M, const RenderScalars& P,
-                                                 const float4* __restrict__ tf, int col, int row,
-                                                 unsigned long long& count, const SegBlock* seg = nullptr)
-{
-    float o[3], d[3], t0, t1;
-    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (!ray_box(P, col, row, o, d, t0, t1)) return acc;
-
-    const int ns = P.n_samples;
-    const float ert = P.ert_alpha;
-    const float dt = (t1 - t0) / static_cast<float>(ns);
-    int kb = 0, ke = ns;
-    if constexpr (SEG) {
-        block_range(*seg, o, d, t0, dt, ns, kb, ke);
-        if (kb >= ke) return acc;
-    }
-    const ShadeParams S = shade_params(P, d);
-    float om[3], dm[3], gs[3];   // ray in span units, gradient scale per axis
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float m = static_cast<float>(M.ax[a].n - M.ax[a].p);
-        om[a] = o[a] * m;
-        dm[a] = d[a] * m;
-        gs[a] = m * Cardinal<Q>::kGradScale;
-    }
-    CardAxis cx{ -INFINITY, 0, false }, cy{ -INFINITY, 0, false }, cz{ -INFINITY, 0, false };
-    int base = 0;
-
-    auto query_at = [&](int k) -> float4 {
-        const float t = fmaf(static_cast<float>(k) + 0.5f, dt, t0);
-        const float x = fmaf(t, dm[0], om[0]);
-        const float y = fmaf(t, dm[1], om[1]);
-        const float z = fmaf(t, dm[2], om[2]);
-        float tx = x - cx.jf, ty = y - cy.jf, tz = z - cz.jf;
-        const bool ox = !(tx >= 0.0f && tx < 1.0f);
-        const bool oy = !(ty >= 0.0f && ty < 1.0f);
-        const bool oz = !(tz >= 0.0f && tz < 1.0f);
-        if (ox | oy | oz) {
-            if (ox) {
-                card_update(M.ax[0], cx, x);
-                tx = x - cx.jf;
-            }
-            if (oy) {
-                card_update(M.ax[1], cy, y);
-                ty = y - cy.jf;
-            }
-            if (oz) {
-                card_update(M.ax[2], cz, z);
-                tz = z - cz.jf;
-            }
-            base = (cz.j * M.nyp + cy.j) * M.nxp + cx.j;
-        }
-        float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];
-        if (cx.edge | cy.edge | cz.edge) {
-            card_basis<Q>(M.ax[0], cx, tx, Nx, Dx);
-            card_basis<Q>(M.ax[1], cy, ty, Ny, Dy);
-            card_basis<Q>(M.ax[2], cz, tz, Nz, Dz);
-        } else {
-            cardinal_basis<Q>(tx, Nx, Dx);
-            cardinal_basis<Q>(ty, Ny, Dy);
-            cardinal_basis<Q>(tz, Nz, Dz);
-        }
-        float4 q = contract_at<Q, STORAGE>(M, base, Nx, Dx, Ny, Dy, Nz, Dz);
-        q.x *= Cardinal<Q>::kValScale;
-        q.y *= gs[0];
-        q.z *= gs[1];
-        q.w *= gs[2];
-        return q;
-    };
-
-    float4 q = query_at(kb);
-    int k = kb;   // next sample to composite
-    while (k < ke) {
-        const float4 qn = query_at(min(k + 1, ke - 1));
-        const float4 c = sample_colour(tf, S, q);
-        const float wgt = (1.0f - acc.w) * c.w;
-        acc.x = fmaf(wgt, c.x, acc.x);
-        acc.y = fmaf(wgt, c.y, acc.y);
-        acc.z = fmaf(wgt, c.z, acc.z);
-        acc.w += wgt;
-        ++k;
-        if (acc.w >= ert) break;
-        q = qn;
-    }
-    count += static_cast<unsigned>(k - kb);
     return acc;
 }
 
@@ -695,13 +327,6 @@ __device__ __forceinline__ float4 march_bricked(const ModelDev& M, const RenderS
         if (fits) seg = min(seg * 2, kSegMax);
     }
     return acc;
-}
-
-__device__ __forceinline__ void add_count(unsigned long long* dst, unsigned long long count)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) count += __shfl_xor_sync(0xFFFFFFFFu, count, o);
-    if ((threadIdx.x & 31) == 0 && count) atomicAdd(dst, count);
 }
 
 // ----------------------------------------------------------------------------------------
