@@ -65,8 +65,8 @@ DECODE_WINDOW_BYTES = {1: 1 * 2 * 16, 2: 2 * 3 * 32, 3: 2 * 4 * 32, 4: 3 * 5 * 4
 # sources it was taken on (their SHA-256 is checked at run time; any change -> null).
 RENDER_TRAFFIC = {"src_sha256": "5512bb9d31aaa0112cb8d691f46bed0fd1e9f2f6c1dca82a8bf22b7564a25f24",
                   "bytes_per_launch": 16107520}
-KERNEL_SOURCES = ["paper_2312_15073_gb300/csrc/render.cu", "paper_2312_15073_gb300/csrc/bspline.cuh",
-                  "paper_2312_15073_gb300/csrc/mfa_internal.cuh"]
+KERNEL_SOURCES = ["paper_2312_15073_gb300/csrc/render.cu", "paper_2312_15073_gb300/csrc/raycast.cuh",
+                  "paper_2312_15073_gb300/csrc/bspline.cuh", "paper_2312_15073_gb300/csrc/mfa_internal.cuh"]
 
 
 def kernel_sources_sha256() -> str:
@@ -465,6 +465,7 @@ def run_ours(args):
     if ws == 1:
         line["precision"] = storage_throughput(mfa, torch, spec, job, tf)
         line["segments"] = segments_throughput(mfa, torch, model, job, tf, render_s)
+        line["isosurface"] = iso_throughput(mfa, torch, spec, model, job, tf)
     if ws == 1 and not args.no_serve:
         line["serving"] = dict(run_serve(mfa, rates=args.serve_rates, duration=args.serve_duration),
                                note="Poisson requests (sides 512..2048, 512..2048 samples) on 8 resident degree-3 "
@@ -514,6 +515,28 @@ def segments_throughput(mfa, torch, model, job, tf, single_s, frames=5):
         out["x".join(str(x) for x in g)] = {"ms_per_frame": ms, "samples_per_frame": int(cnt.item()) / frames,
                                             "samples_per_s": int(cnt.item()) / frames / (ms / 1e3)}
     return out
+
+
+def iso_throughput(mfa, torch, spec, model, job, tf, frames=5):
+    """Isosurface frames of the same model and view (iso = the median control point):
+    time per frame, queries per frame (samples marched plus refinement), pixels hit."""
+    W, H, NS = job.width, job.height, job.n_samples
+    iso = float(np.median(spec.ctrl))
+    img = torch.empty((H, W, 4), device="cuda")
+    depth = torch.empty((H, W), device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    mfa.render_iso(model, job.camera, tf, W, H, NS, iso, out=img, depth=depth)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(frames):
+        mfa.render_iso(model, job.camera, tf, W, H, NS, iso, out=img, depth=depth, samples_out=cnt)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b) / frames
+    q = int(cnt.item()) / frames
+    return {"iso": iso, "ms_per_frame": ms, "queries_per_frame": q, "queries_per_s": q / (ms / 1e3),
+            "pixels_hit": int(torch.isfinite(depth).sum().item())}
 
 
 def storage_throughput(mfa, torch, spec, job, tf, frames=5):

@@ -205,6 +205,25 @@ int mfa_render_segments(const mfa_model* model, const mfa_camera* camera, const 
                         const mfa_render_opts* opts);
 
 /*
+ * Isosurface rendering through MFA queries (Sec. IV-A.4 names isosurfaces as the other
+ * visualization the query interface serves).  Per pixel, the ray's samples (those of
+ * mfa_render) are queried in order until f - iso_value changes sign between two of them;
+ * the crossing is refined by 8 Newton steps on g(t) = f(o + t d) - iso_value with the
+ * analytic derivative grad f . d, kept inside the bracket (the bracket shrinks to the side
+ * where g changes sign; a Newton point outside it is replaced by its midpoint).  The hit is
+ * shaded like a volume sample of value iso_value (transfer-function colour, Phong with
+ * grad f when tf->shading) and is opaque: rgba_out (DEVICE, as mfa_render) holds
+ * (r, g, b, 1), or 0 where the ray has no crossing; depth_out (DEVICE [height][width]
+ * FP32, may be NULL) the hit's ray parameter t (distance from the eye for perspective
+ * views), +inf on a miss.  opts may be NULL (its tile_shape and samples_out -- the number
+ * of queries made -- apply).  MFA_ERR_ARG for a non-finite iso_value, otherwise errors as
+ * mfa_render_ex.
+ */
+int mfa_render_iso(const mfa_model* model, const mfa_camera* camera, const mfa_transfer_fn* tf, int width,
+                   int height, int n_samples, float iso_value, float* rgba_out, float* depth_out,
+                   const mfa_render_opts* opts);
+
+/*
  * Host-buffer forms of mfa_decode and mfa_render_ex: the same queries (Sec. III-B, the
  * query of Fig. 8 in Sec. V-D.3) and the same ray casting (Sec. IV-A.4), for data in HOST
  * memory.

@@ -119,6 +119,9 @@ def lib():
         L.mfa_render_ex.restype = c_int
         L.mfa_render_ex.argtypes = [c_void_p, POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int, c_void_p,
                                     POINTER(_Opts)]
+        L.mfa_render_iso.restype = c_int
+        L.mfa_render_iso.argtypes = [c_void_p, POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int, c_float, c_void_p,
+                                     c_void_p, POINTER(_Opts)]
         L.mfa_render_segments.restype = c_int
         L.mfa_render_segments.argtypes = [c_void_p, POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int, c_void_p,
                                           c_void_p, POINTER(_Opts)]
@@ -401,6 +404,31 @@ def render_host(model: Model, cam, tf: transfer_fn, width: int, height: int, n_s
     if sync:
         torch.cuda.current_stream().synchronize()
     return out
+
+
+def render_iso(model: Model, cam, tf: transfer_fn, width: int, height: int, n_samples: int, iso: float, out=None,
+               depth=None, samples_out=None, tile_shape: int = 0):
+    """Isosurface f = iso: (rgba (height, width, 4), depth (height, width)) CUDA tensors;
+    opaque shaded hits, transparent black and depth +inf where a ray has no crossing."""
+    import torch
+    if out is None:
+        out = torch.empty((height, width, 4), device="cuda", dtype=torch.float32)
+    if depth is None:
+        depth = torch.empty((height, width), device="cuda", dtype=torch.float32)
+    for t, name, n in ((out, "out", height * width * 4), (depth, "depth", height * width)):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.numel() == n):
+            raise ValueError(f"{name} must be a contiguous FP32 CUDA tensor of {n} values")
+    c = cam if isinstance(cam, _Camera) else camera(cam)
+    opts = _Opts()
+    opts.tile_shape = int(tile_shape)
+    if samples_out is not None:
+        if not (samples_out.is_cuda and samples_out.dtype == torch.int64):
+            raise TypeError("samples_out must be an int64 CUDA tensor")
+        opts.samples_out = samples_out.data_ptr()
+    _bind_stream()
+    _check(lib().mfa_render_iso(model.handle, ctypes.byref(c), ctypes.byref(tf.struct), width, height, n_samples,
+                                float(iso), out.data_ptr(), depth.data_ptr(), ctypes.byref(opts)))
+    return out, depth
 
 
 def render_segments(model: Model, cam, tf: transfer_fn, width: int, height: int, n_samples: int, blocks, out=None,

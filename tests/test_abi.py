@@ -70,6 +70,11 @@ def test_host_side_argument_checks(libmfa):
     g = (ctypes.c_int * 3)(8, 8, 2)
     assert L.mfa_render_segments(None, ctypes.byref(cam), ctypes.byref(tf.struct), 8, 8, 8, g, None, None) == -1
     assert "at most 64" in L.mfa_last_error().decode()
+    assert L.mfa_render_iso(None, ctypes.byref(cam), ctypes.byref(tf.struct), 8, 8, 8, ctypes.c_float(float("nan")),
+                            None, None, None) == -1
+    assert "finite" in L.mfa_last_error().decode()
+    assert L.mfa_render_iso(None, ctypes.byref(cam), ctypes.byref(tf.struct), 8, 8, 8, ctypes.c_float(0.5),
+                            None, None, None) == -1
     # model creation rejects bad degrees, counts and knots before any device work
     deg = (ctypes.c_int * 3)(3, 3, 5)
     nc = (ctypes.c_int * 3)(8, 8, 8)
