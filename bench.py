@@ -466,6 +466,7 @@ def run_ours(args):
         line["precision"] = storage_throughput(mfa, torch, spec, job, tf)
         line["segments"] = segments_throughput(mfa, torch, model, job, tf, render_s)
         line["isosurface"] = iso_throughput(mfa, torch, spec, model, job, tf)
+        line["marschner_lobb"] = ml_throughput(mfa, torch, tf)
     if ws == 1 and not args.no_serve:
         line["serving"] = dict(run_serve(mfa, rates=args.serve_rates, duration=args.serve_duration),
                                note="Poisson requests (sides 512..2048, 512..2048 samples) on 8 resident degree-3 "
@@ -515,6 +516,36 @@ def segments_throughput(mfa, torch, model, job, tf, single_s, frames=5):
         out["x".join(str(x) for x in g)] = {"ms_per_frame": ms, "samples_per_frame": int(cnt.item()) / frames,
                                             "samples_per_s": int(cnt.item()) / frames / (ms / 1e3)}
     return out
+
+
+def ml_throughput(mfa, torch, tf, frames=5):
+    """The paper's scalability workload shape on the Marschner-Lobb signal: degree 2, 256^3
+    control points (Greville-sampled), 768^2, 1024 samples per ray, Phong."""
+    import synth
+    spec = synth.marschner_lobb_model(256, 2)
+    model = mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl)
+    cam = synth.orbit_camera((0.5, 0.5, 0.5), 2.4, 0.6, 0.35, 32.0)
+    W = H = 768
+    NS = 1024
+    ml_tf = mfa.transfer_fn(synth.ramp_tf(256, 0.06), shading=True)
+    img = torch.empty((H, W, 4), device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    tuned, _ = mfa.tune_render(model, cam, ml_tf, W, H, NS, reps=3)
+    mfa.render(model, cam, ml_tf, W, H, NS, out=img, use_tuned=True)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(frames):
+        mfa.render(model, cam, ml_tf, W, H, NS, out=img, samples_out=cnt, use_tuned=True)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b) / frames
+    samples = int(cnt.item()) / frames
+    flops = samples * (query_flops(2) + RENDER_EXTRA_FLOPS)
+    model.close()
+    return {"model": "Marschner-Lobb, degree 2, 256^3 control points", "image": "768x768", "n_samples": NS,
+            "tuned": tuned, "ms_per_frame": ms, "samples_per_frame": samples, "samples_per_s": samples / (ms / 1e3),
+            "frac_fp32_peak": flops / (ms / 1e3) / 1e12 / (SMS * FP32_LANES * 2 * 2070e6 / 1e12)}
 
 
 def iso_throughput(mfa, torch, spec, model, job, tf, frames=5):

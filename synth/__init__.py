@@ -189,6 +189,39 @@ def view_up_for(direction: np.ndarray) -> tuple:
     return (0.0, 0.0, 1.0) if abs(direction[1]) > 0.99 else (0.0, 1.0, 0.0)
 
 
+@dataclass
+class MarschnerLobb:
+    """The Marschner-Lobb test signal with the paper's constants (f_M = 6, alpha = 0.25):
+        F(x, y, z) = (1 - sin(pi z / 2) + alpha (1 + rho(sqrt(x^2 + y^2)))) / (2 (1 + alpha)),
+        rho(r) = cos(2 pi f_M cos(pi r / 2)),
+    on its standard domain [-1, 1]^3, to which the unit parameter box maps linearly."""
+    f_m: float = 6.0
+    alpha: float = 0.25
+
+    def _f(self, X, Y, Z):
+        x, y, z = 2.0 * X - 1.0, 2.0 * Y - 1.0, 2.0 * Z - 1.0
+        rho = np.cos(2.0 * np.pi * self.f_m * np.cos(np.pi * np.sqrt(x * x + y * y) / 2.0))
+        return (1.0 - np.sin(np.pi * z / 2.0) + self.alpha * (1.0 + rho)) / (2.0 * (1.0 + self.alpha))
+
+    def grid(self, xs: np.ndarray, ys: np.ndarray, zs: np.ndarray) -> np.ndarray:
+        """Field on the tensor grid, shape (len(zs), len(ys), len(xs)), x fastest."""
+        Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+        return self._f(X, Y, Z)
+
+    def at(self, pts: np.ndarray) -> np.ndarray:
+        pts = np.asarray(pts, dtype=np.float64)
+        return self._f(pts[:, 0], pts[:, 1], pts[:, 2])
+
+
+def marschner_lobb_model(n: int = 256, degree: int = 2, dtype=np.float32) -> ModelSpec:
+    """Degree-p clamped-uniform model with n^3 control points: the Marschner-Lobb signal at
+    the Greville sites (a stand-in for the paper's MFA encoding of the sampled signal)."""
+    knots = [knots_uniform(n, degree)] * 3
+    f = MarschnerLobb()
+    P = sample_ctrl(f, knots, (degree,) * 3, None, 0.0)
+    return ModelSpec((degree,) * 3, (n, n, n), knots, P.astype(dtype), f)
+
+
 def orbit_camera(centre, dist: float, azimuth: float, elevation: float, fov_y_deg: float) -> dict:
     """Perspective camera on a sphere of radius `dist` around `centre`."""
     d = np.array([math.cos(elevation) * math.cos(azimuth), math.sin(elevation),

@@ -400,3 +400,22 @@ def test_random_models_against_oracle(mfa, orc, seed):
     g, r, gc, rc = _render_both(mfa, orc, model, ref, job)
     assert np.all(image_rmse(g, r) <= IMAGE_RMSE_TOL), (degree, nctrl, uniform, storage)
     assert abs(gc - rc) <= max(2, 1e-3 * rc)
+
+
+def test_render_marschner_lobb(mfa, orc):
+    """The Marschner-Lobb signal (degree 2, Greville-sampled): a small model's full image,
+    and the paper's scalability shape -- 256^3 control points, 768^2, 1024 samples -- on
+    2048 seeded pixels, against the oracle."""
+    cam = synth.orbit_camera((0.5, 0.5, 0.5), 2.4, 0.6, 0.35, 32.0)
+    table = synth.ramp_tf(256, 0.06)
+    for n, W, H, ns, pixels in ((40, 64, 48, 256, None), (256, 768, 768, 1024, 2048)):
+        spec = synth.marschner_lobb_model(n, 2)
+        model = mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl)
+        ref = orc.Model.from_spec(spec)
+        pix = None if pixels is None else np.random.default_rng(n).choice(W * H, pixels, replace=False)
+        job = synth.RenderJob(cam, W, H, ns, table, True)
+        g, r, gc, rc = _render_both(mfa, orc, model, ref, job, pixels=pix)
+        assert np.all(image_rmse(g, r) <= IMAGE_RMSE_TOL), (n, image_rmse(g, r))
+        assert r[..., 3].max() > 0.5
+        if pix is None:
+            assert abs(gc - rc) <= max(2, 1e-3 * rc)
