@@ -467,6 +467,7 @@ def run_ours(args):
         line["segments"] = segments_throughput(mfa, torch, model, job, tf, render_s)
         line["isosurface"] = iso_throughput(mfa, torch, spec, model, job, tf)
         line["marschner_lobb"] = ml_throughput(mfa, torch, tf)
+        line["encoding"] = encode_throughput(mfa, torch)
     if ws == 1 and not args.no_serve:
         line["serving"] = dict(run_serve(mfa, rates=args.serve_rates, duration=args.serve_duration),
                                note="Poisson requests (sides 512..2048, 512..2048 samples) on 8 resident degree-3 "
@@ -546,6 +547,30 @@ def ml_throughput(mfa, torch, tf, frames=5):
     return {"model": "Marschner-Lobb, degree 2, 256^3 control points", "image": "768x768", "n_samples": NS,
             "tuned": tuned, "ms_per_frame": ms, "samples_per_frame": samples, "samples_per_s": samples / (ms / 1e3),
             "frac_fp32_peak": flops / (ms / 1e3) / 1e12 / (SMS * FP32_LANES * 2 * 2070e6 / 1e12)}
+
+
+def encode_throughput(mfa, torch):
+    """MFA encoding of the Marschner-Lobb signal sampled on a 256^3 grid: one least-squares
+    fit to 128^3 degree-2 control points, and the adaptive encoding to 1 % of the signal's
+    range (time, control points, fits)."""
+    import synth
+    m = 256
+    u = np.arange(m, dtype=np.float64) / (m - 1)
+    data = torch.from_numpy(synth.MarschnerLobb().grid(u, u, u).astype(np.float32)).cuda()
+    out = {"data": "Marschner-Lobb at 256^3 grid points"}
+    mfa.fit_ctrl((2, 2, 2), (128, 128, 128), None, data)          # warm-up (pool, kernels)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    mfa.fit_ctrl((2, 2, 2), (128, 128, 128), None, data)
+    torch.cuda.synchronize()
+    out["fit_128cube_deg2_ms"] = 1e3 * (time.perf_counter() - t)
+    t = time.perf_counter()
+    model, res = mfa.model_encode((2, 2, 2), data, 0.01, max_ctrl=(256, 256, 256))
+    torch.cuda.synchronize()
+    out["adaptive"] = dict(res, err_max=0.01, seconds=time.perf_counter() - t,
+                           compression=m ** 3 / float(np.prod(res["nctrl"])))
+    model.close()
+    return out
 
 
 def iso_throughput(mfa, torch, spec, model, job, tf, frames=5):

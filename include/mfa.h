@@ -404,6 +404,47 @@ void mfa_server_destroy(mfa_server* server);
 int mfa_render_batch_static(const mfa_render_request* reqs, int n);
 
 /*
+ * MFA encoding (Sec. III-A, Sec. IV-A.2: the model a block is rendered from is fitted to the
+ * block's regular grid of values before visualization).  data: DEVICE FP32
+ * [ndata[2]][ndata[1]][ndata[0]], x fastest, the values at the uniform parameters
+ * u_i = i / (ndata[0] - 1) (likewise v, w).  The fit minimises the sum of squared errors
+ * at the data points over the control points (least squares along x, then y, then z; FP64,
+ * normal equations with a banded Cholesky factor per axis).  Errors: MFA_ERR_ARG when a
+ * knot span holds too few data parameters to determine the spline, ndata[d] < nctrl[d],
+ * bad knots (as mfa_model_create); MFA_ERR_UNSUPPORTED for a degree outside 1..4.  All
+ * three synchronise the bound stream.
+ *   mfa_fit_ctrl:      the fitted control points, DEVICE FP64 [nctrl[2]][nctrl[1]][nctrl[0]].
+ *   mfa_model_fit:     a model of the fit with the given storage type; *max_err (may be
+ *                      NULL) receives the largest |f - data| over the data points, with f
+ *                      evaluated by the model (FP32 arithmetic).
+ *   mfa_model_encode:  adaptive encoding: from degree + 1 control points per axis, fit and,
+ *                      while the largest error exceeds cfg->err_max, insert a knot at the
+ *                      middle of every knot span whose data exceed it (the error projected
+ *                      onto each axis by its maximum over the other two), refit; stop when
+ *                      the error is within err_max, when no axis can take another knot (a
+ *                      span with fewer than two data parameters, or cfg->max_ctrl reached --
+ *                      0 means ndata -- leftmost spans first), or after cfg->max_iter fits.
+ *                      *result (may be NULL) receives the fits made, the final error and
+ *                      control-point counts.
+ */
+typedef struct {
+    double err_max;      /* target largest |f - data| */
+    int max_ctrl[3];     /* control-point limit per axis (0: ndata) */
+    int max_iter;        /* fits at most, 1..1000 */
+} mfa_encode_config;
+typedef struct {
+    int iterations;      /* fits made */
+    double max_err;      /* largest error of the returned model */
+    int nctrl[3];        /* its control points per axis */
+} mfa_encode_result;
+int mfa_fit_ctrl(const int degree[3], const int nctrl[3], const double* const knots[3], const int ndata[3],
+                 const float* data, double* ctrl_out);
+mfa_model* mfa_model_fit(const int degree[3], const int nctrl[3], const double* const knots[3], const int ndata[3],
+                         const float* data, mfa_dtype storage, double* max_err);
+mfa_model* mfa_model_encode(const int degree[3], const int ndata[3], const float* data, mfa_dtype storage,
+                            const mfa_encode_config* cfg, mfa_encode_result* result);
+
+/*
  * Calibration for the roofline denominators (no counterpart in the paper: measurement
  * infrastructure).  Runs, on the current device and the bound stream, a chip-wide FP32
  * FMA kernel (scalar and packed FP32x2 forms) and a kernel of random 32-byte gathers from

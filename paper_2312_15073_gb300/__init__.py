@@ -81,6 +81,14 @@ class _Peaks(ctypes.Structure):
                 ("l2_gather_gbs", ctypes.c_double), ("fma_clock_mhz", ctypes.c_double), ("sm_count", c_int)]
 
 
+class _EncodeConfig(ctypes.Structure):
+    _fields_ = [("err_max", ctypes.c_double), ("max_ctrl", c_int * 3), ("max_iter", c_int)]
+
+
+class _EncodeResult(ctypes.Structure):
+    _fields_ = [("iterations", c_int), ("max_err", ctypes.c_double), ("nctrl", c_int * 3)]
+
+
 class _Info(ctypes.Structure):
     _fields_ = [("degree", c_int * 3), ("nctrl", c_int * 3), ("storage", c_int), ("vmin", c_float),
                 ("vmax", c_float), ("device_bytes", c_size_t), ("device", c_int), ("cardinal", c_int)]
@@ -119,6 +127,13 @@ def lib():
         L.mfa_render_ex.restype = c_int
         L.mfa_render_ex.argtypes = [c_void_p, POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int, c_void_p,
                                     POINTER(_Opts)]
+        L.mfa_fit_ctrl.restype = c_int
+        L.mfa_fit_ctrl.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+        L.mfa_model_fit.restype = c_void_p
+        L.mfa_model_fit.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p]
+        L.mfa_model_encode.restype = c_void_p
+        L.mfa_model_encode.argtypes = [c_void_p, c_void_p, c_void_p, c_int, POINTER(_EncodeConfig),
+                                       POINTER(_EncodeResult)]
         L.mfa_render_iso.restype = c_int
         L.mfa_render_iso.argtypes = [c_void_p, POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int, c_float, c_void_p,
                                      c_void_p, POINTER(_Opts)]
@@ -228,6 +243,20 @@ class Model:
         self.degree = tuple(int(d) for d in degree)
         self.nctrl = tuple(int(n) for n in nctrl)
         self.storage = storage
+
+    @classmethod
+    def _wrap(cls, h, storage: int) -> "Model":
+        """A Model owning an existing handle (made by the library, e.g. by a fit)."""
+        m = cls.__new__(cls)
+        m._h = h
+        m._knots = None
+        m._ctrl_keep = None
+        i = _Info()
+        _check(lib().mfa_model_get_info(h, ctypes.byref(i)))
+        m.degree = tuple(i.degree)
+        m.nctrl = tuple(i.nctrl)
+        m.storage = storage
+        return m
 
     @property
     def handle(self) -> int:
@@ -404,6 +433,66 @@ def render_host(model: Model, cam, tf: transfer_fn, width: int, height: int, n_s
     if sync:
         torch.cuda.current_stream().synchronize()
     return out
+
+
+def _fit_data(data):
+    import torch
+    if not (data.is_cuda and data.dtype == torch.float32 and data.is_contiguous() and data.dim() == 3):
+        raise ValueError("data must be a contiguous (m_z, m_y, m_x) FP32 CUDA tensor")
+    mz, my, mx = data.shape
+    return (c_int * 3)(int(mx), int(my), int(mz))
+
+
+def _knot_ptrs(knots):
+    if knots is None:
+        return None, None
+    keep = [None if k is None else np.ascontiguousarray(k, dtype=np.float64) for k in knots]
+    return keep, (c_void_p * 3)(*[None if k is None else k.ctypes.data for k in keep])
+
+
+def fit_ctrl(degree, nctrl, knots, data):
+    """Least-squares control points (n_z, n_y, n_x) FP64 CUDA tensor of a fit to data
+    (m_z, m_y, m_x) FP32 CUDA tensor at uniform parameters."""
+    import torch
+    md = _fit_data(data)
+    deg = (c_int * 3)(*[int(d) for d in degree])
+    nc = (c_int * 3)(*[int(n) for n in nctrl])
+    keep, kp = _knot_ptrs(knots)
+    out = torch.empty((int(nctrl[2]), int(nctrl[1]), int(nctrl[0])), device="cuda", dtype=torch.float64)
+    _bind_stream()
+    _check(lib().mfa_fit_ctrl(ctypes.byref(deg), ctypes.byref(nc), ctypes.byref(kp) if kp is not None else None,
+                              ctypes.byref(md), data.data_ptr(), out.data_ptr()))
+    return out
+
+
+def model_fit(degree, nctrl, knots, data, storage: int = MFA_F32):
+    """(Model of the least-squares fit, largest error at the data points)."""
+    md = _fit_data(data)
+    deg = (c_int * 3)(*[int(d) for d in degree])
+    nc = (c_int * 3)(*[int(n) for n in nctrl])
+    keep, kp = _knot_ptrs(knots)
+    err = ctypes.c_double()
+    _bind_stream()
+    h = lib().mfa_model_fit(ctypes.byref(deg), ctypes.byref(nc), ctypes.byref(kp) if kp is not None else None,
+                            ctypes.byref(md), data.data_ptr(), int(storage), ctypes.byref(err))
+    if not h:
+        raise MfaError(-1, lib().mfa_last_error().decode())
+    return Model._wrap(h, storage), err.value
+
+
+def model_encode(degree, data, err_max: float, max_ctrl=(0, 0, 0), max_iter: int = 64, storage: int = MFA_F32):
+    """Adaptive encoding of data (m_z, m_y, m_x) FP32 CUDA tensor: (Model, result dict with
+    iterations, max_err, nctrl)."""
+    md = _fit_data(data)
+    deg = (c_int * 3)(*[int(d) for d in degree])
+    cfg = _EncodeConfig(float(err_max), (c_int * 3)(*[int(x) for x in max_ctrl]), int(max_iter))
+    res = _EncodeResult()
+    _bind_stream()
+    h = lib().mfa_model_encode(ctypes.byref(deg), ctypes.byref(md), data.data_ptr(), int(storage), ctypes.byref(cfg),
+                               ctypes.byref(res))
+    if not h:
+        raise MfaError(-1, lib().mfa_last_error().decode())
+    return Model._wrap(h, storage), dict(iterations=res.iterations, max_err=res.max_err, nctrl=tuple(res.nctrl))
 
 
 def render_iso(model: Model, cam, tf: transfer_fn, width: int, height: int, n_samples: int, iso: float, out=None,

@@ -184,8 +184,12 @@ void mfa_model_destroy(mfa_model* m)
     delete m;
 }
 
-mfa_model* mfa_model_create_ex(const int degree[3], const int nctrl[3], const double* const knots[3],
-                               const void* ctrl, mfa_dtype in_dtype, mfa_dtype storage)
+}  // extern "C"
+
+namespace mfa {
+
+mfa_model* model_create(const int degree[3], const int nctrl[3], const double* const knots[3], const void* ctrl,
+                        mfa_dtype in_dtype, mfa_dtype storage, bool ctrl_on_device)
 {
     g_error.clear();
     if (!degree || !nctrl || !ctrl) return fail(MFA_ERR_ARG, "degree, nctrl and ctrl must be non-NULL"), nullptr;
@@ -254,7 +258,7 @@ mfa_model* mfa_model_create_ex(const int degree[3], const int nctrl[3], const do
     for (int a = 0; a < 3; ++a) knot_bytes += sizeof(double) * U[a].size();
 
     void* d_stage = nullptr;   // uploaded knots, stats and input control points; freed below
-    const size_t stage_bytes = align_up(knot_bytes, 256) + 256 + in_bytes;
+    const size_t stage_bytes = align_up(knot_bytes, 256) + 256 + (ctrl_on_device ? 0 : in_bytes);
     cudaError_t e;
     auto cleanup = [&](int code, const char* what, cudaError_t err) -> mfa_model* {
         if (err != cudaSuccess) cuda_fail(err, what); else fail(code, "%s", what);
@@ -277,8 +281,8 @@ mfa_model* mfa_model_create_ex(const int degree[3], const int nctrl[3], const do
         koff += sizeof(double) * U[a].size();
     }
     int* d_stats = reinterpret_cast<int*>(stage + align_up(knot_bytes, 256));
-    void* d_in = stage + align_up(knot_bytes, 256) + 256;
-    if ((e = cudaMemcpyAsync(d_in, ctrl, in_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    void* d_in = ctrl_on_device ? const_cast<void*>(ctrl) : stage + align_up(knot_bytes, 256) + 256;
+    if (!ctrl_on_device && (e = cudaMemcpyAsync(d_in, ctrl, in_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cleanup(0, "upload control points", e);
 
     char* tabs = static_cast<char*>(M->d_tables);
@@ -324,6 +328,16 @@ mfa_model* mfa_model_create_ex(const int degree[3], const int nctrl[3], const do
     M->dev.cardinal = uniform && degree[0] == Q - 1 && degree[1] == Q - 1 && degree[2] == Q - 1 ? 1 : 0;
     M->bytes = tab + win_bytes;
     return M;
+}
+
+}  // namespace mfa
+
+extern "C" {
+
+mfa_model* mfa_model_create_ex(const int degree[3], const int nctrl[3], const double* const knots[3],
+                               const void* ctrl, mfa_dtype in_dtype, mfa_dtype storage)
+{
+    return model_create(degree, nctrl, knots, ctrl, in_dtype, storage, false);
 }
 
 mfa_model* mfa_model_create(const int degree[3], const int nctrl[3], const double* const knots[3], const void* ctrl,
