@@ -56,9 +56,10 @@ def query_flops(p: int) -> int:
 
 
 RENDER_EXTRA_FLOPS = 40
-# window bytes a degree-p FP32 query gathers: ceil(q/2) layer pairs x q rows x one entry
-# (16 bytes at p = 1, 32 at p = 2, 3, 32 + 16 at p = 4)
-DECODE_WINDOW_BYTES = {1: 1 * 2 * 16, 2: 2 * 3 * 32, 3: 2 * 4 * 32, 4: 3 * 5 * 48}
+# window bytes a degree-p FP32 query gathers: q rows of its support, each row one load of
+# every z-layer pair's entry (16 bytes at p = 1, 32 at p = 3, 32 + 16 at p = 4) or, at
+# p = 2, one entry's layer pair and third-layer row (32 + 16 bytes)
+DECODE_WINDOW_BYTES = {1: 1 * 2 * 16, 2: 1 * 3 * 48, 3: 2 * 4 * 32, 4: 3 * 5 * 48}
 
 # DRAM bytes (read + write) of one k_render launch on this workload, from the ncu capture
 # summarised in profiles/k_render_p3_128cube_persp1024_ns1024.md, valid only for the kernel

@@ -67,7 +67,8 @@ typedef struct mfa_model mfa_model;   /* opaque; owns all of its device memory *
  *   dtype      type of ctrl.  Storage is FP32 for F64/F32 input, FP16 for F16, BF16 for
  *              BF16 (see mfa_model_create_ex to choose).
  * The padded layer-pair window layout the kernels read takes about 32 bytes per control
- * point (FP32 storage) or 16 bytes (FP16/BF16); the product of the padded sizes
+ * point (FP32 storage) or 16 bytes (FP16/BF16), twice that when the largest degree is 2
+ * (each entry also carries a third layer's row); the product of the padded sizes
  * (n_x+4)(n_y+4)(n_z+4) must stay below 2^31.
  * Synchronous: returns after the model is ready.  Returns NULL on error (reason in
  * mfa_last_error()).

@@ -250,7 +250,7 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
         off_rec[a] = tab;
         tab = align_up(tab + sizeof(float) * rec_stride(Q) * (n - p), 256);
     }
-    const size_t win_elem = storage == MFA_F32 ? 32 : 16;   // one layer-pair entry
+    const size_t win_elem = (storage == MFA_F32 ? 4 : 2) * window_values(Q);   // one window entry
     const size_t win_bytes = static_cast<size_t>(nxp * nyp * nzp) * win_elem;
     const size_t nctrl_total = static_cast<size_t>(nctrl[0]) * nctrl[1] * nctrl[2];
     const size_t in_bytes = nctrl_total * dtype_size(in_dtype);
@@ -299,9 +299,9 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
                                   const_cast<int*>(A.grid), A.G, st)) != cudaSuccess)
             return cleanup(0, "span tables", e);
     }
-    if ((e = launch_prep_window(d_in, in_dtype, storage, nctrl[0], nctrl[1], nctrl[2], M->d_win, st)) != cudaSuccess)
+    if ((e = launch_prep_window(d_in, in_dtype, storage, nctrl[0], nctrl[1], nctrl[2], Q, M->d_win, st)) != cudaSuccess)
         return cleanup(0, "window array", e);
-    if ((e = launch_prep_stats(M->d_win, storage, nctrl[0], nctrl[1], nctrl[2], d_stats, st)) != cudaSuccess)
+    if ((e = launch_prep_stats(M->d_win, storage, nctrl[0], nctrl[1], nctrl[2], Q, d_stats, st)) != cudaSuccess)
         return cleanup(0, "control-point statistics", e);
     int stats[3];
     if ((e = cudaMemcpyAsync(stats, d_stats, sizeof stats, cudaMemcpyDeviceToHost, st)) != cudaSuccess)

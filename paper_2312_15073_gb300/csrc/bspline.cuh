@@ -234,12 +234,13 @@ __device__ __forceinline__ void cardinal_basis(float t, float (&M)[Q], float (&G
 // (the same row of two consecutive z-layers side by side, the layout of a packed FP32x2
 // operand).  Entries past Q meet zero basis values; they are always inside the
 // zero-padded window array.  FP32: one 256-bit load (a 16-byte one for Q = 2; Q = 5 adds
-// 16 bytes of entry i + 4).
+// 16 bytes of entry i + 4).  load_triple (Q = 3) also returns the entry's third-layer row
+// r3[a] = P[k+2][j][i+a] (a 128-bit load of the entry's second half).
 template <int Q>
 struct PairF32 {
     static __device__ __forceinline__ void load(const void* win, int idx, f2 (&pr)[qpair(Q)])
     {
-        const float* e = static_cast<const float*>(win) + 8LL * idx;
+        const float* e = static_cast<const float*>(win) + static_cast<long long>(window_values(Q)) * idx;
         if constexpr (qpair(Q) == 2) {
             asm("ld.global.nc.v2.b64 {%0, %1}, [%2];" : "=l"(pr[0].v), "=l"(pr[1].v) : "l"(e));
         } else {
@@ -250,9 +251,19 @@ struct PairF32 {
         if constexpr (qpair(Q) == 6)
             asm("ld.global.nc.v2.b64 {%0, %1}, [%2];" : "=l"(pr[4].v), "=l"(pr[5].v) : "l"(e + 32));
     }
+    static __device__ __forceinline__ void load_triple(const void* win, int idx, f2 (&pr)[4], float (&r3)[4])
+    {
+        static_assert(Q == 3, "third-layer rows exist in degree-class-3 windows only");
+        load(win, idx, pr);
+        const float* e = static_cast<const float*>(win) + static_cast<long long>(window_values(Q)) * idx;
+        asm("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+            : "=f"(r3[0]), "=f"(r3[1]), "=f"(r3[2]), "=f"(r3[3])
+            : "l"(e + 8));
+    }
 };
 
-// 16-bit storage: an entry is 16 bytes, one 32-bit word {layer k, layer k+1} per column.
+// 16-bit storage: an entry is 16 bytes, one 32-bit word {layer k, layer k+1} per column
+// (32 bytes for Q = 3, the third-layer row in the first 8 bytes of the second half).
 template <int Q, bool BF16>
 struct Pair16 {
     static __device__ __forceinline__ float2 cvt(unsigned int bits)
@@ -272,7 +283,7 @@ struct Pair16 {
     }
     static __device__ __forceinline__ void load(const void* win, int idx, f2 (&pr)[qpair(Q)])
     {
-        const unsigned short* e = static_cast<const unsigned short*>(win) + 8LL * idx;
+        const unsigned short* e = static_cast<const unsigned short*>(win) + static_cast<long long>(window_values(Q)) * idx;
         if constexpr (qpair(Q) == 2) {
             const uint2 w = __ldg(reinterpret_cast<const uint2*>(e));
             pr[0] = cvt2(w.x);
@@ -290,6 +301,18 @@ struct Pair16 {
             pr[5] = cvt2(w.y);
         }
     }
+    static __device__ __forceinline__ void load_triple(const void* win, int idx, f2 (&pr)[4], float (&r3)[4])
+    {
+        static_assert(Q == 3, "third-layer rows exist in degree-class-3 windows only");
+        load(win, idx, pr);
+        const unsigned short* e = static_cast<const unsigned short*>(win) + static_cast<long long>(window_values(Q)) * idx;
+        const uint2 w = __ldg(reinterpret_cast<const uint2*>(e + 8));
+        const float2 lo = cvt(w.x), hi = cvt(w.y);
+        r3[0] = lo.x;
+        r3[1] = lo.y;
+        r3[2] = hi.x;
+        r3[3] = hi.y;
+    }
 };
 
 template <int Q, int STORAGE>
@@ -301,6 +324,62 @@ template <int Q> struct PairLoader<Q, 3> : Pair16<Q, true> {};     // MFA_BF16
 // ----------------------------------------------------------------------------------------
 // contraction
 // ----------------------------------------------------------------------------------------
+
+// Degree class 3: the support's three z-layers are the pair (k0, k0+1) of each entry, run
+// packed as in contract_pairs, and the entry's third-layer row k0+2, run as plain FP32
+// FMAs beside it (the same x, y and z sums; no lane multiplies a padding layer).  Weights
+// arrive packed as for contract_pairs: nz[0] = {Nz_0, Nz_1}, nz[1] = {Nz_2, 0}.
+__device__ __forceinline__ float lo2(f2 x)
+{
+    float a, b;
+    upk2(x, a, b);
+    return a;
+}
+
+template <int STORAGE>
+__device__ __forceinline__ float4 contract_triple(const ModelDev& M, int base, const f2 (&nx)[3], const f2 (&dx)[3],
+                                                  const f2 (&ny)[3], const f2 (&dy)[3], const f2 (&nz)[2],
+                                                  const f2 (&dz)[2])
+{
+    f2 CC, DD, EE;
+    float C3, D3, E3;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        f2 pr[4];
+        float r3[4];
+        PairLoader<3, STORAGE>::load_triple(M.win, base + b * M.nxp, pr, r3);
+        f2 A = mul2(nx[0], pr[0]);
+        f2 B = mul2(dx[0], pr[0]);
+        float A3 = lo2(nx[0]) * r3[0];
+        float B3 = lo2(dx[0]) * r3[0];
+#pragma unroll
+        for (int a = 1; a < 3; ++a) {
+            A = fma2(nx[a], pr[a], A);
+            B = fma2(dx[a], pr[a], B);
+            A3 = fmaf(lo2(nx[a]), r3[a], A3);
+            B3 = fmaf(lo2(dx[a]), r3[a], B3);
+        }
+        const float nyb = lo2(ny[b]), dyb = lo2(dy[b]);
+        if (b == 0) {
+            CC = mul2(ny[0], A);
+            DD = mul2(dy[0], A);
+            EE = mul2(ny[0], B);
+            C3 = nyb * A3;
+            D3 = dyb * A3;
+            E3 = nyb * B3;
+        } else {
+            CC = fma2(ny[b], A, CC);
+            DD = fma2(dy[b], A, DD);
+            EE = fma2(ny[b], B, EE);
+            C3 = fmaf(nyb, A3, C3);
+            D3 = fmaf(dyb, A3, D3);
+            E3 = fmaf(nyb, B3, E3);
+        }
+    }
+    const float nz2 = lo2(nz[1]), dz2 = lo2(dz[1]);
+    return make_float4(fmaf(nz2, C3, hsum2(mul2(nz[0], CC))), fmaf(nz2, E3, hsum2(mul2(nz[0], EE))),
+                       fmaf(nz2, D3, hsum2(mul2(nz[0], DD))), fmaf(dz2, C3, hsum2(mul2(dz[0], CC))));
+}
 
 // Sum-factorised contraction over the Q^3 support whose first row is window entry `base`
 // (= (k0 nyp + j0) nxp + i0 for the support origin (i0, j0, k0)):
@@ -321,6 +400,7 @@ __device__ __forceinline__ float4 contract_pairs(const ModelDev& M, int base, co
                                                  const f2 (&ny)[Q], const f2 (&dy)[Q], const f2 (&nz)[qpair(Q) / 2],
                                                  const f2 (&dz)[qpair(Q) / 2])
 {
+    if constexpr (Q == 3) return contract_triple<STORAGE>(M, base, nx, dx, ny, dy, nz, dz);
     constexpr int NP = qpair(Q) / 2;
     const int pair_step = 2 * M.nxp * M.nyp;
     f2 F, FX, FY, FZ;

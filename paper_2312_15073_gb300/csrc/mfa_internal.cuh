@@ -7,7 +7,10 @@
 //     storage) or 16 bytes (FP16 / BF16).  One aligned 256-bit load then fetches the same
 //     x-row of two z-layers of a (p+1)^3 support for p <= 3 (plus 16 bytes for p = 4), and
 //     each column pair is a ready operand of a packed FP32x2 FMA that advances both
-//     layers.  Costs 8x the plain array.
+//     layers.  Costs 8x the plain array.  Degree class Q = 3 (degree <= 2) appends the row
+//     of the third layer, P[k+2][j][i..i+3], and pads the entry to 16 values, so that one
+//     256-bit and one 128-bit load fetch a whole z-column of a support row (16x the plain
+//     array); window_values(Q) is the entry size in values.
 //   * per axis: kup[n+p+1]  the FP64 knots rounded UP to FP32, so that for an FP32
 //     coordinate u, (u >= kup[s]) is exactly (u >= U[s]) in real arithmetic;
 //     grid[G]  (G = 4 (n - p)) the span containing g / G, a starting guess for the span
@@ -34,6 +37,7 @@ constexpr int kPad = 4;                 // zero padding added to every axis of t
 // basis functions per axis rounded up to pairs, and floats per span record for
 // Q = p_max + 1: {U_s, 1/h, lo, hi} + Q*QP coefficients, padded to float4
 constexpr int kRecHead = 4;
+__host__ __device__ constexpr int window_values(int q) { return q == 3 ? 16 : 8; }
 __host__ __device__ constexpr int qpair(int q) { return (q + 1) / 2 * 2; }
 __host__ __device__ constexpr int rec_stride(int q) { return ((kRecHead + q * qpair(q)) + 3) / 4 * 4; }
 
@@ -117,9 +121,9 @@ __host__ __device__ constexpr int batch_group_cardinal(int g) { return g / 12; }
 // launchers (defined in the .cu files), all asynchronous on `stream`
 cudaError_t launch_prep_axis(const double* d_knots, int n, int p, int q, float* kup, float* rec, int* grid,
                              int G, cudaStream_t stream);
-cudaError_t launch_prep_window(const void* d_ctrl, int in_dtype, int storage, int nx, int ny, int nz,
+cudaError_t launch_prep_window(const void* d_ctrl, int in_dtype, int storage, int nx, int ny, int nz, int q,
                                void* win, cudaStream_t stream);
-cudaError_t launch_prep_stats(const void* win, int storage, int nx, int ny, int nz, int* d_stats,
+cudaError_t launch_prep_stats(const void* win, int storage, int nx, int ny, int nz, int q, int* d_stats,
                               cudaStream_t stream);
 cudaError_t launch_decode(const ModelDev& m, const float* pts, long long n, float* val, float* grad,
                           cudaStream_t stream);

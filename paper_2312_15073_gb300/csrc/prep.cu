@@ -2,7 +2,7 @@
 //
 // Turns the uploaded FP64 knots and input-dtype control points into the tables the query
 // kernels read (layout in mfa_internal.cuh): knots rounded up to FP32, the span-start
-// grid, per-span power-basis records, the 4-wide window array in the storage dtype, and
+// grid, per-span power-basis records, the layer-pair window array in the storage dtype, and
 // the min / max / max-abs of the stored control points.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -114,7 +114,7 @@ __device__ __forceinline__ unsigned short to16(double x, int storage)
 }
 
 // The layer-pair window array (layout in mfa_internal.cuh), one entry per thread.
-__global__ void k_window(const void* __restrict__ ctrl, int in_dtype, int storage, int nx, int ny, int nz,
+__global__ void k_window(const void* __restrict__ ctrl, int in_dtype, int storage, int nx, int ny, int nz, int q,
                          void* __restrict__ win)
 {
     const int nxp = nx + kPad, nyp = ny + kPad, nzp = nz + kPad;
@@ -125,30 +125,36 @@ __global__ void k_window(const void* __restrict__ ctrl, int in_dtype, int storag
         const long long jk = e / nxp;
         const int j = static_cast<int>(jk % nyp);
         const int k = static_cast<int>(jk / nyp);
-        double v[8];   // v[2a + r] = P[k + r][j][i + a]
+        // v[2a + r] = P[k + r][j][i + a]; for q == 3 also v[8 + a] = P[k + 2][j][i + a], then zeros
+        double v[16];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
+            for (int r = 0; r < 3; ++r) {
                 const int ia = i + a, kr = k + r;
-                v[2 * a + r] = (ia < nx && j < ny && kr < nz)
-                                   ? load_in(ctrl, in_dtype, (static_cast<long long>(kr) * ny + j) * nx + ia)
-                                   : 0.0;
+                const double x = (ia < nx && j < ny && kr < nz)
+                                     ? load_in(ctrl, in_dtype, (static_cast<long long>(kr) * ny + j) * nx + ia)
+                                     : 0.0;
+                if (r < 2) v[2 * a + r] = x; else v[8 + a] = x;
             }
+            v[12 + a] = 0.0;
         }
+        const int nv = window_values(q);
         if (storage == 1) {
-            float4* w = static_cast<float4*>(win) + 2 * e;
-            w[0] = make_float4(__double2float_rn(v[0]), __double2float_rn(v[1]), __double2float_rn(v[2]),
-                               __double2float_rn(v[3]));
-            w[1] = make_float4(__double2float_rn(v[4]), __double2float_rn(v[5]), __double2float_rn(v[6]),
-                               __double2float_rn(v[7]));
+            float4* w = static_cast<float4*>(win) + (nv / 4) * e;
+            for (int c = 0; c < nv / 4; ++c)
+                w[c] = make_float4(__double2float_rn(v[4 * c]), __double2float_rn(v[4 * c + 1]),
+                                   __double2float_rn(v[4 * c + 2]), __double2float_rn(v[4 * c + 3]));
         } else {
-            unsigned int b[4];
+            uint4* w = static_cast<uint4*>(win) + (nv / 8) * e;
+            for (int c = 0; c < nv / 8; ++c) {
+                unsigned int b[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
-                b[a] = static_cast<unsigned>(to16(v[2 * a], storage)) |
-                       (static_cast<unsigned>(to16(v[2 * a + 1], storage)) << 16);
-            static_cast<uint4*>(win)[e] = make_uint4(b[0], b[1], b[2], b[3]);
+                for (int a = 0; a < 4; ++a)
+                    b[a] = static_cast<unsigned>(to16(v[8 * c + 2 * a], storage)) |
+                           (static_cast<unsigned>(to16(v[8 * c + 2 * a + 1], storage)) << 16);
+                w[c] = make_uint4(b[0], b[1], b[2], b[3]);
+            }
         }
     }
 }
@@ -169,9 +175,11 @@ __global__ void k_stats_init(int* stats)
 
 // min, max and max |P| over the stored values (first element of each window entry in the
 // unpadded region)
-__global__ void k_stats(const void* __restrict__ win, int storage, int nx, int ny, int nz, int* __restrict__ stats)
+__global__ void k_stats(const void* __restrict__ win, int storage, int nx, int ny, int nz, int q,
+                        int* __restrict__ stats)
 {
     const int nxp = nx + kPad, nyp = ny + kPad;
+    const long long nv = window_values(q);
     const long long total = static_cast<long long>(nx) * ny * nz;
     float mn = INFINITY, mx = -INFINITY, ma = 0.0f;
     for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
@@ -183,9 +191,9 @@ __global__ void k_stats(const void* __restrict__ win, int storage, int nx, int n
         const long long w = (static_cast<long long>(k) * nyp + j) * nxp + i;
         float v;
         if (storage == 1) {
-            v = static_cast<const float*>(win)[8 * w];
+            v = static_cast<const float*>(win)[nv * w];
         } else {
-            const unsigned short b = static_cast<const unsigned short*>(win)[8 * w];
+            const unsigned short b = static_cast<const unsigned short*>(win)[nv * w];
             v = storage == 2 ? __half2float(__ushort_as_half(b)) : __bfloat162float(__ushort_as_bfloat16(b));
         }
         mn = fminf(mn, v);
@@ -224,23 +232,24 @@ cudaError_t launch_prep_axis(const double* d_knots, int n, int p, int q, float* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_prep_window(const void* d_ctrl, int in_dtype, int storage, int nx, int ny, int nz, void* win,
-                               cudaStream_t stream)
+cudaError_t launch_prep_window(const void* d_ctrl, int in_dtype, int storage, int nx, int ny, int nz, int q,
+                               void* win, cudaStream_t stream)
 {
     const long long total = static_cast<long long>(nx + kPad) * (ny + kPad) * (nz + kPad);
     const long long want = (total + 255) / 256;
     const int blocks = static_cast<int>(want < 65536 ? want : 65536);
-    k_window<<<blocks, 256, 0, stream>>>(d_ctrl, in_dtype, storage, nx, ny, nz, win);
+    k_window<<<blocks, 256, 0, stream>>>(d_ctrl, in_dtype, storage, nx, ny, nz, q, win);
     return cudaGetLastError();
 }
 
-cudaError_t launch_prep_stats(const void* win, int storage, int nx, int ny, int nz, int* d_stats, cudaStream_t stream)
+cudaError_t launch_prep_stats(const void* win, int storage, int nx, int ny, int nz, int q, int* d_stats,
+                              cudaStream_t stream)
 {
     k_stats_init<<<1, 1, 0, stream>>>(d_stats);
     const long long total = static_cast<long long>(nx) * ny * nz;
     const long long want = (total + 255) / 256;
     const int blocks = static_cast<int>(want < 4096 ? want : 4096);
-    k_stats<<<blocks, 256, 0, stream>>>(win, storage, nx, ny, nz, d_stats);
+    k_stats<<<blocks, 256, 0, stream>>>(win, storage, nx, ny, nz, q, d_stats);
     return cudaGetLastError();
 }
 

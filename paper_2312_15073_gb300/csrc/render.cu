@@ -158,15 +158,15 @@ constexpr int kSegMax = 64;
 
 // Row (k, j) of window entry idx, P[k][j][i..i+3], as FP32 (the even members of the
 // entry's column pairs).
-template <int STORAGE>
+template <int Q, int STORAGE>
 __device__ __forceinline__ float4 window_f32(const void* win, long long idx)
 {
     if constexpr (STORAGE == 1) {
-        const float4* e = static_cast<const float4*>(win) + 2 * idx;
+        const float4* e = static_cast<const float4*>(win) + (window_values(Q) / 4) * idx;
         const float4 lo = __ldg(e), hi = __ldg(e + 1);
         return make_float4(lo.x, lo.z, hi.x, hi.z);
     } else {
-        const uint4 w = __ldg(static_cast<const uint4*>(win) + idx);
+        const uint4 w = __ldg(static_cast<const uint4*>(win) + (window_values(Q) / 8) * idx);
         using P = Pair16<4, STORAGE == 3>;
         return make_float4(P::cvt(w.x).x, P::cvt(w.y).x, P::cvt(w.z).x, P::cvt(w.w).x);
     }
@@ -281,7 +281,7 @@ __device__ __forceinline__ float4 march_bricked(const ModelDev& M, const RenderS
                 const int ey = r % ext[1], ez = r / ext[1];
                 const long long gidx =
                     (static_cast<long long>(org[2] + ez) * nyp + (org[1] + ey)) * nxp + (org[0] + ex);
-                brick[(ez * kBrick + ey) * kBrick + ex] = window_f32<STORAGE>(M.win, gidx);
+                brick[(ez * kBrick + ey) * kBrick + ex] = window_f32<Q, STORAGE>(M.win, gidx);
             }
             __syncwarp();
         }
