@@ -12,7 +12,10 @@ Each function cites what it follows:
   * `eval_points` (decode): the value and analytic gradient of the tensor-product
     B-spline volume (Sec. III-B, Sec. V-D.3);
   * `render`: MFA-VV ray casting with the over operation between neighbouring samples
-    (Sec. IV-A.4) and user-set transfer function and shading (Sec. IV-B).
+    (Sec. IV-A.4) and user-set transfer function and shading (Sec. IV-B);
+  * `ml_eval`, `render_ml`: the closed-form Marschner-Lobb signal (Sec. V-A.1, Eq. 1) and
+    its direct render, the ground truth the paper compares renders against (Sec. V-D.3);
+  * `quality` (module): MSE, PSNR and SSIM between two images (Table II's metrics).
 
 Pins (see tests/test_oracle_*.py): partition of unity, the derivative sum, the
 Bernstein closed form, degree-1 trilinear interpolation, exact reproduction of linear
@@ -99,6 +102,11 @@ def _load():
         lib.orc_block_range.restype = None
         lib.orc_block_range.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_double, c_int,
                                         POINTER(c_int), POINTER(c_int)]
+        lib.orc_ml_eval.argtypes = [c_double, c_double, c_void_p, c_void_p]
+        lib.orc_ml_eval.restype = None
+        lib.orc_render_ml.argtypes = [c_double, c_double, POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int,
+                                      c_void_p, c_longlong, c_void_p, c_int]
+        lib.orc_render_ml.restype = c_longlong
         _lib = lib
     return _lib
 
@@ -322,6 +330,41 @@ def render_iso(model: Model, cam: dict, tf_rgba, width: int, height: int, n_samp
                                 n_samples, float(iso), pix_ptr, npix, _ptr(out), _ptr(depth),
                                 nthreads or default_threads())
     return out, depth, int(nq)
+
+
+def ml_eval(uvw, f_m: float = 6.0, alpha: float = 0.25) -> np.ndarray:
+    """{F, dF/du, dF/dv, dF/dw} of the Marschner-Lobb signal at a point of the unit box."""
+    x = _f64(uvw)
+    out = np.zeros(4)
+    _load().orc_ml_eval(f_m, alpha, _ptr(x), _ptr(out))
+    return out
+
+
+def render_ml(cam: dict, tf_rgba, width: int, height: int, n_samples: int, *, f_m: float = 6.0,
+              alpha: float = 0.25, shading: bool = False, ka=0.3, kd=0.6, ks=0.3, shininess=32.0,
+              ert_alpha=0.99, vmin=math.nan, vmax=math.nan, pixels=None, nthreads: int | None = None):
+    """render() of the closed-form Marschner-Lobb signal (vmin / vmax default to its range
+    [0, 1]).  Returns (rgba, samples evaluated)."""
+    tf_rgba = np.ascontiguousarray(tf_rgba, dtype=np.float32).reshape(-1, 4)
+    tf = _TF()
+    tf.n_entries = tf_rgba.shape[0]
+    tf.rgba = _ptr(tf_rgba)
+    tf.vmin = vmin
+    tf.vmax = vmax
+    tf.shading = 1 if shading else 0
+    tf.ka, tf.kd, tf.ks, tf.shininess = ka, kd, ks, shininess
+    tf.ert_alpha = ert_alpha
+    cam_s = _camera(cam)
+    if pixels is None:
+        out = np.zeros((height, width, 4))
+        npix, pix_ptr = width * height, None
+    else:
+        pixels = np.ascontiguousarray(pixels, dtype=np.int64)
+        out = np.zeros((len(pixels), 4))
+        npix, pix_ptr = len(pixels), _ptr(pixels)
+    ns = _load().orc_render_ml(f_m, alpha, ctypes.byref(cam_s), ctypes.byref(tf), width, height, n_samples,
+                               pix_ptr, npix, _ptr(out), nthreads or default_threads())
+    return out, int(ns)
 
 
 def block_range(blocks, block, o, d, t0: float, dt: float, n_samples: int):

@@ -388,13 +388,28 @@ static void tf_lookup(const orc_tf* tf, double f, double c[4])
 
 static double clamp01(double x) { return x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x); }
 
+void orc_ml_eval(double f_m, double alpha, const double uvw[3], double out[4]);
+
+/* The scalar field a ray samples: an MFA model, or (m == NULL) the closed-form
+ * Marschner-Lobb signal with constants f_m and alpha. */
+typedef struct {
+    const orc_model* m;
+    double f_m, alpha;
+} orc_field;
+
+static void orc_field_eval(const orc_field* fld, const double x[3], double q[4])
+{
+    if (fld->m) orc_eval(fld->m, x, q, NULL);
+    else orc_ml_eval(fld->f_m, fld->alpha, x, q);
+}
+
 /* Colour of the sample at ray parameter t (transfer function, then Phong if enabled). */
-static void orc_sample_colour(const orc_model* m, const orc_tf* tf, const double o[3], const double d[3],
+static void orc_sample_colour(const orc_field* fld, const orc_tf* tf, const double o[3], const double d[3],
                           double t, double gtiny, double c[4])
 {
     double x[3] = { o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2] };
     double q[4];
-    orc_eval(m, x, q, NULL);
+    orc_field_eval(fld, x, q);
     tf_lookup(tf, q[0], c);
     if (tf->shading) {
         double g[3] = { q[1], q[2], q[3] };
@@ -417,7 +432,7 @@ static void orc_sample_colour(const orc_model* m, const orc_tf* tf, const double
 }
 
 /* One pixel: returns premultiplied RGBA and the number of samples evaluated. */
-static long long orc_render_pixel(const orc_model* m, const orc_camera* cam, const orc_tf* tf,
+static long long orc_render_pixel(const orc_field* fld, const orc_camera* cam, const orc_tf* tf,
                                   int W, int H, int ns, int col, int row, double gtiny, double rgba[4])
 {
     double o[3], d[3], t0, t1;
@@ -429,7 +444,7 @@ static long long orc_render_pixel(const orc_model* m, const orc_camera* cam, con
     long long count = 0;
     for (int k = 0; k < ns; ++k) {
         double c[4];
-        orc_sample_colour(m, tf, o, d, t0 + (k + 0.5) * dt, gtiny, c);
+        orc_sample_colour(fld, tf, o, d, t0 + (k + 0.5) * dt, gtiny, c);
         ++count;
         double a = c[3];
         for (int ch = 0; ch < 3; ++ch) C[ch] += (1.0 - A) * a * c[ch];
@@ -441,7 +456,7 @@ static long long orc_render_pixel(const orc_model* m, const orc_camera* cam, con
 }
 
 typedef struct {
-    const orc_model* m; const orc_camera* cam; const orc_tf* tf;
+    const orc_field* fld; const orc_camera* cam; const orc_tf* tf;
     int W, H, ns; const long long* pix; double gtiny; double* out;
 } orc_render_ctx;
 
@@ -451,7 +466,7 @@ static void orc_render_body(void* vctx, long long b, long long e, long long* cou
     for (long long i = b; i < e; ++i) {
         long long p = c->pix ? c->pix[i] : i;
         int col = (int)(p % c->W), row = (int)(p / c->W);
-        *counter += orc_render_pixel(c->m, c->cam, c->tf, c->W, c->H, c->ns, col, row, c->gtiny, &c->out[4 * i]);
+        *counter += orc_render_pixel(c->fld, c->cam, c->tf, c->W, c->H, c->ns, col, row, c->gtiny, &c->out[4 * i]);
     }
 }
 
@@ -487,7 +502,8 @@ long long orc_render(const orc_model* m, const orc_camera* cam, const orc_tf* tf
     double gtiny;
     orc_prepare_tf(m, tf_in, &tf, &gtiny);
     if (!pix) npix = (long long)W * H;
-    orc_render_ctx ctx = { m, cam, &tf, W, H, ns, pix, gtiny, out };
+    const orc_field fld = { m, 0.0, 0.0 };
+    orc_render_ctx ctx = { &fld, cam, &tf, W, H, ns, pix, gtiny, out };
     return orc_parallel(npix, 16, nthreads, orc_render_body, &ctx);
 }
 
@@ -554,6 +570,7 @@ static long long orc_render_pixel_segments(const orc_model* m, const orc_camera*
     if (!orc_clip_unit_box(o, d, &t0, &t1)) return 0;
     const double dt = (t1 - t0) / ns;
     const int nb = g[0] * g[1] * g[2];
+    const orc_field fld = { m, 0.0, 0.0 };
     int kb[ORC_MAX_BLOCKS], ke[ORC_MAX_BLOCKS], done[ORC_MAX_BLOCKS];
     double part[ORC_MAX_BLOCKS][4];
     long long count = 0;
@@ -564,7 +581,7 @@ static long long orc_render_pixel_segments(const orc_model* m, const orc_camera*
         double C[3] = { 0.0, 0.0, 0.0 }, A = 0.0;
         for (int k = kb[b]; k < ke[b]; ++k) {   /* the block's segment, front to back */
             double c[4];
-            orc_sample_colour(m, tf, o, d, t0 + (k + 0.5) * dt, gtiny, c);
+            orc_sample_colour(&fld, tf, o, d, t0 + (k + 0.5) * dt, gtiny, c);
             ++count;
             double a = c[3];
             for (int ch = 0; ch < 3; ++ch) C[ch] += (1.0 - A) * a * c[ch];
@@ -740,4 +757,49 @@ long long orc_render_iso(const orc_model* m, const orc_camera* cam, const orc_tf
     if (!pix) npix = (long long)W * H;
     orc_iso_ctx ctx = { m, cam, &tf, W, H, ns, iso, pix, gtiny, out, depth };
     return orc_parallel(npix, 16, nthreads, orc_iso_body, &ctx);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Ground truth of the Marschner-Lobb workload (Sec. V-A.1, Eq. 1)                        */
+/* ------------------------------------------------------------------------------------ */
+/*
+ * The paper evaluates its renders against the closed-form signal
+ *     F(x, y, z) = (1 - sin(pi z / 2) + alpha (1 + rho(r))) / (2 (1 + alpha)),
+ *     rho(r) = cos(2 pi f_M cos(pi r / 2)),  r = sqrt(x^2 + y^2),
+ * rendered directly (its "ground truth" image, Sec. V-D.3).  Reading: the signal lives on
+ * [-1, 1]^3 and the unit parameter box maps onto it by x = 2u - 1 (likewise y, z), so the
+ * gradient with respect to (u, v, w) is twice the one with respect to (x, y, z):
+ *     dF/dz = -(pi / 2) cos(pi z / 2) / (2 (1 + alpha)),
+ *     dF/dx = alpha rho'(r) (x / r) / (2 (1 + alpha)),   likewise dF/dy with y,
+ *     rho'(r) = pi^2 f_M sin(2 pi f_M cos(pi r / 2)) sin(pi r / 2),
+ * where rho'(r) / r is continued to r = 0 by sin(pi r / 2) / r -> pi / 2.  F spans [0, 1]
+ * exactly, which is the transfer function's default value range here; the normal is
+ * undefined where |grad F| <= 1e-6 (the field's range times 1e-6).
+ */
+void orc_ml_eval(double f_m, double alpha, const double uvw[3], double out[4])
+{
+    const double x = 2.0 * uvw[0] - 1.0, y = 2.0 * uvw[1] - 1.0, z = 2.0 * uvw[2] - 1.0;
+    const double r = sqrt(x * x + y * y);
+    const double c = cos(M_PI * r / 2.0);
+    const double rho = cos(2.0 * M_PI * f_m * c);
+    const double den = 2.0 * (1.0 + alpha);
+    out[0] = (1.0 - sin(M_PI * z / 2.0) + alpha * (1.0 + rho)) / den;
+    const double sinc = r > 0.0 ? sin(M_PI * r / 2.0) / r : M_PI / 2.0;
+    const double drho_over_r = M_PI * M_PI * f_m * sin(2.0 * M_PI * f_m * c) * sinc;
+    out[1] = 2.0 * alpha * drho_over_r * x / den;
+    out[2] = 2.0 * alpha * drho_over_r * y / den;
+    out[3] = 2.0 * (-(M_PI / 2.0) * cos(M_PI * z / 2.0)) / den;
+}
+
+/* render() of the closed-form signal instead of a model. */
+long long orc_render_ml(double f_m, double alpha, const orc_camera* cam, const orc_tf* tf_in, int W, int H, int ns,
+                        const long long* pix, long long npix, double* out, int nthreads)
+{
+    orc_tf tf = *tf_in;
+    if (isnan(tf.vmin)) tf.vmin = 0.0;
+    if (isnan(tf.vmax)) tf.vmax = 1.0;
+    if (!pix) npix = (long long)W * H;
+    const orc_field fld = { NULL, f_m, alpha };
+    orc_render_ctx ctx = { &fld, cam, &tf, W, H, ns, pix, 1e-6, out };
+    return orc_parallel(npix, 16, nthreads, orc_render_body, &ctx);
 }
