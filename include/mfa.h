@@ -225,6 +225,48 @@ int mfa_render_iso(const mfa_model* model, const mfa_camera* camera, const mfa_t
                    const mfa_render_opts* opts);
 
 /*
+ * Ground truth of the render-quality comparison (Sec. V-D.3): the closed-form
+ * Marschner-Lobb signal (Sec. V-A.1, Eq. 1)
+ *     F(x, y, z) = (1 - sin(pi z / 2) + alpha (1 + rho(r))) / (2 (1 + alpha)),
+ *     rho(r) = cos(2 pi f_M cos(pi r / 2)),  r = sqrt(x^2 + y^2),
+ * on [-1, 1]^3, which the unit box maps onto by x = 2u - 1 (likewise y, z), rendered with
+ * the rays, samples, transfer function, Phong shading (with the analytic gradient with
+ * respect to (u, v, w)), over and early termination of mfa_render.  A NaN tf->vmin / vmax
+ * means F's range [0, 1]; the normal is undefined where |grad F| <= 1e-6.  Values in FP32.
+ * The paper uses f_M = 6, alpha = 0.25.  rgba_out (DEVICE) and opts as mfa_render_iso.
+ * MFA_ERR_ARG for a NULL signal, f_m or alpha negative or not finite, otherwise errors as
+ * mfa_render_ex.  Asynchronous on the bound stream.
+ */
+typedef struct {
+    double f_m;     /* radial frequency f_M */
+    double alpha;   /* weight of the radial term */
+} mfa_ml_signal;
+int mfa_render_ml(const mfa_ml_signal* signal, const mfa_camera* camera, const mfa_transfer_fn* tf, int width,
+                  int height, int n_samples, float* rgba_out, const mfa_render_opts* opts);
+
+/*
+ * Image metrics of the render-quality comparison (Table II: MSE, PSNR, SSIM) between two
+ * premultiplied RGBA FP32 images of width x height pixels (DEVICE, [height][width][4],
+ * 16-byte aligned).  R, G, B are clamped to [0, 1] and scaled by 255 (alpha is ignored);
+ *   mse      mean over pixels and the three channels of the squared difference;
+ *   psnr_db  10 log10(255^2 / mse), +inf for equal images;
+ *   ssim     the structural similarity of Wang et al. (IEEE TIP 2004) with an 11 x 11
+ *            Gaussian window (sigma 1.5, weights summing to 1), C1 = (0.01 * 255)^2,
+ *            C2 = (0.03 * 255)^2, averaged over the window positions lying inside the
+ *            image and over the three channels (symmetric in the two images).
+ * Sums in FP64 in a fixed order (the result does not depend on timing).  A few KB of
+ * scratch from the library's staging pool; synchronises the bound stream.  MFA_ERR_ARG
+ * for NULL or misaligned pointers or a side outside 11..32768; MFA_ERR_CUDA on a failed
+ * CUDA call.
+ */
+typedef struct {
+    double mse;
+    double psnr_db;
+    double ssim;
+} mfa_image_quality;
+int mfa_image_compare(const float* rgba_test, const float* rgba_ref, int width, int height, mfa_image_quality* out);
+
+/*
  * Host-buffer forms of mfa_decode and mfa_render_ex: the same queries (Sec. III-B, the
  * query of Fig. 8 in Sec. V-D.3) and the same ray casting (Sec. IV-A.4), for data in HOST
  * memory.

@@ -81,6 +81,14 @@ class _Peaks(ctypes.Structure):
                 ("l2_gather_gbs", ctypes.c_double), ("fma_clock_mhz", ctypes.c_double), ("sm_count", c_int)]
 
 
+class _MlSignal(ctypes.Structure):
+    _fields_ = [("f_m", ctypes.c_double), ("alpha", ctypes.c_double)]
+
+
+class _Quality(ctypes.Structure):
+    _fields_ = [("mse", ctypes.c_double), ("psnr_db", ctypes.c_double), ("ssim", ctypes.c_double)]
+
+
 class _EncodeConfig(ctypes.Structure):
     _fields_ = [("err_max", ctypes.c_double), ("max_ctrl", c_int * 3), ("max_iter", c_int)]
 
@@ -140,6 +148,11 @@ def lib():
         L.mfa_render_segments.restype = c_int
         L.mfa_render_segments.argtypes = [c_void_p, POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int, c_void_p,
                                           c_void_p, POINTER(_Opts)]
+        L.mfa_render_ml.restype = c_int
+        L.mfa_render_ml.argtypes = [POINTER(_MlSignal), POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int, c_void_p,
+                                    POINTER(_Opts)]
+        L.mfa_image_compare.restype = c_int
+        L.mfa_image_compare.argtypes = [c_void_p, c_void_p, c_int, c_int, POINTER(_Quality)]
         L.mfa_measure_peaks.restype = c_int
         L.mfa_measure_peaks.argtypes = [POINTER(_Peaks)]
         L.mfa_decode_host.restype = c_int
@@ -518,6 +531,44 @@ def render_iso(model: Model, cam, tf: transfer_fn, width: int, height: int, n_sa
     _check(lib().mfa_render_iso(model.handle, ctypes.byref(c), ctypes.byref(tf.struct), width, height, n_samples,
                                 float(iso), out.data_ptr(), depth.data_ptr(), ctypes.byref(opts)))
     return out, depth
+
+
+def render_ml(cam, tf: transfer_fn, width: int, height: int, n_samples: int, f_m: float = 6.0, alpha: float = 0.25,
+              out=None, samples_out=None, tile_shape: int = 0):
+    """Render of the closed-form Marschner-Lobb signal (the render-quality ground truth) with
+    the rays, samples, shading and compositing of render(): a (height, width, 4) CUDA tensor."""
+    import torch
+    if out is None:
+        out = torch.empty((height, width, 4), device="cuda", dtype=torch.float32)
+    if not (out.is_cuda and out.dtype == torch.float32 and out.is_contiguous() and out.numel() == height * width * 4):
+        raise ValueError("out must be a contiguous (height, width, 4) FP32 CUDA tensor")
+    c = cam if isinstance(cam, _Camera) else camera(cam)
+    sig = _MlSignal(float(f_m), float(alpha))
+    opts = _Opts()
+    opts.tile_shape = int(tile_shape)
+    if samples_out is not None:
+        if not (samples_out.is_cuda and samples_out.dtype == torch.int64):
+            raise TypeError("samples_out must be an int64 CUDA tensor")
+        opts.samples_out = samples_out.data_ptr()
+    _bind_stream()
+    _check(lib().mfa_render_ml(ctypes.byref(sig), ctypes.byref(c), ctypes.byref(tf.struct), width, height, n_samples,
+                               out.data_ptr(), ctypes.byref(opts)))
+    return out
+
+
+def image_compare(test, ref) -> dict:
+    """MSE, PSNR (dB) and SSIM of two (height, width, 4) FP32 CUDA images (RGB on the
+    0..255 display scale)."""
+    for t, name in ((test, "test"), (ref, "ref")):
+        if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 4 and t.is_contiguous()
+                and t.dim() == 3 and t.shape[2] == 4):
+            raise ValueError(f"{name} must be a contiguous (height, width, 4) FP32 CUDA tensor")
+    if test.shape != ref.shape:
+        raise ValueError("images differ in shape")
+    q = _Quality()
+    _bind_stream()
+    _check(lib().mfa_image_compare(test.data_ptr(), ref.data_ptr(), test.shape[1], test.shape[0], ctypes.byref(q)))
+    return {"mse": q.mse, "psnr_db": q.psnr_db, "ssim": q.ssim}
 
 
 def render_segments(model: Model, cam, tf: transfer_fn, width: int, height: int, n_samples: int, blocks, out=None,

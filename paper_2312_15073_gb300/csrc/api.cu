@@ -84,19 +84,20 @@ int check_model_device(const mfa_model* m)
     return MFA_OK;
 }
 
-// Validates one render call and fills the kernel's scalars and table.  Checks the model,
-// camera, transfer function, sizes and output; returns MFA_OK or an error code.
-int setup_render(const mfa_model* m, const mfa_camera* cam, const mfa_transfer_fn* tf, int width, int height,
-                 int n_samples, float* rgba_out, unsigned long long* samples_out, RenderScalars& S, float4* table)
+// Validates the view of one render call (camera, transfer function, sizes, output) and
+// fills the kernel's scalars and table.  The field's value range [fmin, fmax] replaces a NaN
+// vmin / vmax; gtiny is the gradient norm below which the normal is undefined.
+int setup_view(const mfa_camera* cam, const mfa_transfer_fn* tf, int width, int height, int n_samples,
+               float* rgba_out, unsigned long long* samples_out, float fmin, float fmax, double gtiny,
+               RenderScalars& S, float4* table)
 {
-    if (!m || !cam || !tf || !rgba_out) return fail(MFA_ERR_ARG, "model, camera, tf and rgba_out must be non-NULL");
+    if (!cam || !tf || !rgba_out) return fail(MFA_ERR_ARG, "camera, tf and rgba_out must be non-NULL");
     if (width < 1 || width > 32768 || height < 1 || height > 32768)
         return fail(MFA_ERR_ARG, "image size %dx%d outside 1..32768", width, height);
     if (n_samples < 1 || n_samples > (1 << 20)) return fail(MFA_ERR_ARG, "n_samples = %d outside 1..2^20", n_samples);
     if (tf->n_entries < 1 || tf->n_entries > kTfMax || !tf->rgba)
         return fail(MFA_ERR_ARG, "transfer function needs 1..%d rows and a table", kTfMax);
     if (cam->projection != 0 && cam->projection != 1) return fail(MFA_ERR_ARG, "projection must be 0 or 1");
-    if (int rc = check_model_device(m)) return rc;
 
     // camera frame in FP64, handed to the kernel in FP32
     double f[3], r[3], u[3];
@@ -140,8 +141,8 @@ int setup_render(const mfa_model* m, const mfa_camera* cam, const mfa_transfer_f
     S.n_samples = n_samples;
     S.inv_w = 1.0f / static_cast<float>(width);
     S.inv_h = 1.0f / static_cast<float>(height);
-    const float vmin = std::isnan(tf->vmin) ? m->vmin : tf->vmin;
-    const float vmax = std::isnan(tf->vmax) ? m->vmax : tf->vmax;
+    const float vmin = std::isnan(tf->vmin) ? fmin : tf->vmin;
+    const float vmax = std::isnan(tf->vmax) ? fmax : tf->vmax;
     S.vmin = vmin;
     S.inv_range = vmax > vmin ? static_cast<float>(1.0 / (static_cast<double>(vmax) - vmin)) : 0.0f;
     S.tf_n = tf->n_entries;
@@ -151,16 +152,28 @@ int setup_render(const mfa_model* m, const mfa_camera* cam, const mfa_transfer_f
     S.ks = tf->ks;
     S.shininess = tf->shininess;
     S.ert_alpha = tf->ert_alpha >= 1.0f ? INFINITY : tf->ert_alpha;
-    int spans = 0;
-    for (int a = 0; a < 3; ++a) spans = std::max(spans, m->nctrl[a] - m->degree[a]);
-    double scale = std::max(static_cast<double>(m->vmax) - m->vmin, static_cast<double>(m->maxabs));
-    double gt = 1e-6 * scale * spans;
-    S.gtiny2 = static_cast<float>(gt * gt);
+    S.gtiny2 = static_cast<float>(gtiny * gtiny);
     S.samples_out = samples_out;
     S.out = reinterpret_cast<float4*>(rgba_out);
     for (int i = 0; i < tf->n_entries; ++i)
         table[i] = make_float4(tf->rgba[4 * i], tf->rgba[4 * i + 1], tf->rgba[4 * i + 2], tf->rgba[4 * i + 3]);
     return MFA_OK;
+}
+
+// Validates one render call of a model and fills the kernel's scalars and table: the model
+// (on the current device), then the view with the model's value range and a normal
+// threshold of 1e-6 G, G = max(range, max |P|) x the most spans of an axis (a bound on the
+// gradient's scale).
+int setup_render(const mfa_model* m, const mfa_camera* cam, const mfa_transfer_fn* tf, int width, int height,
+                 int n_samples, float* rgba_out, unsigned long long* samples_out, RenderScalars& S, float4* table)
+{
+    if (!m) return fail(MFA_ERR_ARG, "model, camera, tf and rgba_out must be non-NULL");
+    if (int rc = check_model_device(m)) return rc;
+    int spans = 0;
+    for (int a = 0; a < 3; ++a) spans = std::max(spans, m->nctrl[a] - m->degree[a]);
+    const double scale = std::max(static_cast<double>(m->vmax) - m->vmin, static_cast<double>(m->maxabs));
+    return setup_view(cam, tf, width, height, n_samples, rgba_out, samples_out, m->vmin, m->vmax, 1e-6 * scale * spans,
+                      S, table);
 }
 
 }  // namespace mfa

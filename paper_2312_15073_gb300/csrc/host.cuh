@@ -42,7 +42,13 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
 // The library's device staging pool on device `dev` (created on first use, memory kept
 // cached between calls; allocate and free with the stream-ordered pool calls).
 cudaError_t staging_pool(int dev, cudaMemPool_t* out);
-// Validates one render call and fills the kernel's scalars and table (tf_n rows).
+// Validates the view of a render call (camera, transfer function, sizes, output) and fills
+// the kernel's scalars and table; [fmin, fmax] stands in for a NaN vmin / vmax, gtiny is the
+// gradient norm below which the normal is undefined.
+int setup_view(const mfa_camera* cam, const mfa_transfer_fn* tf, int width, int height, int n_samples,
+               float* rgba_out, unsigned long long* samples_out, float fmin, float fmax, double gtiny,
+               RenderScalars& S, float4* table);
+// Validates one render call of a model and fills the kernel's scalars and table (tf_n rows).
 int setup_render(const mfa_model* m, const mfa_camera* cam, const mfa_transfer_fn* tf, int width, int height,
                  int n_samples, float* rgba_out, unsigned long long* samples_out, RenderScalars& S, float4* table);
 

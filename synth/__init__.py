@@ -212,6 +212,20 @@ class MarschnerLobb:
         pts = np.asarray(pts, dtype=np.float64)
         return self._f(pts[:, 0], pts[:, 1], pts[:, 2])
 
+    def grid_device(self, m: int, device="cuda"):
+        """The field at the m^3 uniform grid parameters i / (m - 1), as an (m, m, m) FP32
+        torch tensor built on `device` (FP64 arithmetic; the signal is a z term plus an
+        (x, y) term, so only their sum is m^3 work)."""
+        import torch
+        u = torch.arange(m, dtype=torch.float64, device=device) / (m - 1)
+        x = 2.0 * u - 1.0
+        den = 2.0 * (1.0 + self.alpha)
+        r = torch.sqrt(x[:, None] ** 2 + x[None, :] ** 2)                      # [y][x]
+        rho = torch.cos(2.0 * math.pi * self.f_m * torch.cos(math.pi * r / 2.0))
+        fxy = (self.alpha * (1.0 + rho) / den).to(torch.float32)
+        fz = ((1.0 - torch.sin(math.pi * x / 2.0)) / den).to(torch.float32)
+        return fz[:, None, None] + fxy[None, :, :]
+
 
 def marschner_lobb_model(n: int = 256, degree: int = 2, dtype=np.float32) -> ModelSpec:
     """Degree-p clamped-uniform model with n^3 control points: the Marschner-Lobb signal at

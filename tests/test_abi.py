@@ -75,6 +75,21 @@ def test_host_side_argument_checks(libmfa):
     assert "finite" in L.mfa_last_error().decode()
     assert L.mfa_render_iso(None, ctypes.byref(cam), ctypes.byref(tf.struct), 8, 8, 8, ctypes.c_float(0.5),
                             None, None, None) == -1
+    # the ground-truth render and the image metrics check their arguments first too
+    assert L.mfa_render_ml(None, ctypes.byref(cam), ctypes.byref(tf.struct), 8, 8, 8, None, None) == -1
+    assert "signal" in L.mfa_last_error().decode()
+    sig = mfa._MlSignal(6.0, -0.25)
+    assert L.mfa_render_ml(ctypes.byref(sig), ctypes.byref(cam), ctypes.byref(tf.struct), 8, 8, 8, None, None) == -1
+    assert "alpha" in L.mfa_last_error().decode()
+    sig = mfa._MlSignal(6.0, 0.25)
+    assert L.mfa_render_ml(ctypes.byref(sig), ctypes.byref(cam), ctypes.byref(tf.struct), 8, 8, 8, None, None) == -1
+    assert "NULL" in L.mfa_last_error().decode()
+    q = mfa._Quality()
+    assert L.mfa_image_compare(None, None, 16, 16, ctypes.byref(q)) == -1
+    assert L.mfa_image_compare(0x1004, 0x2000, 16, 16, ctypes.byref(q)) == -1
+    assert "aligned" in L.mfa_last_error().decode()
+    assert L.mfa_image_compare(0x1000, 0x2000, 10, 16, ctypes.byref(q)) == -1
+    assert "11..32768" in L.mfa_last_error().decode()
     # model creation rejects bad degrees, counts and knots before any device work
     deg = (ctypes.c_int * 3)(3, 3, 5)
     nc = (ctypes.c_int * 3)(8, 8, 8)

@@ -33,3 +33,14 @@ def test_range_and_model():
     assert spec.ctrl.shape == (20, 20, 20) and spec.degree == (2, 2, 2)
     g = synth.greville(spec.knots[0], 2)
     np.testing.assert_allclose(spec.ctrl[3, 5, 7], f.at(np.array([[g[7], g[5], g[3]]]))[0], rtol=1e-6)
+
+
+def test_device_grid_matches_host_grid():
+    torch = __import__("pytest").importorskip("torch")
+    f = synth.MarschnerLobb()
+    m = 17
+    u = np.arange(m, dtype=np.float64) / (m - 1)
+    ref = f.grid(u, u, u)
+    got = f.grid_device(m, device="cpu").numpy()
+    assert got.shape == (m, m, m) and got.dtype == np.float32
+    np.testing.assert_allclose(got, ref, rtol=0, atol=2e-7)
