@@ -1,7 +1,8 @@
 // iso.cu -- isosurface rendering through MFA queries (mfa_render_iso): the other
 // visualization the paper names for its query interface (Sec. IV-A.4).  One thread per
 // pixel: the ray's samples (the volume render's positions) are queried in order until
-// f - iso changes sign between two of them; the crossing is refined by kIsoSteps Newton
+// f - iso changes sign between two of them (value-only queries: no derivative weights, about
+// half the multiply-adds of a value+gradient query); the crossing is refined by kIsoSteps Newton
 // steps on g(t) = f(o + t d) - iso with the analytic derivative g'(t) = grad f . d, kept
 // inside the bracket (each step shrinks the bracket to the side where g changes sign and
 // falls back to its midpoint when the Newton point leaves it); the hit is shaded like a
@@ -38,11 +39,10 @@ struct RayQuery<Q, STORAGE, true> {
         base = 0;
     }
 
-    // {f, df/du, df/dv, df/dw} at the parameter point (u, v, w) of the unit box
-    __device__ __forceinline__ float4 at(const ModelDev& M, float u, float v, float w)
+    // brings the span state to the point and returns the local coordinates
+    __device__ __forceinline__ void locate(const ModelDev& M, float u, float v, float w, float (&t)[3])
     {
         const float x[3] = { u * m[0], v * m[1], w * m[2] };
-        float t[3];
         bool moved = false;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -54,6 +54,25 @@ struct RayQuery<Q, STORAGE, true> {
             }
         }
         if (moved) base = (c[2].j * M.nyp + c[1].j) * M.nxp + c[0].j;
+    }
+
+    // f at the parameter point (u, v, w) of the unit box
+    __device__ __forceinline__ float value(const ModelDev& M, float u, float v, float w)
+    {
+        float t[3];
+        locate(M, u, v, w, t);
+        float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];   // derivatives unused: dropped by the compiler
+        card_basis<Q>(M.ax[0], c[0], t[0], Nx, Dx);
+        card_basis<Q>(M.ax[1], c[1], t[1], Ny, Dy);
+        card_basis<Q>(M.ax[2], c[2], t[2], Nz, Dz);
+        return value_at<Q, STORAGE>(M, base, Nx, Ny, Nz) * Cardinal<Q>::kValScale;
+    }
+
+    // {f, df/du, df/dv, df/dw} at the parameter point (u, v, w) of the unit box
+    __device__ __forceinline__ float4 at(const ModelDev& M, float u, float v, float w)
+    {
+        float t[3];
+        locate(M, u, v, w, t);
         float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];
         card_basis<Q>(M.ax[0], c[0], t[0], Nx, Dx);
         card_basis<Q>(M.ax[1], c[1], t[1], Ny, Dy);
@@ -78,6 +97,19 @@ struct RayQuery<Q, STORAGE, false> {
         for (int a = 0; a < 3; ++a) c[a].s = -1;
     }
 
+    __device__ __forceinline__ float value(const ModelDev& M, float u, float v, float w)
+    {
+        const float x[3] = { clamp01(u), clamp01(v), clamp01(w) };
+#pragma unroll
+        for (int a = 0; a < 3; ++a) axis_update<Q>(M.ax[a], c[a], x[a]);
+        float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];   // derivatives unused: dropped by the compiler
+        record_basis<Q>(c[0].rec, x[0], Nx, Dx);
+        record_basis<Q>(c[1].rec, x[1], Ny, Dy);
+        record_basis<Q>(c[2].rec, x[2], Nz, Dz);
+        return value_at<Q, STORAGE>(
+            M, ((c[2].s - M.ax[2].p) * M.nyp + (c[1].s - M.ax[1].p)) * M.nxp + (c[0].s - M.ax[0].p), Nx, Ny, Nz);
+    }
+
     __device__ __forceinline__ float4 at(const ModelDev& M, float u, float v, float w)
     {
         const float x[3] = { clamp01(u), clamp01(v), clamp01(w) };
@@ -97,7 +129,7 @@ struct RayQuery<Q, STORAGE, false> {
 };
 
 template <int Q, int STORAGE, bool CARD>
-__global__ void __launch_bounds__(kIsoThreads, 4)
+__global__ void __launch_bounds__(kIsoThreads, Q <= 4 ? 4 : 3)
     k_render_iso(ModelDev M, const __grid_constant__ RenderParams P, float iso, float* __restrict__ depth, int shape)
 {
     __shared__ float4 tf[kTfMax + 1];
@@ -121,12 +153,16 @@ __global__ void __launch_bounds__(kIsoThreads, 4)
                 ++count;
                 return rq.at(M, fmaf(t, d[0], o[0]), fmaf(t, d[1], o[1]), fmaf(t, d[2], o[2]));
             };
+            auto value = [&](float t) {
+                ++count;
+                return rq.value(M, fmaf(t, d[0], o[0]), fmaf(t, d[1], o[1]), fmaf(t, d[2], o[2]));
+            };
             // first sign change of g = f - iso between consecutive samples
             float ta = 0.0f, ga = 0.0f, tb = 0.0f;
             bool found = false;
             for (int k = 0; k < ns; ++k) {
                 const float t = fmaf(static_cast<float>(k) + 0.5f, dt, t0);
-                const float g = query(t).x - iso;
+                const float g = value(t) - iso;
                 if (g == 0.0f) {
                     ta = tb = t;
                     found = true;
