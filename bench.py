@@ -463,7 +463,7 @@ def run_ours(args):
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
     }
-    if ws == 1:
+    if ws == 1 and not args.no_side_rows:
         line["precision"] = storage_throughput(mfa, torch, spec, job, tf)
         line["segments"] = segments_throughput(mfa, torch, model, job, tf, render_s)
         line["isosurface"] = iso_throughput(mfa, torch, spec, model, job, tf)
@@ -747,6 +747,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving comparison")
+    ap.add_argument("--no-side-rows", action="store_true",
+                    help="skip the rows after the timed step (precision, segments, isosurface, Marschner-Lobb, "
+                         "encoding, render quality), e.g. for profiling runs")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[20.0, 50.0], help="request rates (1/s)")
     ap.add_argument("--serve-duration", type=float, default=6.0, help="seconds of arrivals per rate")
     ap.add_argument("--variant", type=int, default=None, help="render kernel variant (skips the autotuner)")
