@@ -177,46 +177,73 @@ __global__ void __launch_bounds__(kFitThreads)
 }
 
 // Errors of a model at every data point: |f(u_i, v_j, w_k) - D[k][j][i]| folded, by
-// atomic maximum on the FP32 bit pattern (errors are non-negative), into the per-axis
-// projections ex[i], ey[j], ez[k].
+// maximum on the FP32 bit pattern (errors are non-negative), into the per-axis projections
+// ex[i], ey[j], ez[k] (zeroed by the caller).  One warp per x-line (j, k) at a time, its
+// lanes on consecutive i (coalesced data reads): the line's maximum goes to ey[j] and ez[k]
+// with one atomic each after a warp reduction, and ex[i] is gathered per block in shared
+// memory (when n_x fits) and flushed once per block, so the global atomics number about
+// two per line plus n_x per block instead of three per data point.
+constexpr int kErrThreads = 256;
+constexpr int kErrShared = 8192;   // ex entries a block gathers in shared memory
+
 template <int Q, int STORAGE, bool CARD>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kErrThreads)
     k_fit_error(ModelDev M, const float* __restrict__ D, int mx, int my, int mz, unsigned* __restrict__ ex,
                 unsigned* __restrict__ ey, unsigned* __restrict__ ez)
 {
-    const long long total = static_cast<long long>(mx) * my * mz;
-    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
-         e += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int i = static_cast<int>(e % mx);
-        const long long jk = e / mx;
-        const int j = static_cast<int>(jk % my), k = static_cast<int>(jk / my);
-        const float u = mx > 1 ? static_cast<float>(static_cast<double>(i) / (mx - 1)) : 0.0f;
+    __shared__ unsigned sx[kErrShared];
+    const bool shared_x = mx <= kErrShared;
+    if (shared_x)
+        for (int i = threadIdx.x; i < mx; i += kErrThreads) sx[i] = 0u;
+    __syncthreads();
+    constexpr int kWarps = kErrThreads / 32;
+    const int lane = threadIdx.x & 31;
+    const long long lines = static_cast<long long>(my) * mz;
+    for (long long L = blockIdx.x * static_cast<long long>(kWarps) + (threadIdx.x >> 5); L < lines;
+         L += static_cast<long long>(gridDim.x) * kWarps) {
+        const int j = static_cast<int>(L % my), k = static_cast<int>(L / my);
         const float v = my > 1 ? static_cast<float>(static_cast<double>(j) / (my - 1)) : 0.0f;
         const float w = mz > 1 ? static_cast<float>(static_cast<double>(k) / (mz - 1)) : 0.0f;
-        float f;
-        if constexpr (CARD) {
-            f = query_cardinal<Q, STORAGE>(M, u, v, w).x;
-        } else {
-            f = query2<Q, STORAGE>(M, u, v, w, locate_span(M.ax[0], u), locate_span(M.ax[1], v),
-                                   locate_span(M.ax[2], w)).x;
+        const float* line = D + L * mx;
+        unsigned lmax = 0u;
+        for (int i = lane; i < mx; i += 32) {
+            const float u = mx > 1 ? static_cast<float>(static_cast<double>(i) / (mx - 1)) : 0.0f;
+            float f;
+            if constexpr (CARD) {
+                f = query_cardinal<Q, STORAGE>(M, u, v, w).x;
+            } else {
+                f = query2<Q, STORAGE>(M, u, v, w, locate_span(M.ax[0], u), locate_span(M.ax[1], v),
+                                       locate_span(M.ax[2], w)).x;
+            }
+            const unsigned err = __float_as_uint(fabsf(f - line[i]));
+            lmax = max(lmax, err);
+            if (shared_x)
+                atomicMax(sx + i, err);
+            else
+                atomicMax(ex + i, err);
         }
-        const unsigned err = __float_as_uint(fabsf(f - D[e]));
-        atomicMax(ex + i, err);
-        atomicMax(ey + j, err);
-        atomicMax(ez + k, err);
+        lmax = __reduce_max_sync(0xFFFFFFFFu, lmax);
+        if (lane == 0 && lmax) {
+            atomicMax(ey + j, lmax);
+            atomicMax(ez + k, lmax);
+        }
     }
+    __syncthreads();
+    if (shared_x)
+        for (int i = threadIdx.x; i < mx; i += kErrThreads)
+            if (sx[i]) atomicMax(ex + i, sx[i]);
 }
 
 template <int Q, int STORAGE>
 cudaError_t fit_error_qs(const ModelDev& m, const float* D, const int md[3], unsigned* ex, unsigned* ey, unsigned* ez,
                          cudaStream_t st)
 {
-    const long long total = static_cast<long long>(md[0]) * md[1] * md[2];
-    const int blocks = static_cast<int>(std::min<long long>((total + 255) / 256, 152LL * 16));
+    const long long lines = static_cast<long long>(md[1]) * md[2];
+    const int blocks = static_cast<int>(std::min<long long>((lines + 7) / 8, 152LL * 16));
     if (m.cardinal)
-        k_fit_error<Q, STORAGE, true><<<blocks, 256, 0, st>>>(m, D, md[0], md[1], md[2], ex, ey, ez);
+        k_fit_error<Q, STORAGE, true><<<blocks, kErrThreads, 0, st>>>(m, D, md[0], md[1], md[2], ex, ey, ez);
     else
-        k_fit_error<Q, STORAGE, false><<<blocks, 256, 0, st>>>(m, D, md[0], md[1], md[2], ex, ey, ez);
+        k_fit_error<Q, STORAGE, false><<<blocks, kErrThreads, 0, st>>>(m, D, md[0], md[1], md[2], ex, ey, ez);
     return cudaGetLastError();
 }
 

@@ -17,8 +17,9 @@ namespace {
 // wait on L2 gathers, so occupancy matters more than registers: 4 blocks of 256 per SM
 // (64 registers) measure 9 % faster than the 3 that 76 registers allow (0.566 against
 // 0.622 ms for 2^24 points on the 128^3 degree-3 FP32 model); degree 4 keeps 3 (64
-// registers would spill).
-template <int Q, int STORAGE, bool CARD>
+// registers would spill).  GRAD false (no gradient output) leaves the derivative weights
+// and sums unused, so the compiler drops them: a value-only query.
+template <int Q, int STORAGE, bool CARD, bool GRAD>
 __global__ void __launch_bounds__(256, Q <= 4 ? 4 : 3)
     k_decode(ModelDev M, const float* __restrict__ pts, long long n, float* __restrict__ val, float* __restrict__ grad)
 {
@@ -37,7 +38,7 @@ __global__ void __launch_bounds__(256, Q <= 4 ? 4 : 3)
             r = query2<Q, STORAGE>(M, u, v, w, sx, sy, sz);
         }
         val[i] = r.x;
-        if (grad) {
+        if (GRAD && grad) {
             grad[3 * i + 0] = r.y;
             grad[3 * i + 1] = r.z;
             grad[3 * i + 2] = r.w;
@@ -65,17 +66,24 @@ int grid_for(long long n, int threads)
     return static_cast<int>(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
-template <int Q, bool CARD>
-cudaError_t decode_qc(const ModelDev& m, const float* pts, long long n, float* val, float* grad, cudaStream_t st)
+template <int Q, bool CARD, bool GRAD>
+cudaError_t decode_qcg(const ModelDev& m, const float* pts, long long n, float* val, float* grad, cudaStream_t st)
 {
     const int blocks = grid_for(n, 256);
     switch (m.storage) {
-    case 1: k_decode<Q, 1, CARD><<<blocks, 256, 0, st>>>(m, pts, n, val, grad); break;
-    case 2: k_decode<Q, 2, CARD><<<blocks, 256, 0, st>>>(m, pts, n, val, grad); break;
-    case 3: k_decode<Q, 3, CARD><<<blocks, 256, 0, st>>>(m, pts, n, val, grad); break;
+    case 1: k_decode<Q, 1, CARD, GRAD><<<blocks, 256, 0, st>>>(m, pts, n, val, grad); break;
+    case 2: k_decode<Q, 2, CARD, GRAD><<<blocks, 256, 0, st>>>(m, pts, n, val, grad); break;
+    case 3: k_decode<Q, 3, CARD, GRAD><<<blocks, 256, 0, st>>>(m, pts, n, val, grad); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+template <int Q, bool CARD>
+cudaError_t decode_qc(const ModelDev& m, const float* pts, long long n, float* val, float* grad, cudaStream_t st)
+{
+    return grad ? decode_qcg<Q, CARD, true>(m, pts, n, val, grad, st)
+                : decode_qcg<Q, CARD, false>(m, pts, n, val, grad, st);
 }
 
 template <int Q>
