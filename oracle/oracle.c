@@ -28,6 +28,8 @@
  *    value+gradient query per sample, a 1-D transfer function and gradient shading set
  *    by the user (Sec. IV-B), and the over operation between neighbouring samples,
  *    front to back (Sec. IV-A.4, IV-A.5).
+ *  - The same ray casting of the closed-form Marschner-Lobb signal (Sec. V-A.1, Eq. 1),
+ *    the ground truth of the render-quality comparison (Sec. V-D.3).
  *
  * Readings of what the paper leaves open (also listed in the design notes):
  *  - knots are clamped and span [0,1]; a coordinate on an interior knot belongs to the
