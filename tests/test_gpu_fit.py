@@ -85,3 +85,26 @@ def test_fit_rejects_undetermined_data(mfa):
     with pytest.raises(mfa.MfaError, match="determine"):
         mfa.fit_ctrl((1, 1, 1), (5, 3, 3), [U, None, None], D)
     mfa.fit_ctrl((1, 1, 1), (5, 3, 3), None, D)                       # uniform knots: determined
+
+
+def test_wide_x_error_projection_matches_oracle(mfa):
+    """More than 8192 data points along x: the error pass folds the x-projection with global
+    atomics instead of its per-block shared-memory table; the error and the adaptive loop's
+    knot decisions (which read the x-projection) still match the oracle's."""
+    rng = np.random.default_rng(10)
+    m = (8500, 6, 5)
+    x = of.grid_params(m[0])
+    fx = np.sin(9.0 * x) + 0.5 * np.exp(-((x - 0.3) / 0.05) ** 2)
+    D = (fx[None, None, :] * (1.0 + 0.1 * of.grid_params(m[1])[None, :, None])
+         + 0.05 * of.grid_params(m[2])[:, None, None]).astype(np.float32)
+    degree, nctrl = (2, 1, 1), (40, 4, 3)
+    knots = [synth.knots_uniform(nctrl[a], degree[a]) for a in range(3)]
+    P = of.fit(degree, knots, D.astype(np.float64))
+    ref_err = np.abs(of.evaluate_grid(degree, knots, P, D.shape) - D.astype(np.float64)).max()
+    model, err = mfa.model_fit(degree, nctrl, None, _cuda(D))
+    assert err == pytest.approx(ref_err, rel=1e-3, abs=1e-6 * np.abs(D).max())
+    err_max = 2e-3 * float(np.abs(D).max())
+    knots_ref, _, hist = of.encode(degree, D.astype(np.float64), err_max, max_ctrl=(96, 6, 5))
+    model, res = mfa.model_encode(degree, _cuda(D), err_max, max_ctrl=(96, 6, 5))
+    assert res["nctrl"] == hist[-1][1] and res["iterations"] == len(hist)
+    assert res["max_err"] == pytest.approx(hist[-1][0], rel=1e-3)
