@@ -616,7 +616,8 @@ def render_quality(mfa, torch):
 
 def iso_throughput(mfa, torch, spec, model, job, tf, frames=5):
     """Isosurface frames of the same model and view (iso = the median control point):
-    time per frame, queries per frame (samples marched plus refinement), pixels hit."""
+    time per frame, samples per frame (samples examined -- with or without a query, as
+    the cell bounds decide -- plus refinement queries), pixels hit."""
     W, H, NS = job.width, job.height, job.n_samples
     iso = float(np.median(spec.ctrl))
     img = torch.empty((H, W, 4), device="cuda")
@@ -632,7 +633,7 @@ def iso_throughput(mfa, torch, spec, model, job, tf, frames=5):
     b.synchronize()
     ms = a.elapsed_time(b) / frames
     q = int(cnt.item()) / frames
-    return {"iso": iso, "ms_per_frame": ms, "queries_per_frame": q, "queries_per_s": q / (ms / 1e3),
+    return {"iso": iso, "ms_per_frame": ms, "samples_per_frame": q, "samples_per_s": q / (ms / 1e3),
             "pixels_hit": int(torch.isfinite(depth).sum().item())}
 
 

@@ -68,7 +68,8 @@ typedef struct mfa_model mfa_model;   /* opaque; owns all of its device memory *
  *              BF16 (see mfa_model_create_ex to choose).
  * The padded layer-pair window layout the kernels read takes about 32 bytes per control
  * point (FP32 storage) or 16 bytes (FP16/BF16), twice that when the largest degree is 2
- * (each entry also carries a third layer's row); the product of the padded sizes
+ * (each entry also carries a third layer's row), plus 8 bytes per knot-span cell (the
+ * {min, max} bounds the isosurface search reads); the product of the padded sizes
  * (n_x+4)(n_y+4)(n_z+4) must stay below 2^31.
  * Synchronous: returns after the model is ready.  Returns NULL on error (reason in
  * mfa_last_error()).
@@ -216,9 +217,11 @@ int mfa_render_segments(const mfa_model* model, const mfa_camera* camera, const 
  * grad f when tf->shading) and is opaque: rgba_out (DEVICE, as mfa_render) holds
  * (r, g, b, 1), or 0 where the ray has no crossing; depth_out (DEVICE [height][width]
  * FP32, may be NULL) the hit's ray parameter t (distance from the eye for perspective
- * views), +inf on a miss.  opts may be NULL (its tile_shape and samples_out -- the number
- * of queries made -- apply).  MFA_ERR_ARG for a non-finite iso_value, otherwise errors as
- * mfa_render_ex.
+ * views), +inf on a miss.  A sample whose knot-span cell has every control point of its
+ * support on one side of iso_value takes that side's sign without a query (the model lies
+ * in their convex hull; the per-cell bounds are built with the model).  opts may be NULL
+ * (its tile_shape and samples_out -- samples examined plus refinement queries -- apply).
+ * MFA_ERR_ARG for a non-finite iso_value, otherwise errors as mfa_render_ex.
  */
 int mfa_render_iso(const mfa_model* model, const mfa_camera* camera, const mfa_transfer_fn* tf, int width,
                    int height, int n_samples, float iso_value, float* rgba_out, float* depth_out,

@@ -263,6 +263,9 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
         off_rec[a] = tab;
         tab = align_up(tab + sizeof(float) * rec_stride(Q) * (n - p), 256);
     }
+    const size_t off_cell = tab;   // per knot-span cell {min, max} of its support
+    const size_t ncells = static_cast<size_t>(nctrl[0] - degree[0]) * (nctrl[1] - degree[1]) * (nctrl[2] - degree[2]);
+    tab = align_up(tab + sizeof(float2) * ncells, 256);
     const size_t win_elem = (storage == MFA_F32 ? 4 : 2) * window_values(Q);   // one window entry
     const size_t win_bytes = static_cast<size_t>(nxp * nyp * nzp) * win_elem;
     const size_t nctrl_total = static_cast<size_t>(nctrl[0]) * nctrl[1] * nctrl[2];
@@ -316,6 +319,9 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
         return cleanup(0, "window array", e);
     if ((e = launch_prep_stats(M->d_win, storage, nctrl[0], nctrl[1], nctrl[2], Q, d_stats, st)) != cudaSuccess)
         return cleanup(0, "control-point statistics", e);
+    float2* d_cell = reinterpret_cast<float2*>(tabs + off_cell);
+    if ((e = launch_prep_cells(M->d_win, storage, Q, degree, nctrl, d_cell, st)) != cudaSuccess)
+        return cleanup(0, "cell bounds", e);
     int stats[3];
     if ((e = cudaMemcpyAsync(stats, d_stats, sizeof stats, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cleanup(0, "read statistics", e);
@@ -339,6 +345,10 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
     M->dev.q = Q;
     M->dev.storage = storage;
     M->dev.cardinal = uniform && degree[0] == Q - 1 && degree[1] == Q - 1 && degree[2] == Q - 1 ? 1 : 0;
+    M->dev.cell = d_cell;
+    M->dev.ncx = nctrl[0] - degree[0];
+    M->dev.ncy = nctrl[1] - degree[1];
+    M->dev.ncz = nctrl[2] - degree[2];
     M->bytes = tab + win_bytes;
     return M;
 }

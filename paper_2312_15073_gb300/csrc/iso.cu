@@ -1,8 +1,10 @@
 // iso.cu -- isosurface rendering through MFA queries (mfa_render_iso): the other
 // visualization the paper names for its query interface (Sec. IV-A.4).  One thread per
-// pixel: the ray's samples (the volume render's positions) are queried in order until
-// f - iso changes sign between two of them (value-only queries: no derivative weights, about
-// half the multiply-adds of a value+gradient query); the crossing is refined by kIsoSteps Newton
+// pixel: the ray's samples (the volume render's positions) are examined in order until
+// f - iso changes sign between two of them.  A sample whose knot-span cell has all the
+// control points of its support on one side of iso has that sign without a query (the
+// model lies in the convex hull of those control points); the others take a value-only
+// query (no derivative weights).  The crossing is refined by kIsoSteps Newton
 // steps on g(t) = f(o + t d) - iso with the analytic derivative g'(t) = grad f . d, kept
 // inside the bracket (each step shrinks the bracket to the side where g changes sign and
 // falls back to its midpoint when the Newton point leaves it); the hit is shaded like a
@@ -56,16 +58,20 @@ struct RayQuery<Q, STORAGE, true> {
         if (moved) base = (c[2].j * M.nyp + c[1].j) * M.nxp + c[0].j;
     }
 
-    // f at the parameter point (u, v, w) of the unit box
-    __device__ __forceinline__ float value(const ModelDev& M, float u, float v, float w)
+    // f - iso at the parameter point (u, v, w) of the unit box, or, where the point's cell
+    // bounds the model away from iso, a stand-in of the same sign without a query
+    __device__ __forceinline__ float g(const ModelDev& M, float u, float v, float w, float iso)
     {
         float t[3];
         locate(M, u, v, w, t);
+        const float2 r = __ldg(M.cell + (c[2].j * M.ncy + c[1].j) * M.ncx + c[0].j);
+        if (iso < r.x) return r.x - iso;
+        if (iso > r.y) return r.y - iso;
         float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];   // derivatives unused: dropped by the compiler
         card_basis<Q>(M.ax[0], c[0], t[0], Nx, Dx);
         card_basis<Q>(M.ax[1], c[1], t[1], Ny, Dy);
         card_basis<Q>(M.ax[2], c[2], t[2], Nz, Dz);
-        return value_at<Q, STORAGE>(M, base, Nx, Ny, Nz) * Cardinal<Q>::kValScale;
+        return value_at<Q, STORAGE>(M, base, Nx, Ny, Nz) * Cardinal<Q>::kValScale - iso;
     }
 
     // {f, df/du, df/dv, df/dw} at the parameter point (u, v, w) of the unit box
@@ -97,17 +103,23 @@ struct RayQuery<Q, STORAGE, false> {
         for (int a = 0; a < 3; ++a) c[a].s = -1;
     }
 
-    __device__ __forceinline__ float value(const ModelDev& M, float u, float v, float w)
+    __device__ __forceinline__ float g(const ModelDev& M, float u, float v, float w, float iso)
     {
         const float x[3] = { clamp01(u), clamp01(v), clamp01(w) };
 #pragma unroll
         for (int a = 0; a < 3; ++a) axis_update<Q>(M.ax[a], c[a], x[a]);
+        const float2 r = __ldg(M.cell + ((c[2].s - M.ax[2].p) * M.ncy + (c[1].s - M.ax[1].p)) * M.ncx +
+                               (c[0].s - M.ax[0].p));
+        if (iso < r.x) return r.x - iso;
+        if (iso > r.y) return r.y - iso;
         float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];   // derivatives unused: dropped by the compiler
         record_basis<Q>(c[0].rec, x[0], Nx, Dx);
         record_basis<Q>(c[1].rec, x[1], Ny, Dy);
         record_basis<Q>(c[2].rec, x[2], Nz, Dz);
         return value_at<Q, STORAGE>(
-            M, ((c[2].s - M.ax[2].p) * M.nyp + (c[1].s - M.ax[1].p)) * M.nxp + (c[0].s - M.ax[0].p), Nx, Ny, Nz);
+                   M, ((c[2].s - M.ax[2].p) * M.nyp + (c[1].s - M.ax[1].p)) * M.nxp + (c[0].s - M.ax[0].p), Nx, Ny,
+                   Nz) -
+               iso;
     }
 
     __device__ __forceinline__ float4 at(const ModelDev& M, float u, float v, float w)
@@ -153,16 +165,16 @@ __global__ void __launch_bounds__(kIsoThreads, Q <= 4 ? 4 : 3)
                 ++count;
                 return rq.at(M, fmaf(t, d[0], o[0]), fmaf(t, d[1], o[1]), fmaf(t, d[2], o[2]));
             };
-            auto value = [&](float t) {
+            auto g_at = [&](float t) {
                 ++count;
-                return rq.value(M, fmaf(t, d[0], o[0]), fmaf(t, d[1], o[1]), fmaf(t, d[2], o[2]));
+                return rq.g(M, fmaf(t, d[0], o[0]), fmaf(t, d[1], o[1]), fmaf(t, d[2], o[2]), iso);
             };
             // first sign change of g = f - iso between consecutive samples
             float ta = 0.0f, ga = 0.0f, tb = 0.0f;
             bool found = false;
             for (int k = 0; k < ns; ++k) {
                 const float t = fmaf(static_cast<float>(k) + 0.5f, dt, t0);
-                const float g = value(t) - iso;
+                const float g = g_at(t);
                 if (g == 0.0f) {
                     ta = tb = t;
                     found = true;

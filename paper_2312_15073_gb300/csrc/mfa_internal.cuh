@@ -58,6 +58,10 @@ struct ModelDev {
     int storage;        // mfa_dtype of the window values
     int cardinal;       // 1: uniform knots and degree Q-1 on all three axes, so interior
                         // spans share the cardinal basis (render variant 6 applies)
+    const float2* cell; // per knot-span cell (i, j, k) = (span - p per axis), x fastest:
+                        // {min, max} of the stored control points of its support, which
+                        // bound the model on the cell (convex hull property)
+    int ncx, ncy, ncz;  // cells per axis, n - p
 };
 
 // Per-image render parameters (camera frame, image size, transfer-function scalars).
@@ -123,6 +127,8 @@ cudaError_t launch_prep_axis(const double* d_knots, int n, int p, int q, float* 
                              int G, cudaStream_t stream);
 cudaError_t launch_prep_window(const void* d_ctrl, int in_dtype, int storage, int nx, int ny, int nz, int q,
                                void* win, cudaStream_t stream);
+cudaError_t launch_prep_cells(const void* win, int storage, int q, const int degree[3], const int nctrl[3],
+                              float2* cell, cudaStream_t stream);
 cudaError_t launch_prep_stats(const void* win, int storage, int nx, int ny, int nz, int q, int* d_stats,
                               cudaStream_t stream);
 cudaError_t launch_decode(const ModelDev& m, const float* pts, long long n, float* val, float* grad,

@@ -159,6 +159,36 @@ __global__ void k_window(const void* __restrict__ ctrl, int in_dtype, int storag
     }
 }
 
+// {min, max} over the (p_x+1)(p_y+1)(p_z+1) stored control points of each knot-span cell's
+// support, read from the window array (element 0 of entry (k, j, i) is P[k][j][i]).
+__global__ void k_cell_range(const void* __restrict__ win, int storage, int nv, int px, int py, int pz, int ncx,
+                             int ncy, int ncz, int nxp, int nyp, float2* __restrict__ cell)
+{
+    const long long total = static_cast<long long>(ncx) * ncy * ncz;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int i0 = static_cast<int>(e % ncx);
+        const long long jk = e / ncx;
+        const int j0 = static_cast<int>(jk % ncy), k0 = static_cast<int>(jk / ncy);
+        float mn = INFINITY, mx = -INFINITY;
+        for (int c = 0; c <= pz; ++c)
+            for (int b = 0; b <= py; ++b)
+                for (int a = 0; a <= px; ++a) {
+                    const long long w = (static_cast<long long>(k0 + c) * nyp + (j0 + b)) * nxp + (i0 + a);
+                    float v;
+                    if (storage == 1) {
+                        v = static_cast<const float*>(win)[nv * w];
+                    } else {
+                        const unsigned short h = static_cast<const unsigned short*>(win)[nv * w];
+                        v = storage == 2 ? __half2float(__ushort_as_half(h)) : __bfloat162float(__ushort_as_bfloat16(h));
+                    }
+                    mn = fminf(mn, v);
+                    mx = fmaxf(mx, v);
+                }
+        cell[e] = make_float2(mn, mx);
+    }
+}
+
 // order-preserving float <-> int map for atomicMin / atomicMax
 __device__ __forceinline__ int f2ord(float f)
 {
@@ -239,6 +269,18 @@ cudaError_t launch_prep_window(const void* d_ctrl, int in_dtype, int storage, in
     const long long want = (total + 255) / 256;
     const int blocks = static_cast<int>(want < 65536 ? want : 65536);
     k_window<<<blocks, 256, 0, stream>>>(d_ctrl, in_dtype, storage, nx, ny, nz, q, win);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_cells(const void* win, int storage, int q, const int degree[3], const int nctrl[3],
+                              float2* cell, cudaStream_t stream)
+{
+    const int ncx = nctrl[0] - degree[0], ncy = nctrl[1] - degree[1], ncz = nctrl[2] - degree[2];
+    const long long total = static_cast<long long>(ncx) * ncy * ncz;
+    const long long want = (total + 255) / 256;
+    const int blocks = static_cast<int>(want < 8192 ? want : 8192);
+    k_cell_range<<<blocks, 256, 0, stream>>>(win, storage, window_values(q), degree[0], degree[1], degree[2], ncx, ncy,
+                                             ncz, nctrl[0] + kPad, nctrl[1] + kPad, cell);
     return cudaGetLastError();
 }
 

@@ -107,3 +107,35 @@ def test_iso_rejects_bad_arguments(mfa):
         mfa.render_iso(m, cam, tf, 8, 8, 16, float("nan"))
     with pytest.raises(mfa.MfaError):
         mfa.render_iso(m, cam, tf, 8, 8, 0, 0.5)
+
+
+def test_iso_localised_surface_matches_oracle(mfa, orc):
+    """A field that crosses iso only inside one small bump: almost every cell's control
+    points lie below iso, so most samples are decided by the cell bounds without a query;
+    hits, depths and colours still match the oracle, which queries every sample."""
+    import torch
+    deg, n = (3, 3, 3), (40, 36, 44)
+    knots = [synth.knots_uniform(n[a], deg[a]) for a in range(3)]
+    g = [synth.greville(knots[a], deg[a]) for a in range(3)]
+    Z, Y, X = np.meshgrid(g[2], g[1], g[0], indexing="ij")
+    P = np.exp(-(((X - 0.45) / 0.22) ** 2 + ((Y - 0.55) / 0.2) ** 2 + ((Z - 0.5) / 0.24) ** 2)) - 0.02 * X
+    iso = 0.35                                                    # 92 % of the cells lie off iso
+    for storage in (1, 2):
+        m = mfa.Model(deg, n, knots, P, storage=storage)
+        stored = _stored(P, storage, orc)
+        ref = orc.Model(deg, n, knots, stored)
+        cam = synth.camera_persp((1.6, 1.3, 2.1), (0.5, 0.5, 0.5), (0, 1, 0), 24.0)
+        table = synth.ramp_tf(256, 1.0)
+        tf = mfa.transfer_fn(table, shading=True, vmin=-0.1, vmax=1.0)
+        W, H, ns = 56, 44, 160
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        img, depth = mfa.render_iso(m, cam, tf, W, H, ns, iso, samples_out=cnt)
+        img, depth = img.cpu().numpy(), depth.cpu().numpy()
+        r, rd, rq = orc.render_iso(ref, cam, table, W, H, ns, iso, shading=True, vmin=-0.1, vmax=1.0)
+        hg, ho = np.isfinite(depth), np.isfinite(rd)
+        assert 0.05 * W * H < ho.sum() < 0.6 * W * H                 # a small surface in view
+        assert (hg != ho).sum() <= 2
+        both = hg & ho
+        assert np.abs(depth[both] - rd[both]).max() <= 1e-4
+        assert np.abs(img[both] - r[both]).max() <= 2e-3
+        assert abs(int(cnt.item()) - rq) <= 0.02 * rq
