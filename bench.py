@@ -455,7 +455,10 @@ def run_ours(args):
                       "frac": DECODE_WINDOW_BYTES[spec.degree[0]] * n_pts / (statistics.mean(decode_ms) / 1e3) / 1e9
                       / peaks["l2_gather_gbs"],
                       "note": "decode reads its support as random 32-byte window entries (8 at degree 3, FP32); "
-                              "peak = random 32-byte gathers from an L2-resident buffer"},
+                              "peak = random 32-byte gathers from an L2-resident buffer",
+                      "fp32_frac": query_flops(spec.degree[0]) * n_pts / (statistics.mean(decode_ms) / 1e3) / 1e12
+                      / peak_tflops,
+                      "fp32_note": "the same decode against the FP32 peak (algorithmic flops per value+gradient query)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.mean(e2e_ms),
                 "path": "mfa_render_host + mfa_decode_host (page-locked host buffers, library-staged "
