@@ -473,6 +473,7 @@ def run_ours(args):
         line["marschner_lobb"] = ml_throughput(mfa, torch, tf)
         line["encoding"] = encode_throughput(mfa, torch)
         line["render_quality"] = render_quality(mfa, torch)
+        line["query_sweep"] = query_sweep(mfa, torch)
     if ws == 1 and not args.no_serve:
         line["serving"] = dict(run_serve(mfa, rates=args.serve_rates, duration=args.serve_duration),
                                note="Poisson requests (sides 512..2048, 512..2048 samples) on 8 resident degree-3 "
@@ -615,6 +616,33 @@ def render_quality(mfa, torch):
             "fitted_vs_truth": fitted, "greville_vs_truth": sampled,
             "paper_table2_mfa": {"mse": 50.76, "psnr_db": 31.08, "ssim": 0.96,
                                  "note": "the paper's camera and transfer function are not given: context only"}}
+
+
+def query_sweep(mfa, torch, n_pts=1 << 22, reps=5):
+    """Value+gradient query rate against the control-point count and the degree (the
+    paper's query-time study, Fig. 8, in spirit): 2^22 uniform random points per model,
+    uniform knots, random control points (the rate does not depend on the values)."""
+    rng = np.random.default_rng(20231215)
+    pts = torch.rand((n_pts, 3), device="cuda", generator=torch.Generator(device="cuda").manual_seed(8))
+    val = torch.empty(n_pts, device="cuda")
+    grad = torch.empty((n_pts, 3), device="cuda")
+    rows = []
+    for degree, n in ((3, 32), (3, 64), (3, 128), (3, 256), (3, 512), (1, 128), (2, 128), (4, 128)):
+        m = mfa.Model((degree,) * 3, (n,) * 3, None, rng.standard_normal((n, n, n), dtype=np.float32))
+        for _ in range(3):
+            mfa.decode(m, pts, val, grad)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            mfa.decode(m, pts, val, grad)
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b) / reps
+        rows.append({"degree": degree, "nctrl": n, "model_bytes": m.info()["device_bytes"], "ms": ms,
+                     "queries_per_s": n_pts / (ms / 1e3)})
+        m.close()
+    return {"points": n_pts, "rows": rows}
 
 
 def iso_throughput(mfa, torch, spec, model, job, tf, frames=5):
