@@ -102,6 +102,24 @@ typedef struct {
 /* Fills *info.  MFA_ERR_ARG on NULL arguments. */
 int mfa_model_get_info(const mfa_model* model, mfa_model_info* info);
 
+/*
+ * Checkpoint (the paper writes each block's model after encoding and reads it back for
+ * rendering, Sec. IV-A.2).
+ *   mfa_model_get_ctrl: copies the stored control points to host_out (HOST, caller-owned,
+ *     n_x n_y n_z values [n_z][n_y][n_x] of the storage type: 4 bytes FP32, 2 bytes FP16 or
+ *     BF16 bits); synchronises the bound stream.
+ *   mfa_model_save: writes the model to a file (a 64-byte header with the magic "MFAMODL1",
+ *     degrees, counts and storage type; the FP64 knots; the stored control points).
+ *   mfa_model_load: creates a model from such a file on the current device; its stored
+ *     values are bit-identical to the saved model's.  The header, sizes and file length are
+ *     checked before any device work; NULL on error (reason in mfa_last_error()).
+ * MFA_ERR_ARG for NULL arguments or a file that cannot be written; MFA_ERR_CUDA on a failed
+ * CUDA call.
+ */
+int mfa_model_get_ctrl(const mfa_model* model, void* host_out);
+int mfa_model_save(const mfa_model* model, const char* path);
+mfa_model* mfa_model_load(const char* path);
+
 /* Binds a CUDA stream (a cudaStream_t passed as void*) for later calls on the calling
  * thread; NULL selects the legacy default stream.  Always MFA_OK. */
 int mfa_set_stream(void* cuda_stream);

@@ -148,6 +148,12 @@ def lib():
         L.mfa_render_segments.restype = c_int
         L.mfa_render_segments.argtypes = [c_void_p, POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int, c_void_p,
                                           c_void_p, POINTER(_Opts)]
+        L.mfa_model_get_ctrl.restype = c_int
+        L.mfa_model_get_ctrl.argtypes = [c_void_p, c_void_p]
+        L.mfa_model_save.restype = c_int
+        L.mfa_model_save.argtypes = [c_void_p, ctypes.c_char_p]
+        L.mfa_model_load.restype = c_void_p
+        L.mfa_model_load.argtypes = [ctypes.c_char_p]
         L.mfa_render_ml.restype = c_int
         L.mfa_render_ml.argtypes = [POINTER(_MlSignal), POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int, c_void_p,
                                     POINTER(_Opts)]
@@ -280,6 +286,31 @@ class Model:
         _check(lib().mfa_model_get_info(self._h, ctypes.byref(i)))
         return dict(degree=tuple(i.degree), nctrl=tuple(i.nctrl), storage=i.storage, vmin=i.vmin, vmax=i.vmax,
                     device_bytes=i.device_bytes, device=i.device, cardinal=bool(i.cardinal))
+
+    def ctrl(self) -> np.ndarray:
+        """The stored control points (n_z, n_y, n_x): float32, float16, or uint16 BF16 bits."""
+        n = self.nctrl
+        dt = {MFA_F32: np.float32, MFA_F16: np.float16, MFA_BF16: np.uint16}[self.storage]
+        out = np.empty((n[2], n[1], n[0]), dtype=dt)
+        _bind_stream()
+        _check(lib().mfa_model_get_ctrl(self._h, out.ctypes.data))
+        return out
+
+    def save(self, path: str):
+        """Writes the model (degrees, FP64 knots, stored control points) to a file."""
+        _bind_stream()
+        _check(lib().mfa_model_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path: str) -> "Model":
+        """A model read from a file written by save(), on the current device."""
+        _bind_stream()
+        h = lib().mfa_model_load(os.fsencode(path))
+        if not h:
+            raise MfaError(-1, lib().mfa_last_error().decode())
+        i = _Info()
+        _check(lib().mfa_model_get_info(h, ctypes.byref(i)))
+        return cls._wrap(h, i.storage)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -247,6 +247,7 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
     }
     M->storage = storage;
     M->uniform = uniform;
+    for (int a = 0; a < 3; ++a) M->knots[a] = U[a];
     const int Q = qmax;
     cudaStream_t st = g_stream;
 

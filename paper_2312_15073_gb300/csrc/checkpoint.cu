@@ -1,0 +1,142 @@
+// checkpoint.cu -- reading a model's control points back and writing / reading models to
+// files (the paper stores each block's MFA model after encoding and reads it back for
+// rendering, Sec. IV-A.2).  A file holds what defines the model exactly: the degrees,
+// counts, storage type, FP64 knots and the stored control points; loading it creates a
+// model whose stored values are bit-identical (rounding a value already in the storage
+// type to that type is the identity).
+//
+// File layout (little-endian): a 64-byte header {char magic[8] = "MFAMODL1"; int32 version
+// = 1; int32 degree[3]; int32 nctrl[3]; int32 storage; int32 reserved[6] = 0}, then the
+// three knot vectors (n_d + p_d + 1 FP64 values each, x, y, z), then the control points
+// [n_z][n_y][n_x] in the storage type (4 bytes FP32, 2 bytes FP16 / BF16).
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "host.cuh"
+
+namespace mfa {
+namespace {
+
+// Element 0 of window entry (k, j, i) is P[k][j][i]: copy the stored values out, densely.
+__global__ void k_extract_ctrl(const void* __restrict__ win, int storage, int nv, int nx, int ny, int nz, int nxp,
+                               int nyp, void* __restrict__ out)
+{
+    const long long total = static_cast<long long>(nx) * ny * nz;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int i = static_cast<int>(e % nx);
+        const long long jk = e / nx;
+        const int j = static_cast<int>(jk % ny), k = static_cast<int>(jk / ny);
+        const long long w = (static_cast<long long>(k) * nyp + j) * nxp + i;
+        if (storage == MFA_F32)
+            static_cast<float*>(out)[e] = static_cast<const float*>(win)[nv * w];
+        else
+            static_cast<unsigned short*>(out)[e] = static_cast<const unsigned short*>(win)[nv * w];
+    }
+}
+
+struct FileHeader {
+    char magic[8];
+    int32_t version;
+    int32_t degree[3];
+    int32_t nctrl[3];
+    int32_t storage;
+    int32_t reserved[6];
+};
+static_assert(sizeof(FileHeader) == 64, "the file header is 64 bytes");
+constexpr char kMagic[8] = { 'M', 'F', 'A', 'M', 'O', 'D', 'L', '1' };
+
+size_t storage_bytes(int storage) { return storage == MFA_F32 ? 4 : 2; }
+
+}  // namespace
+}  // namespace mfa
+
+using namespace mfa;
+
+extern "C" int mfa_model_get_ctrl(const mfa_model* m, void* host_out)
+{
+    if (!m || !host_out) return fail(MFA_ERR_ARG, "model and host_out must be non-NULL");
+    if (int rc = check_model_device(m)) return rc;
+    const int nx = m->nctrl[0], ny = m->nctrl[1], nz = m->nctrl[2];
+    const size_t bytes = static_cast<size_t>(nx) * ny * nz * storage_bytes(m->storage);
+    cudaMemPool_t pool;
+    cudaError_t e = staging_pool(m->device, &pool);
+    if (e != cudaSuccess) return cuda_fail(e, "staging pool");
+    cudaStream_t st = current_stream();
+    void* d = nullptr;
+    if ((e = cudaMallocFromPoolAsync(&d, bytes, pool, st)) != cudaSuccess) return cuda_fail(e, "staging memory");
+    const long long total = static_cast<long long>(nx) * ny * nz;
+    const long long want = (total + 255) / 256;
+    k_extract_ctrl<<<static_cast<int>(want < 8192 ? want : 8192), 256, 0, st>>>(
+        m->dev.win, m->storage, window_values(m->dev.q), nx, ny, nz, m->dev.nxp, m->dev.nyp, d);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, d, bytes, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(d, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? MFA_OK : cuda_fail(e, "read control points");
+}
+
+extern "C" int mfa_model_save(const mfa_model* m, const char* path)
+{
+    if (!m || !path) return fail(MFA_ERR_ARG, "model and path must be non-NULL");
+    const size_t n = static_cast<size_t>(m->nctrl[0]) * m->nctrl[1] * m->nctrl[2];
+    std::vector<unsigned char> ctrl(n * storage_bytes(m->storage));
+    if (int rc = mfa_model_get_ctrl(m, ctrl.data())) return rc;
+    FileHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, kMagic, sizeof kMagic);
+    h.version = 1;
+    for (int a = 0; a < 3; ++a) {
+        h.degree[a] = m->degree[a];
+        h.nctrl[a] = m->nctrl[a];
+    }
+    h.storage = m->storage;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(MFA_ERR_ARG, "cannot open %s for writing", path);
+    bool ok = std::fwrite(&h, sizeof h, 1, f) == 1;
+    for (int a = 0; a < 3 && ok; ++a)
+        ok = std::fwrite(m->knots[a].data(), sizeof(double), m->knots[a].size(), f) == m->knots[a].size();
+    ok = ok && std::fwrite(ctrl.data(), 1, ctrl.size(), f) == ctrl.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? MFA_OK : fail(MFA_ERR_ARG, "cannot write %s", path);
+}
+
+extern "C" mfa_model* mfa_model_load(const char* path)
+{
+    if (!path) return fail(MFA_ERR_ARG, "path must be non-NULL"), nullptr;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(MFA_ERR_ARG, "cannot open %s", path), nullptr;
+    auto bad = [&](const char* why) -> mfa_model* {
+        std::fclose(f);
+        fail(MFA_ERR_ARG, "%s: %s", path, why);
+        return nullptr;
+    };
+    FileHeader h;
+    if (std::fread(&h, sizeof h, 1, f) != 1) return bad("shorter than the header");
+    if (std::memcmp(h.magic, kMagic, sizeof kMagic) != 0) return bad("not an MFA model file");
+    if (h.version != 1) return bad("unsupported version");
+    if (h.storage != MFA_F32 && h.storage != MFA_F16 && h.storage != MFA_BF16) return bad("bad storage type");
+    for (int a = 0; a < 3; ++a)
+        if (h.degree[a] < 1 || h.degree[a] > kMaxDegree || h.nctrl[a] < h.degree[a] + 1 || h.nctrl[a] > (1 << 24))
+            return bad("bad degree or control-point count");
+    if (static_cast<long long>(h.nctrl[0] + kPad) * (h.nctrl[1] + kPad) * (h.nctrl[2] + kPad) >= (1LL << 31))
+        return bad("model too large");
+    std::vector<double> U[3];
+    for (int a = 0; a < 3; ++a) {
+        U[a].resize(static_cast<size_t>(h.nctrl[a]) + h.degree[a] + 1);
+        if (std::fread(U[a].data(), sizeof(double), U[a].size(), f) != U[a].size()) return bad("truncated knots");
+    }
+    const size_t n = static_cast<size_t>(h.nctrl[0]) * h.nctrl[1] * h.nctrl[2];
+    std::vector<unsigned char> ctrl(n * storage_bytes(h.storage));
+    if (std::fread(ctrl.data(), 1, ctrl.size(), f) != ctrl.size()) return bad("truncated control points");
+    unsigned char extra;
+    if (std::fread(&extra, 1, 1, f) != 0) return bad("trailing bytes");
+    std::fclose(f);
+    const int degree[3] = { h.degree[0], h.degree[1], h.degree[2] };
+    const int nctrl[3] = { h.nctrl[0], h.nctrl[1], h.nctrl[2] };
+    const double* const knots[3] = { U[0].data(), U[1].data(), U[2].data() };
+    const mfa_dtype st = static_cast<mfa_dtype>(h.storage);
+    return model_create(degree, nctrl, knots, ctrl.data(), st, st, false);
+}

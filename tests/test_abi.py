@@ -90,6 +90,25 @@ def test_host_side_argument_checks(libmfa):
     assert "aligned" in L.mfa_last_error().decode()
     assert L.mfa_image_compare(0x1000, 0x2000, 10, 16, ctypes.byref(q)) == -1
     assert "11..32768" in L.mfa_last_error().decode()
+    # checkpoint calls check their arguments and the file before any device work
+    assert L.mfa_model_get_ctrl(None, None) == -1
+    assert L.mfa_model_save(None, b"/nonexistent/x.mfa") == -1
+    assert not L.mfa_model_load(b"/nonexistent/x.mfa")
+    assert "cannot open" in L.mfa_last_error().decode()
+    import tempfile, os, struct
+    with tempfile.TemporaryDirectory() as d:
+        p = os.path.join(d, "bad.mfa")
+        open(p, "wb").write(b"NOTMFA!!" + bytes(56))
+        assert not L.mfa_model_load(p.encode())
+        assert "not an MFA model file" in L.mfa_last_error().decode()
+        hdr = b"MFAMODL1" + struct.pack("<i3i3ii6i", 1, 3, 3, 9, 8, 8, 8, 1, *([0] * 6))
+        open(p, "wb").write(hdr)
+        assert not L.mfa_model_load(p.encode())
+        assert "degree" in L.mfa_last_error().decode()
+        hdr = b"MFAMODL1" + struct.pack("<i3i3ii6i", 1, 3, 3, 3, 8, 8, 8, 1, *([0] * 6))
+        open(p, "wb").write(hdr + bytes(8 * 36))                 # knots but no control points
+        assert not L.mfa_model_load(p.encode())
+        assert "truncated" in L.mfa_last_error().decode()
     # model creation rejects bad degrees, counts and knots before any device work
     deg = (ctypes.c_int * 3)(3, 3, 5)
     nc = (ctypes.c_int * 3)(8, 8, 8)
