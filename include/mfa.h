@@ -525,6 +525,18 @@ typedef struct {
 } mfa_peaks;
 int mfa_measure_peaks(mfa_peaks* out);
 
+/*
+ * Debug builds (libmfa_debug.so, compiled with -DMFA_DEBUG; paper_2312_15073_gb300.build
+ * builds it with debug=True) check every control-point window, span-record, cell and
+ * transfer-function index on the device before the load.  A bad index is replaced by 0
+ * (nothing traps) and recorded in a per-device word: mfa_debug_status waits for the device,
+ * returns the flags (1 window, 2 span record, 4 cell bound, 8 transfer function) and the
+ * number of bad indices since the last call, and clears them.  Release builds report 0.
+ * mfa_debug_build returns 1 in a debug build, else 0.
+ */
+int mfa_debug_build(void);
+int mfa_debug_status(unsigned int* flags, unsigned int* count);
+
 /* Text of the last error on the calling thread ("" if none). */
 const char* mfa_last_error(void);
 

@@ -26,7 +26,9 @@ __all__ = ["Model", "decode", "locate_spans", "render", "lib", "MFA_F64", "MFA_F
 
 MFA_F64, MFA_F32, MFA_F16, MFA_BF16 = 0, 1, 2, 3
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libmfa.so")
+# The library the binding loads: libmfa.so, or the file MFA_LIB names (e.g. the debug
+# build libmfa_debug.so).  A missing library raises; there is no fallback.
+LIB_PATH = os.environ.get("MFA_LIB") or os.path.join(_PKG, "libmfa.so")
 
 
 class MfaError(RuntimeError):
@@ -148,6 +150,10 @@ def lib():
         L.mfa_render_segments.restype = c_int
         L.mfa_render_segments.argtypes = [c_void_p, POINTER(_Camera), POINTER(_TF), c_int, c_int, c_int, c_void_p,
                                           c_void_p, POINTER(_Opts)]
+        L.mfa_debug_build.restype = c_int
+        L.mfa_debug_build.argtypes = []
+        L.mfa_debug_status.restype = c_int
+        L.mfa_debug_status.argtypes = [POINTER(ctypes.c_uint), POINTER(ctypes.c_uint)]
         L.mfa_model_get_ctrl.restype = c_int
         L.mfa_model_get_ctrl.argtypes = [c_void_p, c_void_p]
         L.mfa_model_save.restype = c_int
@@ -411,6 +417,14 @@ def render(model: Model, cam, tf: transfer_fn, width: int, height: int, n_sample
     _check(lib().mfa_render_ex(model.handle, ctypes.byref(c), ctypes.byref(tf.struct), width, height, n_samples,
                                out.data_ptr(), ctypes.byref(opts)))
     return out
+
+
+def debug_status() -> dict:
+    """Device-side index checks of a debug build (libmfa_debug.so): the flags raised and the
+    number of bad indices since the last call (both 0 in a release build)."""
+    f, c = ctypes.c_uint(), ctypes.c_uint()
+    _check(lib().mfa_debug_status(ctypes.byref(f), ctypes.byref(c)))
+    return {"debug_build": bool(lib().mfa_debug_build()), "flags": f.value, "count": c.value}
 
 
 def measure_peaks() -> dict:

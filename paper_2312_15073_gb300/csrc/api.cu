@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -41,6 +42,31 @@ int cuda_fail(cudaError_t e, const char* what)
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 bool valid_dtype(int d) { return d >= MFA_F64 && d <= MFA_BF16; }
+
+// The debug word of device `dev` ({flags, count}, zeroed device memory, allocated on first
+// use): what kernels of a debug build write bad indices into.  NULL in release builds.
+unsigned* debug_word(int dev)
+{
+#ifdef MFA_DEBUG
+    static std::mutex mu;
+    static unsigned* words[64] = {};
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> g(mu);
+    if (!words[dev]) {
+        unsigned* w = nullptr;
+        if (cudaMalloc(&w, 2 * sizeof(unsigned)) != cudaSuccess) return nullptr;
+        if (cudaMemset(w, 0, 2 * sizeof(unsigned)) != cudaSuccess) {
+            cudaFree(w);
+            return nullptr;
+        }
+        words[dev] = w;
+    }
+    return words[dev];
+#else
+    (void)dev;
+    return nullptr;
+#endif
+}
 size_t dtype_size(int d) { return d == MFA_F64 ? 8 : d == MFA_F32 ? 4 : 2; }
 
 // Checks one knot vector: length n+p+1, non-decreasing, clamped on [0,1] with exactly
@@ -153,6 +179,9 @@ int setup_view(const mfa_camera* cam, const mfa_transfer_fn* tf, int width, int 
     S.shininess = tf->shininess;
     S.ert_alpha = tf->ert_alpha >= 1.0f ? INFINITY : tf->ert_alpha;
     S.gtiny2 = static_cast<float>(gtiny * gtiny);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    S.dbg = debug_word(dev);
     S.samples_out = samples_out;
     S.out = reinterpret_cast<float4*>(rgba_out);
     for (int i = 0; i < tf->n_entries; ++i)
@@ -185,6 +214,34 @@ const char* mfa_last_error(void) { return g_error.c_str(); }
 int mfa_set_stream(void* cuda_stream)
 {
     g_stream = static_cast<cudaStream_t>(cuda_stream);
+    return MFA_OK;
+}
+
+int mfa_debug_build(void)
+{
+#ifdef MFA_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int mfa_debug_status(unsigned* flags, unsigned* count)
+{
+    if (!flags || !count) return fail(MFA_ERR_ARG, "flags and count must be non-NULL");
+    *flags = 0;
+    *count = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    unsigned* w = debug_word(dev);
+    if (!w) return MFA_OK;
+    unsigned h[2];
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(h, w, sizeof h, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(w, 0, sizeof h);
+    if (e != cudaSuccess) return cuda_fail(e, "debug status");
+    *flags = h[0];
+    *count = h[1];
     return MFA_OK;
 }
 
@@ -350,6 +407,8 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
     M->dev.ncx = nctrl[0] - degree[0];
     M->dev.ncy = nctrl[1] - degree[1];
     M->dev.ncz = nctrl[2] - degree[2];
+    M->dev.dbg = debug_word(M->device);
+    for (int a = 0; a < 3; ++a) M->dev.ax[a].dbg = M->dev.dbg;
     M->bytes = tab + win_bytes;
     return M;
 }

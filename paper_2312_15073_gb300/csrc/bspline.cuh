@@ -92,7 +92,9 @@ template <int Q>
 __device__ __forceinline__ void load_record(const AxisDev& A, int s, float (&rec)[rec_stride(Q)])
 {
     constexpr int RS = rec_stride(Q);
-    const float4* r4 = reinterpret_cast<const float4*>(A.rec + (s - A.p) * RS);
+    int r = s - A.p;
+    MFA_DBG_INDEX(A.dbg, r, A.n - A.p, kDbgRecord);
+    const float4* r4 = reinterpret_cast<const float4*>(A.rec + r * RS);
 #pragma unroll
     for (int v = 0; v < RS / 4; ++v) {
         float4 x = __ldg(r4 + v);
@@ -347,7 +349,9 @@ __device__ __forceinline__ float4 contract_triple(const ModelDev& M, int base, c
     for (int b = 0; b < 3; ++b) {
         f2 pr[4];
         float r3[4];
-        PairLoader<3, STORAGE>::load_triple(M.win, base + b * M.nxp, pr, r3);
+        int idx = base + b * M.nxp;
+        MFA_DBG_INDEX(M.dbg, idx, static_cast<long long>(M.nxp) * M.nyp * M.nzp, kDbgWindow);
+        PairLoader<3, STORAGE>::load_triple(M.win, idx, pr, r3);
         f2 A = mul2(nx[0], pr[0]);
         f2 B = mul2(dx[0], pr[0]);
         float A3 = lo2(nx[0]) * r3[0];
@@ -410,7 +414,9 @@ __device__ __forceinline__ float4 contract_pairs(const ModelDev& M, int base, co
 #pragma unroll
         for (int b = 0; b < Q; ++b) {
             f2 pr[qpair(Q)];
-            PairLoader<Q, STORAGE>::load(M.win, base + m * pair_step + b * M.nxp, pr);
+            int idx = base + m * pair_step + b * M.nxp;   // Q = 5 also reads entry idx + 1
+            MFA_DBG_INDEX(M.dbg, idx, static_cast<long long>(M.nxp) * M.nyp * M.nzp - (qpair(Q) == 6), kDbgWindow);
+            PairLoader<Q, STORAGE>::load(M.win, idx, pr);
             f2 A = mul2(nx[0], pr[0]);
             f2 B = mul2(dx[0], pr[0]);
 #pragma unroll
@@ -457,7 +463,9 @@ __device__ __forceinline__ float contract_value(const ModelDev& M, int base, con
         for (int b = 0; b < 3; ++b) {
             f2 pr[4];
             float r3[4];
-            PairLoader<3, STORAGE>::load_triple(M.win, base + b * M.nxp, pr, r3);
+            int idx = base + b * M.nxp;
+            MFA_DBG_INDEX(M.dbg, idx, static_cast<long long>(M.nxp) * M.nyp * M.nzp, kDbgWindow);
+            PairLoader<3, STORAGE>::load_triple(M.win, idx, pr, r3);
             f2 A = mul2(nx[0], pr[0]);
             float A3 = lo2(nx[0]) * r3[0];
 #pragma unroll
@@ -480,7 +488,9 @@ __device__ __forceinline__ float contract_value(const ModelDev& M, int base, con
 #pragma unroll
             for (int b = 0; b < Q; ++b) {
                 f2 pr[qpair(Q)];
-                PairLoader<Q, STORAGE>::load(M.win, base + m * pair_step + b * M.nxp, pr);
+                int idx = base + m * pair_step + b * M.nxp;
+                MFA_DBG_INDEX(M.dbg, idx, static_cast<long long>(M.nxp) * M.nyp * M.nzp - (qpair(Q) == 6), kDbgWindow);
+                PairLoader<Q, STORAGE>::load(M.win, idx, pr);
                 f2 A = mul2(nx[0], pr[0]);
 #pragma unroll
                 for (int a = 1; a < Q; ++a) A = fma2(nx[a], pr[a], A);

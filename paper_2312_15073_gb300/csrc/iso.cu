@@ -64,7 +64,9 @@ struct RayQuery<Q, STORAGE, true> {
     {
         float t[3];
         locate(M, u, v, w, t);
-        const float2 r = __ldg(M.cell + (c[2].j * M.ncy + c[1].j) * M.ncx + c[0].j);
+        int ci = (c[2].j * M.ncy + c[1].j) * M.ncx + c[0].j;
+        MFA_DBG_INDEX(M.dbg, ci, static_cast<long long>(M.ncx) * M.ncy * M.ncz, kDbgCell);
+        const float2 r = __ldg(M.cell + ci);
         if (iso < r.x) return r.x - iso;
         if (iso > r.y) return r.y - iso;
         float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];   // derivatives unused: dropped by the compiler
@@ -108,8 +110,9 @@ struct RayQuery<Q, STORAGE, false> {
         const float x[3] = { clamp01(u), clamp01(v), clamp01(w) };
 #pragma unroll
         for (int a = 0; a < 3; ++a) axis_update<Q>(M.ax[a], c[a], x[a]);
-        const float2 r = __ldg(M.cell + ((c[2].s - M.ax[2].p) * M.ncy + (c[1].s - M.ax[1].p)) * M.ncx +
-                               (c[0].s - M.ax[0].p));
+        int ci = ((c[2].s - M.ax[2].p) * M.ncy + (c[1].s - M.ax[1].p)) * M.ncx + (c[0].s - M.ax[0].p);
+        MFA_DBG_INDEX(M.dbg, ci, static_cast<long long>(M.ncx) * M.ncy * M.ncz, kDbgCell);
+        const float2 r = __ldg(M.cell + ci);
         if (iso < r.x) return r.x - iso;
         if (iso > r.y) return r.y - iso;
         float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];   // derivatives unused: dropped by the compiler

@@ -41,6 +41,27 @@ __host__ __device__ constexpr int window_values(int q) { return q == 3 ? 16 : 8;
 __host__ __device__ constexpr int qpair(int q) { return (q + 1) / 2 * 2; }
 __host__ __device__ constexpr int rec_stride(int q) { return ((kRecHead + q * qpair(q)) + 3) / 4 * 4; }
 
+// Debug builds (compiled with -DMFA_DEBUG) check every window, span-record, cell and
+// transfer-function index before its load.  A bad index sets a bit of the device's debug
+// word (dbg[0]), counts itself in dbg[1] and is replaced by 0, so the kernel completes and
+// the host reads the word with mfa_debug_status; nothing traps.  Release builds compile the
+// checks away (dbg stays NULL).
+enum : unsigned { kDbgWindow = 1u, kDbgRecord = 2u, kDbgCell = 4u, kDbgTf = 8u };
+#ifdef MFA_DEBUG
+__device__ __forceinline__ long long dbg_index(unsigned* dbg, long long i, long long n, unsigned bit)
+{
+    if (i >= 0 && i < n) return i;
+    if (dbg) {
+        atomicOr(dbg, bit);
+        atomicAdd(dbg + 1, 1u);
+    }
+    return 0;
+}
+#define MFA_DBG_INDEX(dbg, i, n, bit) ((i) = static_cast<decltype(i)>(dbg_index((dbg), (i), (n), (bit))))
+#else
+#define MFA_DBG_INDEX(dbg, i, n, bit) ((void)0)
+#endif
+
 struct AxisDev {
     const float* kup;   // n + p + 1 knots rounded up to FP32
     const float* rec;   // n - p span records of rec_stride(Q) floats
@@ -48,6 +69,7 @@ struct AxisDev {
     int n, p;           // control points and degree on this axis
     int G;              // grid cells
     float Gf;           // (float)G
+    unsigned* dbg;      // debug word (debug builds) or NULL
 };
 
 struct ModelDev {
@@ -62,6 +84,7 @@ struct ModelDev {
                         // {min, max} of the stored control points of its support, which
                         // bound the model on the cell (convex hull property)
     int ncx, ncy, ncz;  // cells per axis, n - p
+    unsigned* dbg;      // debug word (debug builds) or NULL
 };
 
 // Per-image render parameters (camera frame, image size, transfer-function scalars).
@@ -82,6 +105,7 @@ struct RenderScalars {
     float gtiny2;       // squared gradient-norm threshold for an undefined normal
     unsigned long long* samples_out;   // optional device counter
     float4* out;        // height * width premultiplied RGBA
+    unsigned* dbg;      // debug word (debug builds) or NULL
 };
 
 // Single-image launch: the scalars and the table travel as kernel arguments (about 4.3 KB).

@@ -109,6 +109,9 @@ __device__ __forceinline__ void axis_update(const AxisDev& A, AxisCache<Q>& C, f
 struct ShadeParams {
     float vmin, inv_range, tscale, ka, kd, ks, shin, gtiny2, lx, ly, lz;
     int tf_last, shading;
+#ifdef MFA_DEBUG
+    unsigned* dbg;
+#endif
 };
 
 __device__ __forceinline__ ShadeParams shade_params(const RenderScalars& P, const float (&d)[3])
@@ -127,6 +130,9 @@ __device__ __forceinline__ ShadeParams shade_params(const RenderScalars& P, cons
     S.lx = -d[0];
     S.ly = -d[1];
     S.lz = -d[2];
+#ifdef MFA_DEBUG
+    S.dbg = P.dbg;
+#endif
     return S;
 }
 
@@ -134,7 +140,8 @@ __device__ __forceinline__ float4 sample_colour(const float4* __restrict__ tf, c
 {
     const float tt = clamp01((q.x - S.vmin) * S.inv_range);
     const float xx = tt * S.tscale;
-    const int i0 = min(static_cast<int>(xx), S.tf_last);
+    int i0 = min(static_cast<int>(xx), S.tf_last);
+    MFA_DBG_INDEX(S.dbg, i0, S.tf_last + 1, kDbgTf);   // rows i0 and i0 + 1 are read
     const float wt = xx - static_cast<float>(i0);
     const float4 c0 = tf[i0], c1 = tf[i0 + 1];
     // c = c0 + wt (c1 - c0), two channels per packed instruction

@@ -101,7 +101,8 @@ __device__ __forceinline__ float4 march(const ModelDev& M, const RenderScalars& 
         float4 c;
         if (tf_n > 1) {
             const float xx = tt * tscale;
-            const int i0 = min(static_cast<int>(xx), tf_n - 2);
+            int i0 = min(static_cast<int>(xx), tf_n - 2);
+            MFA_DBG_INDEX(P.dbg, i0, tf_n - 1, kDbgTf);   // rows i0 and i0 + 1 are read
             const float wt = xx - static_cast<float>(i0);
             const float4 c0 = tf[i0], c1 = tf[i0 + 1];
             c.x = fmaf(wt, c1.x - c0.x, c0.x);
@@ -279,8 +280,9 @@ __device__ __forceinline__ float4 march_bricked(const ModelDev& M, const RenderS
             for (int e = lane; e < total; e += 32) {
                 const int ex = e % ext[0], r = e / ext[0];
                 const int ey = r % ext[1], ez = r / ext[1];
-                const long long gidx =
+                long long gidx =
                     (static_cast<long long>(org[2] + ez) * nyp + (org[1] + ey)) * nxp + (org[0] + ex);
+                MFA_DBG_INDEX(M.dbg, gidx, static_cast<long long>(nxp) * nyp * M.nzp, kDbgWindow);
                 brick[(ez * kBrick + ey) * kBrick + ex] = window_f32<Q, STORAGE>(M.win, gidx);
             }
             __syncwarp();
