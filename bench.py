@@ -474,6 +474,7 @@ def run_ours(args):
         line["encoding"] = encode_throughput(mfa, torch)
         line["render_quality"] = render_quality(mfa, torch)
         line["query_sweep"] = query_sweep(mfa, torch)
+        line["empty_space"] = empty_space(mfa, torch, spec, model, job)
     if ws == 1 and not args.no_serve:
         line["serving"] = dict(run_serve(mfa, rates=args.serve_rates, duration=args.serve_duration),
                                note="Poisson requests (sides 512..2048, 512..2048 samples) on 8 resident degree-3 "
@@ -616,6 +617,35 @@ def render_quality(mfa, torch):
             "fitted_vs_truth": fitted, "greville_vs_truth": sampled,
             "paper_table2_mfa": {"mse": 50.76, "psnr_db": 31.08, "ssim": 0.96,
                                  "note": "the paper's camera and transfer function are not given: context only"}}
+
+
+def empty_space(mfa, torch, spec, model, job, frames=5):
+    """Empty-space skipping (variant 7) against variant 6 on the same model and view with a
+    transfer function transparent below the median control point: ms per frame and samples
+    evaluated (the images agree to FP32 rounding)."""
+    import synth
+    W, H, NS = job.width, job.height, job.n_samples
+    lo, hi = float(spec.ctrl.min()), float(spec.ctrl.max())
+    cut = (float(np.median(spec.ctrl)) - lo) / (hi - lo)
+    table = synth.ramp_tf(256, 0.05).copy()
+    table[np.linspace(0.0, 1.0, len(table)) < cut, 3] = 0.0
+    tf = mfa.transfer_fn(table, shading=True)
+    img = torch.empty((H, W, 4), device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    out = {"transfer_function": "ramp, alpha 0 below the median control point"}
+    for variant in (6, 7):
+        mfa.render(model, job.camera, tf, W, H, NS, out=img, variant=variant)
+        torch.cuda.synchronize()
+        cnt.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(frames):
+            mfa.render(model, job.camera, tf, W, H, NS, out=img, variant=variant, samples_out=cnt)
+        b.record()
+        b.synchronize()
+        out[f"variant{variant}"] = {"ms_per_frame": a.elapsed_time(b) / frames,
+                                    "samples_per_frame": int(cnt.item()) / frames}
+    return out
 
 
 def query_sweep(mfa, torch, n_pts=1 << 22, reps=5):

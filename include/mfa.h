@@ -177,9 +177,17 @@ typedef struct {
                                          memory as FP32 (degree <= 3 on every axis; otherwise
                                          4); 6 = uniform knots: interior spans evaluate
                                          the one cardinal basis without span records
-                                         (cardinal models only; otherwise 4).  Variants
-                                         differ only in FP32 rounding order.
-                                         MFA_ERR_ARG outside 0..6. */
+                                         (cardinal models only; otherwise 4); 7 = 6 with
+                                         empty-space skipping (mfa_render_ex only): a
+                                         sample whose knot-span cell's value bound maps
+                                         only to transfer-function rows of zero opacity is
+                                         neither queried nor composited -- the image
+                                         equals 6's up to FP32 rounding order,
+                                         samples_out counts the evaluated samples; a pass over the cells builds
+                                         the per-render visibility bits (one bit per cell,
+                                         from the staging pool).  Variants 1-6 differ only
+                                         in FP32 rounding order.
+                                         MFA_ERR_ARG outside 0..7. */
     int tile_shape;                   /* ray tile: 0 = 16x8 pixels per CTA with 8x4 per warp
                                          (default), 1 = 32x4 / 8x4, 2 = 8x16 / 4x8,
                                          3 = 16x8 / 16x2.  MFA_ERR_ARG outside 0..3. */

@@ -473,14 +473,28 @@ int mfa_render_ex(const mfa_model* m, const mfa_camera* cam, const mfa_transfer_
 {
     int variant = opts ? opts->variant : 0;
     int shape = opts ? opts->tile_shape : 0;
-    if (variant < 0 || variant > 6) return fail(MFA_ERR_ARG, "render variant %d outside 0..6", variant);
+    if (variant < 0 || variant > 7) return fail(MFA_ERR_ARG, "render variant %d outside 0..7", variant);
     if (shape < 0 || shape >= kTileShapes) return fail(MFA_ERR_ARG, "tile_shape %d outside 0..%d", shape, kTileShapes - 1);
     if (opts && opts->use_tuned && m) tuned_lookup(m, width, height, n_samples, &variant, &shape);
     RenderParams P;
     if (int rc = setup_render(m, cam, tf, width, height, n_samples, rgba_out, opts ? opts->samples_out : nullptr, P.s,
                               P.tf))
         return rc;
-    cudaError_t e = launch_render(m->dev, P, variant, shape, g_stream);
+    cudaStream_t st = current_stream();
+    unsigned* bits = nullptr;   // variant 7: per-cell visibility under this transfer function
+    cudaError_t e = cudaSuccess;
+    if (variant == 7 && m->dev.cardinal) {
+        cudaMemPool_t pool;
+        const size_t words = (static_cast<size_t>(m->dev.ncx) * m->dev.ncy * m->dev.ncz + 31) / 32;
+        if ((e = staging_pool(m->device, &pool)) != cudaSuccess) return cuda_fail(e, "staging pool");
+        if ((e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&bits), words * sizeof(unsigned), pool, st)) !=
+            cudaSuccess)
+            return cuda_fail(e, "staging memory");
+        e = launch_cell_visibility(m->dev, P, bits, st);
+        P.s.cell_vis = bits;
+    }
+    if (e == cudaSuccess) e = launch_render(m->dev, P, variant, shape, st);
+    if (bits) cudaFreeAsync(bits, st);
     return e == cudaSuccess ? MFA_OK : cuda_fail(e, "render launch");
 }
 

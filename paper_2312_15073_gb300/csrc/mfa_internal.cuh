@@ -106,6 +106,8 @@ struct RenderScalars {
     unsigned long long* samples_out;   // optional device counter
     float4* out;        // height * width premultiplied RGBA
     unsigned* dbg;      // debug word (debug builds) or NULL
+    const unsigned* cell_vis;   // variant 7: bit c set where knot-span cell c can be visible
+                                // under this transfer function (NULL: every cell)
 };
 
 // Single-image launch: the scalars and the table travel as kernel arguments (about 4.3 KB).
@@ -159,6 +161,8 @@ cudaError_t launch_decode(const ModelDev& m, const float* pts, long long n, floa
                           cudaStream_t stream);
 cudaError_t launch_spans(const ModelDev& m, const float* pts, long long n, int* spans, cudaStream_t stream);
 cudaError_t launch_render(const ModelDev& m, const RenderParams& rp, int variant, int shape, cudaStream_t stream);
+// Variant 7's visibility bits (one per knot-span cell, (ncx ncy ncz + 31) / 32 words).
+cudaError_t launch_cell_visibility(const ModelDev& m, const RenderParams& rp, unsigned* bits, cudaStream_t stream);
 // Object-space decomposition into g[0] x g[1] x g[2] blocks (at most 64): every block's ray
 // segments into partial[block][height][width] (the variant picks the cardinal path unless
 // it is 4), then their over-merge into s.out.

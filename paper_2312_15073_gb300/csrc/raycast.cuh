@@ -297,7 +297,14 @@ __device__ __forceinline__ float4 march_pipelined(const ModelDev& M, const Rende
 // until a span changes.  The end spans, whose functions see the repeated end knots, read
 // their record from global memory (L1-resident, a few hundred bytes per axis) for each
 // sample.  Software-pipelined like variant 4.
-template <int Q, int STORAGE, bool SEG = false>
+//
+// SKIP (variant 7, empty-space skipping): P.cell_vis marks the knot-span cells whose value
+// range (the convex hull bound of their support) reaches a transfer-function row of
+// non-zero opacity.  A sample in an unmarked cell would composite with alpha exactly 0 and
+// change nothing, so it is neither queried nor composited; the image equals variant 6's
+// up to FP32 rounding order (the two instantiations may fuse multiply-adds differently)
+// and only evaluated samples are counted.
+template <int Q, int STORAGE, bool SEG = false, bool SKIP = false>
 __device__ __forceinline__ float4 march_cardinal(const ModelDev& M, const RenderScalars& P,
                                                  const float4* __restrict__ tf, int col, int row,
                                                  unsigned long long& count, const SegBlock* seg = nullptr)
@@ -325,8 +332,9 @@ __device__ __forceinline__ float4 march_cardinal(const ModelDev& M, const Render
     }
     CardAxis cx{ -INFINITY, 0, false }, cy{ -INFINITY, 0, false }, cz{ -INFINITY, 0, false };
     int base = 0;
+    bool cell_vis = true;   // SKIP: the current cell may be visible
 
-    auto query_at = [&](int k) -> float4 {
+    auto query_at = [&](int k, bool& vis) -> float4 {
         const float t = fmaf(static_cast<float>(k) + 0.5f, dt, t0);
         const float x = fmaf(t, dm[0], om[0]);
         const float y = fmaf(t, dm[1], om[1]);
@@ -349,6 +357,15 @@ __device__ __forceinline__ float4 march_cardinal(const ModelDev& M, const Render
                 tz = z - cz.jf;
             }
             base = (cz.j * M.nyp + cy.j) * M.nxp + cx.j;
+            if constexpr (SKIP) {
+                int ci = (cz.j * M.ncy + cy.j) * M.ncx + cx.j;
+                MFA_DBG_INDEX(P.dbg, ci, static_cast<long long>(M.ncx) * M.ncy * M.ncz, kDbgCell);
+                cell_vis = (__ldg(P.cell_vis + (ci >> 5)) >> (ci & 31)) & 1u;
+            }
+        }
+        vis = cell_vis;
+        if constexpr (SKIP) {
+            if (!cell_vis) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
         float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];
         if (cx.edge | cy.edge | cz.edge) {
@@ -368,21 +385,27 @@ __device__ __forceinline__ float4 march_cardinal(const ModelDev& M, const Render
         return q;
     };
 
-    float4 q = query_at(kb);
+    bool v, vn;
+    float4 q = query_at(kb, v);
     int k = kb;   // next sample to composite
+    int evaluated = 0;
     while (k < ke) {
-        const float4 qn = query_at(min(k + 1, ke - 1));
-        const float4 c = sample_colour(tf, S, q);
-        const float wgt = (1.0f - acc.w) * c.w;
-        acc.x = fmaf(wgt, c.x, acc.x);
-        acc.y = fmaf(wgt, c.y, acc.y);
-        acc.z = fmaf(wgt, c.z, acc.z);
-        acc.w += wgt;
+        const float4 qn = query_at(min(k + 1, ke - 1), vn);
+        if (!SKIP || v) {
+            const float4 c = sample_colour(tf, S, q);
+            const float wgt = (1.0f - acc.w) * c.w;
+            acc.x = fmaf(wgt, c.x, acc.x);
+            acc.y = fmaf(wgt, c.y, acc.y);
+            acc.z = fmaf(wgt, c.z, acc.z);
+            acc.w += wgt;
+            ++evaluated;
+        }
         ++k;
         if (acc.w >= ert) break;
         q = qn;
+        v = vn;
     }
-    count += static_cast<unsigned>(k - kb);
+    count += static_cast<unsigned>(SKIP ? evaluated : k - kb);
     return acc;
 }
 

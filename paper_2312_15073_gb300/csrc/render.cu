@@ -359,11 +359,52 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_render(ModelDev M, con
             acc = march_pipelined<Q, STORAGE>(M, P.s, tf, col, row, count);
         else if constexpr (MODE == 6)
             acc = march_cardinal<Q, STORAGE>(M, P.s, tf, col, row, count);
+        else if constexpr (MODE == 7)
+            acc = march_cardinal<Q, STORAGE, false, true>(M, P.s, tf, col, row, count);
         else
             acc = march<Q, STORAGE, MODE>(M, P.s, tf, col, row, count);
         P.s.out[static_cast<long long>(row) * P.s.width + col] = acc;
     }
     if (P.s.samples_out) add_count(P.s.samples_out, count);
+}
+
+// Variant 7's visibility bits: bit c of the knot-span cell c is set where some value in the
+// cell's bound [min, max] of its support's control points maps to a transfer-function row
+// pair with non-zero opacity.  The rows a sample of value f reads are i0(f) and i0(f) + 1
+// with i0 monotone in f, so the cell's samples read rows i0(min) .. i0(max) + 1; one row
+// more on each side covers FP32 rounding of f just outside the bound.  A prefix count of
+// the rows with non-zero opacity answers each cell in O(1).  One thread per 32 cells.
+__global__ void __launch_bounds__(256) k_cell_visible(ModelDev M, const __grid_constant__ RenderParams P,
+                                                      unsigned* __restrict__ bits)
+{
+    __shared__ int nz[kTfMax + 2];   // nz[r] = rows below r with non-zero alpha
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int r = 0; r < P.s.tf_n; ++r) {
+            nz[r] = c;
+            c += P.tf[r].w != 0.0f;
+        }
+        nz[P.s.tf_n] = c;
+    }
+    __syncthreads();
+    const long long cells = static_cast<long long>(M.ncx) * M.ncy * M.ncz;
+    const long long words = (cells + 31) / 32;
+    const float tscale = static_cast<float>(P.s.tf_n - 1);
+    const int tf_last = max(P.s.tf_n - 2, 0);
+    for (long long w = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; w < words;
+         w += static_cast<long long>(gridDim.x) * blockDim.x) {
+        unsigned word = 0u;
+        for (int b = 0; b < 32; ++b) {
+            const long long c = 32 * w + b;
+            if (c >= cells) break;
+            const float2 r = M.cell[c];
+            const float tl = clamp01((r.x - P.s.vmin) * P.s.inv_range), th = clamp01((r.y - P.s.vmin) * P.s.inv_range);
+            const int lo = max(min(static_cast<int>(tl * tscale), tf_last) - 1, 0);
+            const int hi = min(min(static_cast<int>(th * tscale), tf_last) + 2, P.s.tf_n - 1);
+            if (nz[hi + 1] - nz[lo] > 0) word |= 1u << b;
+        }
+        bits[w] = word;
+    }
 }
 
 template <int Q, int STORAGE>
@@ -374,6 +415,14 @@ cudaError_t render_qs(const ModelDev& m, const RenderParams& rp, int variant, in
     switch (variant) {
     case 2: k_render<Q, STORAGE, 2><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
     case 1: k_render<Q, STORAGE, 1><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
+    case 7:   // empty-space skipping on the cardinal path (needs the visibility bits)
+        if (m.cardinal && rp.s.cell_vis)
+            k_render<Q, STORAGE, 7><<<grid, kThreads, 0, st>>>(m, rp, shape);
+        else if (m.cardinal)
+            k_render<Q, STORAGE, 6><<<grid, kThreads, 0, st>>>(m, rp, shape);
+        else
+            k_render<Q, STORAGE, 4><<<grid, kThreads, 0, st>>>(m, rp, shape);
+        break;
     case 0:   // default: the cardinal path where it applies, else variant 4
     case 6:
         if (m.cardinal)
@@ -628,6 +677,14 @@ int render_tile_dims(int shape, int* tw, int* th)
     *tw = tile_shape(shape).tw;
     *th = tile_shape(shape).th;
     return 0;
+}
+
+cudaError_t launch_cell_visibility(const ModelDev& m, const RenderParams& rp, unsigned* bits, cudaStream_t stream)
+{
+    const long long words = (static_cast<long long>(m.ncx) * m.ncy * m.ncz + 31) / 32;
+    const long long want = (words + 255) / 256;
+    k_cell_visible<<<static_cast<int>(want < 2048 ? want : 2048), 256, 0, stream>>>(m, rp, bits);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_render(const ModelDev& m, const RenderParams& rp, int variant, int shape, cudaStream_t stream)
