@@ -379,8 +379,11 @@ typedef struct {
 /* Times every variant x tile-shape candidate on this render (one warm-up plus `reps`
  * launches each, CUDA events on the bound stream; synchronises it), stores the fastest as
  * the choice for the workload's class and returns it in *best; `all` (may be NULL)
- * receives up to max_all measured candidates, *n_all their count.  rgba_out is
- * overwritten.  Any render argument error is returned as by mfa_render. */
+ * receives up to max_all measured candidates, *n_all their count.  Candidates: variants
+ * 1-5, plus 6 and 7 for cardinal models.  The class does not include the transfer
+ * function, so a stored variant 7 (chosen where this render's table is partly
+ * transparent) also serves later renders with other tables: same images, at most its
+ * visibility pass slower where nothing is transparent; batches run it as 6.  rgba_out is overwritten.  Any render argument error is returned as by mfa_render. */
 int mfa_tune_render(const mfa_model* model, const mfa_camera* camera, const mfa_transfer_fn* tf, int width,
                     int height, int n_samples, float* rgba_out, int reps, mfa_tune_result* best,
                     mfa_tune_result* all, int max_all, int* n_all);

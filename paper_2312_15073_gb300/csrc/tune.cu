@@ -68,7 +68,8 @@ int mfa_tune_render(const mfa_model* m, const mfa_camera* cam, const mfa_transfe
     if (e != cudaSuccess) return cuda_fail(e, "tuner events");
     mfa_tune_result top{ 0, 0, INFINITY };
     int count = 0, rc = MFA_OK;
-    const int last_variant = m && m->dev.cardinal ? 6 : 5;   // 6 is the cardinal path
+    // 6 is the cardinal path, 7 the cardinal path with empty-space skipping
+    const int last_variant = m && m->dev.cardinal ? 7 : 5;
     for (int variant = 1; variant <= last_variant && rc == MFA_OK; ++variant) {
         for (int shape = 0; shape < kTileShapes && rc == MFA_OK; ++shape) {
             mfa_render_opts o{};
@@ -171,7 +172,7 @@ int mfa_tune_load(const char* path)
         int q, s, pb, sb, u, nb, v, t;
         float ms;
         if (std::sscanf(line, "%d %d %d %d %d %d %d %d %f", &q, &s, &pb, &sb, &u, &nb, &v, &t, &ms) != 9) continue;
-        if (v < 1 || v > 6 || t < 0 || t >= kTileShapes) continue;
+        if (v < 1 || v > 7 || t < 0 || t >= kTileShapes) continue;
         g_cache[Key(q, s, pb, sb, u, nb)] = mfa_tune_result{ v, t, ms };
         ++loaded;
     }

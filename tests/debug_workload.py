@@ -1,6 +1,6 @@
 """Runs a spread of workloads through the library named by MFA_LIB (the debug build in
 tests/test_gpu_debug.py) and prints its debug status as one JSON line: every kernel family
-(render variants 1-6, segments, isosurfaces, decode, batches, fits, the ground-truth render
+(render variants 1-7, segments, isosurfaces, decode, batches, fits, the ground-truth render
 and metrics), uniform and non-uniform knots, degrees 1-4, all storage types, points
 outside the box."""
 import json
@@ -32,10 +32,11 @@ def main():
         models.append(m)
         mfa.decode(m, pts)
         mfa.decode(m, pts, want_grad=False)
-        for variant in range(0, 7):
-            if variant == 6 and not m.info()["cardinal"]:
-                continue
+        for variant in range(0, 8):   # 6 and 7 fall back to 4 on non-cardinal models
             mfa.render(m, cam, tf, 33, 27, 80, variant=variant)
+        clear_low = synth.ramp_tf(64, 0.1).copy()
+        clear_low[:32, 3] = 0.0
+        mfa.render(m, cam, mfa.transfer_fn(clear_low, shading=True), 33, 27, 80, variant=7)
         mfa.render_segments(m, cam, tf, 33, 27, 80, (2, 2, 2))
         mfa.render_iso(m, cam, tf, 33, 27, 80, float(np.median(P)))
     reqs = [mfa.Request(m, cam, tf, 24, 20, 64) for m in models]
