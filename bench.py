@@ -463,7 +463,8 @@ def run_ours(args):
                 "ms_per_step": statistics.mean(e2e_ms),
                 "path": "mfa_render_host + mfa_decode_host (page-locked host buffers, library-staged "
                         "copies), enqueued on two streams so that they overlap"},
-        "gpu_launches": 2 * args.steps,
+        # per step: the render (plus its visibility pass under variant 7) and the decode
+        "gpu_launches": (3 if tuned.get("variant") == 7 else 2) * args.steps,
         "clocks": clk,
     }
     if ws == 1 and not args.no_side_rows:
