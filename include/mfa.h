@@ -177,12 +177,13 @@ typedef struct {
                                          memory as FP32 (degree <= 3 on every axis; otherwise
                                          4); 6 = uniform knots: interior spans evaluate
                                          the one cardinal basis without span records
-                                         (cardinal models only; otherwise 4); 7 = 6 with
-                                         empty-space skipping (mfa_render_ex only): a
+                                         (cardinal models only; otherwise 4); 7 = 6 (4 off
+                                         the cardinal path) with empty-space skipping
+                                         (mfa_render_ex and the server only): a
                                          sample whose knot-span cell's value bound maps
                                          only to transfer-function rows of zero opacity is
                                          neither queried nor composited -- the image
-                                         equals 6's up to FP32 rounding order,
+                                         equals 6's (4's) up to FP32 rounding order,
                                          samples_out counts the evaluated samples; a pass over the cells builds
                                          the per-render visibility bits (one bit per cell,
                                          from the staging pool).  Variants 1-6 differ only
@@ -380,7 +381,7 @@ typedef struct {
  * launches each, CUDA events on the bound stream; synchronises it), stores the fastest as
  * the choice for the workload's class and returns it in *best; `all` (may be NULL)
  * receives up to max_all measured candidates, *n_all their count.  Candidates: variants
- * 1-5, plus 6 and 7 for cardinal models.  The class does not include the transfer
+ * 1-5 and 7, plus 6 for cardinal models.  The class does not include the transfer
  * function, so a stored variant 7 (chosen where this render's table is partly
  * transparent) also serves later renders with other tables: same images, at most its
  * visibility pass slower where nothing is transparent; batches run it as 6.  rgba_out is overwritten.  Any render argument error is returned as by mfa_render. */

@@ -483,7 +483,7 @@ int mfa_render_ex(const mfa_model* m, const mfa_camera* cam, const mfa_transfer_
     cudaStream_t st = current_stream();
     unsigned* bits = nullptr;   // variant 7: per-cell visibility under this transfer function
     cudaError_t e = cudaSuccess;
-    if (variant == 7 && m->dev.cardinal) {
+    if (variant == 7) {
         cudaMemPool_t pool;
         const size_t words = (static_cast<size_t>(m->dev.ncx) * m->dev.ncy * m->dev.ncz + 31) / 32;
         if ((e = staging_pool(m->device, &pool)) != cudaSuccess) return cuda_fail(e, "staging pool");

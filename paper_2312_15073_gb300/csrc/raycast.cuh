@@ -222,8 +222,9 @@ __device__ __forceinline__ void block_range(const SegBlock& B, const float (&o)[
 // hides behind the contraction of the next.  The three span checks share one branch.
 // The last iteration queries the final sample a second time (its result is not used).
 // SEG: march only the samples of one block of the object-space decomposition (seg), with
-// early termination on the segment's own alpha.
-template <int Q, int STORAGE, bool SEG = false>
+// early termination on the segment's own alpha.  SKIP: empty-space skipping as in
+// march_cardinal (variant 7 on models off the cardinal path).
+template <int Q, int STORAGE, bool SEG = false, bool SKIP = false>
 __device__ __forceinline__ float4 march_pipelined(const ModelDev& M, const RenderScalars& P,
                                                   const float4* __restrict__ tf, int col, int row,
                                                   unsigned long long& count, const SegBlock* seg = nullptr)
@@ -243,8 +244,9 @@ __device__ __forceinline__ float4 march_pipelined(const ModelDev& M, const Rende
     const ShadeParams S = shade_params(P, d);
     AxisCache<Q> cx, cy, cz;
     cx.s = cy.s = cz.s = -1;
+    bool cell_vis = true;   // SKIP: the current cell may be visible
 
-    auto query_at = [&](int k) -> float4 {
+    auto query_at = [&](int k, bool& vis) -> float4 {
         const float t = fmaf(static_cast<float>(k) + 0.5f, dt, t0);
         const float u = clamp01(fmaf(t, d[0], o[0]));
         const float v = clamp01(fmaf(t, d[1], o[1]));
@@ -256,6 +258,15 @@ __device__ __forceinline__ float4 march_pipelined(const ModelDev& M, const Rende
             if (ox) axis_update<Q>(M.ax[0], cx, u);
             if (oy) axis_update<Q>(M.ax[1], cy, v);
             if (oz) axis_update<Q>(M.ax[2], cz, w);
+            if constexpr (SKIP) {
+                int ci = ((cz.s - M.ax[2].p) * M.ncy + (cy.s - M.ax[1].p)) * M.ncx + (cx.s - M.ax[0].p);
+                MFA_DBG_INDEX(P.dbg, ci, static_cast<long long>(M.ncx) * M.ncy * M.ncz, kDbgCell);
+                cell_vis = (__ldg(P.cell_vis + (ci >> 5)) >> (ci & 31)) & 1u;
+            }
+        }
+        vis = cell_vis;
+        if constexpr (SKIP) {
+            if (!cell_vis) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
         float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];
         record_basis<Q>(cx.rec, u, Nx, Dx);
@@ -269,18 +280,22 @@ __device__ __forceinline__ float4 march_pipelined(const ModelDev& M, const Rende
         return q;
     };
 
-    float4 q = query_at(kb);
+    bool v, vn;
+    float4 q = query_at(kb, v);
     for (int k = kb; k < ke; ++k) {
-        const float4 qn = query_at(min(k + 1, ke - 1));
-        const float4 c = sample_colour(tf, S, q);
-        const float wgt = (1.0f - acc.w) * c.w;
-        acc.x = fmaf(wgt, c.x, acc.x);
-        acc.y = fmaf(wgt, c.y, acc.y);
-        acc.z = fmaf(wgt, c.z, acc.z);
-        acc.w += wgt;
-        ++count;
+        const float4 qn = query_at(min(k + 1, ke - 1), vn);
+        if (!SKIP || v) {
+            const float4 c = sample_colour(tf, S, q);
+            const float wgt = (1.0f - acc.w) * c.w;
+            acc.x = fmaf(wgt, c.x, acc.x);
+            acc.y = fmaf(wgt, c.y, acc.y);
+            acc.z = fmaf(wgt, c.z, acc.z);
+            acc.w += wgt;
+            ++count;
+        }
         if (acc.w >= ert) break;
         q = qn;
+        v = vn;
     }
     return acc;
 }

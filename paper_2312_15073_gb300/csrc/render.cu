@@ -42,6 +42,11 @@ constexpr int kThreads = 128;
 // the 128^3 degree-3 frame: cap 128 -> 6.33 ms, cap 168 (3 CTAs) -> 7.01 ms, cap 96 (5
 // CTAs, spills) -> 10.4 ms.
 constexpr int kMinBlocks = 4;
+// Degree class 5 (degree 4) off the cardinal path: the span records of three axes and a
+// 5x5x5 support do not fit in 128 registers (variant 4 spilled 720 bytes), so those kernels
+// take the register budget of three CTAs per SM.
+template <int Q, bool CARD>
+constexpr int min_blocks() { return Q <= 4 || CARD ? kMinBlocks : 3; }
 // The cardinal path (variant 6) holds no span records and would fit more CTAs per SM, but
 // with the packed layer-pair contraction 4 CTAs (128 registers) still measures best on the
 // 128^3 degree-3 1024^2 frame: FP32 4.87 ms against 5.05 ms at 5 CTAs (96 registers, with
@@ -336,7 +341,7 @@ __device__ __forceinline__ float4 march_bricked(const ModelDev& M, const RenderS
 // ----------------------------------------------------------------------------------------
 
 template <int Q, int STORAGE, int MODE>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_render(ModelDev M, const __grid_constant__ RenderParams P,
+__global__ void __launch_bounds__(kThreads, min_blocks<Q, MODE == 6 || MODE == 7>()) k_render(ModelDev M, const __grid_constant__ RenderParams P,
                                                                  int shape)
 {
     __shared__ float4 tf[kTfMax + 1];
@@ -361,6 +366,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_render(ModelDev M, con
             acc = march_cardinal<Q, STORAGE>(M, P.s, tf, col, row, count);
         else if constexpr (MODE == 7)
             acc = march_cardinal<Q, STORAGE, false, true>(M, P.s, tf, col, row, count);
+        else if constexpr (MODE == 8)   // variant 7 off the cardinal path
+            acc = march_pipelined<Q, STORAGE, false, true>(M, P.s, tf, col, row, count);
         else
             acc = march<Q, STORAGE, MODE>(M, P.s, tf, col, row, count);
         P.s.out[static_cast<long long>(row) * P.s.width + col] = acc;
@@ -415,9 +422,11 @@ cudaError_t render_qs(const ModelDev& m, const RenderParams& rp, int variant, in
     switch (variant) {
     case 2: k_render<Q, STORAGE, 2><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
     case 1: k_render<Q, STORAGE, 1><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
-    case 7:   // empty-space skipping on the cardinal path (needs the visibility bits)
+    case 7:   // empty-space skipping (needs the visibility bits; without them, variant 6 / 4)
         if (m.cardinal && rp.s.cell_vis)
             k_render<Q, STORAGE, 7><<<grid, kThreads, 0, st>>>(m, rp, shape);
+        else if (rp.s.cell_vis)
+            k_render<Q, STORAGE, 8><<<grid, kThreads, 0, st>>>(m, rp, shape);
         else if (m.cardinal)
             k_render<Q, STORAGE, 6><<<grid, kThreads, 0, st>>>(m, rp, shape);
         else
@@ -468,7 +477,7 @@ cudaError_t render_q(const ModelDev& m, const RenderParams& rp, int variant, int
 constexpr int kMaxSegBlocks = 64;
 
 template <int Q, int STORAGE, int MODE>
-__global__ void __launch_bounds__(kThreads, kMinBlocks)
+__global__ void __launch_bounds__(kThreads, min_blocks<Q, MODE == 6>())
     k_render_segments(ModelDev M, const __grid_constant__ RenderParams P, int shape, int gx, int gy, int gz,
                       float4* __restrict__ partial)
 {
@@ -583,7 +592,7 @@ cudaError_t segments_q(const ModelDev& m, const RenderParams& rp, bool cardinal,
 // repeat until the counter passes the group's last tile.  One kernel per group keeps each
 // degree's (and each path's) register allocation free of the others'.
 template <int Q, int STORAGE, bool CARD>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_batch(BatchHead* __restrict__ table, int group,
+__global__ void __launch_bounds__(kThreads, min_blocks<Q, CARD>()) k_render_batch(BatchHead* __restrict__ table, int group,
                                                                        int shape)
 {
     __shared__ BatchItem item;

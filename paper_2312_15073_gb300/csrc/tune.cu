@@ -68,9 +68,10 @@ int mfa_tune_render(const mfa_model* m, const mfa_camera* cam, const mfa_transfe
     if (e != cudaSuccess) return cuda_fail(e, "tuner events");
     mfa_tune_result top{ 0, 0, INFINITY }, top_skip{ 0, 0, INFINITY };   // top: variants 1-6
     int count = 0, rc = MFA_OK;
-    // 6 is the cardinal path, 7 the cardinal path with empty-space skipping
-    const int last_variant = m && m->dev.cardinal ? 7 : 5;
-    for (int variant = 1; variant <= last_variant && rc == MFA_OK; ++variant) {
+    // 6 is the cardinal path (cardinal models only), 7 empty-space skipping
+    const bool cardinal = m && m->dev.cardinal;
+    for (int variant = 1; variant <= 7 && rc == MFA_OK; ++variant) {
+        if (variant == 6 && !cardinal) continue;
         for (int shape = 0; shape < kTileShapes && rc == MFA_OK; ++shape) {
             mfa_render_opts o{};
             o.variant = variant;

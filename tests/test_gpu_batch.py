@@ -147,7 +147,7 @@ def test_autotuner_render_and_batch(mfa, orc, tmp_path):
     reqs, jobs = _requests(mfa, models, rng)
     m, ref, cam, table, tf, W, H, ns = jobs[0]
     best, allr = mfa.tune_render(m, cam, tf, W, H, ns, reps=2)
-    n_variants = 7 if m.info()["cardinal"] else 5
+    n_variants = 7 if m.info()["cardinal"] else 6
     assert len(allr) == 4 * n_variants and all(r["ms"] > 0 for r in allr)
     assert best["ms"] == min(r["ms"] for r in allr)
     a = mfa.render(m, cam, tf, W, H, ns, use_tuned=True)
