@@ -64,8 +64,8 @@ DECODE_WINDOW_BYTES = {1: 1 * 2 * 16, 2: 1 * 3 * 48, 3: 2 * 4 * 32, 4: 3 * 5 * 4
 # DRAM bytes (read + write) of one k_render launch on this workload, from the ncu capture
 # summarised in profiles/k_render_p3_128cube_persp1024_ns1024.md, valid only for the kernel
 # sources it was taken on (their SHA-256 is checked at run time; any change -> null).
-RENDER_TRAFFIC = {"src_sha256": "e98efccb1433f5f327cd94fdb6e018cc2c044e44ffb0a101423c6ada9c3ec001",
-                  "bytes_per_launch": 16105984}
+RENDER_TRAFFIC = {"src_sha256": "5ec5df64696fcacc14aead3d96b7776bb26a829406586a0c160c40c537378ad5",
+                  "bytes_per_launch": 16107008}
 KERNEL_SOURCES = ["paper_2312_15073_gb300/csrc/render.cu", "paper_2312_15073_gb300/csrc/raycast.cuh",
                   "paper_2312_15073_gb300/csrc/bspline.cuh", "paper_2312_15073_gb300/csrc/mfa_internal.cuh"]
 
