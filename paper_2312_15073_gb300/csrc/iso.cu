@@ -3,8 +3,9 @@
 // pixel: the ray's samples (the volume render's positions) are examined in order until
 // f - iso changes sign between two of them.  A sample whose knot-span cell has all the
 // control points of its support on one side of iso has that sign without a query (the
-// model lies in the convex hull of those control points); the others take a value-only
-// query (no derivative weights).  The crossing is refined by kIsoSteps Newton
+// model lies in the convex hull of those control points), and so do the cell's later
+// samples: the search steps to the cell's exit; the others take a value-only query (no
+// derivative weights).  The crossing is refined by kIsoSteps Newton
 // steps on g(t) = f(o + t d) - iso with the analytic derivative g'(t) = grad f . d, kept
 // inside the bracket (each step shrinks the bracket to the side where g changes sign and
 // falls back to its midpoint when the Newton point leaves it); the hit is shaded like a
@@ -60,13 +61,14 @@ struct RayQuery<Q, STORAGE, true> {
 
     // f - iso at the parameter point (u, v, w) of the unit box, or, where the point's cell
     // bounds the model away from iso, a stand-in of the same sign without a query
-    __device__ __forceinline__ float g(const ModelDev& M, float u, float v, float w, float iso)
+    __device__ __forceinline__ float g(const ModelDev& M, float u, float v, float w, float iso, bool& bounded)
     {
         float t[3];
         locate(M, u, v, w, t);
         int ci = (c[2].j * M.ncy + c[1].j) * M.ncx + c[0].j;
         MFA_DBG_INDEX(M.dbg, ci, static_cast<long long>(M.ncx) * M.ncy * M.ncz, kDbgCell);
         const float2 r = __ldg(M.cell + ci);
+        bounded = iso < r.x || iso > r.y;
         if (iso < r.x) return r.x - iso;
         if (iso > r.y) return r.y - iso;
         float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];   // derivatives unused: dropped by the compiler
@@ -74,6 +76,19 @@ struct RayQuery<Q, STORAGE, true> {
         card_basis<Q>(M.ax[1], c[1], t[1], Ny, Dy);
         card_basis<Q>(M.ax[2], c[2], t[2], Nz, Dz);
         return value_at<Q, STORAGE>(M, base, Nx, Ny, Nz) * Cardinal<Q>::kValScale - iso;
+    }
+
+    // ray parameter at which the ray o + t d leaves the current cell: the cell spans
+    // [j/m, (j+1)/m) along each axis of the unit box
+    __device__ __forceinline__ float cell_exit(const float (&o)[3], const float (&d)[3]) const
+    {
+        float te = INFINITY;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (d[a] > 0.0f) te = fminf(te, (static_cast<float>(c[a].j + 1) / m[a] - o[a]) / d[a]);
+            else if (d[a] < 0.0f) te = fminf(te, (static_cast<float>(c[a].j) / m[a] - o[a]) / d[a]);
+        }
+        return te;
     }
 
     // {f, df/du, df/dv, df/dw} at the parameter point (u, v, w) of the unit box
@@ -105,7 +120,7 @@ struct RayQuery<Q, STORAGE, false> {
         for (int a = 0; a < 3; ++a) c[a].s = -1;
     }
 
-    __device__ __forceinline__ float g(const ModelDev& M, float u, float v, float w, float iso)
+    __device__ __forceinline__ float g(const ModelDev& M, float u, float v, float w, float iso, bool& bounded)
     {
         const float x[3] = { clamp01(u), clamp01(v), clamp01(w) };
 #pragma unroll
@@ -113,6 +128,7 @@ struct RayQuery<Q, STORAGE, false> {
         int ci = ((c[2].s - M.ax[2].p) * M.ncy + (c[1].s - M.ax[1].p)) * M.ncx + (c[0].s - M.ax[0].p);
         MFA_DBG_INDEX(M.dbg, ci, static_cast<long long>(M.ncx) * M.ncy * M.ncz, kDbgCell);
         const float2 r = __ldg(M.cell + ci);
+        bounded = iso < r.x || iso > r.y;
         if (iso < r.x) return r.x - iso;
         if (iso > r.y) return r.y - iso;
         float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];   // derivatives unused: dropped by the compiler
@@ -123,6 +139,19 @@ struct RayQuery<Q, STORAGE, false> {
                    M, ((c[2].s - M.ax[2].p) * M.nyp + (c[1].s - M.ax[1].p)) * M.nxp + (c[0].s - M.ax[0].p), Nx, Ny,
                    Nz) -
                iso;
+    }
+
+    // ray parameter at which the ray o + t d leaves the current cell: the span records'
+    // FP32 bounds [lo, hi) along each axis
+    __device__ __forceinline__ float cell_exit(const float (&o)[3], const float (&d)[3]) const
+    {
+        float te = INFINITY;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (d[a] > 0.0f) te = fminf(te, (c[a].rec[3] - o[a]) / d[a]);
+            else if (d[a] < 0.0f) te = fminf(te, (c[a].rec[2] - o[a]) / d[a]);
+        }
+        return te;
     }
 
     __device__ __forceinline__ float4 at(const ModelDev& M, float u, float v, float w)
@@ -168,9 +197,10 @@ __global__ void __launch_bounds__(kIsoThreads, Q <= 4 ? 4 : 3)
                 ++count;
                 return rq.at(M, fmaf(t, d[0], o[0]), fmaf(t, d[1], o[1]), fmaf(t, d[2], o[2]));
             };
+            bool bounded = false;
             auto g_at = [&](float t) {
                 ++count;
-                return rq.g(M, fmaf(t, d[0], o[0]), fmaf(t, d[1], o[1]), fmaf(t, d[2], o[2]), iso);
+                return rq.g(M, fmaf(t, d[0], o[0]), fmaf(t, d[1], o[1]), fmaf(t, d[2], o[2]), iso, bounded);
             };
             // first sign change of g = f - iso between consecutive samples
             float ta = 0.0f, ga = 0.0f, tb = 0.0f;
@@ -190,6 +220,19 @@ __global__ void __launch_bounds__(kIsoThreads, Q <= 4 ? 4 : 3)
                 }
                 ta = t;
                 ga = g;
+                if (bounded) {
+                    // every sample of this cell has g's sign: step to the cell's last sample
+                    // but one (a sample of margin against rounding), counting the samples
+                    // passed as examined
+                    const float kf = (rq.cell_exit(o, d) - t0) / dt - 0.5f;   // samples k' < kf precede the exit
+                    const int klast = kf < static_cast<float>(ns) ? static_cast<int>(ceilf(kf)) - 1 : ns - 1;
+                    const int kj = klast - 1;
+                    if (kj > k) {
+                        count += static_cast<unsigned>(kj - k);
+                        ta = fmaf(static_cast<float>(kj) + 0.5f, dt, t0);
+                        k = kj;
+                    }
+                }
             }
             if (found) {
                 float t = 0.5f * (ta + tb);
