@@ -25,9 +25,11 @@ __global__ void __launch_bounds__(256, Q <= 4 ? 4 : 3)
 {
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const float u = clamp01(__ldg(pts + 3 * i + 0));
-        const float v = clamp01(__ldg(pts + 3 * i + 1));
-        const float w = clamp01(__ldg(pts + 3 * i + 2));
+        // points and results stream through once: evict-first loads and stores keep them from
+        // pushing the window array out of L2
+        const float u = clamp01(__ldcs(pts + 3 * i + 0));
+        const float v = clamp01(__ldcs(pts + 3 * i + 1));
+        const float w = clamp01(__ldcs(pts + 3 * i + 2));
         float4 r;
         if constexpr (CARD) {
             r = query_cardinal<Q, STORAGE>(M, u, v, w);
@@ -37,11 +39,11 @@ __global__ void __launch_bounds__(256, Q <= 4 ? 4 : 3)
             const int sz = locate_span(M.ax[2], w);
             r = query2<Q, STORAGE>(M, u, v, w, sx, sy, sz);
         }
-        val[i] = r.x;
+        __stcs(val + i, r.x);
         if (GRAD && grad) {
-            grad[3 * i + 0] = r.y;
-            grad[3 * i + 1] = r.z;
-            grad[3 * i + 2] = r.w;
+            __stcs(grad + 3 * i + 0, r.y);
+            __stcs(grad + 3 * i + 1, r.z);
+            __stcs(grad + 3 * i + 2, r.w);
         }
     }
 }
