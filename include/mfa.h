@@ -484,7 +484,7 @@ int mfa_render_batch_static(const mfa_render_request* reqs, int n);
  * block's regular grid of values before visualization).  data: DEVICE FP32
  * [ndata[2]][ndata[1]][ndata[0]], x fastest, the values at the uniform parameters
  * u_i = i / (ndata[0] - 1) (likewise v, w).  The fit minimises the sum of squared errors
- * at the data points over the control points (least squares along x, then y, then z; FP64,
+ * at the data points over the control points (least squares along each axis -- z, y, x; FP64,
  * normal equations with a banded Cholesky factor per axis).  Errors: MFA_ERR_ARG when a
  * knot span holds too few data parameters to determine the spline, ndata[d] < nctrl[d],
  * bad knots (as mfa_model_create); MFA_ERR_UNSUPPORTED for a degree outside 1..4.  All

@@ -5,8 +5,9 @@
 // Least squares.  The data D[k][j][i] sit at the uniform parameters u_i = i/(m_x - 1) (and
 // v_j, w_k).  With collocation matrices A_x[i][c] = N_c(u_i) (A_y, A_z likewise) of full
 // column rank, the control points minimising sum (f(u_i, v_j, w_k) - D[k][j][i])^2 are
-// P = (A_z^+ (x) A_y^+ (x) A_x^+) D: a least-squares solve along x for every line, then
-// along y, then along z.  Each 1-D solve uses the normal equations: the Gram matrix
+// P = (A_z^+ (x) A_y^+ (x) A_x^+) D: a least-squares solve along each axis for every line;
+// the three commute, and run along z, then y, then x (coalesced passes over the large
+// arrays first).  Each 1-D solve uses the normal equations: the Gram matrix
 // G = A^T A is symmetric positive definite and banded (half-bandwidth p), so a banded
 // Cholesky factor L is computed once per axis, and every line solves L L^T x = A^T y by
 // forward and back substitution -- one thread per line, FP64 throughout.  The right-hand
@@ -324,10 +325,10 @@ int fit_device(const int degree[3], const int nctrl[3], const std::vector<double
     }
     const size_t off_status = total;
     total += 256;
-    const size_t off_t1 = total;   // after x: [m_z][m_y][n_x]
-    total += al(sizeof(double) * static_cast<size_t>(md[2]) * md[1] * nctrl[0]);
-    const size_t off_t2 = total;   // after y: [m_z][n_y][n_x]
-    total += al(sizeof(double) * static_cast<size_t>(md[2]) * nctrl[1] * nctrl[0]);
+    const size_t off_t1 = total;   // after z: [n_z][m_y][m_x]
+    total += al(sizeof(double) * static_cast<size_t>(nctrl[2]) * md[1] * md[0]);
+    const size_t off_t2 = total;   // after y: [n_z][n_y][m_x]
+    total += al(sizeof(double) * static_cast<size_t>(nctrl[2]) * nctrl[1] * md[0]);
     char* w = nullptr;
     if ((e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&w), total, pool, st)) != cudaSuccess)
         return cuda_fail(e, "fit work space");
@@ -355,29 +356,33 @@ int fit_device(const int degree[3], const int nctrl[3], const std::vector<double
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     for (int a = 0; a < 3; ++a) bad |= st_host[a] ? (1 << a) : 0;
     if (e == cudaSuccess && !bad) {
-        const int mx = md[0], my = md[1], mz = md[2], nx = nctrl[0], ny = nctrl[1], nz = nctrl[2];
+        const int mx = md[0], my = md[1], nx = nctrl[0], ny = nctrl[1], nz = nctrl[2];
         double* t1 = reinterpret_cast<double*>(P(off_t1));
         double* t2 = reinterpret_cast<double*>(P(off_t2));
         auto blocks = [](long long lines) { return static_cast<unsigned>((lines + kFitThreads - 1) / kFitThreads); };
-        // x: lines (k, j), data stride 1
-        long long lines = static_cast<long long>(mz) * my;
+        // The three axis solves commute; they run z, y, x so that the two passes over the
+        // large arrays (the data, then the z-reduced data) read and write along the x-fastest
+        // index across a warp's threads (coalesced) and only the last, smallest array is read
+        // line by line.
+        // z: lines (j, i), data stride m_y m_x
+        long long lines = static_cast<long long>(my) * mx;
         k_fit_lines<float><<<blocks(lines), kFitThreads, 0, st>>>(
-            D, t1, lines, 1, mx, 0, 1, nx, 0, 1, nx, degree[0], reinterpret_cast<int*>(P(off_span[0])),
-            reinterpret_cast<double*>(P(off_N[0])), reinterpret_cast<int*>(P(off_first[0])),
-            reinterpret_cast<int*>(P(off_last[0])), reinterpret_cast<double*>(P(off_L[0])));
-        // y: lines (k, i), stride n_x
-        lines = static_cast<long long>(mz) * nx;
+            D, t1, lines, lines, 0, 1, lines, 0, 1, lines, nz, degree[2], reinterpret_cast<int*>(P(off_span[2])),
+            reinterpret_cast<double*>(P(off_N[2])), reinterpret_cast<int*>(P(off_first[2])),
+            reinterpret_cast<int*>(P(off_last[2])), reinterpret_cast<double*>(P(off_L[2])));
+        // y: lines (k, i), stride m_x
+        lines = static_cast<long long>(nz) * mx;
         k_fit_lines<double><<<blocks(lines), kFitThreads, 0, st>>>(
-            t1, t2, lines, nx, static_cast<long long>(my) * nx, 1, nx, static_cast<long long>(ny) * nx, 1, nx, ny,
+            t1, t2, lines, mx, static_cast<long long>(my) * mx, 1, mx, static_cast<long long>(ny) * mx, 1, mx, ny,
             degree[1], reinterpret_cast<int*>(P(off_span[1])), reinterpret_cast<double*>(P(off_N[1])),
             reinterpret_cast<int*>(P(off_first[1])), reinterpret_cast<int*>(P(off_last[1])),
             reinterpret_cast<double*>(P(off_L[1])));
-        // z: lines (j, i), stride n_y n_x
-        lines = static_cast<long long>(ny) * nx;
+        // x: lines (k, j), stride 1
+        lines = static_cast<long long>(nz) * ny;
         k_fit_lines<double><<<blocks(lines), kFitThreads, 0, st>>>(
-            t2, ctrl, lines, lines, 0, 1, lines, 0, 1, lines, nz, degree[2], reinterpret_cast<int*>(P(off_span[2])),
-            reinterpret_cast<double*>(P(off_N[2])), reinterpret_cast<int*>(P(off_first[2])),
-            reinterpret_cast<int*>(P(off_last[2])), reinterpret_cast<double*>(P(off_L[2])));
+            t2, ctrl, lines, 1, mx, 0, 1, nx, 0, 1, nx, degree[0], reinterpret_cast<int*>(P(off_span[0])),
+            reinterpret_cast<double*>(P(off_N[0])), reinterpret_cast<int*>(P(off_first[0])),
+            reinterpret_cast<int*>(P(off_last[0])), reinterpret_cast<double*>(P(off_L[0])));
         e = cudaGetLastError();
     }
     cudaError_t ef = cudaFreeAsync(w, st);
