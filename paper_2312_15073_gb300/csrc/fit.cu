@@ -99,10 +99,12 @@ __global__ void k_fit_gram(const int* __restrict__ span, const double* __restric
     for (int d = 0; d <= p; ++d) G[static_cast<long long>(c) * (p + 1) + d] = g[d];
 }
 
-// Banded Cholesky G = L L^T (one thread: O(n p^2) sequential work).  L[c][d] = L(c, c-d).
+// Banded Cholesky G = L L^T (one thread: O(n p^2) sequential work).  L[c][d] = L(c, c-d);
+// Linv[c] = 1 / L(c, c), so that the line solves multiply instead of dividing (an FP64
+// divide costs many FP64 operations, and every line would do 2n of them).
 // status = 1 if a pivot is not positive (the data do not determine the spline).
 __global__ void k_fit_cholesky(const double* __restrict__ G, int n, int p, double* __restrict__ L,
-                               int* __restrict__ status)
+                               double* __restrict__ Linv, int* __restrict__ status)
 {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     *status = 0;
@@ -131,6 +133,7 @@ __global__ void k_fit_cholesky(const double* __restrict__ G, int n, int p, doubl
             return;
         }
         L[static_cast<long long>(c) * w] = sqrt(v);
+        Linv[c] = 1.0 / L[static_cast<long long>(c) * w];
     }
 }
 
@@ -144,7 +147,8 @@ __global__ void __launch_bounds__(kFitThreads)
     k_fit_lines(const T* __restrict__ in, double* __restrict__ out, long long lines, long long inner,
                 long long in_outer, long long in_inner, long long in_stride, long long out_outer, long long out_inner,
                 long long out_stride, int n, int p, const int* __restrict__ span, const double* __restrict__ N,
-                const int* __restrict__ first, const int* __restrict__ last, const double* __restrict__ L)
+                const int* __restrict__ first, const int* __restrict__ last, const double* __restrict__ L,
+                const double* __restrict__ Linv)
 {
     const long long l = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
     if (l >= lines) return;
@@ -160,7 +164,7 @@ __global__ void __launch_bounds__(kFitThreads)
             rhs = fma(N[static_cast<long long>(i) * w + (c - span[i] + p)], static_cast<double>(y[i * in_stride]), rhs);
         double v = rhs;
         for (int d = 1; d <= p; ++d) v -= L[static_cast<long long>(c) * w + d] * h[d];
-        v /= L[static_cast<long long>(c) * w];
+        v *= Linv[c];
         for (int d = p; d >= 2; --d) h[d] = h[d - 1];
         h[1] = v;
         x[c * out_stride] = v;
@@ -170,7 +174,7 @@ __global__ void __launch_bounds__(kFitThreads)
     for (int c = n - 1; c >= 0; --c) {
         double v = x[c * out_stride];
         for (int d = 1; d <= p && c + d < n; ++d) v -= L[static_cast<long long>(c + d) * w + d] * h[d];
-        v /= L[static_cast<long long>(c) * w];
+        v *= Linv[c];
         for (int d = p; d >= 2; --d) h[d] = h[d - 1];
         h[1] = v;
         x[c * out_stride] = v;
@@ -305,7 +309,7 @@ int fit_device(const int degree[3], const int nctrl[3], const std::vector<double
     cudaError_t e = staging_pool(dev, &pool);
     if (e != cudaSuccess) return cuda_fail(e, "staging pool");
     auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-    size_t off_U[3], off_span[3], off_N[3], off_first[3], off_last[3], off_G[3], off_L[3], total = 0;
+    size_t off_U[3], off_span[3], off_N[3], off_first[3], off_last[3], off_G[3], off_L[3], off_Linv[3], total = 0;
     for (int a = 0; a < 3; ++a) {
         const int n = nctrl[a], p = degree[a], m = md[a];
         off_U[a] = total;
@@ -322,6 +326,8 @@ int fit_device(const int degree[3], const int nctrl[3], const std::vector<double
         total += al(sizeof(double) * n * (p + 1));
         off_L[a] = total;
         total += al(sizeof(double) * n * (p + 1));
+        off_Linv[a] = total;
+        total += al(sizeof(double) * n);
     }
     const size_t off_status = total;
     total += 256;
@@ -348,7 +354,8 @@ int fit_device(const int degree[3], const int nctrl[3], const std::vector<double
                                                     reinterpret_cast<int*>(P(off_last[a])),
                                                     reinterpret_cast<double*>(P(off_G[a])));
         k_fit_cholesky<<<1, 1, 0, st>>>(reinterpret_cast<double*>(P(off_G[a])), n, p,
-                                        reinterpret_cast<double*>(P(off_L[a])), status + a);
+                                        reinterpret_cast<double*>(P(off_L[a])),
+                                        reinterpret_cast<double*>(P(off_Linv[a])), status + a);
         e = cudaGetLastError();
     }
     int st_host[3] = { 0, 0, 0 };
@@ -369,20 +376,23 @@ int fit_device(const int degree[3], const int nctrl[3], const std::vector<double
         k_fit_lines<float><<<blocks(lines), kFitThreads, 0, st>>>(
             D, t1, lines, lines, 0, 1, lines, 0, 1, lines, nz, degree[2], reinterpret_cast<int*>(P(off_span[2])),
             reinterpret_cast<double*>(P(off_N[2])), reinterpret_cast<int*>(P(off_first[2])),
-            reinterpret_cast<int*>(P(off_last[2])), reinterpret_cast<double*>(P(off_L[2])));
+            reinterpret_cast<int*>(P(off_last[2])), reinterpret_cast<double*>(P(off_L[2])),
+            reinterpret_cast<double*>(P(off_Linv[2])));
         // y: lines (k, i), stride m_x
         lines = static_cast<long long>(nz) * mx;
         k_fit_lines<double><<<blocks(lines), kFitThreads, 0, st>>>(
             t1, t2, lines, mx, static_cast<long long>(my) * mx, 1, mx, static_cast<long long>(ny) * mx, 1, mx, ny,
             degree[1], reinterpret_cast<int*>(P(off_span[1])), reinterpret_cast<double*>(P(off_N[1])),
             reinterpret_cast<int*>(P(off_first[1])), reinterpret_cast<int*>(P(off_last[1])),
-            reinterpret_cast<double*>(P(off_L[1])));
+            reinterpret_cast<double*>(P(off_L[1])),
+            reinterpret_cast<double*>(P(off_Linv[1])));
         // x: lines (k, j), stride 1
         lines = static_cast<long long>(nz) * ny;
         k_fit_lines<double><<<blocks(lines), kFitThreads, 0, st>>>(
             t2, ctrl, lines, 1, mx, 0, 1, nx, 0, 1, nx, degree[0], reinterpret_cast<int*>(P(off_span[0])),
             reinterpret_cast<double*>(P(off_N[0])), reinterpret_cast<int*>(P(off_first[0])),
-            reinterpret_cast<int*>(P(off_last[0])), reinterpret_cast<double*>(P(off_L[0])));
+            reinterpret_cast<int*>(P(off_last[0])), reinterpret_cast<double*>(P(off_L[0])),
+            reinterpret_cast<double*>(P(off_Linv[0])));
         e = cudaGetLastError();
     }
     cudaError_t ef = cudaFreeAsync(w, st);
