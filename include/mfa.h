@@ -183,7 +183,9 @@ typedef struct {
                                          sample whose knot-span cell's value bound maps
                                          only to transfer-function rows of zero opacity is
                                          neither queried nor composited -- the image
-                                         equals 6's (4's) up to FP32 rounding order,
+                                         equals 6's (4's) up to FP32 rounding order
+                                         (which can move an early-termination decision
+                                         by one sample: (1 - ert_alpha) x alpha at most),
                                          samples_out counts the evaluated samples; a pass over the cells builds
                                          the per-render visibility bits (one bit per cell,
                                          from the staging pool).  Variants 1-6 differ only

@@ -92,3 +92,29 @@ def test_skip_edge_tables_and_fallback(mfa):
         i7, c7 = _render(mfa, mn, cam, _table("window"), 7)
         np.testing.assert_allclose(i7, i4, rtol=0, atol=1e-5)
         assert 0 < c7 < c4
+
+
+def test_skip_full_size_sampled(mfa, orc):
+    """The bench's empty-space row at full size -- the 128^3 model, 1024^2, 1024 samples, a
+    transfer function transparent below the median control point -- on 2048 seeded pixels
+    against the oracle, and against variant 6 on the whole image."""
+    import torch
+    wl = synth.config2(with_points=False)
+    spec, job = wl.model, wl.render
+    m = mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl)
+    ref = orc.Model.from_spec(spec)
+    lo, hi = float(spec.ctrl.min()), float(spec.ctrl.max())
+    table = synth.ramp_tf(256, 0.05).copy()
+    table[np.linspace(0.0, 1.0, len(table)) < (float(np.median(spec.ctrl)) - lo) / (hi - lo), 3] = 0.0
+    W, H, ns = job.width, job.height, job.n_samples
+    i6, c6 = _render(mfa, m, job.camera, table, 6, W, H, ns)
+    i7, c7 = _render(mfa, m, job.camera, table, 7, W, H, ns)
+    # alpha sums that differ in the last bit may cross the 0.99 termination threshold one
+    # sample apart: such a pixel moves by at most (1 - 0.99) x the table's largest alpha
+    d = np.abs(i7 - i6).max(axis=-1)
+    assert d.max() <= 0.01 * 0.05 * 1.2 and (d > 1e-5).mean() < 1e-3, (d.max(), (d > 1e-5).mean())
+    assert c7 < 0.5 * c6
+    pix = np.random.default_rng(77).choice(W * H, 2048, replace=False)
+    r, _ = orc.render(ref, job.camera, table, W, H, ns, shading=True, pixels=pix)
+    assert np.all(image_rmse(i7.reshape(-1, 4)[pix], r) <= IMAGE_RMSE_TOL)
+    assert r[:, 3].max() > 0.1
