@@ -475,6 +475,7 @@ def run_ours(args):
         line["encoding"] = encode_throughput(mfa, torch)
         line["render_quality"] = render_quality(mfa, torch)
         line["query_sweep"] = query_sweep(mfa, torch)
+        line["c3_precision"] = c3_precision(mfa, torch)
         line["empty_space"] = empty_space(mfa, torch, spec, model, job)
     if ws == 1 and not args.no_serve:
         line["serving"] = dict(run_serve(mfa, rates=args.serve_rates, duration=args.serve_duration),
@@ -646,6 +647,38 @@ def empty_space(mfa, torch, spec, model, job, frames=5):
         b.synchronize()
         out[f"variant{variant}"] = {"ms_per_frame": a.elapsed_time(b) / frames,
                                     "samples_per_frame": int(cnt.item()) / frames}
+    return out
+
+
+def c3_precision(mfa, torch, frames=3):
+    """The precision-sweep workload: degree 3, 512x512x256 control points on non-uniform
+    knots (turbulence), perspective 2048^2, 2048 samples per ray, Phong; one frame time and
+    sample rate per storage type (FP32, FP16, BF16 from the same FP64 values), default
+    kernel (variant 4: the record path)."""
+    import synth
+    wl = synth.config3(dtype_in=np.float64)
+    spec, job = wl.model, wl.render
+    W, H, NS = job.width, job.height, job.n_samples
+    tf = mfa.transfer_fn(job.tf, shading=True)
+    img = torch.empty((H, W, 4), device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    out = {"model": "degree 3, 512x512x256, non-uniform knots, turbulence", "image": f"{W}x{H}", "n_samples": NS}
+    for storage, name in ((mfa.MFA_F32, "f32"), (mfa.MFA_F16, "f16"), (mfa.MFA_BF16, "bf16")):
+        m = mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl, storage=storage)
+        mfa.render(m, job.camera, tf, W, H, NS, out=img)
+        torch.cuda.synchronize()
+        cnt.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(frames):
+            mfa.render(m, job.camera, tf, W, H, NS, out=img, samples_out=cnt)
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b) / frames
+        samples = int(cnt.item()) / frames
+        out[name] = {"ms_per_frame": ms, "samples_per_s": samples / (ms / 1e3),
+                     "model_bytes": m.info()["device_bytes"]}
+        m.close()
     return out
 
 
