@@ -476,6 +476,7 @@ def run_ours(args):
         line["render_quality"] = render_quality(mfa, torch)
         line["query_sweep"] = query_sweep(mfa, torch)
         line["c3_precision"] = c3_precision(mfa, torch)
+        line["batch"] = batch_throughput(mfa, torch)
         line["empty_space"] = empty_space(mfa, torch, spec, model, job)
     if ws == 1 and not args.no_serve:
         line["serving"] = dict(run_serve(mfa, rates=args.serve_rates, duration=args.serve_duration),
@@ -648,6 +649,45 @@ def empty_space(mfa, torch, spec, model, job, frames=5):
         out[f"variant{variant}"] = {"ms_per_frame": a.elapsed_time(b) / frames,
                                     "samples_per_frame": int(cnt.item()) / frames}
     return out
+
+
+def batch_throughput(mfa, torch, reps=3):
+    """The batched workload: 16 models (degrees 2, 3, 4; uniform and non-uniform knots;
+    32..256 control points per axis), one image each (256^2..1024^2, 256..1024 samples):
+    one CUDA-graph launch of the persistent batch kernels (tile shape from the batch
+    autotuner) against the 16 images rendered one launch after another."""
+    import synth
+    pairs = synth.config4()
+    models = [mfa.Model(sp.degree, sp.nctrl, sp.knots, sp.ctrl) for sp, _ in pairs]
+    tfs = [mfa.transfer_fn(job.tf, shading=True) for _, job in pairs]
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    reqs = [mfa.Request(m, job.camera, tf, job.width, job.height, job.n_samples, samples_out=cnt)
+            for m, tf, (_, job) in zip(models, tfs, pairs)]
+    batch = mfa.Batch(len(reqs))
+    tuned = mfa.tune_batch(batch, reqs)
+    batch.configure(tile_shape=tuned["tile_shape"])
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        cnt.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / reps, int(cnt.item()) / reps
+
+    ms_batch, samples = timed(lambda: batch.render(reqs))
+    ms_single, _ = timed(lambda: [mfa.render(q.model, q.cam, q.tf, q.width, q.height, q.n_samples, out=q.out,
+                                             samples_out=cnt) for q in reqs])
+    batch.close()
+    for m in models:
+        m.close()
+    return {"requests": len(reqs), "tile_shape": tuned["tile_shape"], "ms_per_batch": ms_batch,
+            "samples_per_batch": samples, "samples_per_s": samples / (ms_batch / 1e3),
+            "ms_separate_launches": ms_single}
 
 
 def c3_precision(mfa, torch, frames=3):
