@@ -285,6 +285,17 @@ def test_render_edge_cases(mfa, orc):
         g, r, gc, rc = _render_both(mfa, orc, model, ref, job)
         np.testing.assert_allclose(g, r, atol=1e-4)
         assert gc == rc
+    # the largest image side and the largest sample count the API accepts
+    wide = synth.RenderJob(cam, 32768, 1, 8, synth.ramp_tf(64, 0.3), True)
+    g, r, gc, rc = _render_both(mfa, orc, model, ref, wide, pixels=np.arange(0, 32768, 97))
+    assert np.all(image_rmse(g, r) <= IMAGE_RMSE_TOL)
+    # (early termination on: with it off, FP32 alpha sums over 2^20 samples of opacity 1e-4
+    # lose the increments below half an ulp of the sum -- a limit of FP32 compositing; near
+    # the threshold each sample adds ~1e-6, so the FP32 and FP64 sums may cross it a few
+    # thousand samples apart, which moves the image by far less than the gate)
+    deep = synth.RenderJob(cam, 2, 2, 1 << 20, synth.ramp_tf(64, 1e-4), True)
+    g, r, gc, rc = _render_both(mfa, orc, model, ref, deep)
+    assert np.all(image_rmse(g, r) <= IMAGE_RMSE_TOL) and abs(gc - rc) <= 0.05 * rc and rc > 40000
     # rejected arguments leave the output untouched
     out = torch.full((4, 4, 4), 7.0, device="cuda")
     with pytest.raises(mfa.MfaError):
@@ -292,7 +303,7 @@ def test_render_edge_cases(mfa, orc):
     assert float(out.min()) == 7.0
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("degree", [(3, 3, 3), (2, 3, 4), (4, 4, 4)])
 def test_render_variants_match_oracle(mfa, orc, variant, degree):
     """Every kernel variant (support cached / records cached / nothing cached) against the
