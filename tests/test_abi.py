@@ -90,6 +90,14 @@ def test_host_side_argument_checks(libmfa):
     assert "aligned" in L.mfa_last_error().decode()
     assert L.mfa_image_compare(0x1000, 0x2000, 10, 16, ctypes.byref(q)) == -1
     assert "11..32768" in L.mfa_last_error().decode()
+    # render options are checked before anything else: variants 0..7, tile shapes 0..3
+    opts = mfa._Opts()
+    opts.variant = 8
+    assert L.mfa_render_ex(None, ctypes.byref(cam), ctypes.byref(tf.struct), 8, 8, 8, None, ctypes.byref(opts)) == -1
+    assert "0..7" in L.mfa_last_error().decode()
+    opts.variant, opts.tile_shape = 7, 4
+    assert L.mfa_render_ex(None, ctypes.byref(cam), ctypes.byref(tf.struct), 8, 8, 8, None, ctypes.byref(opts)) == -1
+    assert "tile_shape" in L.mfa_last_error().decode()
     # checkpoint calls check their arguments and the file before any device work
     assert L.mfa_model_get_ctrl(None, None) == -1
     assert L.mfa_model_save(None, b"/nonexistent/x.mfa") == -1
