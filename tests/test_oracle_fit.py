@@ -82,3 +82,33 @@ def test_data_parameters_and_collocation_rows():
     np.testing.assert_allclose(A.sum(axis=1), 1.0, atol=1e-15)        # partition of unity per row
     assert A[0, 0] == 1.0 and A[-1, -1] == 1.0                         # clamped ends interpolate
     assert (np.count_nonzero(A, axis=1) <= 3).all()                    # p + 1 functions per row
+
+
+def test_clamped_uniform_knots():
+    # the textbook clamped uniform vector: p + 1 zeros, interior knots i / (n - p), p + 1 ones
+    np.testing.assert_array_equal(of.clamped_uniform(7, 3), [0, 0, 0, 0, 0.25, 0.5, 0.75, 1, 1, 1, 1])
+    np.testing.assert_array_equal(of.clamped_uniform(3, 2), [0, 0, 0, 1, 1, 1])
+
+
+def test_adaptive_inserts_only_where_the_error_exceeds_the_bound():
+    # f(x) = (1/4 - x)^3 left of 1/4, 0 right of it: C2 at 1/4, so a cubic spline with knots
+    # {1/4, 1/2} reproduces it exactly.  The first refinement splits [0, 1] at 1/2; then only
+    # the left span exceeds the bound and gets its midpoint 1/4 -- the right span does not.
+    m = (65, 5, 4)
+    x = of.grid_params(m[0])
+    fx = np.where(x < 0.25, (0.25 - x) ** 3, 0.0)
+    D = np.broadcast_to(fx[None, None, :], (m[2], m[1], m[0])).copy()
+    knots, P, hist = of.encode((3, 1, 1), D, 1e-3)
+    kx = knots[0]
+    np.testing.assert_allclose(kx[(kx > 0) & (kx < 1)], [0.25, 0.5])
+    assert hist[-1][0] <= 1e-12
+
+
+def test_adaptive_stops_at_the_first_fit_within_the_bound():
+    m = (96, 5, 4)
+    x = of.grid_params(m[0])
+    D = np.broadcast_to(np.exp(-((x - 0.2) / 0.04) ** 2)[None, None, :], (m[2], m[1], m[0])).copy()
+    err_max = 0.025
+    _, _, hist = of.encode((3, 1, 1), D, err_max)
+    assert all(h[0] > err_max for h in hist[:-1]) and hist[-1][0] <= err_max
+    assert len(hist) >= 4
