@@ -395,7 +395,9 @@ int mfa_tune_render(const mfa_model* model, const mfa_camera* camera, const mfa_
 int mfa_tune_batch(mfa_batch* batch, const mfa_render_request* reqs, int n, int reps, mfa_tune_result* best);
 /* The stored choice for a workload's class; MFA_ERR_ARG if there is none. */
 int mfa_tune_lookup(const mfa_model* model, int width, int height, int n_samples, mfa_tune_result* out);
-/* Writes / reads the stored choices (one text line per class). */
+/* Writes / reads the stored choices (one text line per class).  With the environment
+ * variable MFA_TUNE_CACHE naming a file, the choices in it are read on the first use of the
+ * stored choices (a missing file reads as none), and every mfa_tune_render rewrites it. */
 int mfa_tune_save(const char* path);
 int mfa_tune_load(const char* path);
 

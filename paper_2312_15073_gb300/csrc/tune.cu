@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -25,6 +26,56 @@ using Key = std::tuple<int, int, int, int, int, int>;
 
 std::mutex g_mu;
 std::map<Key, mfa_tune_result> g_cache;
+bool g_env_read = false;   // MFA_TUNE_CACHE consulted (first use of the cache)
+
+// Reads the choices in `path` into the cache (g_mu held); returns how many were read, or
+// -1 if the file cannot be opened.
+int read_cache_file(const char* path)
+{
+    FILE* f = std::fopen(path, "r");
+    if (!f) return -1;
+    char line[256];
+    int loaded = 0;
+    while (std::fgets(line, sizeof line, f)) {
+        if (line[0] == '#') continue;
+        int q, s, pb, sb, u, nb, v, t;
+        float ms;
+        if (std::sscanf(line, "%d %d %d %d %d %d %d %d %f", &q, &s, &pb, &sb, &u, &nb, &v, &t, &ms) != 9) continue;
+        if (v < 1 || v > 7 || t < 0 || t >= kTileShapes) continue;
+        g_cache[Key(q, s, pb, sb, u, nb)] = mfa_tune_result{ v, t, ms };
+        ++loaded;
+    }
+    std::fclose(f);
+    return loaded;
+}
+
+// Writes the cache to `path` (g_mu held); false if the file cannot be written.
+bool write_cache_file(const char* path)
+{
+    FILE* f = std::fopen(path, "w");
+    if (!f) return false;
+    std::fprintf(f, "# q storage pixel_bucket sample_bucket uniform size_bucket variant tile_shape ms\n");
+    for (const auto& kv : g_cache)
+        std::fprintf(f, "%d %d %d %d %d %d %d %d %.6f\n", std::get<0>(kv.first), std::get<1>(kv.first),
+                     std::get<2>(kv.first), std::get<3>(kv.first), std::get<4>(kv.first), std::get<5>(kv.first),
+                     kv.second.variant, kv.second.tile_shape, kv.second.ms);
+    return std::fclose(f) == 0;
+}
+
+// The environment's persistent cache: MFA_TUNE_CACHE names a file whose choices are read
+// on the first use of the cache (a missing file is an empty cache) and which every tuning
+// run rewrites.  (g_mu held.)
+const char* env_cache_path()
+{
+    const char* p = std::getenv("MFA_TUNE_CACHE");
+    return p && *p ? p : nullptr;
+}
+void read_env_cache()
+{
+    if (g_env_read) return;
+    g_env_read = true;
+    if (const char* p = env_cache_path()) read_cache_file(p);
+}
 
 int log_bucket(double x, double base) { return x <= 1.0 ? 0 : static_cast<int>(std::floor(std::log(x) / std::log(base))); }
 
@@ -44,6 +95,7 @@ namespace mfa {
 bool tuned_lookup(const mfa_model* m, int w, int h, int ns, int* variant, int* shape)
 {
     std::lock_guard<std::mutex> g(g_mu);
+    read_env_cache();
     auto it = g_cache.find(key_of(m, w, h, ns));
     if (it == g_cache.end()) return false;
     *variant = it->second.variant;
@@ -103,7 +155,10 @@ int mfa_tune_render(const mfa_model* m, const mfa_camera* cam, const mfa_transfe
     if (n_all) *n_all = count;
     *best = top;
     std::lock_guard<std::mutex> g(g_mu);
+    read_env_cache();
     g_cache[key_of(m, width, height, n_samples)] = top;
+    if (const char* p = env_cache_path())
+        if (!write_cache_file(p)) return fail(MFA_ERR_ARG, "cannot write MFA_TUNE_CACHE file %s", p);
     return MFA_OK;
 }
 
@@ -143,6 +198,7 @@ int mfa_tune_lookup(const mfa_model* m, int width, int height, int n_samples, mf
 {
     if (!m || !out) return fail(MFA_ERR_ARG, "model and out must be non-NULL");
     std::lock_guard<std::mutex> g(g_mu);
+    read_env_cache();
     auto it = g_cache.find(key_of(m, width, height, n_samples));
     if (it == g_cache.end()) return fail(MFA_ERR_ARG, "no tuned choice for this workload class");
     *out = it->second;
@@ -152,36 +208,18 @@ int mfa_tune_lookup(const mfa_model* m, int width, int height, int n_samples, mf
 int mfa_tune_save(const char* path)
 {
     if (!path) return fail(MFA_ERR_ARG, "path is NULL");
-    FILE* f = std::fopen(path, "w");
-    if (!f) return fail(MFA_ERR_ARG, "cannot write %s", path);
     std::lock_guard<std::mutex> g(g_mu);
-    std::fprintf(f, "# q storage pixel_bucket sample_bucket uniform size_bucket variant tile_shape ms\n");
-    for (const auto& kv : g_cache)
-        std::fprintf(f, "%d %d %d %d %d %d %d %d %.6f\n", std::get<0>(kv.first), std::get<1>(kv.first),
-                     std::get<2>(kv.first), std::get<3>(kv.first), std::get<4>(kv.first), std::get<5>(kv.first),
-                     kv.second.variant, kv.second.tile_shape, kv.second.ms);
-    std::fclose(f);
-    return MFA_OK;
+    read_env_cache();
+    return write_cache_file(path) ? MFA_OK : fail(MFA_ERR_ARG, "cannot write %s", path);
 }
 
 int mfa_tune_load(const char* path)
 {
     if (!path) return fail(MFA_ERR_ARG, "path is NULL");
-    FILE* f = std::fopen(path, "r");
-    if (!f) return fail(MFA_ERR_ARG, "cannot read %s", path);
-    char line[256];
-    int loaded = 0;
     std::lock_guard<std::mutex> g(g_mu);
-    while (std::fgets(line, sizeof line, f)) {
-        if (line[0] == '#') continue;
-        int q, s, pb, sb, u, nb, v, t;
-        float ms;
-        if (std::sscanf(line, "%d %d %d %d %d %d %d %d %f", &q, &s, &pb, &sb, &u, &nb, &v, &t, &ms) != 9) continue;
-        if (v < 1 || v > 7 || t < 0 || t >= kTileShapes) continue;
-        g_cache[Key(q, s, pb, sb, u, nb)] = mfa_tune_result{ v, t, ms };
-        ++loaded;
-    }
-    std::fclose(f);
+    read_env_cache();
+    const int loaded = read_cache_file(path);
+    if (loaded < 0) return fail(MFA_ERR_ARG, "cannot read %s", path);
     return loaded > 0 ? MFA_OK : fail(MFA_ERR_ARG, "no tuning entries in %s", path);
 }
 

@@ -161,3 +161,23 @@ def test_tune_cache_file_errors(libmfa, tmp_path):
     out = tmp_path / "out.txt"
     assert libmfa.mfa_tune_save(str(out).encode()) == 0
     assert "4 1 10 10 1 7 2 3" in out.read_text()
+
+
+def test_tune_cache_from_the_environment(libmfa, tmp_path):
+    """MFA_TUNE_CACHE: the named file's choices are read on the first use of the cache (a
+    fresh process; no GPU needed to read and write the cache)."""
+    import subprocess
+    import sys
+    cache = tmp_path / "tune.txt"
+    cache.write_text("# q storage pixel_bucket sample_bucket uniform size_bucket variant tile_shape ms\n"
+                     "3 2 9 9 0 8 7 1 2.5\n")
+    out = tmp_path / "out.txt"
+    code = ("import ctypes, sys; L = ctypes.CDLL(sys.argv[1]); "
+            "sys.exit(L.mfa_tune_save(sys.argv[2].encode()))")
+    env = dict(os.environ, MFA_TUNE_CACHE=str(cache))
+    r = subprocess.run([sys.executable, "-c", code, libmfa._name, str(out)], env=env, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert "3 2 9 9 0 8 7 1" in out.read_text()
+    env["MFA_TUNE_CACHE"] = str(tmp_path / "missing.txt")          # a missing file is an empty cache
+    r = subprocess.run([sys.executable, "-c", code, libmfa._name, str(out)], env=env, capture_output=True, text=True)
+    assert r.returncode == 0 and "3 2 9 9" not in out.read_text()
