@@ -40,8 +40,18 @@ sys.path.insert(0, ROOT)
 METRIC = "MFA samples/s (value+grad) & frames/s at 1024^2; p50/p99 frame latency vs plain FP32"
 UNIT = "samples/s"
 WORKLOAD = "mfa_p3_128cube_f32: persp 1024x1024, 1024 samples/ray, Phong, ERT 0.99 + decode 2^24 pts"
-SMS = 152
-FP32_LANES = 128
+FP32_LANES = 128          # FP32 lanes per SM (sm_100 family)
+DEFAULT_SM_MAX_MHZ = 2070.0
+
+
+def device_sms(torch) -> int:
+    """Streaming multiprocessors of the current device (cudaDeviceProp)."""
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
+def fp32_peak_tflops(sms: int, mhz: float) -> float:
+    """FP32 FMA peak: SMs x 128 lanes x 2 flops x clock."""
+    return sms * FP32_LANES * 2 * mhz * 1e6 / 1e12
 
 # Algorithmic FP32 flops per value+grad query at degree p (q = p + 1):
 #   contraction (sum-factorised)       2 (2q^3 + 3q^2 + 4q)
@@ -61,9 +71,9 @@ RENDER_EXTRA_FLOPS = 40
 # p = 2, one entry's layer pair and third-layer row (32 + 16 bytes)
 DECODE_WINDOW_BYTES = {1: 1 * 2 * 16, 2: 1 * 3 * 48, 3: 2 * 4 * 32, 4: 3 * 5 * 48}
 
-# DRAM bytes (read + write) of one k_render launch on this workload, from the ncu capture
-# summarised in profiles/k_render_p3_128cube_persp1024_ns1024.md, valid only for the kernel
-# sources it was taken on (their SHA-256 is checked at run time; any change -> null).
+# DRAM bytes (read + write) of one k_render launch on this workload, measured by an ncu
+# capture of the frame (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
+# kernel sources it was taken on (their SHA-256 is checked at run time; any change -> null).
 RENDER_TRAFFIC = {"src_sha256": "5ec5df64696fcacc14aead3d96b7776bb26a829406586a0c160c40c537378ad5",
                   "bytes_per_launch": 16107008}
 KERNEL_SOURCES = ["paper_2312_15073_gb300/csrc/render.cu", "paper_2312_15073_gb300/csrc/raycast.cuh",
@@ -413,7 +423,9 @@ def run_ours(args):
     flops_sample = query_flops(p) + RENDER_EXTRA_FLOPS
     achieved_tflops = samples_per_frame * flops_sample / render_s / 1e12
     clk = clocks.summary()
-    peak_tflops = SMS * FP32_LANES * 2 * 2070e6 / 1e12
+    sms = device_sms(torch)
+    sm_max_mhz = clk["sm_max_mhz"] or _peaks().get("sm_max_mhz") or DEFAULT_SM_MAX_MHZ
+    peak_tflops = fp32_peak_tflops(sms, sm_max_mhz)
     sorted_ms = sorted(render_ms)
 
     def pct(q):
@@ -442,8 +454,9 @@ def run_ours(args):
                      "flops_note": "algorithmic count (sum-factorised contraction + span-local Cox-de Boor "
                                    "basis and derivative + chain rule, + TF/Phong/over); on uniform knots the "
                                    "cardinal path executes 42 instead of 126 basis flops per sample",
-                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
-                     "peak_at_median_clock": (SMS * FP32_LANES * 2 * clk["sm_mhz"] * 1e6 / 1e12)
+                     "peak_basis": f"{sms} SMs (cudaDeviceProp) x {FP32_LANES} FP32 lanes x 2 flop x "
+                                   f"{sm_max_mhz:.0f} MHz (max SM clock, nvidia-smi)",
+                     "peak_at_median_clock": fp32_peak_tflops(sms, clk["sm_mhz"])
                      if clk["sm_mhz"] else None,
                      "measured_fma": {"tflops": peaks["fp32_tflops"], "fp32x2_tflops": peaks["fp32x2_tflops"],
                                       "clock_mhz": peaks["fma_clock_mhz"],
@@ -471,7 +484,7 @@ def run_ours(args):
         line["precision"] = storage_throughput(mfa, torch, spec, job, tf)
         line["segments"] = segments_throughput(mfa, torch, model, job, tf, render_s)
         line["isosurface"] = iso_throughput(mfa, torch, spec, model, job, tf)
-        line["marschner_lobb"] = ml_throughput(mfa, torch, tf)
+        line["marschner_lobb"] = ml_throughput(mfa, torch, tf, peak_tflops)
         line["encoding"] = encode_throughput(mfa, torch)
         line["render_quality"] = render_quality(mfa, torch)
         line["query_sweep"] = query_sweep(mfa, torch)
@@ -529,7 +542,7 @@ def segments_throughput(mfa, torch, model, job, tf, single_s, frames=5):
     return out
 
 
-def ml_throughput(mfa, torch, tf, frames=5):
+def ml_throughput(mfa, torch, tf, peak_tflops, frames=5):
     """The paper's scalability workload shape on the Marschner-Lobb signal: degree 2, 256^3
     control points (Greville-sampled), 768^2, 1024 samples per ray, Phong."""
     import synth
@@ -556,7 +569,7 @@ def ml_throughput(mfa, torch, tf, frames=5):
     model.close()
     return {"model": "Marschner-Lobb, degree 2, 256^3 control points", "image": "768x768", "n_samples": NS,
             "tuned": tuned, "ms_per_frame": ms, "samples_per_frame": samples, "samples_per_s": samples / (ms / 1e3),
-            "frac_fp32_peak": flops / (ms / 1e3) / 1e12 / (SMS * FP32_LANES * 2 * 2070e6 / 1e12)}
+            "frac_fp32_peak": flops / (ms / 1e3) / 1e12 / peak_tflops}
 
 
 def encode_throughput(mfa, torch):

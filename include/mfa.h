@@ -136,10 +136,12 @@ int mfa_set_stream(void* cuda_stream);
 int mfa_decode(const mfa_model* model, const float* pts, long long n, float* val, float* grad);
 
 /*
- * Knot spans of n points, as the query above finds them: spans[3i + d] = the largest s
- * in [degree_d, nctrl_d - 1] with U_d[s] <= u_d after clamping (a coordinate on an interior
- * knot goes to the span on its right; u = 1 goes to the last span).  The comparison is
- * exact against the FP64 knots.
+ * Knot spans of n points, computed by the same device code mfa_decode runs for this model
+ * (the span search on general knots; on the uniform-knot path, floor((n - p) u) with its
+ * exact check against the knots): spans[3i + d] = the largest s in [degree_d, nctrl_d - 1]
+ * with U_d[s] <= u_d after clamping (a coordinate on an interior knot goes to the span on
+ * its right; u = 1 goes to the last span).  The comparison is exact against the FP64
+ * knots (Sec. III-A, Sec. III-B).
  *   pts    DEVICE, n * 3 FP32.   spans  DEVICE, n * 3 int32.
  */
 int mfa_locate_spans(const mfa_model* model, const float* pts, long long n, int* spans);
@@ -474,12 +476,17 @@ void mfa_server_destroy(mfa_server* server);
  * Every GPU that loads the library holds that array until the process exits.
  *   reqs, n  as mfa_batch_render; n in 0..32, MFA_ERR_ARG beyond (nothing launched).
  * Asynchronous on the bound stream; it makes no allocation (no cudaMalloc, cudaFree or
- * cudaMallocHost).  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before any stream
- * capture.  All calls share the one array, which keeps the previous call's contents
- * (each call rewrites everything the kernels read, tile counters included): calls whose
- * work overlaps on the GPU -- on different streams, or from different threads -- race and
- * must be serialised by the caller.
+ * cudaMallocHost).  The work table is filled by host-to-device copies from this call's
+ * own memory, so the call cannot be recorded into a CUDA graph: on a stream that is being
+ * captured it returns MFA_ERR_UNSUPPORTED and enqueues nothing (the capture stays valid).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; with lazy module loading that first call also loads the
+ * library's device code, which places the array and the kernels in device memory, so make
+ * it before the caller's own pool reserves the rest of the device.  All calls share the
+ * one array, which keeps the previous call's contents (each call rewrites everything the
+ * kernels read, tile counters included): calls whose work overlaps on the GPU -- on
+ * different streams, or from different threads -- race and must be serialised by the
+ * caller.
  */
 int mfa_render_batch_static(const mfa_render_request* reqs, int n);
 

@@ -610,24 +610,56 @@ __device__ __forceinline__ float4 query2(const ModelDev& M, float u, float v, fl
 // queries on the cardinal path (ModelDev::cardinal: uniform knots, degree Q-1 on every axis)
 // ----------------------------------------------------------------------------------------
 //
-// Coordinates are taken in span units x = (n - p) u: the span is j = floor(x), clamped to
-// 0..n-p-1, and its local coordinate is t = x - j (exact in FP32 for x >= 0).  Spans at
-// least p-1 from both ends use cardinal_basis; the p-1 end spans on each side, whose
-// functions see the repeated end knots, evaluate their record at the same t (uniform
-// spacing makes the record's local coordinate equal to x - j) and rescale to M, G.
+// Coordinates are taken in span units x = (n - p) u.  A query at a given parameter u takes
+// the exact span of u (cardinal_span: floor(x) checked against the knots); a ray march,
+// whose samples are positioned in span units directly, takes floor(x), the span of its
+// position x / (n - p).  Either way the span index j is clamped to 0..n-p-1 and the local
+// coordinate is t = x - j (exact in FP32).  Spans at least p-1 from both ends use
+// cardinal_basis; the p-1 end spans on each side, whose functions see the repeated end
+// knots, evaluate their record at the same t (uniform spacing makes the record's local
+// coordinate equal to x - j) and rescale to M, G.
 struct CardAxis {
     float jf;    // span index as a float: t = x - jf
     int j;       // span index, 0..n-p-1
     bool edge;   // one of the p-1 end spans: evaluate from its record
 };
 
-__device__ __forceinline__ void card_update(const AxisDev& A, CardAxis& C, float x)
+__device__ __forceinline__ void card_set(const AxisDev& A, CardAxis& C, int j)
 {
-    const int m = A.n - A.p;
-    const int j = min(max(__float2int_rd(x), 0), m - 1);   // positions just outside the box clamp
     C.j = j;
     C.jf = static_cast<float>(j);
-    C.edge = j < A.p - 1 || j > m - A.p;
+    C.edge = j < A.p - 1 || j > A.n - 2 * A.p;
+}
+
+// Ray marches (span-unit positions x, no parameter u): the span is floor(x), clamped so
+// that positions just outside the box take the end spans.
+__device__ __forceinline__ void card_update(const AxisDev& A, CardAxis& C, float x)
+{
+    card_set(A, C, min(max(__float2int_rd(x), 0), A.n - A.p - 1));
+}
+
+// Span-unit coordinate of a clamped FP32 parameter u (one FP32 multiply).
+__device__ __forceinline__ float cardinal_coord(const AxisDev& A, float u)
+{
+    return u * static_cast<float>(A.n - A.p);
+}
+
+// Knot span of a clamped FP32 parameter u on the cardinal path, as j = s - p: the largest
+// s with U_s <= u, exactly as locate_span finds it.  x = cardinal_coord(u) is the product
+// (n - p) u rounded to FP32, so floor(x) can sit one span off when the rounding carries x
+// onto or across an integer (u within an ulp of a knot, e.g. u = fl32(0.04) just below
+// the knot 5/125 while x rounds to 5.0).  floor(x) is never more than one span away, so
+// one exact comparison on each side against the knots rounded up to FP32 (u >= kup[s]
+// iff u >= U_s) settles it.  The local coordinate x - j then lies in [-ulp, 1].
+__device__ __forceinline__ int cardinal_span(const AxisDev& A, float u, float x)
+{
+    const int m = A.n - A.p;
+    int j = min(max(__float2int_rd(x), 0), m - 1);
+    if (j > 0 && u < __ldg(A.kup + A.p + j))
+        --j;
+    else if (j < m - 1 && u >= __ldg(A.kup + A.p + j + 1))
+        ++j;
+    return j;
 }
 
 // Scaled basis (M = p! N, G = (p-1)! dN/dt) on the axis's current span.
@@ -648,17 +680,18 @@ __device__ __forceinline__ void card_basis(const AxisDev& A, const CardAxis& C, 
     }
 }
 
-// Value and parameter-space gradient at a clamped point on the cardinal path.
+// Value and parameter-space gradient at a clamped point on the cardinal path (spans exact,
+// as cardinal_span finds them).
 template <int Q, int STORAGE>
 __device__ __forceinline__ float4 query_cardinal(const ModelDev& M, float u, float v, float w)
 {
-    const float x = u * static_cast<float>(M.ax[0].n - M.ax[0].p);
-    const float y = v * static_cast<float>(M.ax[1].n - M.ax[1].p);
-    const float z = w * static_cast<float>(M.ax[2].n - M.ax[2].p);
+    const float x = cardinal_coord(M.ax[0], u);
+    const float y = cardinal_coord(M.ax[1], v);
+    const float z = cardinal_coord(M.ax[2], w);
     CardAxis cx, cy, cz;
-    card_update(M.ax[0], cx, x);
-    card_update(M.ax[1], cy, y);
-    card_update(M.ax[2], cz, z);
+    card_set(M.ax[0], cx, cardinal_span(M.ax[0], u, x));
+    card_set(M.ax[1], cy, cardinal_span(M.ax[1], v, y));
+    card_set(M.ax[2], cz, cardinal_span(M.ax[2], w, z));
     float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];
     card_basis<Q>(M.ax[0], cx, x - cx.jf, Nx, Dx);
     card_basis<Q>(M.ax[1], cy, y - cy.jf, Ny, Dy);

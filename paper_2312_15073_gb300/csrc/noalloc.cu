@@ -25,10 +25,10 @@ using namespace mfa;
 namespace {
 
 constexpr int kStaticMaxRequests = 32;
-// heads + 32 items + 32 full tables, rounded up
+// heads + 32 items, rounded up to 256 bytes where the table rows start, + 32 full tables
 constexpr size_t kStaticTableBytes = 176 * 1024;
-static_assert(kBatchItemsOffset + sizeof(BatchItem) * kStaticMaxRequests + sizeof(float4) * kTfMax * kStaticMaxRequests <=
-                  kStaticTableBytes,
+constexpr size_t kStaticRowsOffset = (kBatchItemsOffset + sizeof(BatchItem) * kStaticMaxRequests + 255) / 256 * 256;
+static_assert(kStaticRowsOffset + sizeof(float4) * kTfMax * kStaticMaxRequests <= kStaticTableBytes,
               "static work table too small");
 
 static __device__ __align__(256) unsigned char g_static_table[kStaticTableBytes];
@@ -61,32 +61,47 @@ extern "C" int mfa_render_batch_static(const mfa_render_request* reqs, int n)
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "current device");
     if (dev < 0 || dev >= kMaxDevices) return fail(MFA_ERR_UNSUPPORTED, "device ordinal %d >= %d", dev, kMaxDevices);
+    // The table is filled by copies from host memory owned by this call and its caller: a
+    // graph captured from them would replay copies from memory that is gone, so a capturing
+    // stream is refused before anything is enqueued (the capture stays valid).
+    cudaStream_t st = current_stream();
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) return cuda_fail(e, "stream capture status");
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(MFA_ERR_UNSUPPORTED, "the allocation-free batch cannot be captured into a CUDA graph");
 
-    // pass 1: validate everything and count each group's requests and tiles
+    // pass 1: validate everything, build every request's item (scalars, model, ray tiles)
+    // and count each group's requests and tiles
     int count[kBatchGroups] = {};
     long long tiles[kBatchGroups] = {};
-    RenderScalars S;
+    BatchItem items[kStaticMaxRequests];
+    int group_of[kStaticMaxRequests];
     float4 rows[kTfMax];
+    int tw, th;
+    render_tile_dims(0, &tw, &th);
     for (int r = 0; r < n; ++r) {
         const mfa_render_request& q = reqs[r];
         if (!q.model) return fail(MFA_ERR_ARG, "request %d: model is NULL", r);
+        BatchItem& it = items[r];
+        std::memset(&it, 0, sizeof it);
         if (int rc = setup_render(q.model, &q.camera, q.tf, q.width, q.height, q.n_samples, q.rgba_out, q.samples_out,
-                                  S, rows)) {
+                                  it.s, rows)) {
             fail(rc, "request %d: %s", r, mfa_last_error());
             return rc;
         }
-        int tw, th;
-        render_tile_dims(0, &tw, &th);
         const int g = batch_group(q.model->dev.q, q.model->storage, q.model->dev.cardinal);
+        group_of[r] = g;
+        it.m = q.model->dev;
+        it.tiles_x = (q.width + tw - 1) / tw;
+        it.tile_begin = static_cast<int>(tiles[g]);   // tiles of a group follow request order
         ++count[g];
-        tiles[g] += static_cast<long long>((q.width + tw - 1) / tw) * ((q.height + th - 1) / th);
+        tiles[g] += static_cast<long long>(it.tiles_x) * ((q.height + th - 1) / th);
         if (tiles[g] > (1LL << 30)) return fail(MFA_ERR_ARG, "batch too large: more than 2^30 ray tiles");
     }
 
     void* table = nullptr;
     if ((e = static_table(dev, &table)) != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static work table)");
     char* d = static_cast<char*>(table);
-    cudaStream_t st = current_stream();
 
     // heads: item offsets by group, tile counters cleared (the array keeps the last call's
     // contents, so everything the kernels read is rewritten here)
@@ -99,30 +114,23 @@ extern "C" int mfa_render_batch_static(const mfa_render_request* reqs, int n)
         heads[g].items_offset = static_cast<int>(off);
         off += sizeof(BatchItem) * count[g];
     }
-    const size_t tf_base = (off + 255) / 256 * 256;
+    const size_t tf_base = (off + 255) / 256 * 256;   // <= kStaticRowsOffset
     if ((e = cudaMemcpyAsync(d, heads, sizeof heads, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_fail(e, "static table heads");
 
-    // pass 2: items and table rows, each copied from the stack (a pageable source is staged
-    // before cudaMemcpyAsync returns, so the buffers can be reused at once)
+    // pass 2: items (from pass 1) and table rows (the caller's RGBA rows, already laid out
+    // as float4), copied from pageable host memory, which cudaMemcpyAsync stages before it
+    // returns, so none of it has to outlive the call
     int placed[kBatchGroups] = {};
-    long long next_tile[kBatchGroups] = {};
     for (int r = 0; r < n; ++r) {
         const mfa_render_request& q = reqs[r];
-        BatchItem it;
-        std::memset(&it, 0, sizeof it);
-        setup_render(q.model, &q.camera, q.tf, q.width, q.height, q.n_samples, q.rgba_out, q.samples_out, it.s, rows);
-        int tw, th;
-        render_tile_dims(0, &tw, &th);
-        const int g = batch_group(q.model->dev.q, q.model->storage, q.model->dev.cardinal);
-        it.m = q.model->dev;
-        it.tiles_x = (q.width + tw - 1) / tw;
-        it.tile_begin = static_cast<int>(next_tile[g]);
-        next_tile[g] += static_cast<long long>(it.tiles_x) * ((q.height + th - 1) / th);
+        BatchItem& it = items[r];
+        const int g = group_of[r];
         char* tf_dst = d + tf_base + sizeof(float4) * kTfMax * static_cast<size_t>(r);
         it.tf = reinterpret_cast<const float4*>(tf_dst);
         char* item_dst = d + heads[g].items_offset + sizeof(BatchItem) * placed[g]++;
-        if ((e = cudaMemcpyAsync(tf_dst, rows, sizeof(float4) * it.s.tf_n, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        if ((e = cudaMemcpyAsync(tf_dst, q.tf->rgba, sizeof(float4) * it.s.tf_n, cudaMemcpyHostToDevice, st)) !=
+                cudaSuccess ||
             (e = cudaMemcpyAsync(item_dst, &it, sizeof it, cudaMemcpyHostToDevice, st)) != cudaSuccess)
             return cuda_fail(e, "static table items");
     }

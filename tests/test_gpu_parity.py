@@ -160,6 +160,37 @@ def test_decode_full_size_128cube_2pow24(mfa, orc):
     assert ev <= VALUE_TOL and eg <= GRAD_TOL
 
 
+def test_cardinal_spans_at_every_knot_128cube(mfa, orc):
+    """The bench model (degree 3, 128^3, clamped uniform knots: the cardinal path) at the
+    FP32 values nearest every knot and their FP32 neighbours on each axis: the spans the
+    decode uses (mfa_locate_spans runs the same device code) equal the oracle's bit for bit,
+    and the values and gradients there meet the gates.  The points include cases where the
+    rounded product fl32((n - p) u) lands on the wrong side of an integer, so a span taken
+    from floor((n - p) u) alone would fail."""
+    import torch
+    wl = synth.config2(decode_n=1 << 10)
+    spec = wl.model
+    model = mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl)
+    assert model.info()["cardinal"]
+    ref = orc.Model.from_spec(spec)
+    rng = np.random.default_rng(_seed("cardinal-knots-128"))
+    pts = _edge_points(ref.knots, rng, 4096)
+    spans = mfa.locate_spans(model, torch.from_numpy(pts).cuda())
+    v, g = mfa.decode(model, torch.from_numpy(pts).cuda())
+    torch.cuda.synchronize()
+    vr, gr, sr = ref.decode(pts, spans=True)
+    np.testing.assert_array_equal(spans.cpu().numpy(), sr)
+    # the rounded product alone misplaces some of these points (so the check has teeth)
+    u = np.clip(np.nan_to_num(pts, nan=0.0), 0, 1).astype(np.float32)
+    naive = np.empty_like(sr)
+    for a in range(3):
+        m = spec.nctrl[a] - spec.degree[a]
+        naive[:, a] = np.clip(np.floor(u[:, a] * np.float32(m)), 0, m - 1).astype(np.int64) + spec.degree[a]
+    assert np.count_nonzero(naive != sr) > 0
+    ev, eg = value_error(v.cpu().numpy(), vr, ref.ctrl), grad_error(g.cpu().numpy(), gr)
+    assert ev <= VALUE_TOL and eg <= GRAD_TOL, (ev, eg)
+
+
 # ----------------------------------------------------------------------------------------
 # rendering
 # ----------------------------------------------------------------------------------------

@@ -21,11 +21,15 @@ pytestmark = pytest.mark.gpu
 
 def _requests(mfa, rng, n_req):
     import torch
-    specs = [((3, 3, 3), (20, 18, 22), 1), ((2, 2, 2), (14, 16, 12), 2), ((4, 4, 4), (12, 12, 13), 1),
-             ((3, 3, 3), (16, 24, 14), 3)]
+    # (degree, control points, storage, uniform knots): non-uniform knots take the record
+    # path, uniform knots with one degree the cardinal path (its own kernels and heads)
+    specs = [((3, 3, 3), (20, 18, 22), 1, False), ((2, 2, 2), (14, 16, 12), 2, False),
+             ((4, 4, 4), (12, 12, 13), 1, False), ((3, 3, 3), (16, 24, 14), 3, False),
+             ((3, 3, 3), (17, 21, 15), 1, True), ((2, 2, 2), (13, 11, 16), 2, True)]
     models = []
-    for deg, n, storage in specs:
-        knots = [synth.knots_nonuniform(n[a], deg[a], rng) for a in range(3)]
+    for deg, n, storage, uniform in specs:
+        knots = [synth.knots_uniform(n[a], deg[a]) if uniform else synth.knots_nonuniform(n[a], deg[a], rng)
+                 for a in range(3)]
         P = synth.sample_ctrl(synth.GaussianSum.draw(rng, 6), knots, deg, rng, 0.01)
         models.append(mfa.Model(deg, n, knots, P, storage=storage))
     reqs = []
@@ -45,8 +49,9 @@ def test_static_batch_matches_allocating_batch_twice():
     build.build()
     import paper_2312_15073_gb300 as mfa
     rng = np.random.default_rng(777)
-    for call, n_req in enumerate((11, 6)):          # two calls in a row, the second smaller
+    for call, n_req in enumerate((13, 7)):          # two calls in a row, the second smaller
         models, reqs = _requests(mfa, rng, n_req)
+        assert any(m.info()["cardinal"] for m in models) and not all(m.info()["cardinal"] for m in models)
         arr = mfa._request_array(reqs)
         mfa._bind_stream()
         rc = mfa.lib().mfa_render_batch_static(ctypes.addressof(arr), len(reqs))
@@ -78,3 +83,33 @@ def test_static_batch_rejects_oversize_without_launching():
     assert rc == -1 and "0..32" in mfa.lib().mfa_last_error().decode()
     torch.cuda.synchronize()
     assert all(float(q.out.min()) == 5.0 for q in reqs)
+
+
+def test_static_batch_refused_under_capture():
+    """Under stream capture the call returns MFA_ERR_UNSUPPORTED before enqueueing anything
+    (its table copies come from host memory that a replayed graph could not reach), and the
+    capture it was called in stays valid: the captured graph replays."""
+    import torch
+    import paper_2312_15073_gb300 as mfa
+    rng = np.random.default_rng(779)
+    models, reqs = _requests(mfa, rng, 3)
+    for q in reqs:
+        q.out.fill_(5.0)
+    arr = mfa._request_array(reqs)
+    x = torch.zeros(16, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        mfa._bind_stream()
+        with torch.cuda.graph(graph, stream=side):
+            rc = mfa.lib().mfa_render_batch_static(ctypes.addressof(arr), len(reqs))
+            x.add_(1.0)
+    torch.cuda.current_stream().wait_stream(side)
+    mfa._bind_stream()
+    assert rc == -6 and "captured" in mfa.lib().mfa_last_error().decode()
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert float(x.min()) == 2.0 and float(x.max()) == 2.0
+    assert all(float(q.out.min()) == 5.0 and float(q.out.max()) == 5.0 for q in reqs)
