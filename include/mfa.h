@@ -60,8 +60,9 @@ typedef struct mfa_model mfa_model;   /* opaque; owns all of its device memory *
  *   knots      knots[d] is a HOST array of nctrl[d] + degree[d] + 1 FP64 values,
  *              non-decreasing, clamped (the first degree+1 equal 0, the last degree+1
  *              equal 1).  knots == NULL or knots[d] == NULL selects the clamped uniform
- *              vector (interior knots i / (nctrl - degree)); knots within 1e-12 of it
- *              count as uniform (mfa_model_info.cardinal).
+ *              vector (interior knots i / (nctrl - degree)); caller's knots equal to
+ *              it in FP64 count as uniform (mfa_model_info.cardinal: with one degree on
+ *              all axes, the uniform-knot kernels apply).
  *   ctrl       HOST array of nctrl[0]*nctrl[1]*nctrl[2] values of type `dtype`,
  *              [n_z][n_y][n_x], x fastest.  Copied; the caller keeps ownership.
  *   dtype      type of ctrl.  Storage is FP32 for F64/F32 input, FP16 for F16, BF16 for

@@ -278,9 +278,10 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
     if (nxp * nyp * nzp >= (1LL << 31))
         return fail(MFA_ERR_UNSUPPORTED, "model too large: (nx+4)(ny+4)(nz+4) must stay below 2^31"), nullptr;
 
-    // knot vectors (host, FP64): caller's or clamped uniform.  Caller's knots within 1e-12
-    // of the clamped uniform ones count as uniform: the basis they give differs from the
-    // cardinal one far below FP32 resolution.
+    // knot vectors (host, FP64): caller's or clamped uniform.  Caller's knots count as
+    // uniform (the cardinal path) only when they equal the clamped uniform vector exactly,
+    // i/(n-p) correctly rounded to FP64: the exactness of the cardinal path's span (floor of
+    // the rounded product (n-p) u, checked only where it lands on an integer) rests on it.
     std::vector<double> U[3];
     bool uniform = true;
     for (int a = 0; a < 3; ++a) {
@@ -290,7 +291,7 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
             U[a][i] = i <= p ? 0.0 : (i >= n ? 1.0 : static_cast<double>(i - p) / static_cast<double>(n - p));
         if (knots && knots[a]) {
             for (int i = 0; i < m; ++i)
-                if (!(std::fabs(knots[a][i] - U[a][i]) <= 1e-12)) uniform = false;
+                if (!(knots[a][i] == U[a][i])) uniform = false;
             std::memcpy(U[a].data(), knots[a], sizeof(double) * m);
             if (!check_knots(U[a].data(), n, p, a)) return nullptr;
         }
@@ -327,12 +328,19 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
     const size_t win_elem = (storage == MFA_F32 ? 4 : 2) * window_values(Q);   // one window entry
     const size_t win_bytes = static_cast<size_t>(nxp * nyp * nzp) * win_elem;
     const size_t nctrl_total = static_cast<size_t>(nctrl[0]) * nctrl[1] * nctrl[2];
+    const size_t raw_bytes = nctrl_total * (storage == MFA_F32 ? 4 : 2);
+    const size_t off_raw = tab;   // the stored control points, plain array
+    tab = align_up(tab + raw_bytes, 256);
     const size_t in_bytes = nctrl_total * dtype_size(in_dtype);
     size_t knot_bytes = 0;
     for (int a = 0; a < 3; ++a) knot_bytes += sizeof(double) * U[a].size();
+    const bool pow_rows = power_rows(Q, storage);
+    // FP64 power coefficients of the x spans (power rows only), used while building the window
+    const size_t coef_bytes = pow_rows ? sizeof(double) * Q * Q * (nctrl[0] - degree[0]) : 0;
 
-    void* d_stage = nullptr;   // uploaded knots, stats and input control points; freed below
-    const size_t stage_bytes = align_up(knot_bytes, 256) + 256 + (ctrl_on_device ? 0 : in_bytes);
+    void* d_stage = nullptr;   // uploaded knots, stats, x coefficients and input control points; freed below
+    const size_t stage_bytes =
+        align_up(knot_bytes, 256) + 256 + align_up(coef_bytes, 256) + (ctrl_on_device ? 0 : in_bytes);
     cudaError_t e;
     auto cleanup = [&](int code, const char* what, cudaError_t err) -> mfa_model* {
         if (err != cudaSuccess) cuda_fail(err, what); else fail(code, "%s", what);
@@ -355,7 +363,9 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
         koff += sizeof(double) * U[a].size();
     }
     int* d_stats = reinterpret_cast<int*>(stage + align_up(knot_bytes, 256));
-    void* d_in = ctrl_on_device ? const_cast<void*>(ctrl) : stage + align_up(knot_bytes, 256) + 256;
+    double* d_coef = pow_rows ? reinterpret_cast<double*>(stage + align_up(knot_bytes, 256) + 256) : nullptr;
+    void* d_in = ctrl_on_device ? const_cast<void*>(ctrl)
+                                : stage + align_up(knot_bytes, 256) + 256 + align_up(coef_bytes, 256);
     if (!ctrl_on_device && (e = cudaMemcpyAsync(d_in, ctrl, in_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cleanup(0, "upload control points", e);
 
@@ -370,15 +380,19 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
         A.G = G[a];
         A.Gf = static_cast<float>(G[a]);
         if ((e = launch_prep_axis(d_knots[a], A.n, A.p, Q, const_cast<float*>(A.kup), const_cast<float*>(A.rec),
-                                  const_cast<int*>(A.grid), A.G, st)) != cudaSuccess)
+                                  const_cast<int*>(A.grid), A.G, a == 0 ? d_coef : nullptr, st)) != cudaSuccess)
             return cleanup(0, "span tables", e);
     }
-    if ((e = launch_prep_window(d_in, in_dtype, storage, nctrl[0], nctrl[1], nctrl[2], Q, M->d_win, st)) != cudaSuccess)
+    void* d_raw = tabs + off_raw;
+    if ((e = launch_prep_raw(d_in, in_dtype, storage, static_cast<long long>(nctrl_total), d_raw, st)) != cudaSuccess)
+        return cleanup(0, "stored control points", e);
+    if ((e = launch_prep_window(d_raw, storage, nctrl[0], nctrl[1], nctrl[2], Q, d_coef, degree[0], M->d_win, st)) !=
+        cudaSuccess)
         return cleanup(0, "window array", e);
-    if ((e = launch_prep_stats(M->d_win, storage, nctrl[0], nctrl[1], nctrl[2], Q, d_stats, st)) != cudaSuccess)
+    if ((e = launch_prep_stats(d_raw, storage, static_cast<long long>(nctrl_total), d_stats, st)) != cudaSuccess)
         return cleanup(0, "control-point statistics", e);
     float2* d_cell = reinterpret_cast<float2*>(tabs + off_cell);
-    if ((e = launch_prep_cells(M->d_win, storage, Q, degree, nctrl, d_cell, st)) != cudaSuccess)
+    if ((e = launch_prep_cells(d_raw, storage, degree, nctrl, d_cell, st)) != cudaSuccess)
         return cleanup(0, "cell bounds", e);
     int stats[3];
     if ((e = cudaMemcpyAsync(stats, d_stats, sizeof stats, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -397,6 +411,7 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
     M->vmax = ord2f(stats[1]);
     M->maxabs = ord2f(stats[2]);
     M->dev.win = M->d_win;
+    M->dev.raw = d_raw;
     M->dev.nxp = static_cast<int>(nxp);
     M->dev.nyp = static_cast<int>(nyp);
     M->dev.nzp = static_cast<int>(nzp);

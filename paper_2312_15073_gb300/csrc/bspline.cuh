@@ -177,17 +177,28 @@ __device__ __forceinline__ void span_basis(const AxisDev& A, int s, float u, flo
 //   N^k_r = ((t + k - r) N^{k-1}_{r-1} + (r + 1 - t) N^{k-1}_r) / k,   N^0_0 = 1,
 // (out-of-range terms zero) and dN^p_r/dt = N^{p-1}_{r-1} - N^{p-1}_r.  cardinal_basis
 // returns the scaled values M = p! N^p and G = (p-1)! dN^p/dt, which drops every division
-// from the triangle; the contraction's results are scaled back once per sample by
-// kValScale and kGradScale.  This holds on every span whose 2p surrounding knots are all
-// uniform, i.e. all spans but the p-1 at each end of a clamped knot vector.
+// from the triangle; the contraction's results are scaled back once per sample.  This holds
+// on every span whose 2p surrounding knots are all uniform, i.e. all spans but the p-1 at
+// each end of a clamped knot vector.  The y and z weights are always the scaled M and G;
+// the x factor is scaled the same way on 16-bit models and exact on FP32 models, whose
+// window rows carry the x span's polynomial (power rows, below), hence the per-storage
+// scale factors of the value, the x partial and the y / z partials.
 __host__ __device__ constexpr float factorial(int k) { return k <= 1 ? 1.0f : k * factorial(k - 1); }
 template <int Q>
 struct Cardinal {
     static constexpr int p = Q - 1;
     static constexpr float kBasisScale = factorial(p);        // M = kBasisScale N
     static constexpr float kDerivScale = factorial(p - 1);    // G = kDerivScale dN/dt
-    static constexpr float kValScale = 1.0f / (factorial(p) * factorial(p) * factorial(p));
-    static constexpr float kGradScale = 1.0f / (factorial(p - 1) * factorial(p) * factorial(p));
+    template <int STORAGE>
+    static constexpr float x_val() { return power_rows(Q, STORAGE) ? 1.0f : factorial(p); }
+    template <int STORAGE>
+    static constexpr float x_der() { return power_rows(Q, STORAGE) ? 1.0f : factorial(p - 1); }
+    template <int STORAGE>
+    static constexpr float val_scale() { return 1.0f / (x_val<STORAGE>() * factorial(p) * factorial(p)); }
+    template <int STORAGE>
+    static constexpr float gradx_scale() { return 1.0f / (x_der<STORAGE>() * factorial(p) * factorial(p)); }
+    template <int STORAGE>
+    static constexpr float gradyz_scale() { return 1.0f / (x_val<STORAGE>() * factorial(p - 1) * factorial(p)); }
 };
 
 template <int Q>
@@ -271,8 +282,10 @@ struct Pair16 {
     static __device__ __forceinline__ float2 cvt(unsigned int bits)
     {
         if constexpr (BF16) {
-            __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&bits);
-            return __bfloat1622float2(h);
+            // BF16 is the upper half of an FP32 pattern: the word's high value is the word
+            // with its low 16 bits cleared, the low value the word shifted up by 16 (two
+            // integer operations, no conversion instruction)
+            return make_float2(__uint_as_float(bits << 16), __uint_as_float(bits & 0xFFFF0000u));
         } else {
             __half2 h = *reinterpret_cast<__half2*>(&bits);
             return __half22float2(h);
@@ -324,13 +337,104 @@ template <int Q> struct PairLoader<Q, 2> : Pair16<Q, false> {};    // MFA_F16
 template <int Q> struct PairLoader<Q, 3> : Pair16<Q, true> {};     // MFA_BF16
 
 // ----------------------------------------------------------------------------------------
-// contraction
+// the x-pass: power rows (FP32 models) or basis-weighted rows (16-bit models)
 // ----------------------------------------------------------------------------------------
+//
+// On one x span the B-spline restricted to a row of control points is a polynomial in the
+// span's local coordinate t: sum_r N_{i+r}(t) P_{i+r} = sum_c W_c t^c with
+// W_c = sum_r c_{c,r} P_{i+r}, c_{c,r} the power-basis coefficients of the span's basis
+// functions.  FP32 models store W in place of P in each window row (computed in FP64 from
+// the stored control points at model creation, then rounded once to FP32; a row is only
+// ever read by samples in its own x span), so the x-pass is a Horner evaluation: Q-1
+// packed FMAs for the row's value A and Q-2 for dA/dt, against 2Q for the basis-weighted
+// sums, and the x basis itself is never evaluated.  16-bit models keep the control points
+// (W in 16 bits would add its own rounding to the model) and weight them by the x basis.
 
-// Degree class 3: the support's three z-layers are the pair (k0, k0+1) of each entry, run
-// packed as in contract_pairs, and the entry's third-layer row k0+2, run as plain FP32
-// FMAs beside it (the same x, y and z sums; no lane multiplies a padding layer).  Weights
-// arrive packed as for contract_pairs: nz[0] = {Nz_0, Nz_1}, nz[1] = {Nz_2, 0}.
+// What the x-pass needs: the local coordinate t (power rows) or the x basis values and
+// derivatives (control-point rows).  XPk is the same packed for the FP32x2 x-pass, each
+// value duplicated into both lanes; contractions pack their input on entry.
+template <int Q, bool POW>
+struct XInT {
+    float n[Q], d[Q];
+};
+template <int Q>
+struct XInT<Q, true> {
+    float t;
+};
+template <int Q, int STORAGE>
+using XIn = XInT<Q, power_rows(Q, STORAGE)>;
+
+template <int Q, bool POW>
+struct XPk {
+    f2 n[Q], d[Q];
+};
+template <int Q>
+struct XPk<Q, true> {
+    f2 t;
+};
+
+// A = sum_c W_c t^c and B = dA/dt of a window row (both z-layers of the pair at once), by
+// one Horner sweep that carries the derivative: d <- d t + a, a <- a t + W_c.
+template <int Q>
+__device__ __forceinline__ void power_row(const f2 (&w)[qpair(Q)], f2 t, f2& A, f2& B)
+{
+    if constexpr (Q == 2) {
+        A = fma2(w[1], t, w[0]);
+        B = w[1];
+    } else {
+        f2 a = fma2(w[Q - 1], t, w[Q - 2]);
+        f2 d = w[Q - 1];
+#pragma unroll
+        for (int c = Q - 3; c >= 0; --c) {
+            d = fma2(d, t, a);
+            a = fma2(a, t, w[c]);
+        }
+        A = a;
+        B = d;
+    }
+}
+
+// The row's value only.
+template <int Q>
+__device__ __forceinline__ f2 power_row_value(const f2 (&w)[qpair(Q)], f2 t)
+{
+    f2 a = fma2(w[Q - 1], t, w[Q - 2]);
+#pragma unroll
+    for (int c = Q - 3; c >= 0; --c) a = fma2(a, t, w[c]);
+    return a;
+}
+
+// {A, B} of one window row for either kind of row.
+template <int Q, int STORAGE>
+__device__ __forceinline__ void x_row(const f2 (&pr)[qpair(Q)], const XPk<Q, power_rows(Q, STORAGE)>& X, f2& A,
+                                      f2& B)
+{
+    if constexpr (power_rows(Q, STORAGE)) {
+        power_row<Q>(pr, X.t, A, B);
+    } else {
+        A = mul2(X.n[0], pr[0]);
+        B = mul2(X.d[0], pr[0]);
+#pragma unroll
+        for (int a = 1; a < Q; ++a) {
+            A = fma2(X.n[a], pr[a], A);
+            B = fma2(X.d[a], pr[a], B);
+        }
+    }
+}
+
+template <int Q, int STORAGE>
+__device__ __forceinline__ f2 x_row_value(const f2 (&pr)[qpair(Q)], const XPk<Q, power_rows(Q, STORAGE)>& X)
+{
+    if constexpr (power_rows(Q, STORAGE)) {
+        return power_row_value<Q>(pr, X.t);
+    } else {
+        f2 A = mul2(X.n[0], pr[0]);
+#pragma unroll
+        for (int a = 1; a < Q; ++a) A = fma2(X.n[a], pr[a], A);
+        return A;
+    }
+}
+
 __device__ __forceinline__ float lo2(f2 x)
 {
     float a, b;
@@ -338,11 +442,120 @@ __device__ __forceinline__ float lo2(f2 x)
     return a;
 }
 
+// The third-layer row of a degree-class-3 entry (plain FP32): its A and B.
 template <int STORAGE>
-__device__ __forceinline__ float4 contract_triple(const ModelDev& M, int base, const f2 (&nx)[3], const f2 (&dx)[3],
+__device__ __forceinline__ void x_row3(const float (&r3)[4], const XPk<3, power_rows(3, STORAGE)>& X, float& A3,
+                                       float& B3)
+{
+    if constexpr (power_rows(3, STORAGE)) {
+        const float t = lo2(X.t);
+        const float a = fmaf(r3[2], t, r3[1]);
+        B3 = fmaf(r3[2], t, a);
+        A3 = fmaf(a, t, r3[0]);
+    } else {
+        A3 = lo2(X.n[0]) * r3[0];
+        B3 = lo2(X.d[0]) * r3[0];
+#pragma unroll
+        for (int a = 1; a < 3; ++a) {
+            A3 = fmaf(lo2(X.n[a]), r3[a], A3);
+            B3 = fmaf(lo2(X.d[a]), r3[a], B3);
+        }
+    }
+}
+
+template <int STORAGE>
+__device__ __forceinline__ float x_row3_value(const float (&r3)[4], const XPk<3, power_rows(3, STORAGE)>& X)
+{
+    if constexpr (power_rows(3, STORAGE)) {
+        const float t = lo2(X.t);
+        return fmaf(fmaf(r3[2], t, r3[1]), t, r3[0]);
+    } else {
+        float A3 = lo2(X.n[0]) * r3[0];
+#pragma unroll
+        for (int a = 1; a < 3; ++a) A3 = fmaf(lo2(X.n[a]), r3[a], A3);
+        return A3;
+    }
+}
+
+// {X_a, X_a} for every a
+template <int Q>
+__device__ __forceinline__ void pack_dup(const float (&X)[Q], f2 (&X2)[Q])
+{
+#pragma unroll
+    for (int a = 0; a < Q; ++a) X2[a] = pk2(X[a], X[a]);
+}
+
+// {X_2m, X_2m+1} (zero past Q)
+template <int Q>
+__device__ __forceinline__ void pack_pairs(const float (&X)[Q], f2 (&X2)[qpair(Q) / 2])
+{
+#pragma unroll
+    for (int m = 0; m < qpair(Q) / 2; ++m) X2[m] = pk2(X[2 * m], 2 * m + 1 < Q ? X[2 * m + 1] : 0.0f);
+}
+
+// x-pass input from basis values and derivatives (control-point rows) or the local
+// coordinate t (power rows).
+template <int Q>
+__device__ __forceinline__ XInT<Q, false> xin_basis(const float (&N)[Q], const float (&D)[Q])
+{
+    XInT<Q, false> X;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        X.n[a] = N[a];
+        X.d[a] = D[a];
+    }
+    return X;
+}
+template <int Q>
+__device__ __forceinline__ XInT<Q, true> xin_t(float t)
+{
+    XInT<Q, true> X;
+    X.t = t;
+    return X;
+}
+
+// The packed form of an x-pass input.
+template <int Q, bool POW>
+__device__ __forceinline__ XPk<Q, POW> pack_x(const XInT<Q, POW>& X)
+{
+    XPk<Q, POW> P;
+    if constexpr (POW) {
+        P.t = pk2(X.t, X.t);
+    } else {
+        pack_dup<Q>(X.n, P.n);
+        pack_dup<Q>(X.d, P.d);
+    }
+    return P;
+}
+
+// x-pass input on a span whose record is in registers, at parameter u: the record's local
+// coordinate t = (u - U_s)/h, or the basis by Horner on the record.
+template <int Q, int STORAGE>
+__device__ __forceinline__ XIn<Q, STORAGE> xin_record(const float (&rec)[rec_stride(Q)], float u)
+{
+    if constexpr (power_rows(Q, STORAGE)) {
+        return xin_t<Q>((u - rec[0]) * rec[1]);
+    } else {
+        float N[Q], D[Q];
+        record_basis<Q>(rec, u, N, D);
+        return xin_basis<Q>(N, D);
+    }
+}
+
+// ----------------------------------------------------------------------------------------
+// contraction
+// ----------------------------------------------------------------------------------------
+
+// Degree class 3: the support's three z-layers are the pair (k0, k0+1) of each entry, run
+// packed as in contract_pairs, and the entry's third-layer row k0+2, run as plain FP32
+// FMAs beside it (the same x, y and z sums; no lane multiplies a padding layer).  Weights
+// arrive packed as for contract_pairs: nz[0] = {Nz_0, Nz_1}, nz[1] = {Nz_2, 0}.
+template <int STORAGE>
+__device__ __forceinline__ float4 contract_triple(const ModelDev& M, int base, const XIn<3, STORAGE>& Xin,
                                                   const f2 (&ny)[3], const f2 (&dy)[3], const f2 (&nz)[2],
                                                   const f2 (&dz)[2])
 {
+    const auto X = pack_x(Xin);
     f2 CC, DD, EE;
     float C3, D3, E3;
 #pragma unroll
@@ -352,17 +565,10 @@ __device__ __forceinline__ float4 contract_triple(const ModelDev& M, int base, c
         int idx = base + b * M.nxp;
         MFA_DBG_INDEX(M.dbg, idx, static_cast<long long>(M.nxp) * M.nyp * M.nzp, kDbgWindow);
         PairLoader<3, STORAGE>::load_triple(M.win, idx, pr, r3);
-        f2 A = mul2(nx[0], pr[0]);
-        f2 B = mul2(dx[0], pr[0]);
-        float A3 = lo2(nx[0]) * r3[0];
-        float B3 = lo2(dx[0]) * r3[0];
-#pragma unroll
-        for (int a = 1; a < 3; ++a) {
-            A = fma2(nx[a], pr[a], A);
-            B = fma2(dx[a], pr[a], B);
-            A3 = fmaf(lo2(nx[a]), r3[a], A3);
-            B3 = fmaf(lo2(dx[a]), r3[a], B3);
-        }
+        f2 A, B;
+        float A3, B3;
+        x_row<3, STORAGE>(pr, X, A, B);
+        x_row3<STORAGE>(r3, X, A3, B3);
         const float nyb = lo2(ny[b]), dyb = lo2(dy[b]);
         if (b == 0) {
             CC = mul2(ny[0], A);
@@ -387,75 +593,76 @@ __device__ __forceinline__ float4 contract_triple(const ModelDev& M, int base, c
 
 // Sum-factorised contraction over the Q^3 support whose first row is window entry `base`
 // (= (k0 nyp + j0) nxp + i0 for the support origin (i0, j0, k0)):
-//   x-pass  A_jk = sum_i Nx_i P_ijk,  B_jk = sum_i Dx_i P_ijk          (2 Q^3 FMA)
+//   x-pass  A_jk = sum_i Nx_i P_ijk,  B_jk = sum_i Dx_i P_ijk   (x_row: a Horner sweep of the
+//           power row, or 2 Q^3 FMA against the x basis)
 //   y-pass  C_k = sum_j Ny_j A_jk, D_k = sum_j Dy_j A_jk, E_k = sum_j Ny_j B_jk   (3 Q^2)
 //   z-pass  f = sum_k Nz_k C_k, f_z = sum Dz_k C_k, f_y = sum Nz_k D_k, f_x = sum Nz_k E_k
 // Returns {f, df/dtx, df/dty, df/dtz} (derivatives in the local span coordinates).
 //
 // All three passes run on packed FP32x2 values over pairs of z-layers (k, k+1): one
-// window entry gives {A_jk, A_j,k+1} = sum_i {Nx_i, Nx_i} * pr[i] (and B likewise), the
-// y-pass turns them into {C_k, C_k+1}, {D_k, D_k+1}, {E_k, E_k+1} with weights
-// {Ny_j, Ny_j}, and the z-pass accumulates those against {Nz_k, Nz_k+1}; the two halves of
-// each of the four results are added once at the end.  nx, dx, ny, dy hold each basis value
-// twice, nz, dz the values of functions (2m, 2m+1) (zero past Q).  Each lane is an ordinary
-// FP32 FMA; the z sums add their even and odd terms separately before the final addition.
+// window entry gives {A_jk, A_j,k+1} (and B likewise), the y-pass turns them into
+// {C_k, C_k+1}, {D_k, D_k+1}, {E_k, E_k+1} with weights {Ny_j, Ny_j}, and the z-pass
+// accumulates those against {Nz_k, Nz_k+1}; the two halves of each of the four results are
+// added once at the end.  ny, dy hold each basis value twice, nz, dz the values of
+// functions (2m, 2m+1) (zero past Q).  Each lane is an ordinary FP32 FMA; the z sums add
+// their even and odd terms separately before the final addition.
 template <int Q, int STORAGE>
-__device__ __forceinline__ float4 contract_pairs(const ModelDev& M, int base, const f2 (&nx)[Q], const f2 (&dx)[Q],
+__device__ __forceinline__ float4 contract_pairs(const ModelDev& M, int base, const XIn<Q, STORAGE>& Xin,
                                                  const f2 (&ny)[Q], const f2 (&dy)[Q], const f2 (&nz)[qpair(Q) / 2],
                                                  const f2 (&dz)[qpair(Q) / 2])
 {
-    if constexpr (Q == 3) return contract_triple<STORAGE>(M, base, nx, dx, ny, dy, nz, dz);
-    constexpr int NP = qpair(Q) / 2;
-    const int pair_step = 2 * M.nxp * M.nyp;
-    f2 F, FX, FY, FZ;
+    if constexpr (Q == 3) {
+        return contract_triple<STORAGE>(M, base, Xin, ny, dy, nz, dz);
+    } else {
+        const auto X = pack_x(Xin);
+        constexpr int NP = qpair(Q) / 2;
+        const int pair_step = 2 * M.nxp * M.nyp;
+        f2 F, FX, FY, FZ;
 #pragma unroll
-    for (int m = 0; m < NP; ++m) {
-        f2 CC, DD, EE;
+        for (int m = 0; m < NP; ++m) {
+            f2 CC, DD, EE;
 #pragma unroll
-        for (int b = 0; b < Q; ++b) {
-            f2 pr[qpair(Q)];
-            int idx = base + m * pair_step + b * M.nxp;   // Q = 5 also reads entry idx + 1
-            MFA_DBG_INDEX(M.dbg, idx, static_cast<long long>(M.nxp) * M.nyp * M.nzp - (qpair(Q) == 6), kDbgWindow);
-            PairLoader<Q, STORAGE>::load(M.win, idx, pr);
-            f2 A = mul2(nx[0], pr[0]);
-            f2 B = mul2(dx[0], pr[0]);
-#pragma unroll
-            for (int a = 1; a < Q; ++a) {
-                A = fma2(nx[a], pr[a], A);
-                B = fma2(dx[a], pr[a], B);
+            for (int b = 0; b < Q; ++b) {
+                f2 pr[qpair(Q)];
+                int idx = base + m * pair_step + b * M.nxp;   // Q = 5 also reads entry idx + 1
+                MFA_DBG_INDEX(M.dbg, idx, static_cast<long long>(M.nxp) * M.nyp * M.nzp - (qpair(Q) == 6), kDbgWindow);
+                PairLoader<Q, STORAGE>::load(M.win, idx, pr);
+                f2 A, B;
+                x_row<Q, STORAGE>(pr, X, A, B);
+                if (b == 0) {
+                    CC = mul2(ny[0], A);
+                    DD = mul2(dy[0], A);
+                    EE = mul2(ny[0], B);
+                } else {
+                    CC = fma2(ny[b], A, CC);
+                    DD = fma2(dy[b], A, DD);
+                    EE = fma2(ny[b], B, EE);
+                }
             }
-            if (b == 0) {
-                CC = mul2(ny[0], A);
-                DD = mul2(dy[0], A);
-                EE = mul2(ny[0], B);
+            if (m == 0) {
+                F = mul2(nz[0], CC);
+                FZ = mul2(dz[0], CC);
+                FY = mul2(nz[0], DD);
+                FX = mul2(nz[0], EE);
             } else {
-                CC = fma2(ny[b], A, CC);
-                DD = fma2(dy[b], A, DD);
-                EE = fma2(ny[b], B, EE);
+                F = fma2(nz[m], CC, F);
+                FZ = fma2(dz[m], CC, FZ);
+                FY = fma2(nz[m], DD, FY);
+                FX = fma2(nz[m], EE, FX);
             }
         }
-        if (m == 0) {
-            F = mul2(nz[0], CC);
-            FZ = mul2(dz[0], CC);
-            FY = mul2(nz[0], DD);
-            FX = mul2(nz[0], EE);
-        } else {
-            F = fma2(nz[m], CC, F);
-            FZ = fma2(dz[m], CC, FZ);
-            FY = fma2(nz[m], DD, FY);
-            FX = fma2(nz[m], EE, FX);
-        }
+        return make_float4(hsum2(F), hsum2(FX), hsum2(FY), hsum2(FZ));
     }
-    return make_float4(hsum2(F), hsum2(FX), hsum2(FY), hsum2(FZ));
 }
 
-// Value only: the x-, y- and z-sums of contract_pairs (contract_triple for Q = 3) with the
-// basis values alone, Q^3 + Q^2 + Q multiply-adds instead of 2Q^3 + 3Q^2 + 4Q, in the same
-// order, so f is bit-identical to the value contract_pairs returns.
+// Value only: the x-, y- and z-sums of contract_pairs (contract_triple for Q = 3) without
+// the derivative sums, in the same order, so f is bit-identical to the value contract_pairs
+// returns.
 template <int Q, int STORAGE>
-__device__ __forceinline__ float contract_value(const ModelDev& M, int base, const f2 (&nx)[Q], const f2 (&ny)[Q],
-                                                const f2 (&nz)[qpair(Q) / 2])
+__device__ __forceinline__ float contract_value(const ModelDev& M, int base, const XIn<Q, STORAGE>& Xin,
+                                                const f2 (&ny)[Q], const f2 (&nz)[qpair(Q) / 2])
 {
+    const auto X = pack_x(Xin);
     if constexpr (Q == 3) {
         f2 CC;
         float C3;
@@ -466,13 +673,8 @@ __device__ __forceinline__ float contract_value(const ModelDev& M, int base, con
             int idx = base + b * M.nxp;
             MFA_DBG_INDEX(M.dbg, idx, static_cast<long long>(M.nxp) * M.nyp * M.nzp, kDbgWindow);
             PairLoader<3, STORAGE>::load_triple(M.win, idx, pr, r3);
-            f2 A = mul2(nx[0], pr[0]);
-            float A3 = lo2(nx[0]) * r3[0];
-#pragma unroll
-            for (int a = 1; a < 3; ++a) {
-                A = fma2(nx[a], pr[a], A);
-                A3 = fmaf(lo2(nx[a]), r3[a], A3);
-            }
+            const f2 A = x_row_value<3, STORAGE>(pr, X);
+            const float A3 = x_row3_value<STORAGE>(r3, X);
             const float nyb = lo2(ny[b]);
             CC = b == 0 ? mul2(ny[0], A) : fma2(ny[b], A, CC);
             C3 = b == 0 ? nyb * A3 : fmaf(nyb, A3, C3);
@@ -491,9 +693,7 @@ __device__ __forceinline__ float contract_value(const ModelDev& M, int base, con
                 int idx = base + m * pair_step + b * M.nxp;
                 MFA_DBG_INDEX(M.dbg, idx, static_cast<long long>(M.nxp) * M.nyp * M.nzp - (qpair(Q) == 6), kDbgWindow);
                 PairLoader<Q, STORAGE>::load(M.win, idx, pr);
-                f2 A = mul2(nx[0], pr[0]);
-#pragma unroll
-                for (int a = 1; a < Q; ++a) A = fma2(nx[a], pr[a], A);
+                const f2 A = x_row_value<Q, STORAGE>(pr, X);
                 CC = b == 0 ? mul2(ny[0], A) : fma2(ny[b], A, CC);
             }
             F = m == 0 ? mul2(nz[0], CC) : fma2(nz[m], CC, F);
@@ -502,57 +702,38 @@ __device__ __forceinline__ float contract_value(const ModelDev& M, int base, con
     }
 }
 
-// {X_a, X_a} for every a
-template <int Q>
-__device__ __forceinline__ void pack_dup(const float (&X)[Q], f2 (&X2)[Q])
-{
-#pragma unroll
-    for (int a = 0; a < Q; ++a) X2[a] = pk2(X[a], X[a]);
-}
-
-// {X_2m, X_2m+1} (zero past Q)
-template <int Q>
-__device__ __forceinline__ void pack_pairs(const float (&X)[Q], f2 (&X2)[qpair(Q) / 2])
-{
-#pragma unroll
-    for (int m = 0; m < qpair(Q) / 2; ++m) X2[m] = pk2(X[2 * m], 2 * m + 1 < Q ? X[2 * m + 1] : 0.0f);
-}
-
-// Contraction from scalar basis values.
+// Contraction from the x-pass input and scalar y / z basis values.
 template <int Q, int STORAGE>
-__device__ __forceinline__ float4 contract_at(const ModelDev& M, int base, const float (&Nx)[Q], const float (&Dx)[Q],
+__device__ __forceinline__ float4 contract_at(const ModelDev& M, int base, const XIn<Q, STORAGE>& X,
                                               const float (&Ny)[Q], const float (&Dy)[Q], const float (&Nz)[Q],
                                               const float (&Dz)[Q])
 {
-    f2 nx[Q], dx[Q], ny[Q], dy[Q], nz[qpair(Q) / 2], dz[qpair(Q) / 2];
-    pack_dup<Q>(Nx, nx);
-    pack_dup<Q>(Dx, dx);
+    f2 ny[Q], dy[Q], nz[qpair(Q) / 2], dz[qpair(Q) / 2];
     pack_dup<Q>(Ny, ny);
     pack_dup<Q>(Dy, dy);
     pack_pairs<Q>(Nz, nz);
     pack_pairs<Q>(Dz, dz);
-    return contract_pairs<Q, STORAGE>(M, base, nx, dx, ny, dy, nz, dz);
+    return contract_pairs<Q, STORAGE>(M, base, X, ny, dy, nz, dz);
 }
 
-// Value only, from scalar basis values.
+// Value only, from the x-pass input and scalar y / z basis values.
 template <int Q, int STORAGE>
-__device__ __forceinline__ float value_at(const ModelDev& M, int base, const float (&Nx)[Q], const float (&Ny)[Q],
+__device__ __forceinline__ float value_at(const ModelDev& M, int base, const XIn<Q, STORAGE>& X, const float (&Ny)[Q],
                                           const float (&Nz)[Q])
 {
-    f2 nx[Q], ny[Q], nz[qpair(Q) / 2];
-    pack_dup<Q>(Nx, nx);
+    f2 ny[Q], nz[qpair(Q) / 2];
     pack_dup<Q>(Ny, ny);
     pack_pairs<Q>(Nz, nz);
-    return contract_value<Q, STORAGE>(M, base, nx, ny, nz);
+    return contract_value<Q, STORAGE>(M, base, X, ny, nz);
 }
 
 // Same, from the support's origin (i0, j0, k0) in the window array.
 template <int Q, int STORAGE>
-__device__ __forceinline__ float4 contract(const ModelDev& M, int i0, int j0, int k0, const float (&Nx)[Q],
-                                           const float (&Dx)[Q], const float (&Ny)[Q], const float (&Dy)[Q],
-                                           const float (&Nz)[Q], const float (&Dz)[Q])
+__device__ __forceinline__ float4 contract(const ModelDev& M, int i0, int j0, int k0, const XIn<Q, STORAGE>& X,
+                                           const float (&Ny)[Q], const float (&Dy)[Q], const float (&Nz)[Q],
+                                           const float (&Dz)[Q])
 {
-    return contract_at<Q, STORAGE>(M, (k0 * M.nyp + j0) * M.nxp + i0, Nx, Dx, Ny, Dy, Nz, Dz);
+    return contract_at<Q, STORAGE>(M, (k0 * M.nyp + j0) * M.nxp + i0, X, Ny, Dy, Nz, Dz);
 }
 
 // Full query at a clamped parameter point: value and world gradient (unit-cube domain,
@@ -560,12 +741,13 @@ __device__ __forceinline__ float4 contract(const ModelDev& M, int i0, int j0, in
 template <int Q, int STORAGE>
 __device__ __forceinline__ float4 query(const ModelDev& M, float u, float v, float w, int sx, int sy, int sz)
 {
-    float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q], hx, hy, hz;
-    span_basis<Q>(M.ax[0], sx, u, Nx, Dx, hx);
+    float rx[rec_stride(Q)], Ny[Q], Dy[Q], Nz[Q], Dz[Q], hy, hz;
+    load_record<Q>(M.ax[0], sx, rx);
     span_basis<Q>(M.ax[1], sy, v, Ny, Dy, hy);
     span_basis<Q>(M.ax[2], sz, w, Nz, Dz, hz);
-    float4 r = contract<Q, STORAGE>(M, sx - M.ax[0].p, sy - M.ax[1].p, sz - M.ax[2].p, Nx, Dx, Ny, Dy, Nz, Dz);
-    r.y *= hx;
+    float4 r = contract<Q, STORAGE>(M, sx - M.ax[0].p, sy - M.ax[1].p, sz - M.ax[2].p, xin_record<Q, STORAGE>(rx, u),
+                                    Ny, Dy, Nz, Dz);
+    r.y *= rx[1];
     r.z *= hy;
     r.w *= hz;
     return r;
@@ -579,16 +761,14 @@ __device__ __forceinline__ float4 query2_rec(const ModelDev& M, const float (&rx
                                              float u, float v, float w, int i0, int j0, int k0)
 {
     constexpr int NP = qpair(Q) / 2;
-    float Nx[Q], Dx[Q], Ny[Q], Dy[Q];
-    f2 nx[Q], dx[Q], ny[Q], dy[Q], nz[NP], dz[NP];
-    record_basis<Q>(rx, u, Nx, Dx);
+    float Ny[Q], Dy[Q];
+    f2 ny[Q], dy[Q], nz[NP], dz[NP];
+    const XIn<Q, STORAGE> X = xin_record<Q, STORAGE>(rx, u);
     record_basis<Q>(ry, v, Ny, Dy);
     record_basis2<Q>(rz, w, nz, dz);
-    pack_dup<Q>(Nx, nx);
-    pack_dup<Q>(Dx, dx);
     pack_dup<Q>(Ny, ny);
     pack_dup<Q>(Dy, dy);
-    float4 r = contract_pairs<Q, STORAGE>(M, (k0 * M.nyp + j0) * M.nxp + i0, nx, dx, ny, dy, nz, dz);
+    float4 r = contract_pairs<Q, STORAGE>(M, (k0 * M.nyp + j0) * M.nxp + i0, X, ny, dy, nz, dz);
     r.y *= rx[1];
     r.z *= ry[1];
     r.w *= rz[1];
@@ -614,7 +794,7 @@ __device__ __forceinline__ float4 query2(const ModelDev& M, float u, float v, fl
 // the exact span of u (cardinal_span: floor(x) checked against the knots); a ray march,
 // whose samples are positioned in span units directly, takes floor(x), the span of its
 // position x / (n - p).  Either way the span index j is clamped to 0..n-p-1 and the local
-// coordinate is t = x - j (exact in FP32).  Spans at least p-1 from both ends use
+// coordinate is t = x - j (exact in FP32, in [0, 1]).  Spans at least p-1 from both ends use
 // cardinal_basis; the p-1 end spans on each side, whose functions see the repeated end
 // knots, evaluate their record at the same t (uniform spacing makes the record's local
 // coordinate equal to x - j) and rescale to M, G.
@@ -646,19 +826,20 @@ __device__ __forceinline__ float cardinal_coord(const AxisDev& A, float u)
 
 // Knot span of a clamped FP32 parameter u on the cardinal path, as j = s - p: the largest
 // s with U_s <= u, exactly as locate_span finds it.  x = cardinal_coord(u) is the product
-// (n - p) u rounded to FP32, so floor(x) can sit one span off when the rounding carries x
-// onto or across an integer (u within an ulp of a knot, e.g. u = fl32(0.04) just below
-// the knot 5/125 while x rounds to 5.0).  floor(x) is never more than one span away, so
-// one exact comparison on each side against the knots rounded up to FP32 (u >= kup[s]
-// iff u >= U_s) settles it.  The local coordinate x - j then lies in [-ulp, 1].
+// (n - p) u correctly rounded to FP32, and rounding is monotone with every integer below
+// 2^24 representable, so x > j implies (n - p) u > j and x < j + 1 implies (n - p) u <
+// j + 1: floor(x) is the span of the exact product, except when the rounding carried x
+// onto the integer j itself from below (u within half an ulp of a knot, e.g. u =
+// fl32(0.04) just below the knot 5/125 with x = 5.0).  Only then is u compared with the
+// knot, exactly (kup holds the knots rounded up to FP32: u >= kup[s] iff u >= U_s), and
+// j moves down one span when u lies below it; the local coordinate x - j is then 1.
+// (The exact product's span is the span against the FP64 knots, which on this path are
+// exactly i/(n-p) rounded to FP64: no FP32 value lies strictly between i/(n-p) and its
+// FP64 rounding.)
 __device__ __forceinline__ int cardinal_span(const AxisDev& A, float u, float x)
 {
-    const int m = A.n - A.p;
-    int j = min(max(__float2int_rd(x), 0), m - 1);
-    if (j > 0 && u < __ldg(A.kup + A.p + j))
-        --j;
-    else if (j < m - 1 && u >= __ldg(A.kup + A.p + j + 1))
-        ++j;
+    int j = min(max(__float2int_rd(x), 0), A.n - A.p - 1);
+    if (x == static_cast<float>(j) && j > 0 && u < __ldg(A.kup + A.p + j)) --j;
     return j;
 }
 
@@ -680,6 +861,40 @@ __device__ __forceinline__ void card_basis(const AxisDev& A, const CardAxis& C, 
     }
 }
 
+// x-pass input on the cardinal path at local coordinate t: t itself (power rows, whose
+// end spans carry their own polynomials), or the scaled basis of the axis's current span.
+template <int Q, int STORAGE>
+__device__ __forceinline__ XIn<Q, STORAGE> xin_card(const AxisDev& A, const CardAxis& C, float t)
+{
+    if constexpr (power_rows(Q, STORAGE)) {
+        return xin_t<Q>(t);
+    } else {
+        float N[Q], D[Q];
+        card_basis<Q>(A, C, t, N, D);
+        return xin_basis<Q>(N, D);
+    }
+}
+
+// Same on an interior span (no record).
+template <int Q, int STORAGE>
+__device__ __forceinline__ XIn<Q, STORAGE> xin_cardinal(float t)
+{
+    if constexpr (power_rows(Q, STORAGE)) {
+        return xin_t<Q>(t);
+    } else {
+        float N[Q], D[Q];
+        cardinal_basis<Q>(t, N, D);
+        return xin_basis<Q>(N, D);
+    }
+}
+
+// Whether any axis needs its end-span record: the x axis only with control-point rows.
+template <int Q, int STORAGE>
+__device__ __forceinline__ bool card_edge(const CardAxis& cx, const CardAxis& cy, const CardAxis& cz)
+{
+    return (power_rows(Q, STORAGE) ? false : cx.edge) | cy.edge | cz.edge;
+}
+
 // Value and parameter-space gradient at a clamped point on the cardinal path (spans exact,
 // as cardinal_span finds them).
 template <int Q, int STORAGE>
@@ -692,15 +907,15 @@ __device__ __forceinline__ float4 query_cardinal(const ModelDev& M, float u, flo
     card_set(M.ax[0], cx, cardinal_span(M.ax[0], u, x));
     card_set(M.ax[1], cy, cardinal_span(M.ax[1], v, y));
     card_set(M.ax[2], cz, cardinal_span(M.ax[2], w, z));
-    float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];
-    card_basis<Q>(M.ax[0], cx, x - cx.jf, Nx, Dx);
+    float Ny[Q], Dy[Q], Nz[Q], Dz[Q];
+    const XIn<Q, STORAGE> X = xin_card<Q, STORAGE>(M.ax[0], cx, x - cx.jf);
     card_basis<Q>(M.ax[1], cy, y - cy.jf, Ny, Dy);
     card_basis<Q>(M.ax[2], cz, z - cz.jf, Nz, Dz);
-    float4 r = contract_at<Q, STORAGE>(M, (cz.j * M.nyp + cy.j) * M.nxp + cx.j, Nx, Dx, Ny, Dy, Nz, Dz);
-    r.x *= Cardinal<Q>::kValScale;
-    r.y *= static_cast<float>(M.ax[0].n - M.ax[0].p) * Cardinal<Q>::kGradScale;
-    r.z *= static_cast<float>(M.ax[1].n - M.ax[1].p) * Cardinal<Q>::kGradScale;
-    r.w *= static_cast<float>(M.ax[2].n - M.ax[2].p) * Cardinal<Q>::kGradScale;
+    float4 r = contract_at<Q, STORAGE>(M, (cz.j * M.nyp + cy.j) * M.nxp + cx.j, X, Ny, Dy, Nz, Dz);
+    r.x *= Cardinal<Q>::template val_scale<STORAGE>();
+    r.y *= static_cast<float>(M.ax[0].n - M.ax[0].p) * Cardinal<Q>::template gradx_scale<STORAGE>();
+    r.z *= static_cast<float>(M.ax[1].n - M.ax[1].p) * Cardinal<Q>::template gradyz_scale<STORAGE>();
+    r.w *= static_cast<float>(M.ax[2].n - M.ax[2].p) * Cardinal<Q>::template gradyz_scale<STORAGE>();
     return r;
 }
 

@@ -19,24 +19,6 @@
 namespace mfa {
 namespace {
 
-// Element 0 of window entry (k, j, i) is P[k][j][i]: copy the stored values out, densely.
-__global__ void k_extract_ctrl(const void* __restrict__ win, int storage, int nv, int nx, int ny, int nz, int nxp,
-                               int nyp, void* __restrict__ out)
-{
-    const long long total = static_cast<long long>(nx) * ny * nz;
-    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
-         e += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int i = static_cast<int>(e % nx);
-        const long long jk = e / nx;
-        const int j = static_cast<int>(jk % ny), k = static_cast<int>(jk / ny);
-        const long long w = (static_cast<long long>(k) * nyp + j) * nxp + i;
-        if (storage == MFA_F32)
-            static_cast<float*>(out)[e] = static_cast<const float*>(win)[nv * w];
-        else
-            static_cast<unsigned short*>(out)[e] = static_cast<const unsigned short*>(win)[nv * w];
-    }
-}
-
 struct FileHeader {
     char magic[8];
     int32_t version;
@@ -61,19 +43,9 @@ extern "C" int mfa_model_get_ctrl(const mfa_model* m, void* host_out)
     if (int rc = check_model_device(m)) return rc;
     const int nx = m->nctrl[0], ny = m->nctrl[1], nz = m->nctrl[2];
     const size_t bytes = static_cast<size_t>(nx) * ny * nz * storage_bytes(m->storage);
-    cudaMemPool_t pool;
-    cudaError_t e = staging_pool(m->device, &pool);
-    if (e != cudaSuccess) return cuda_fail(e, "staging pool");
+    // the plain array of stored values is the model's own copy: one device-to-host copy
     cudaStream_t st = current_stream();
-    void* d = nullptr;
-    if ((e = cudaMallocFromPoolAsync(&d, bytes, pool, st)) != cudaSuccess) return cuda_fail(e, "staging memory");
-    const long long total = static_cast<long long>(nx) * ny * nz;
-    const long long want = (total + 255) / 256;
-    k_extract_ctrl<<<static_cast<int>(want < 8192 ? want : 8192), 256, 0, st>>>(
-        m->dev.win, m->storage, window_values(m->dev.q), nx, ny, nz, m->dev.nxp, m->dev.nyp, d);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, d, bytes, cudaMemcpyDeviceToHost, st);
-    cudaFreeAsync(d, st);
+    cudaError_t e = cudaMemcpyAsync(host_out, m->dev.raw, bytes, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? MFA_OK : cuda_fail(e, "read control points");
 }

@@ -71,11 +71,11 @@ struct RayQuery<Q, STORAGE, true> {
         bounded = iso < r.x || iso > r.y;
         if (iso < r.x) return r.x - iso;
         if (iso > r.y) return r.y - iso;
-        float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];   // derivatives unused: dropped by the compiler
-        card_basis<Q>(M.ax[0], c[0], t[0], Nx, Dx);
+        float Ny[Q], Dy[Q], Nz[Q], Dz[Q];   // derivatives unused: dropped by the compiler
+        const XIn<Q, STORAGE> X = xin_card<Q, STORAGE>(M.ax[0], c[0], t[0]);
         card_basis<Q>(M.ax[1], c[1], t[1], Ny, Dy);
         card_basis<Q>(M.ax[2], c[2], t[2], Nz, Dz);
-        return value_at<Q, STORAGE>(M, base, Nx, Ny, Nz) * Cardinal<Q>::kValScale - iso;
+        return value_at<Q, STORAGE>(M, base, X, Ny, Nz) * Cardinal<Q>::template val_scale<STORAGE>() - iso;
     }
 
     // ray parameter at which the ray o + t d leaves the current cell: the cell spans
@@ -96,15 +96,15 @@ struct RayQuery<Q, STORAGE, true> {
     {
         float t[3];
         locate(M, u, v, w, t);
-        float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];
-        card_basis<Q>(M.ax[0], c[0], t[0], Nx, Dx);
+        float Ny[Q], Dy[Q], Nz[Q], Dz[Q];
+        const XIn<Q, STORAGE> X = xin_card<Q, STORAGE>(M.ax[0], c[0], t[0]);
         card_basis<Q>(M.ax[1], c[1], t[1], Ny, Dy);
         card_basis<Q>(M.ax[2], c[2], t[2], Nz, Dz);
-        float4 q = contract_at<Q, STORAGE>(M, base, Nx, Dx, Ny, Dy, Nz, Dz);
-        q.x *= Cardinal<Q>::kValScale;
-        q.y *= m[0] * Cardinal<Q>::kGradScale;
-        q.z *= m[1] * Cardinal<Q>::kGradScale;
-        q.w *= m[2] * Cardinal<Q>::kGradScale;
+        float4 q = contract_at<Q, STORAGE>(M, base, X, Ny, Dy, Nz, Dz);
+        q.x *= Cardinal<Q>::template val_scale<STORAGE>();
+        q.y *= m[0] * Cardinal<Q>::template gradx_scale<STORAGE>();
+        q.z *= m[1] * Cardinal<Q>::template gradyz_scale<STORAGE>();
+        q.w *= m[2] * Cardinal<Q>::template gradyz_scale<STORAGE>();
         return q;
     }
 };
@@ -131,12 +131,12 @@ struct RayQuery<Q, STORAGE, false> {
         bounded = iso < r.x || iso > r.y;
         if (iso < r.x) return r.x - iso;
         if (iso > r.y) return r.y - iso;
-        float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];   // derivatives unused: dropped by the compiler
-        record_basis<Q>(c[0].rec, x[0], Nx, Dx);
+        float Ny[Q], Dy[Q], Nz[Q], Dz[Q];   // derivatives unused: dropped by the compiler
+        const XIn<Q, STORAGE> X = xin_record<Q, STORAGE>(c[0].rec, x[0]);
         record_basis<Q>(c[1].rec, x[1], Ny, Dy);
         record_basis<Q>(c[2].rec, x[2], Nz, Dz);
         return value_at<Q, STORAGE>(
-                   M, ((c[2].s - M.ax[2].p) * M.nyp + (c[1].s - M.ax[1].p)) * M.nxp + (c[0].s - M.ax[0].p), Nx, Ny,
+                   M, ((c[2].s - M.ax[2].p) * M.nyp + (c[1].s - M.ax[1].p)) * M.nxp + (c[0].s - M.ax[0].p), X, Ny,
                    Nz) -
                iso;
     }
@@ -159,11 +159,11 @@ struct RayQuery<Q, STORAGE, false> {
         const float x[3] = { clamp01(u), clamp01(v), clamp01(w) };
 #pragma unroll
         for (int a = 0; a < 3; ++a) axis_update<Q>(M.ax[a], c[a], x[a]);
-        float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];
-        record_basis<Q>(c[0].rec, x[0], Nx, Dx);
+        float Ny[Q], Dy[Q], Nz[Q], Dz[Q];
+        const XIn<Q, STORAGE> X = xin_record<Q, STORAGE>(c[0].rec, x[0]);
         record_basis<Q>(c[1].rec, x[1], Ny, Dy);
         record_basis<Q>(c[2].rec, x[2], Nz, Dz);
-        float4 q = contract<Q, STORAGE>(M, c[0].s - M.ax[0].p, c[1].s - M.ax[1].p, c[2].s - M.ax[2].p, Nx, Dx, Ny, Dy,
+        float4 q = contract<Q, STORAGE>(M, c[0].s - M.ax[0].p, c[1].s - M.ax[1].p, c[2].s - M.ax[2].p, X, Ny, Dy,
                                         Nz, Dz);
         q.y *= c[0].rec[1];
         q.z *= c[1].rec[1];

@@ -11,6 +11,14 @@
 //     of the third layer, P[k+2][j][i..i+3], and pads the entry to 16 values, so that one
 //     256-bit and one 128-bit load fetch a whole z-column of a support row (16x the plain
 //     array); window_values(Q) is the entry size in values.
+//     FP32 models of degree class Q <= 4 store, in place of each row's control points
+//     P[.][j][i..i+Q-1], the row's
+//     polynomial on x span i in power form, W_c = sum_r c_{c,r} P[.][j][i+r] (c_{c,r} the
+//     power-basis coefficients of span i's basis functions in its local coordinate t),
+//     computed in FP64 from the stored values and rounded once; rows of entries past the
+//     last span are zero.  16-bit models (and degree class 5) store the control points.
+//   * raw  the stored control points as a plain [n_z][n_y][n_x] array (storage type): the
+//     model's values, read by the statistics, the cell bounds, checkpoints and the bricks.
 //   * per axis: kup[n+p+1]  the FP64 knots rounded UP to FP32, so that for an FP32
 //     coordinate u, (u >= kup[s]) is exactly (u >= U[s]) in real arithmetic;
 //     grid[G]  (G = 4 (n - p)) the span containing g / G, a starting guess for the span
@@ -40,6 +48,11 @@ constexpr int kRecHead = 4;
 __host__ __device__ constexpr int window_values(int q) { return q == 3 ? 16 : 8; }
 __host__ __device__ constexpr int qpair(int q) { return (q + 1) / 2 * 2; }
 __host__ __device__ constexpr int rec_stride(int q) { return ((kRecHead + q * qpair(q)) + 3) / 4 * 4; }
+// Whether a model's window rows hold power forms (FP32, degree classes 2..4) rather than
+// control points: degree class 5 (degree 4) keeps control points on every storage type,
+// since its rows share their fifth column with the next entry, which leaves no room for a
+// fifth coefficient of their own.
+__host__ __device__ constexpr bool power_rows(int q, int storage) { return storage == 1 && q <= 4; }
 
 // Debug builds (compiled with -DMFA_DEBUG) check every window, span-record, cell and
 // transfer-function index before its load.  A bad index sets a bit of the device's debug
@@ -75,6 +88,7 @@ struct AxisDev {
 struct ModelDev {
     AxisDev ax[3];
     const void* win;    // window array (see above)
+    const void* raw;    // the stored control points, plain [n_z][n_y][n_x] in the storage type
     int nxp, nyp, nzp;  // padded sizes n + kPad
     int q;              // Q = max degree + 1 (kernel template parameter)
     int storage;        // mfa_dtype of the window values
@@ -150,13 +164,17 @@ __host__ __device__ constexpr int batch_group_cardinal(int g) { return g / 12; }
 
 // launchers (defined in the .cu files), all asynchronous on `stream`
 cudaError_t launch_prep_axis(const double* d_knots, int n, int p, int q, float* kup, float* rec, int* grid,
-                             int G, cudaStream_t stream);
-cudaError_t launch_prep_window(const void* d_ctrl, int in_dtype, int storage, int nx, int ny, int nz, int q,
-                               void* win, cudaStream_t stream);
-cudaError_t launch_prep_cells(const void* win, int storage, int q, const int degree[3], const int nctrl[3],
-                              float2* cell, cudaStream_t stream);
-cudaError_t launch_prep_stats(const void* win, int storage, int nx, int ny, int nz, int q, int* d_stats,
+                             int G, double* coef64, cudaStream_t stream);
+// the stored control points (plain array in the storage type) from the input
+cudaError_t launch_prep_raw(const void* d_ctrl, int in_dtype, int storage, long long total, void* raw,
+                            cudaStream_t stream);
+// the window array from the stored control points (coef64: the x axis's FP64 span
+// coefficients for FP32 power rows, NULL for 16-bit rows)
+cudaError_t launch_prep_window(const void* raw, int storage, int nx, int ny, int nz, int q, const double* coef64,
+                               int px, void* win, cudaStream_t stream);
+cudaError_t launch_prep_cells(const void* raw, int storage, const int degree[3], const int nctrl[3], float2* cell,
                               cudaStream_t stream);
+cudaError_t launch_prep_stats(const void* raw, int storage, long long total, int* d_stats, cudaStream_t stream);
 cudaError_t launch_decode(const ModelDev& m, const float* pts, long long n, float* val, float* grad,
                           cudaStream_t stream);
 cudaError_t launch_spans(const ModelDev& m, const float* pts, long long n, int* spans, cudaStream_t stream);

@@ -43,7 +43,8 @@ __device__ double safe_div(double a, double b) { return b != 0.0 ? a / b : 0.0; 
 // coefficient vectors; each level multiplies the previous one by the linear factors
 // (u - U_i)/(U_{i+k} - U_i) and (U_{i+k+1} - u)/(U_{i+k+1} - U_{i+1}) written in t.
 template <int Q>
-__global__ void k_span_records(const double* __restrict__ U, int n, int p, float* __restrict__ rec)
+__global__ void k_span_records(const double* __restrict__ U, int n, int p, float* __restrict__ rec,
+                               double* __restrict__ coef64)
 {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n - p) return;
@@ -89,6 +90,10 @@ __global__ void k_span_records(const double* __restrict__ U, int n, int p, float
         for (int r = 0; r < QP; ++r)
             out[kRecHead + k * QP + r] = (r <= p && r < Q) ? __double2float_rn(T[r][k]) : 0.0f;
     for (int e = kRecHead + Q * QP; e < RS; ++e) out[e] = 0.0f;
+    // the same coefficients in FP64, [span][k][r] (Q x Q per span), for the power rows
+    if (coef64)
+        for (int k = 0; k < Q; ++k)
+            for (int r = 0; r < Q; ++r) coef64[(static_cast<long long>(idx) * Q + k) * Q + r] = r <= p ? T[r][k] : 0.0;
 }
 
 // ----------------------------------------------------------------------------------------
@@ -113,9 +118,38 @@ __device__ __forceinline__ unsigned short to16(double x, int storage)
     return __bfloat16_as_ushort(__double2bfloat16(x));
 }
 
-// The layer-pair window array (layout in mfa_internal.cuh), one entry per thread.
-__global__ void k_window(const void* __restrict__ ctrl, int in_dtype, int storage, int nx, int ny, int nz, int q,
-                         void* __restrict__ win)
+// The stored control points: one round-to-nearest-even step from the exact input value to
+// the storage type, into the plain array.
+__global__ void k_raw(const void* __restrict__ ctrl, int in_dtype, int storage, long long total, void* __restrict__ raw)
+{
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const double x = load_in(ctrl, in_dtype, e);
+        if (storage == 1)
+            static_cast<float*>(raw)[e] = __double2float_rn(x);
+        else
+            static_cast<unsigned short*>(raw)[e] = to16(x, storage);
+    }
+}
+
+// A stored control point as FP64 (exact), zero outside the grid.
+__device__ __forceinline__ double raw_at(const void* raw, int storage, int nx, int ny, int nz, int i, int j, int k)
+{
+    if (i >= nx || j >= ny || k >= nz) return 0.0;
+    const long long e = (static_cast<long long>(k) * ny + j) * nx + i;
+    if (storage == 1) return static_cast<double>(static_cast<const float*>(raw)[e]);
+    const unsigned short h = static_cast<const unsigned short*>(raw)[e];
+    return storage == 2 ? static_cast<double>(__half2float(__ushort_as_half(h)))
+                        : static_cast<double>(__uint_as_float(static_cast<unsigned>(h) << 16));
+}
+
+// The layer-pair window array (layout in mfa_internal.cuh), one entry per thread, from the
+// stored control points.  16-bit models copy them bit for bit.  FP32 models (coef64 = the
+// x axis's FP64 span coefficients, [span][c][r]) store each row's power form on its x span
+// i: W_c = sum_r c_{c,r} P[i + r], summed in FP64 and rounded once; entries with no span
+// (i >= n_x - p_x) are zero.
+__global__ void k_window(const void* __restrict__ raw, int storage, int nx, int ny, int nz, int q,
+                         const double* __restrict__ coef64, int px, void* __restrict__ win)
 {
     const int nxp = nx + kPad, nyp = ny + kPad, nzp = nz + kPad;
     const long long total = static_cast<long long>(nxp) * nyp * nzp;
@@ -125,18 +159,33 @@ __global__ void k_window(const void* __restrict__ ctrl, int in_dtype, int storag
         const long long jk = e / nxp;
         const int j = static_cast<int>(jk % nyp);
         const int k = static_cast<int>(jk / nyp);
-        // v[2a + r] = P[k + r][j][i + a]; for q == 3 also v[8 + a] = P[k + 2][j][i + a], then zeros
+        // P[r][a] = P[k + r][j][i + a] for the entry's layers r = 0..2 and columns a = 0..3
+        double P[3][4];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) P[r][a] = raw_at(raw, storage, nx, ny, nz, i + a, j, k + r);
+        if (coef64) {   // power rows of x span i (degree px: coefficients c = 0..px)
+            double W[3][4] = {};
+            if (i < nx - px) {
+                const double* c = coef64 + static_cast<long long>(i) * q * q;
+                for (int r = 0; r < 3; ++r)
+                    for (int cc = 0; cc <= px; ++cc) {
+                        double w = 0.0;
+                        for (int a = 0; a <= px; ++a) w += c[cc * q + a] * P[r][a];
+                        W[r][cc] = w;
+                    }
+            }
+            for (int r = 0; r < 3; ++r)
+                for (int a = 0; a < 4; ++a) P[r][a] = W[r][a];
+        }
+        // v[2a + r] = row a of layers r = 0, 1; for q == 3 also v[8 + a] = layer 2; then zeros
         double v[16];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                const int ia = i + a, kr = k + r;
-                const double x = (ia < nx && j < ny && kr < nz)
-                                     ? load_in(ctrl, in_dtype, (static_cast<long long>(kr) * ny + j) * nx + ia)
-                                     : 0.0;
-                if (r < 2) v[2 * a + r] = x; else v[8 + a] = x;
-            }
+            v[2 * a] = P[0][a];
+            v[2 * a + 1] = P[1][a];
+            v[8 + a] = P[2][a];
             v[12 + a] = 0.0;
         }
         const int nv = window_values(q);
@@ -160,9 +209,9 @@ __global__ void k_window(const void* __restrict__ ctrl, int in_dtype, int storag
 }
 
 // {min, max} over the (p_x+1)(p_y+1)(p_z+1) stored control points of each knot-span cell's
-// support, read from the window array (element 0 of entry (k, j, i) is P[k][j][i]).
-__global__ void k_cell_range(const void* __restrict__ win, int storage, int nv, int px, int py, int pz, int ncx,
-                             int ncy, int ncz, int nxp, int nyp, float2* __restrict__ cell)
+// support, read from the plain array.
+__global__ void k_cell_range(const void* __restrict__ raw, int storage, int nx, int ny, int nz, int px, int py, int pz,
+                             int ncx, int ncy, int ncz, float2* __restrict__ cell)
 {
     const long long total = static_cast<long long>(ncx) * ncy * ncz;
     for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
@@ -174,14 +223,7 @@ __global__ void k_cell_range(const void* __restrict__ win, int storage, int nv, 
         for (int c = 0; c <= pz; ++c)
             for (int b = 0; b <= py; ++b)
                 for (int a = 0; a <= px; ++a) {
-                    const long long w = (static_cast<long long>(k0 + c) * nyp + (j0 + b)) * nxp + (i0 + a);
-                    float v;
-                    if (storage == 1) {
-                        v = static_cast<const float*>(win)[nv * w];
-                    } else {
-                        const unsigned short h = static_cast<const unsigned short*>(win)[nv * w];
-                        v = storage == 2 ? __half2float(__ushort_as_half(h)) : __bfloat162float(__ushort_as_bfloat16(h));
-                    }
+                    const float v = static_cast<float>(raw_at(raw, storage, nx, ny, nz, i0 + a, j0 + b, k0 + c));
                     mn = fminf(mn, v);
                     mx = fmaxf(mx, v);
                 }
@@ -203,28 +245,18 @@ __global__ void k_stats_init(int* stats)
     stats[2] = f2ord(0.0f);
 }
 
-// min, max and max |P| over the stored values (first element of each window entry in the
-// unpadded region)
-__global__ void k_stats(const void* __restrict__ win, int storage, int nx, int ny, int nz, int q,
-                        int* __restrict__ stats)
+// min, max and max |P| over the stored values (the plain array)
+__global__ void k_stats(const void* __restrict__ raw, int storage, long long total, int* __restrict__ stats)
 {
-    const int nxp = nx + kPad, nyp = ny + kPad;
-    const long long nv = window_values(q);
-    const long long total = static_cast<long long>(nx) * ny * nz;
     float mn = INFINITY, mx = -INFINITY, ma = 0.0f;
     for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
          e += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int i = static_cast<int>(e % nx);
-        const long long jk = e / nx;
-        const int j = static_cast<int>(jk % ny);
-        const int k = static_cast<int>(jk / ny);
-        const long long w = (static_cast<long long>(k) * nyp + j) * nxp + i;
         float v;
         if (storage == 1) {
-            v = static_cast<const float*>(win)[nv * w];
+            v = static_cast<const float*>(raw)[e];
         } else {
-            const unsigned short b = static_cast<const unsigned short*>(win)[nv * w];
-            v = storage == 2 ? __half2float(__ushort_as_half(b)) : __bfloat162float(__ushort_as_bfloat16(b));
+            const unsigned short b = static_cast<const unsigned short*>(raw)[e];
+            v = storage == 2 ? __half2float(__ushort_as_half(b)) : __uint_as_float(static_cast<unsigned>(b) << 16);
         }
         mn = fminf(mn, v);
         mx = fmaxf(mx, v);
@@ -245,7 +277,7 @@ __global__ void k_stats(const void* __restrict__ win, int storage, int nx, int n
 }  // namespace
 
 cudaError_t launch_prep_axis(const double* d_knots, int n, int p, int q, float* kup, float* rec, int* grid, int G,
-                             cudaStream_t stream)
+                             double* coef64, cudaStream_t stream)
 {
     const int m = n + p + 1;
     k_knots_up<<<(m + 255) / 256, 256, 0, stream>>>(d_knots, m, kup);
@@ -253,45 +285,50 @@ cudaError_t launch_prep_axis(const double* d_knots, int n, int p, int q, float* 
     const int spans = n - p;
     const int blocks = (spans + 127) / 128;
     switch (q) {
-    case 2: k_span_records<2><<<blocks, 128, 0, stream>>>(d_knots, n, p, rec); break;
-    case 3: k_span_records<3><<<blocks, 128, 0, stream>>>(d_knots, n, p, rec); break;
-    case 4: k_span_records<4><<<blocks, 128, 0, stream>>>(d_knots, n, p, rec); break;
-    case 5: k_span_records<5><<<blocks, 128, 0, stream>>>(d_knots, n, p, rec); break;
+    case 2: k_span_records<2><<<blocks, 128, 0, stream>>>(d_knots, n, p, rec, coef64); break;
+    case 3: k_span_records<3><<<blocks, 128, 0, stream>>>(d_knots, n, p, rec, coef64); break;
+    case 4: k_span_records<4><<<blocks, 128, 0, stream>>>(d_knots, n, p, rec, coef64); break;
+    case 5: k_span_records<5><<<blocks, 128, 0, stream>>>(d_knots, n, p, rec, coef64); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_prep_window(const void* d_ctrl, int in_dtype, int storage, int nx, int ny, int nz, int q,
+static int grid_blocks(long long total, long long cap)
+{
+    const long long want = (total + 255) / 256;
+    return static_cast<int>(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+cudaError_t launch_prep_raw(const void* d_ctrl, int in_dtype, int storage, long long total, void* raw,
+                            cudaStream_t stream)
+{
+    k_raw<<<grid_blocks(total, 65536), 256, 0, stream>>>(d_ctrl, in_dtype, storage, total, raw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_window(const void* raw, int storage, int nx, int ny, int nz, int q, const double* coef64, int px,
                                void* win, cudaStream_t stream)
 {
     const long long total = static_cast<long long>(nx + kPad) * (ny + kPad) * (nz + kPad);
-    const long long want = (total + 255) / 256;
-    const int blocks = static_cast<int>(want < 65536 ? want : 65536);
-    k_window<<<blocks, 256, 0, stream>>>(d_ctrl, in_dtype, storage, nx, ny, nz, q, win);
+    k_window<<<grid_blocks(total, 65536), 256, 0, stream>>>(raw, storage, nx, ny, nz, q, coef64, px, win);
     return cudaGetLastError();
 }
 
-cudaError_t launch_prep_cells(const void* win, int storage, int q, const int degree[3], const int nctrl[3],
-                              float2* cell, cudaStream_t stream)
+cudaError_t launch_prep_cells(const void* raw, int storage, const int degree[3], const int nctrl[3], float2* cell,
+                              cudaStream_t stream)
 {
     const int ncx = nctrl[0] - degree[0], ncy = nctrl[1] - degree[1], ncz = nctrl[2] - degree[2];
     const long long total = static_cast<long long>(ncx) * ncy * ncz;
-    const long long want = (total + 255) / 256;
-    const int blocks = static_cast<int>(want < 8192 ? want : 8192);
-    k_cell_range<<<blocks, 256, 0, stream>>>(win, storage, window_values(q), degree[0], degree[1], degree[2], ncx, ncy,
-                                             ncz, nctrl[0] + kPad, nctrl[1] + kPad, cell);
+    k_cell_range<<<grid_blocks(total, 8192), 256, 0, stream>>>(raw, storage, nctrl[0], nctrl[1], nctrl[2], degree[0],
+                                                              degree[1], degree[2], ncx, ncy, ncz, cell);
     return cudaGetLastError();
 }
 
-cudaError_t launch_prep_stats(const void* win, int storage, int nx, int ny, int nz, int q, int* d_stats,
-                              cudaStream_t stream)
+cudaError_t launch_prep_stats(const void* raw, int storage, long long total, int* d_stats, cudaStream_t stream)
 {
     k_stats_init<<<1, 1, 0, stream>>>(d_stats);
-    const long long total = static_cast<long long>(nx) * ny * nz;
-    const long long want = (total + 255) / 256;
-    const int blocks = static_cast<int>(want < 4096 ? want : 4096);
-    k_stats<<<blocks, 256, 0, stream>>>(win, storage, nx, ny, nz, q, d_stats);
+    k_stats<<<grid_blocks(total, 4096), 256, 0, stream>>>(raw, storage, total, d_stats);
     return cudaGetLastError();
 }
 

@@ -268,12 +268,11 @@ __device__ __forceinline__ float4 march_pipelined(const ModelDev& M, const Rende
         if constexpr (SKIP) {
             if (!cell_vis) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
-        float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];
-        record_basis<Q>(cx.rec, u, Nx, Dx);
+        float Ny[Q], Dy[Q], Nz[Q], Dz[Q];
+        const XIn<Q, STORAGE> X = xin_record<Q, STORAGE>(cx.rec, u);
         record_basis<Q>(cy.rec, v, Ny, Dy);
         record_basis<Q>(cz.rec, w, Nz, Dz);
-        float4 q = contract<Q, STORAGE>(M, cx.s - M.ax[0].p, cy.s - M.ax[1].p, cz.s - M.ax[2].p, Nx, Dx, Ny, Dy,
-                                        Nz, Dz);
+        float4 q = contract<Q, STORAGE>(M, cx.s - M.ax[0].p, cy.s - M.ax[1].p, cz.s - M.ax[2].p, X, Ny, Dy, Nz, Dz);
         q.y *= cx.rec[1];
         q.z *= cy.rec[1];
         q.w *= cz.rec[1];
@@ -343,7 +342,7 @@ __device__ __forceinline__ float4 march_cardinal(const ModelDev& M, const Render
         const float m = static_cast<float>(M.ax[a].n - M.ax[a].p);
         om[a] = o[a] * m;
         dm[a] = d[a] * m;
-        gs[a] = m * Cardinal<Q>::kGradScale;
+        gs[a] = m * (a == 0 ? Cardinal<Q>::template gradx_scale<STORAGE>() : Cardinal<Q>::template gradyz_scale<STORAGE>());
     }
     CardAxis cx{ -INFINITY, 0, false }, cy{ -INFINITY, 0, false }, cz{ -INFINITY, 0, false };
     int base = 0;
@@ -382,18 +381,19 @@ __device__ __forceinline__ float4 march_cardinal(const ModelDev& M, const Render
         if constexpr (SKIP) {
             if (!cell_vis) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
-        float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];
-        if (cx.edge | cy.edge | cz.edge) {
-            card_basis<Q>(M.ax[0], cx, tx, Nx, Dx);
+        float Ny[Q], Dy[Q], Nz[Q], Dz[Q];
+        XIn<Q, STORAGE> X;
+        if (card_edge<Q, STORAGE>(cx, cy, cz)) {
+            X = xin_card<Q, STORAGE>(M.ax[0], cx, tx);
             card_basis<Q>(M.ax[1], cy, ty, Ny, Dy);
             card_basis<Q>(M.ax[2], cz, tz, Nz, Dz);
         } else {
-            cardinal_basis<Q>(tx, Nx, Dx);
+            X = xin_cardinal<Q, STORAGE>(tx);
             cardinal_basis<Q>(ty, Ny, Dy);
             cardinal_basis<Q>(tz, Nz, Dz);
         }
-        float4 q = contract_at<Q, STORAGE>(M, base, Nx, Dx, Ny, Dy, Nz, Dz);
-        q.x *= Cardinal<Q>::kValScale;
+        float4 q = contract_at<Q, STORAGE>(M, base, X, Ny, Dy, Nz, Dz);
+        q.x *= Cardinal<Q>::template val_scale<STORAGE>();
         q.y *= gs[0];
         q.z *= gs[1];
         q.w *= gs[2];

@@ -90,11 +90,11 @@ __device__ __forceinline__ float4 march(const ModelDev& M, const RenderScalars& 
             if constexpr (MODE == 1) {
                 q = query2_rec<Q, STORAGE>(M, cx.rec, cy.rec, cz.rec, u, v, w, i0, j0, k0);
             } else {
-                float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];
-                record_basis<Q>(cx.rec, u, Nx, Dx);
+                float Ny[Q], Dy[Q], Nz[Q], Dz[Q];
+                const XIn<Q, STORAGE> X = xin_record<Q, STORAGE>(cx.rec, u);
                 record_basis<Q>(cy.rec, v, Ny, Dy);
                 record_basis<Q>(cz.rec, w, Nz, Dz);
-                q = contract<Q, STORAGE>(M, i0, j0, k0, Nx, Dx, Ny, Dy, Nz, Dz);
+                q = contract<Q, STORAGE>(M, i0, j0, k0, X, Ny, Dy, Nz, Dz);
                 q.y *= cx.rec[1];
                 q.z *= cy.rec[1];
                 q.w *= cz.rec[1];
@@ -152,8 +152,8 @@ __device__ __forceinline__ float4 march(const ModelDev& M, const RenderScalars& 
 // into segments of S sample indices; for each segment the warp computes the bounding box
 // of its rays' sample positions (positions are monotone in the sample index, so the
 // segment's end points bound it), turns the box into a range of knot spans per axis, and
-// copies the control-point windows that range needs into a kBrick^3 brick of shared
-// memory -- converted to FP32 once, whatever the storage type.  Every sample of the
+// copies the stored control points that range needs (rows of the plain array) into a
+// kBrick^3 brick of shared memory -- converted to FP32 once, whatever the storage type.  Every sample of the
 // segment then reads its 16 support rows from the brick at fixed offsets (no per-sample
 // conversion, no 64-bit address arithmetic).  S adapts so the range fits the brick (halved
 // when it does not, doubled back after a segment that fits); a segment of one sample that
@@ -162,20 +162,26 @@ constexpr int kBrick = 8;
 constexpr int kBrickFloats4 = kBrick * kBrick * kBrick;   // 8 KB per warp
 constexpr int kSegMax = 64;
 
-// Row (k, j) of window entry idx, P[k][j][i..i+3], as FP32 (the even members of the
-// entry's column pairs).
-template <int Q, int STORAGE>
-__device__ __forceinline__ float4 window_f32(const void* win, long long idx)
+// Row P[k][j][i..i+3] of the stored control points as FP32 (zero past the ends).
+template <int STORAGE>
+__device__ __forceinline__ float4 raw_row(const ModelDev& M, int i, int j, int k)
 {
-    if constexpr (STORAGE == 1) {
-        const float4* e = static_cast<const float4*>(win) + (window_values(Q) / 4) * idx;
-        const float4 lo = __ldg(e), hi = __ldg(e + 1);
-        return make_float4(lo.x, lo.z, hi.x, hi.z);
-    } else {
-        const uint4 w = __ldg(static_cast<const uint4*>(win) + (window_values(Q) / 8) * idx);
-        using P = Pair16<4, STORAGE == 3>;
-        return make_float4(P::cvt(w.x).x, P::cvt(w.y).x, P::cvt(w.z).x, P::cvt(w.w).x);
+    const int nx = M.ax[0].n, ny = M.ax[1].n, nz = M.ax[2].n;
+    float v[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        v[a] = 0.0f;
+        if (i + a < nx && j < ny && k < nz) {
+            const long long e = (static_cast<long long>(k) * ny + j) * nx + i + a;
+            if constexpr (STORAGE == 1) {
+                v[a] = __ldg(static_cast<const float*>(M.raw) + e);
+            } else {
+                const unsigned short h = __ldg(static_cast<const unsigned short*>(M.raw) + e);
+                v[a] = STORAGE == 2 ? __half2float(__ushort_as_half(h)) : __uint_as_float(static_cast<unsigned>(h) << 16);
+            }
+        }
     }
+    return make_float4(v[0], v[1], v[2], v[3]);
 }
 
 // Sum-factorised contraction over a support held in a shared-memory brick (rows at fixed
@@ -230,7 +236,6 @@ __device__ __forceinline__ float4 march_bricked(const ModelDev& M, const RenderS
     const ShadeParams S = shade_params(P, d);
     AxisCache<Q> cx, cy, cz;
     cx.s = cy.s = cz.s = -1;
-    const int nxp = M.nxp, nyp = M.nyp;
 
     auto pos = [&](int k, float (&u)[3]) {
         const float t = fmaf(static_cast<float>(k) + 0.5f, dt, t0);
@@ -285,10 +290,7 @@ __device__ __forceinline__ float4 march_bricked(const ModelDev& M, const RenderS
             for (int e = lane; e < total; e += 32) {
                 const int ex = e % ext[0], r = e / ext[0];
                 const int ey = r % ext[1], ez = r / ext[1];
-                long long gidx =
-                    (static_cast<long long>(org[2] + ez) * nyp + (org[1] + ey)) * nxp + (org[0] + ex);
-                MFA_DBG_INDEX(M.dbg, gidx, static_cast<long long>(nxp) * nyp * M.nzp, kDbgWindow);
-                brick[(ez * kBrick + ey) * kBrick + ex] = window_f32<Q, STORAGE>(M.win, gidx);
+                brick[(ez * kBrick + ey) * kBrick + ex] = raw_row<STORAGE>(M, org[0] + ex, org[1] + ey, org[2] + ez);
             }
             __syncwarp();
         }
@@ -299,7 +301,7 @@ __device__ __forceinline__ float4 march_bricked(const ModelDev& M, const RenderS
                 axis_update<Q>(M.ax[0], cx, u[0]);
                 axis_update<Q>(M.ax[1], cy, u[1]);
                 axis_update<Q>(M.ax[2], cz, u[2]);
-                float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];
+                float Nx[Q], Dx[Q], Ny[Q], Dy[Q], Nz[Q], Dz[Q];   // the brick holds control points
                 record_basis<Q>(cx.rec, u[0], Nx, Dx);
                 record_basis<Q>(cy.rec, u[1], Ny, Dy);
                 record_basis<Q>(cz.rec, u[2], Nz, Dz);
@@ -310,7 +312,8 @@ __device__ __forceinline__ float4 march_bricked(const ModelDev& M, const RenderS
                     const int rz = min(max(cz.s - M.ax[2].p - org[2], 0), kBrick - Q);
                     q = contract_brick<Q>(brick + (rz * kBrick + ry) * kBrick + rx, Nx, Dx, Ny, Dy, Nz, Dz);
                 } else {
-                    q = contract<Q, STORAGE>(M, cx.s - M.ax[0].p, cy.s - M.ax[1].p, cz.s - M.ax[2].p, Nx, Dx, Ny, Dy,
+                    q = contract<Q, STORAGE>(M, cx.s - M.ax[0].p, cy.s - M.ax[1].p, cz.s - M.ax[2].p,
+                                             xin_record<Q, STORAGE>(cx.rec, u[0]), Ny, Dy,
                                              Nz, Dz);
                 }
                 q.y *= cx.rec[1];

@@ -396,7 +396,8 @@ def test_render_cardinal_matches_oracle(mfa, orc, degree, nctrl, cam, storage):
 
 
 def test_cardinal_flag(mfa, orc):
-    """Which models take the cardinal path: uniform knots (within 1e-12) and one degree."""
+    """Which models take the cardinal path: exactly the clamped uniform knots (i/(n-p) in
+    FP64) and one degree; knots off by even 1e-13 take the record path."""
     rng = np.random.default_rng(31)
     P = rng.standard_normal((9, 8, 7))
     n = (7, 8, 9)
@@ -405,7 +406,7 @@ def test_cardinal_flag(mfa, orc):
     assert mfa.Model((3, 3, 3), n, uni, P).info()["cardinal"]
     near = [k.copy() for k in uni]
     near[1][5] += 1e-13
-    assert mfa.Model((3, 3, 3), n, near, P).info()["cardinal"]
+    assert not mfa.Model((3, 3, 3), n, near, P).info()["cardinal"]
     off = [k.copy() for k in uni]
     off[1][5] += 1e-7
     assert not mfa.Model((3, 3, 3), n, off, P).info()["cardinal"]

@@ -147,3 +147,56 @@ def test_refinement_converges_through_a_sharp_step(orc):
                     continue
                 o, d = orc.ray(cam, W, H, col, row)
                 assert abs(m.eval(np.asarray(o) + depth[row, col] * np.asarray(d))[0] - 0.5) <= tol
+
+
+def test_iso_check_accounts_only_for_near_ties(orc):
+    """The checker the GPU isosurface tests use (tests/iso_check.py): the oracle against
+    itself has nothing to explain; planted disagreements far from any near-tie -- a hit
+    turned into a miss, a hit moved to another bracket, a miss turned into a hit -- are all
+    reported; a disagreement at a crossing whose sample sits on iso is explained."""
+    import iso_check
+    rng = np.random.default_rng(23)
+    deg, n = (3, 3, 3), (12, 11, 13)
+    knots = [knots_uniform(n[a], deg[a]) for a in range(3)]
+    P = synth.sample_ctrl(synth.GaussianSum.draw(rng, 5), knots, deg, rng, 0.01)
+    m = orc.Model(deg, n, knots, P)
+    W, H, ns = 20, 16, 40
+    iso = float(np.percentile(P, 60))
+    table = synth.ramp_tf(16, 1.0)
+    _, depth, _ = orc.render_iso(m, CAM, table, W, H, ns, iso)
+    depth = depth.reshape(-1)
+    bad, ties = iso_check.explain(orc, m, CAM, W, H, ns, iso, depth, depth)
+    assert bad == [] and ties == 0
+
+    # pixels whose every sample is far from iso (no near-tie anywhere on the ray)
+    pmax = float(np.abs(P).max())
+    clear_hit, clear_miss = [], []
+    for p in range(W * H):
+        s = iso_check._samples(orc, m, CAM, W, H, ns, iso, p)
+        if s is None or np.min(np.abs(s[5])) < 1e-3 * pmax:
+            continue
+        (clear_hit if np.isfinite(depth[p]) else clear_miss).append(p)
+    assert len(clear_hit) >= 3 and len(clear_miss) >= 1
+    planted = depth.copy()
+    planted[clear_hit[0]] = np.inf                                      # hit -> miss
+    o, d = orc.ray(CAM, W, H, clear_hit[1] % W, clear_hit[1] // W)
+    _, t0, t1 = orc.clip_unit_box(o, d)
+    planted[clear_hit[1]] = t1 - 0.25 * (t1 - t0) / ns                  # hit -> last bracket
+    o, d = orc.ray(CAM, W, H, clear_miss[0] % W, clear_miss[0] // W)
+    _, t0, t1 = orc.clip_unit_box(o, d)
+    planted[clear_miss[0]] = 0.5 * (t0 + t1)                            # miss -> hit
+    bad, ties = iso_check.explain(orc, m, CAM, W, H, ns, iso, planted, depth)
+    assert sorted(bad) == sorted([clear_hit[0], clear_hit[1], clear_miss[0]]) and ties == 0
+
+    # iso placed exactly on one sample's value: that crossing is a near-tie
+    p = clear_hit[2]
+    s = iso_check._samples(orc, m, CAM, W, H, ns, iso, p)
+    k = int(np.flatnonzero(np.sign(s[5][1:]) != np.sign(s[5][:-1]))[0]) + 1
+    iso2 = iso + s[5][k]
+    _, depth2, _ = orc.render_iso(m, CAM, table, W, H, ns, iso2)
+    depth2 = depth2.reshape(-1)
+    assert np.isfinite(depth2[p])
+    missed = depth2.copy()
+    missed[p] = np.inf
+    bad, ties = iso_check.explain(orc, m, CAM, W, H, ns, iso2, missed, depth2)
+    assert bad == [] and ties == 1
