@@ -176,9 +176,8 @@ template <int Q, int STORAGE, bool CARD>
 __global__ void __launch_bounds__(kIsoThreads, Q <= 4 ? 4 : 3)
     k_render_iso(ModelDev M, const __grid_constant__ RenderParams P, float iso, float* __restrict__ depth, int shape)
 {
-    __shared__ float4 tf[kTfMax + 1];
-    for (int i = threadIdx.x; i < P.s.tf_n; i += kIsoThreads) tf[i] = P.tf[i];
-    if (threadIdx.x == 0 && P.s.tf_n == 1) tf[1] = P.tf[0];   // the branch-free lerp reads row 1
+    __shared__ float4 tf[kTfSmem];
+    stage_tf(tf, P.tf, P.s.tf_n);
     __syncthreads();
 
     int col, row;

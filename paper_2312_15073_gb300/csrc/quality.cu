@@ -47,9 +47,8 @@ __device__ __forceinline__ float4 ml_query(float fm, float alpha, float inv_den,
 __global__ void __launch_bounds__(kMlThreads) k_render_ml(const __grid_constant__ RenderParams P, float fm,
                                                           float alpha, int shape)
 {
-    __shared__ float4 tf[kTfMax + 1];
-    for (int i = threadIdx.x; i < P.s.tf_n; i += kMlThreads) tf[i] = P.tf[i];
-    if (threadIdx.x == 0 && P.s.tf_n == 1) tf[1] = P.tf[0];   // the branch-free lerp reads row 1
+    __shared__ float4 tf[kTfSmem];
+    stage_tf(tf, P.tf, P.s.tf_n);
     __syncthreads();
 
     int col, row;

@@ -103,22 +103,37 @@ __device__ __forceinline__ void axis_update(const AxisDev& A, AxisCache<Q>& C, f
     C.s = s;
 }
 
-// Colour of one sample, without branches: transfer-function lerp (the table has at least
-// two rows in shared memory; a one-row table is duplicated) and, when `shading`, Phong
-// with a headlight.  Same arithmetic as the per-sample code of march().
+// The transfer function in shared memory: row r at tf[2r] and its forward difference
+// row r+1 - row r at tf[2r + 1] (zero for the last row), so a lerp is one packed FMA per two
+// channels; the difference is the same FP32 subtraction the lerp would make per sample.
+// Every thread of the CTA calls it; the caller synchronises before use.
+constexpr int kTfSmem = 2 * kTfMax;
+__device__ __forceinline__ void stage_tf(float4* __restrict__ tf, const float4* __restrict__ src, int n)
+{
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        const float4 a = src[r], b = r + 1 < n ? src[r + 1] : a;
+        tf[2 * r] = a;
+        tf[2 * r + 1] = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, b.w - a.w);
+    }
+}
+
+// Colour of one sample, without branches: transfer-function lerp and, when `shading`,
+// Phong with a headlight.  The table coordinate is t = (f - vmin)/(vmax - vmin) with f the
+// query's value times vscale (the cardinal path's basis scale), folded into one FMA:
+// t = f vmul + vadd.
 struct ShadeParams {
-    float vmin, inv_range, tscale, ka, kd, ks, shin, gtiny2, lx, ly, lz;
+    float vmul, vadd, tscale, ka, kd, ks, shin, gtiny2, lx, ly, lz;
     int tf_last, shading;
 #ifdef MFA_DEBUG
     unsigned* dbg;
 #endif
 };
 
-__device__ __forceinline__ ShadeParams shade_params(const RenderScalars& P, const float (&d)[3])
+__device__ __forceinline__ ShadeParams shade_params(const RenderScalars& P, const float (&d)[3], float vscale = 1.0f)
 {
     ShadeParams S;
-    S.vmin = P.vmin;
-    S.inv_range = P.inv_range;
+    S.vmul = P.inv_range * vscale;
+    S.vadd = -P.vmin * P.inv_range;
     S.tscale = static_cast<float>(P.tf_n - 1);
     S.tf_last = max(P.tf_n - 2, 0);
     S.shading = P.shading;
@@ -138,15 +153,15 @@ __device__ __forceinline__ ShadeParams shade_params(const RenderScalars& P, cons
 
 __device__ __forceinline__ float4 sample_colour(const float4* __restrict__ tf, const ShadeParams& S, const float4 q)
 {
-    const float tt = clamp01((q.x - S.vmin) * S.inv_range);
+    const float tt = clamp01(fmaf(q.x, S.vmul, S.vadd));
     const float xx = tt * S.tscale;
     int i0 = min(static_cast<int>(xx), S.tf_last);
-    MFA_DBG_INDEX(S.dbg, i0, S.tf_last + 1, kDbgTf);   // rows i0 and i0 + 1 are read
+    MFA_DBG_INDEX(S.dbg, i0, S.tf_last + 1, kDbgTf);   // row i0 and its difference are read
     const float wt = xx - static_cast<float>(i0);
-    const float4 c0 = tf[i0], c1 = tf[i0 + 1];
+    const float4 c0 = tf[2 * i0], dc = tf[2 * i0 + 1];
     // c = c0 + wt (c1 - c0), two channels per packed instruction
-    const f2 w2 = pk2(wt, wt), rg0 = pk2(c0.x, c0.y), ba0 = pk2(c0.z, c0.w);
-    const f2 rg = fma2(w2, sub2(pk2(c1.x, c1.y), rg0), rg0), ba = fma2(w2, sub2(pk2(c1.z, c1.w), ba0), ba0);
+    const f2 w2 = pk2(wt, wt);
+    const f2 rg = fma2(w2, pk2(dc.x, dc.y), pk2(c0.x, c0.y)), ba = fma2(w2, pk2(dc.z, dc.w), pk2(c0.z, c0.w));
     float4 c;
     upk2(rg, c.x, c.y);
     upk2(ba, c.z, c.w);
@@ -335,7 +350,7 @@ __device__ __forceinline__ float4 march_cardinal(const ModelDev& M, const Render
         block_range(*seg, o, d, t0, dt, ns, kb, ke);
         if (kb >= ke) return acc;
     }
-    const ShadeParams S = shade_params(P, d);
+    const ShadeParams S = shade_params(P, d, Cardinal<Q>::template val_scale<STORAGE>());
     float om[3], dm[3], gs[3];   // ray in span units, gradient scale per axis
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -392,8 +407,7 @@ __device__ __forceinline__ float4 march_cardinal(const ModelDev& M, const Render
             cardinal_basis<Q>(ty, Ny, Dy);
             cardinal_basis<Q>(tz, Nz, Dz);
         }
-        float4 q = contract_at<Q, STORAGE>(M, base, X, Ny, Dy, Nz, Dz);
-        q.x *= Cardinal<Q>::template val_scale<STORAGE>();
+        float4 q = contract_at<Q, STORAGE>(M, base, X, Ny, Dy, Nz, Dz);   // value left unscaled (S.vmul)
         q.y *= gs[0];
         q.z *= gs[1];
         q.w *= gs[2];

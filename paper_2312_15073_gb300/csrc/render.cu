@@ -107,13 +107,13 @@ __device__ __forceinline__ float4 march(const ModelDev& M, const RenderScalars& 
         if (tf_n > 1) {
             const float xx = tt * tscale;
             int i0 = min(static_cast<int>(xx), tf_n - 2);
-            MFA_DBG_INDEX(P.dbg, i0, tf_n - 1, kDbgTf);   // rows i0 and i0 + 1 are read
+            MFA_DBG_INDEX(P.dbg, i0, tf_n - 1, kDbgTf);   // row i0 and its difference are read
             const float wt = xx - static_cast<float>(i0);
-            const float4 c0 = tf[i0], c1 = tf[i0 + 1];
-            c.x = fmaf(wt, c1.x - c0.x, c0.x);
-            c.y = fmaf(wt, c1.y - c0.y, c0.y);
-            c.z = fmaf(wt, c1.z - c0.z, c0.z);
-            c.w = fmaf(wt, c1.w - c0.w, c0.w);
+            const float4 c0 = tf[2 * i0], dc = tf[2 * i0 + 1];   // row and difference (stage_tf)
+            c.x = fmaf(wt, dc.x, c0.x);
+            c.y = fmaf(wt, dc.y, c0.y);
+            c.z = fmaf(wt, dc.z, c0.z);
+            c.w = fmaf(wt, dc.w, c0.w);
         } else {
             c = tf[0];
         }
@@ -347,9 +347,8 @@ template <int Q, int STORAGE, int MODE>
 __global__ void __launch_bounds__(kThreads, min_blocks<Q, MODE == 6 || MODE == 7>()) k_render(ModelDev M, const __grid_constant__ RenderParams P,
                                                                  int shape)
 {
-    __shared__ float4 tf[kTfMax + 1];
-    for (int i = threadIdx.x; i < P.s.tf_n; i += kThreads) tf[i] = P.tf[i];
-    if (threadIdx.x == 0 && P.s.tf_n == 1) tf[1] = P.tf[0];   // the branch-free lerp reads row 1
+    __shared__ float4 tf[kTfSmem];
+    stage_tf(tf, P.tf, P.s.tf_n);
     __syncthreads();
 
     int col, row;
@@ -484,9 +483,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks<Q, MODE == 6>())
     k_render_segments(ModelDev M, const __grid_constant__ RenderParams P, int shape, int gx, int gy, int gz,
                       float4* __restrict__ partial)
 {
-    __shared__ float4 tf[kTfMax + 1];
-    for (int i = threadIdx.x; i < P.s.tf_n; i += kThreads) tf[i] = P.tf[i];
-    if (threadIdx.x == 0 && P.s.tf_n == 1) tf[1] = P.tf[0];   // the branch-free lerp reads row 1
+    __shared__ float4 tf[kTfSmem];
+    stage_tf(tf, P.tf, P.s.tf_n);
     __syncthreads();
 
     int col, row;
@@ -599,7 +597,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<Q, CARD>()) k_render_batc
                                                                        int shape)
 {
     __shared__ BatchItem item;
-    __shared__ float4 tf[kTfMax + 1];
+    __shared__ float4 tf[kTfSmem];
     __shared__ int s_tile, s_idx;
     BatchHead* head = table + group;
     const BatchItem* items =
@@ -632,8 +630,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<Q, CARD>()) k_render_batc
             int* dst = reinterpret_cast<int*>(&item);
             for (int e = threadIdx.x; e < static_cast<int>(sizeof(BatchItem) / sizeof(int)); e += kThreads) dst[e] = src[e];
             __syncthreads();
-            for (int e = threadIdx.x; e < item.s.tf_n; e += kThreads) tf[e] = item.tf[e];
-            if (threadIdx.x == 0 && item.s.tf_n == 1) tf[1] = item.tf[0];   // the lerp reads row 1
+            stage_tf(tf, item.tf, item.s.tf_n);
             cur = i;
             __syncthreads();
         }
