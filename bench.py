@@ -492,11 +492,13 @@ def run_ours(args):
         line["batch"] = batch_throughput(mfa, torch)
         line["empty_space"] = empty_space(mfa, torch, spec, model, job)
     if ws == 1 and not args.no_serve:
-        line["serving"] = dict(run_serve(mfa, rates=args.serve_rates, duration=args.serve_duration),
+        line["serving"] = dict(run_serve(mfa, rates=args.serve_rates, duration=args.serve_duration,
+                                         min_requests=args.serve_requests),
                                note="Poisson requests (sides 512..2048, 512..2048 samples) on 8 resident degree-3 "
-                                    "models; served = FP16 control points, up to 8 requests in flight on priority "
-                                    "streams; plain = FP32 control points, one request at a time in arrival order; "
-                                    "latency from scheduled arrival to completion")
+                                    "models; served = FP16 control points (FP32 window values), up to 16 requests "
+                                    "in flight drawn tile by tile from the device work queue; plain = FP32 control "
+                                    "points, one request at a time in arrival order, one launch each; latency from "
+                                    "scheduled arrival to completion")
     if ws == 1 and not args.no_cpu_baseline:
         r_rate, d_rate, info = oracle_rates(wl, budget_s=args.cpu_budget)
         cpu_step_s = samples_per_frame / r_rate + n_pts / d_rate
@@ -787,12 +789,15 @@ def iso_throughput(mfa, torch, spec, model, job, tf, frames=5):
 
 def storage_throughput(mfa, torch, spec, job, tf, frames=5):
     """Samples/s of the same frame with FP32, FP16 and BF16 control points (the same
-    FP64-rounded values, FP32 accumulation)."""
+    FP64-rounded values, FP32 accumulation); 16-bit models with their own 16-bit window
+    values and with FP32 window values (MFA_WINDOW_F32)."""
     out = {}
     W, H, NS = job.width, job.height, job.n_samples
     img = torch.empty((H, W, 4), device="cuda")
-    for storage, name in ((mfa.MFA_F32, "f32"), (mfa.MFA_F16, "f16"), (mfa.MFA_BF16, "bf16")):
-        m = mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl, storage=storage)
+    for storage, window, name in ((mfa.MFA_F32, 0, "f32"), (mfa.MFA_F16, 0, "f16"), (mfa.MFA_BF16, 0, "bf16"),
+                                  (mfa.MFA_F16, mfa.MFA_WINDOW_F32, "f16_f32window"),
+                                  (mfa.MFA_BF16, mfa.MFA_WINDOW_F32, "bf16_f32window")):
+        m = mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl, storage=storage, window=window)
         cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
         mfa.render(m, job.camera, tf, W, H, NS, out=img)
         torch.cuda.synchronize()
@@ -814,10 +819,12 @@ def storage_throughput(mfa, torch, spec, job, tf, frames=5):
 # ------------------------------------------------------------------------------------------
 
 def serve_models(mfa, size_scale=1.0):
-    """The 8 serving models twice: FP16 storage (served path) and FP32 (plain path)."""
+    """The 8 serving models twice: FP16 control points with FP32 window values (served
+    path) and FP32 (plain path)."""
     import synth
     specs = synth.config5_models(size_scale)
-    f16 = [mfa.Model(s.degree, s.nctrl, s.knots, s.ctrl64, storage=mfa.MFA_F16) for s in specs]
+    f16 = [mfa.Model(s.degree, s.nctrl, s.knots, s.ctrl64, storage=mfa.MFA_F16, window=mfa.MFA_WINDOW_F32)
+           for s in specs]
     f32 = [mfa.Model(s.degree, s.nctrl, s.knots, s.ctrl64, storage=mfa.MFA_F32) for s in specs]
     return specs, f16, f32
 
@@ -862,7 +869,8 @@ def serve_stream(mfa, server, models, tf, stream):
     return lat, done, rejected, wall
 
 
-def run_serve(mfa, rates, duration, size_scale=1.0, max_slots=8):
+def run_serve(mfa, rates, duration, size_scale=1.0, max_slots=16, min_requests=0):
+    """Each rate's stream lasts max(duration, min_requests / rate) seconds of arrivals."""
     import synth
     specs, f16, f32 = serve_models(mfa, size_scale)
     tf = mfa.transfer_fn(synth.ramp_tf(256, 0.05), shading=True)
@@ -874,10 +882,10 @@ def run_serve(mfa, rates, duration, size_scale=1.0, max_slots=8):
         return v[min(len(v) - 1, int(math.ceil(q * len(v))) - 1)] if v else None
 
     for rate in rates:
-        stream = synth.config5_requests(rate, duration)
+        stream = synth.config5_requests(rate, max(duration, min_requests / rate))
         row = {"requests": len(stream)}
-        for name, models, cfg in (("served_f16", f16, dict(max_slots=max_slots, priority_levels=4)),
-                                  ("plain_f32", f32, dict(max_slots=1, priority_levels=1))):
+        for name, models, cfg in (("served_f16", f16, dict(max_slots=max_slots, mode=0)),
+                                  ("plain_f32", f32, dict(max_slots=1, priority_levels=1, mode=1))):
             srv = mfa.Server(hbm_budget_bytes=budget, max_queue=4096, **cfg)
             lat, done, rej, wall = serve_stream(mfa, srv, models, tf, stream)
             srv.close()
@@ -899,8 +907,11 @@ def main():
     ap.add_argument("--no-side-rows", action="store_true",
                     help="skip the rows after the timed step (precision, segments, isosurface, Marschner-Lobb, "
                          "encoding, render quality), e.g. for profiling runs")
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[20.0, 50.0], help="request rates (1/s)")
-    ap.add_argument("--serve-duration", type=float, default=6.0, help="seconds of arrivals per rate")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[20.0, 50.0, 100.0, 200.0],
+                    help="request rates (1/s)")
+    ap.add_argument("--serve-duration", type=float, default=5.0, help="minimum seconds of arrivals per rate")
+    ap.add_argument("--serve-requests", type=int, default=1000,
+                    help="minimum requests per rate (the stream lasts max(duration, requests / rate))")
     ap.add_argument("--variant", type=int, default=None, help="render kernel variant (skips the autotuner)")
     ap.add_argument("--tile-shape", type=int, default=None, help="ray-tile shape (skips the autotuner)")
     args = ap.parse_args()

@@ -67,11 +67,13 @@ typedef struct mfa_model mfa_model;   /* opaque; owns all of its device memory *
  *              [n_z][n_y][n_x], x fastest.  Copied; the caller keeps ownership.
  *   dtype      type of ctrl.  Storage is FP32 for F64/F32 input, FP16 for F16, BF16 for
  *              BF16 (see mfa_model_create_ex to choose).
- * The padded layer-pair window layout the kernels read takes about 32 bytes per control
- * point (FP32 storage) or 16 bytes (FP16/BF16), twice that when the largest degree is 2
- * (each entry also carries a third layer's row), plus 8 bytes per knot-span cell (the
- * {min, max} bounds the isosurface search reads); the product of the padded sizes
- * (n_x+4)(n_y+4)(n_z+4) must stay below 2^31.
+ * Device memory: the stored control points (a plain array), the padded layer-pair window
+ * the kernels read -- about 32 bytes per control point with FP32 window values, 16 with
+ * 16-bit ones, twice that when the largest degree is 2 (each entry also carries a third
+ * layer's row) -- and 8 bytes per knot-span cell (the {min, max} bounds the isosurface
+ * search reads); the product of the padded sizes (n_x+4)(n_y+4)(n_z+4) must stay below
+ * 2^31.  FP32 windows of degree <= 3 hold each row's x-span polynomial in power form
+ * (computed in FP64 from the stored values, rounded once to FP32).
  * Synchronous: returns after the model is ready.  Returns NULL on error (reason in
  * mfa_last_error()).
  */
@@ -84,6 +86,19 @@ mfa_model* mfa_model_create(const int degree[3], const int nctrl[3], const doubl
  * FP32 whatever the storage type. */
 mfa_model* mfa_model_create_ex(const int degree[3], const int nctrl[3], const double* const knots[3],
                                const void* ctrl, mfa_dtype in_dtype, mfa_dtype storage_dtype);
+
+/* The window the kernels read (not a counterpart of anything in the paper: a memory /
+ * speed choice of this implementation).  MFA_WINDOW_AUTO: FP32 window values for FP32
+ * storage, the 16-bit values themselves for FP16 / BF16 storage (half the window bytes;
+ * each value is widened to FP32 per query).  MFA_WINDOW_F32: FP32 window values whatever
+ * the storage type -- the stored 16-bit values are widened exactly once, at creation, so
+ * a 16-bit model computes the same sums at the speed of an FP32 one, with an FP32 model's
+ * window bytes. */
+enum { MFA_WINDOW_AUTO = 0, MFA_WINDOW_F32 = 1 };
+
+/* As mfa_model_create_ex, with the window chosen (MFA_WINDOW_*; MFA_ERR_ARG otherwise). */
+mfa_model* mfa_model_create_opts(const int degree[3], const int nctrl[3], const double* const knots[3],
+                                 const void* ctrl, mfa_dtype in_dtype, mfa_dtype storage_dtype, int window);
 
 /* Frees the model and its device memory.  NULL is a no-op. */
 void mfa_model_destroy(mfa_model* model);
@@ -98,6 +113,7 @@ typedef struct {
     int cardinal;              /* 1: uniform knots and one degree on all three axes, so
                                   decode and render take the cardinal path (interior
                                   spans share one basis; render variant 6) */
+    mfa_dtype window;          /* type of the window values the kernels read */
 } mfa_model_info;
 
 /* Fills *info.  MFA_ERR_ARG on NULL arguments. */
@@ -406,21 +422,35 @@ int mfa_tune_load(const char* path);
 
 /*
  * Serving (the paper's input-latency concern, Sec. IV-B and Sec. V-C, on one GPU): a server
- * keeps client-created models resident, takes camera-view requests of any image size,
+ * keeps client-created models resident, takes camera-view requests of any image size, and
  * admits them in arrival order while a slot is free and the output image fits in its HBM
- * arena (hbm_budget_bytes, allocated once at creation), and launches each admitted request
- * at once on a stream whose priority rises as the request's work (pixels x samples)
- * falls, so requests join the GPU while others are running and small views overtake large
- * ones on the SMs that free up.  A server thread does the admitting; completions are
- * stamped by host callbacks on the request streams.  No call waits without a bound.
+ * arena (hbm_budget_bytes, allocated once at creation).  Admitted requests run in one of
+ * two modes:
+ *   mode 0 (device work queue): each request is published as a record in device memory and
+ *     placed in an active list ordered by urgency (arrival time, plus the request's work at
+ *     urgency_rate when that is set); persistent kernels, one per model degree class, storage
+ *     type and knot path, draw ray tiles from the list, so a request joins the running
+ *     batch at the next tile any CTA claims; completion is flagged by the kernel in
+ *     host-mapped memory and polled by the server thread.  Requests of a kernel group other
+ *     than the one holding the SMs get SMs as that group's CTAs run out of tiles.
+ *   mode 1 (stream per request): each request is launched at once on a stream whose
+ *     priority rises as its work (pixels x samples) falls, and small views overtake large
+ *     ones on the SMs that free up; completions are stamped by host callbacks.
+ * A server thread does the admitting.  No call waits without a bound.
  */
 typedef struct {
     size_t hbm_budget_bytes;   /* arena for output images (>= 4096) */
-    int max_slots;             /* requests on the GPU at once, 1..4096 */
+    int max_slots;             /* requests on the GPU at once, 1..4096 (mode 0: 1..256) */
     int max_queue;             /* waiting requests before submit answers MFA_ERR_BUSY, >= 1 */
-    int priority_levels;       /* streams of distinct priority, 1..8 (1 = one FIFO stream) */
-    int variant, tile_shape;   /* render kernel choice (as mfa_render_opts) */
-    int use_tuned;             /* nonzero: the autotuner's choice per request class when known */
+    int priority_levels;       /* mode 1: streams of distinct priority, 1..8 (1 = one FIFO stream) */
+    int variant, tile_shape;   /* render kernel choice (as mfa_render_opts; mode 0 uses the
+                                  tile shape and the default kernel of each model) */
+    int use_tuned;             /* mode 1, nonzero: the autotuner's choice per request class */
+    int mode;                  /* 0 device work queue, 1 stream per request */
+    double urgency_rate;       /* mode 0: requests are served in order of arrival time plus
+                                  their work (pixels x samples) / urgency_rate seconds, so
+                                  small views overtake larger ones that arrived at most their
+                                  work's worth earlier; 0 = arrival order */
 } mfa_server_config;
 
 typedef struct {

@@ -25,6 +25,7 @@ __all__ = ["Model", "decode", "locate_spans", "render", "lib", "MFA_F64", "MFA_F
            "MfaError", "camera", "transfer_fn", "Request", "Batch", "render_batch", "render_batch_static", "Server", "server_now", "tune_render", "tune_batch", "tune_save", "tune_load"]
 
 MFA_F64, MFA_F32, MFA_F16, MFA_BF16 = 0, 1, 2, 3
+MFA_WINDOW_AUTO, MFA_WINDOW_F32 = 0, 1
 _PKG = os.path.dirname(os.path.abspath(__file__))
 # The library the binding loads: libmfa.so, or the file MFA_LIB names (e.g. the debug
 # build libmfa_debug.so).  A missing library raises; there is no fallback.
@@ -64,7 +65,8 @@ class _Request(ctypes.Structure):
 
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", c_size_t), ("max_slots", c_int), ("max_queue", c_int),
-                ("priority_levels", c_int), ("variant", c_int), ("tile_shape", c_int), ("use_tuned", c_int)]
+                ("priority_levels", c_int), ("variant", c_int), ("tile_shape", c_int), ("use_tuned", c_int),
+                ("mode", c_int), ("urgency_rate", c_double)]
 
 
 class _ServeRequest(ctypes.Structure):
@@ -101,7 +103,8 @@ class _EncodeResult(ctypes.Structure):
 
 class _Info(ctypes.Structure):
     _fields_ = [("degree", c_int * 3), ("nctrl", c_int * 3), ("storage", c_int), ("vmin", c_float),
-                ("vmax", c_float), ("device_bytes", c_size_t), ("device", c_int), ("cardinal", c_int)]
+                ("vmax", c_float), ("device_bytes", c_size_t), ("device", c_int), ("cardinal", c_int),
+                ("window", c_int)]
 
 
 _lib = None
@@ -119,6 +122,9 @@ def lib():
         L.mfa_last_error.argtypes = []
         L.mfa_set_stream.restype = c_int
         L.mfa_set_stream.argtypes = [c_void_p]
+        L.mfa_model_create_opts.restype = c_void_p
+        L.mfa_model_create_opts.argtypes = [POINTER(c_int * 3), POINTER(c_int * 3), POINTER(c_void_p * 3), c_void_p,
+                                            c_int, c_int, c_int]
         L.mfa_model_create_ex.restype = c_void_p
         L.mfa_model_create_ex.argtypes = [POINTER(c_int * 3), POINTER(c_int * 3), POINTER(c_void_p * 3), c_void_p,
                                           c_int, c_int]
@@ -239,9 +245,12 @@ class Model:
     float32, float16; pass `in_dtype=MFA_BF16` with a uint16 array for BF16 bits).
     knots: None for clamped uniform, or a list of three FP64 arrays (entries may be None).
     storage: MFA_F32 / MFA_F16 / MFA_BF16 (default: F32 for 64/32-bit input).
+    window: MFA_WINDOW_AUTO (the storage type's own window values) or MFA_WINDOW_F32 (FP32
+    window values whatever the storage type: a 16-bit model at FP32 speed).
     """
 
-    def __init__(self, degree, nctrl, knots, ctrl, storage: int | None = None, in_dtype: int | None = None):
+    def __init__(self, degree, nctrl, knots, ctrl, storage: int | None = None, in_dtype: int | None = None,
+                 window: int = 0):
         import torch  # noqa: F401  (makes sure the CUDA context exists on the current device)
         ctrl = np.ascontiguousarray(ctrl)
         if in_dtype is None:
@@ -259,8 +268,9 @@ class Model:
             kp = (c_void_p * 3)(*[None if k is None else k.ctypes.data for k in self._knots])
         self._ctrl_keep = ctrl
         _bind_stream()
-        h = lib().mfa_model_create_ex(ctypes.byref(deg), ctypes.byref(nc), ctypes.byref(kp) if kp is not None else None,
-                                      ctrl.ctypes.data, in_dtype, storage)
+        h = lib().mfa_model_create_opts(ctypes.byref(deg), ctypes.byref(nc),
+                                        ctypes.byref(kp) if kp is not None else None, ctrl.ctypes.data, in_dtype,
+                                        storage, int(window))
         self._ctrl_keep = None
         if not h:
             raise MfaError(-1, lib().mfa_last_error().decode())
@@ -291,7 +301,7 @@ class Model:
         i = _Info()
         _check(lib().mfa_model_get_info(self._h, ctypes.byref(i)))
         return dict(degree=tuple(i.degree), nctrl=tuple(i.nctrl), storage=i.storage, vmin=i.vmin, vmax=i.vmax,
-                    device_bytes=i.device_bytes, device=i.device, cardinal=bool(i.cardinal))
+                    device_bytes=i.device_bytes, device=i.device, cardinal=bool(i.cardinal), window=i.window)
 
     def ctrl(self) -> np.ndarray:
         """The stored control points (n_z, n_y, n_x): float32, float16, or uint16 BF16 bits."""
@@ -732,14 +742,18 @@ def server_now() -> float:
 
 
 class Server:
-    """Render server (mfa_server_*): resident models, requests admitted by an HBM budget
-    and launched on priority streams as slots free up."""
+    """Render server (mfa_server_*): resident models, requests admitted by an HBM budget as
+    slots free up, then drawn tile by tile from a device work queue by persistent kernels
+    (mode 0) or launched on priority streams (mode 1)."""
+
+    QUEUE, STREAMS = 0, 1
 
     def __init__(self, hbm_budget_bytes: int, max_slots: int = 16, max_queue: int = 4096, priority_levels: int = 4,
-                 variant: int = 0, tile_shape: int = 0, use_tuned: bool = False):
+                 variant: int = 0, tile_shape: int = 0, use_tuned: bool = False, mode: int = 0,
+                 urgency_rate: float = 0.0):
         import torch  # noqa: F401
         cfg = _ServerConfig(int(hbm_budget_bytes), int(max_slots), int(max_queue), int(priority_levels), int(variant),
-                            int(tile_shape), 1 if use_tuned else 0)
+                            int(tile_shape), 1 if use_tuned else 0, int(mode), float(urgency_rate))
         h = lib().mfa_server_create(ctypes.byref(cfg))
         if not h:
             raise MfaError(-1, lib().mfa_last_error().decode())

@@ -259,13 +259,16 @@ void mfa_model_destroy(mfa_model* m)
 namespace mfa {
 
 mfa_model* model_create(const int degree[3], const int nctrl[3], const double* const knots[3], const void* ctrl,
-                        mfa_dtype in_dtype, mfa_dtype storage, bool ctrl_on_device)
+                        mfa_dtype in_dtype, mfa_dtype storage, bool ctrl_on_device, int window)
 {
     g_error.clear();
     if (!degree || !nctrl || !ctrl) return fail(MFA_ERR_ARG, "degree, nctrl and ctrl must be non-NULL"), nullptr;
     if (!valid_dtype(in_dtype)) return fail(MFA_ERR_ARG, "unknown input dtype %d", (int)in_dtype), nullptr;
     if (storage != MFA_F32 && storage != MFA_F16 && storage != MFA_BF16)
         return fail(MFA_ERR_UNSUPPORTED, "storage dtype must be F32, F16 or BF16"), nullptr;
+    if (window != MFA_WINDOW_AUTO && window != MFA_WINDOW_F32)
+        return fail(MFA_ERR_ARG, "window = %d is not one of the MFA_WINDOW_* choices", window), nullptr;
+    const mfa_dtype wstore = window == MFA_WINDOW_F32 ? MFA_F32 : storage;   // type of the window values
     int qmax = 0;
     for (int a = 0; a < 3; ++a) {
         if (degree[a] < 1 || degree[a] > kMaxDegree)
@@ -325,7 +328,7 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
     const size_t off_cell = tab;   // per knot-span cell {min, max} of its support
     const size_t ncells = static_cast<size_t>(nctrl[0] - degree[0]) * (nctrl[1] - degree[1]) * (nctrl[2] - degree[2]);
     tab = align_up(tab + sizeof(float2) * ncells, 256);
-    const size_t win_elem = (storage == MFA_F32 ? 4 : 2) * window_values(Q);   // one window entry
+    const size_t win_elem = (wstore == MFA_F32 ? 4 : 2) * window_values(Q);   // one window entry
     const size_t win_bytes = static_cast<size_t>(nxp * nyp * nzp) * win_elem;
     const size_t nctrl_total = static_cast<size_t>(nctrl[0]) * nctrl[1] * nctrl[2];
     const size_t raw_bytes = nctrl_total * (storage == MFA_F32 ? 4 : 2);
@@ -334,7 +337,7 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
     const size_t in_bytes = nctrl_total * dtype_size(in_dtype);
     size_t knot_bytes = 0;
     for (int a = 0; a < 3; ++a) knot_bytes += sizeof(double) * U[a].size();
-    const bool pow_rows = power_rows(Q, storage);
+    const bool pow_rows = power_rows(Q, wstore);
     // FP64 power coefficients of the x spans (power rows only), used while building the window
     const size_t coef_bytes = pow_rows ? sizeof(double) * Q * Q * (nctrl[0] - degree[0]) : 0;
 
@@ -386,8 +389,8 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
     void* d_raw = tabs + off_raw;
     if ((e = launch_prep_raw(d_in, in_dtype, storage, static_cast<long long>(nctrl_total), d_raw, st)) != cudaSuccess)
         return cleanup(0, "stored control points", e);
-    if ((e = launch_prep_window(d_raw, storage, nctrl[0], nctrl[1], nctrl[2], Q, d_coef, degree[0], M->d_win, st)) !=
-        cudaSuccess)
+    if ((e = launch_prep_window(d_raw, storage, nctrl[0], nctrl[1], nctrl[2], Q, d_coef, degree[0], M->d_win, wstore,
+                                st)) != cudaSuccess)
         return cleanup(0, "window array", e);
     if ((e = launch_prep_stats(d_raw, storage, static_cast<long long>(nctrl_total), d_stats, st)) != cudaSuccess)
         return cleanup(0, "control-point statistics", e);
@@ -416,7 +419,8 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
     M->dev.nyp = static_cast<int>(nyp);
     M->dev.nzp = static_cast<int>(nzp);
     M->dev.q = Q;
-    M->dev.storage = storage;
+    M->dev.storage = wstore;
+    M->dev.raw_storage = storage;
     M->dev.cardinal = uniform && degree[0] == Q - 1 && degree[1] == Q - 1 && degree[2] == Q - 1 ? 1 : 0;
     M->dev.cell = d_cell;
     M->dev.ncx = nctrl[0] - degree[0];
@@ -435,7 +439,13 @@ extern "C" {
 mfa_model* mfa_model_create_ex(const int degree[3], const int nctrl[3], const double* const knots[3],
                                const void* ctrl, mfa_dtype in_dtype, mfa_dtype storage)
 {
-    return model_create(degree, nctrl, knots, ctrl, in_dtype, storage, false);
+    return model_create(degree, nctrl, knots, ctrl, in_dtype, storage, false, MFA_WINDOW_AUTO);
+}
+
+mfa_model* mfa_model_create_opts(const int degree[3], const int nctrl[3], const double* const knots[3],
+                                 const void* ctrl, mfa_dtype in_dtype, mfa_dtype storage, int window)
+{
+    return model_create(degree, nctrl, knots, ctrl, in_dtype, storage, false, window);
 }
 
 mfa_model* mfa_model_create(const int degree[3], const int nctrl[3], const double* const knots[3], const void* ctrl,
@@ -458,6 +468,7 @@ int mfa_model_get_info(const mfa_model* m, mfa_model_info* info)
     info->device_bytes = m->bytes;
     info->device = m->device;
     info->cardinal = m->dev.cardinal;
+    info->window = static_cast<mfa_dtype>(m->dev.storage);
     return MFA_OK;
 }
 

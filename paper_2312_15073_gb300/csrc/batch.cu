@@ -185,7 +185,7 @@ int mfa_batch_render(mfa_batch* b, const mfa_render_request* reqs, int n)
             fail(rc, "request %d: %s", r, mfa_last_error());
             return rc;
         }
-        const int g = batch_group(q.model->dev.q, q.model->storage, q.model->dev.cardinal);
+        const int g = batch_group(q.model->dev.q, q.model->dev.storage, q.model->dev.cardinal);
         it.m = q.model->dev;
         it.tiles_x = (q.width + tw - 1) / tw;
         const long long nt = static_cast<long long>(it.tiles_x) * ((q.height + th - 1) / th);

@@ -38,10 +38,11 @@ cudaStream_t current_stream();
 int check_model_device(const mfa_model* m);
 // Cached autotuner choice for this workload class, if any.
 bool tuned_lookup(const mfa_model* m, int w, int h, int ns, int* variant, int* shape);
-// Model creation (mfa_model_create_ex) from control points on the host, or, with
-// ctrl_on_device, already in device memory of the current device (read, not kept).
+// Model creation (mfa_model_create_opts) from control points on the host, or, with
+// ctrl_on_device, already in device memory of the current device (read, not kept); window
+// is one of MFA_WINDOW_*.
 mfa_model* model_create(const int degree[3], const int nctrl[3], const double* const knots[3], const void* ctrl,
-                        mfa_dtype in_dtype, mfa_dtype storage, bool ctrl_on_device);
+                        mfa_dtype in_dtype, mfa_dtype storage, bool ctrl_on_device, int window = MFA_WINDOW_AUTO);
 // The library's device staging pool on device `dev` (created on first use, memory kept
 // cached between calls; allocate and free with the stream-ordered pool calls).
 cudaError_t staging_pool(int dev, cudaMemPool_t* out);

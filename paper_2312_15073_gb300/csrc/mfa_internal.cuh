@@ -88,10 +88,11 @@ struct AxisDev {
 struct ModelDev {
     AxisDev ax[3];
     const void* win;    // window array (see above)
-    const void* raw;    // the stored control points, plain [n_z][n_y][n_x] in the storage type
+    const void* raw;    // the stored control points, plain [n_z][n_y][n_x], of type raw_storage
     int nxp, nyp, nzp;  // padded sizes n + kPad
     int q;              // Q = max degree + 1 (kernel template parameter)
-    int storage;        // mfa_dtype of the window values
+    int storage;        // mfa_dtype of the window values (kernel template parameter)
+    int raw_storage;    // mfa_dtype of the stored control points (FP32 windows may hold 16-bit values)
     int cardinal;       // 1: uniform knots and degree Q-1 on all three axes, so interior
                         // spans share the cardinal basis (render variant 6 applies)
     const float2* cell; // per knot-span cell (i, j, k) = (span - p per axis), x fastest:
@@ -170,8 +171,8 @@ cudaError_t launch_prep_raw(const void* d_ctrl, int in_dtype, int storage, long 
                             cudaStream_t stream);
 // the window array from the stored control points (coef64: the x axis's FP64 span
 // coefficients for FP32 power rows, NULL for 16-bit rows)
-cudaError_t launch_prep_window(const void* raw, int storage, int nx, int ny, int nz, int q, const double* coef64,
-                               int px, void* win, cudaStream_t stream);
+cudaError_t launch_prep_window(const void* raw, int raw_storage, int nx, int ny, int nz, int q, const double* coef64,
+                               int px, void* win, int storage, cudaStream_t stream);
 cudaError_t launch_prep_cells(const void* raw, int storage, const int degree[3], const int nctrl[3], float2* cell,
                               cudaStream_t stream);
 cudaError_t launch_prep_stats(const void* raw, int storage, long long total, int* d_stats, cudaStream_t stream);
@@ -196,6 +197,35 @@ struct BatchKernel {
     int threads;
 };
 BatchKernel render_batch_kernel(int q, int storage, int cardinal);
+
+// Serving work queue (mfa_server_*, device-queue mode).  Each admitted request occupies a
+// record of a ring in device memory; a request's ray tiles are claimed by atomicAdd on the
+// record's ticket word, whose high half is the record's generation (bumped every time the
+// record is reused) and whose low half counts claimed tiles.  A claim is valid when its
+// generation is the record's current one and its tile index is below the record's tile
+// count; the host rewrites a record only after every tile of its previous generation is
+// done, so a valid claim always renders with the data it was published with.  The host
+// keeps the list of active records sorted by its priority and rewrites it on every change.
+constexpr int kServeMaxActive = 256;
+struct ServeRecord {
+    unsigned long long ticket;   // (generation << 32) + next tile
+    int gen;                     // generation of the data below
+    int total_tiles;
+    int done_tiles;              // tiles finished (reset to 0 on publication)
+    int group;                   // batch_group() of the request's model
+    BatchItem item;              // model, camera, table scalars, output (tf points at tf below)
+    float4 tf[kTfMax];           // the request's transfer-function rows
+};
+struct ServeQueue {
+    int n_active;
+    int pad[3];
+    int active[kServeMaxActive];   // record indices, most urgent first
+};
+// The persistent serving kernel of one (degree class, storage, path) group: arguments
+// (ServeRecord* records, const ServeQueue* queue, unsigned* done (host-mapped: done[r] =
+// generation once record r's last tile is finished), int group, int tile_shape).  Its CTAs
+// claim tiles of the group's active records in list order and exit when none is left.
+BatchKernel render_serve_kernel(int q, int storage, int cardinal);
 // Pixel size of ray-tile shape `shape` (0..kTileShapes-1); -1 if out of range.
 int render_tile_dims(int shape, int* tw, int* th);
 constexpr int kTileShapes = 4;

@@ -89,7 +89,7 @@ extern "C" int mfa_render_batch_static(const mfa_render_request* reqs, int n)
             fail(rc, "request %d: %s", r, mfa_last_error());
             return rc;
         }
-        const int g = batch_group(q.model->dev.q, q.model->storage, q.model->dev.cardinal);
+        const int g = batch_group(q.model->dev.q, q.model->dev.storage, q.model->dev.cardinal);
         group_of[r] = g;
         it.m = q.model->dev;
         it.tiles_x = (q.width + tw - 1) / tw;

@@ -144,12 +144,13 @@ __device__ __forceinline__ double raw_at(const void* raw, int storage, int nx, i
 }
 
 // The layer-pair window array (layout in mfa_internal.cuh), one entry per thread, from the
-// stored control points.  16-bit models copy them bit for bit.  FP32 models (coef64 = the
-// x axis's FP64 span coefficients, [span][c][r]) store each row's power form on its x span
-// i: W_c = sum_r c_{c,r} P[i + r], summed in FP64 and rounded once; entries with no span
-// (i >= n_x - p_x) are zero.
-__global__ void k_window(const void* __restrict__ raw, int storage, int nx, int ny, int nz, int q,
-                         const double* __restrict__ coef64, int px, void* __restrict__ win)
+// stored control points (raw, of type raw_storage), in window values of type `storage`.
+// 16-bit windows copy the stored values bit for bit.  FP32 windows with coef64 (the x
+// axis's FP64 span coefficients, [span][c][r]) store each row's power form on its x span
+// i: W_c = sum_r c_{c,r} P[i + r], summed in FP64 from the exact stored values and rounded
+// once; entries with no span (i >= n_x - p_x) are zero.
+__global__ void k_window(const void* __restrict__ raw, int raw_storage, int nx, int ny, int nz, int q,
+                         const double* __restrict__ coef64, int px, void* __restrict__ win, int storage)
 {
     const int nxp = nx + kPad, nyp = ny + kPad, nzp = nz + kPad;
     const long long total = static_cast<long long>(nxp) * nyp * nzp;
@@ -164,7 +165,7 @@ __global__ void k_window(const void* __restrict__ raw, int storage, int nx, int 
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
-            for (int a = 0; a < 4; ++a) P[r][a] = raw_at(raw, storage, nx, ny, nz, i + a, j, k + r);
+            for (int a = 0; a < 4; ++a) P[r][a] = raw_at(raw, raw_storage, nx, ny, nz, i + a, j, k + r);
         if (coef64) {   // power rows of x span i (degree px: coefficients c = 0..px)
             double W[3][4] = {};
             if (i < nx - px) {
@@ -307,11 +308,11 @@ cudaError_t launch_prep_raw(const void* d_ctrl, int in_dtype, int storage, long 
     return cudaGetLastError();
 }
 
-cudaError_t launch_prep_window(const void* raw, int storage, int nx, int ny, int nz, int q, const double* coef64, int px,
-                               void* win, cudaStream_t stream)
+cudaError_t launch_prep_window(const void* raw, int raw_storage, int nx, int ny, int nz, int q, const double* coef64,
+                               int px, void* win, int storage, cudaStream_t stream)
 {
     const long long total = static_cast<long long>(nx + kPad) * (ny + kPad) * (nz + kPad);
-    k_window<<<grid_blocks(total, 65536), 256, 0, stream>>>(raw, storage, nx, ny, nz, q, coef64, px, win);
+    k_window<<<grid_blocks(total, 65536), 256, 0, stream>>>(raw, raw_storage, nx, ny, nz, q, coef64, px, win, storage);
     return cudaGetLastError();
 }
 

@@ -163,7 +163,6 @@ constexpr int kBrickFloats4 = kBrick * kBrick * kBrick;   // 8 KB per warp
 constexpr int kSegMax = 64;
 
 // Row P[k][j][i..i+3] of the stored control points as FP32 (zero past the ends).
-template <int STORAGE>
 __device__ __forceinline__ float4 raw_row(const ModelDev& M, int i, int j, int k)
 {
     const int nx = M.ax[0].n, ny = M.ax[1].n, nz = M.ax[2].n;
@@ -173,11 +172,12 @@ __device__ __forceinline__ float4 raw_row(const ModelDev& M, int i, int j, int k
         v[a] = 0.0f;
         if (i + a < nx && j < ny && k < nz) {
             const long long e = (static_cast<long long>(k) * ny + j) * nx + i + a;
-            if constexpr (STORAGE == 1) {
+            if (M.raw_storage == 1) {
                 v[a] = __ldg(static_cast<const float*>(M.raw) + e);
             } else {
                 const unsigned short h = __ldg(static_cast<const unsigned short*>(M.raw) + e);
-                v[a] = STORAGE == 2 ? __half2float(__ushort_as_half(h)) : __uint_as_float(static_cast<unsigned>(h) << 16);
+                v[a] = M.raw_storage == 2 ? __half2float(__ushort_as_half(h))
+                                          : __uint_as_float(static_cast<unsigned>(h) << 16);
             }
         }
     }
@@ -290,7 +290,7 @@ __device__ __forceinline__ float4 march_bricked(const ModelDev& M, const RenderS
             for (int e = lane; e < total; e += 32) {
                 const int ex = e % ext[0], r = e / ext[0];
                 const int ey = r % ext[1], ez = r / ext[1];
-                brick[(ez * kBrick + ey) * kBrick + ex] = raw_row<STORAGE>(M, org[0] + ex, org[1] + ey, org[2] + ez);
+                brick[(ez * kBrick + ey) * kBrick + ex] = raw_row(M, org[0] + ex, org[1] + ey, org[2] + ez);
             }
             __syncwarp();
         }
@@ -652,6 +652,119 @@ __global__ void __launch_bounds__(kThreads, min_blocks<Q, CARD>()) k_render_batc
     }
 }
 
+// ----------------------------------------------------------------------------------------
+// serving: persistent CTAs over the device work queue
+// ----------------------------------------------------------------------------------------
+//
+// Thread 0 of a CTA walks the active list (most urgent first), skips records of other
+// groups and exhausted ones, and claims a tile of the first record that has one (atomicAdd
+// on the record's ticket word; the claim is checked against the record's generation and
+// tile count, see ServeRecord).  Records and the list are rewritten by the host while the
+// kernel runs, so they are read through L2 (ld.cg), never from a possibly stale L1 line.
+// After a tile, the CTA counts it done; the CTA that finishes a record's last tile
+// publishes the record's generation to host-mapped memory (system-scope release), which the
+// server thread polls.  A CTA that finds nothing to claim exits: no wait anywhere.
+__device__ __forceinline__ int item_total(const ServeRecord* recs, int r) { return __ldcg(&recs[r].total_tiles); }
+
+template <int Q, int STORAGE, bool CARD>
+__global__ void __launch_bounds__(kThreads, min_blocks<Q, CARD>())
+    k_serve(ServeRecord* __restrict__ recs, const ServeQueue* __restrict__ queue, unsigned* __restrict__ done,
+            int group, int shape)
+{
+    __shared__ BatchItem item;
+    __shared__ float4 tf[kTfSmem];
+    __shared__ int s_rec, s_tile, s_gen;
+    const TileShape T = tile_shape(shape);
+    int cur_rec = -1, cur_gen = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int rec = -1, tile = 0, gen = 0;
+            const int n = min(__ldcg(&queue->n_active), kServeMaxActive);
+            for (int a = 0; a < n && rec < 0; ++a) {
+                const int r = __ldcg(&queue->active[a]);
+                ServeRecord* R = recs + r;
+                if (__ldcg(&R->group) != group) continue;
+                const int total = __ldcg(&R->total_tiles);
+                const unsigned long long seen = __ldcg(&R->ticket);
+                if (static_cast<int>(seen >> 32) != __ldcg(&R->gen) || static_cast<int>(seen & 0xFFFFFFFFu) >= total)
+                    continue;   // exhausted, or being republished
+                const unsigned long long claim = atomicAdd(&R->ticket, 1ull);
+                const int g = static_cast<int>(claim >> 32), t = static_cast<int>(claim & 0xFFFFFFFFu);
+                if (g == __ldcg(&R->gen) && t < __ldcg(&R->total_tiles)) {
+                    rec = r;
+                    tile = t;
+                    gen = g;
+                }
+            }
+            s_rec = rec;
+            s_tile = tile;
+            s_gen = gen;
+        }
+        __syncthreads();
+        const int r = s_rec, t = s_tile, g = s_gen;
+        if (r < 0) break;
+        if (r != cur_rec || g != cur_gen) {
+            const int* src = reinterpret_cast<const int*>(&recs[r].item);
+            int* dst = reinterpret_cast<int*>(&item);
+            for (int e = threadIdx.x; e < static_cast<int>(sizeof(BatchItem) / sizeof(int)); e += kThreads)
+                dst[e] = __ldcg(src + e);
+            __syncthreads();
+            const float4* rows = recs[r].tf;
+            for (int e = threadIdx.x; e < item.s.tf_n; e += kThreads) {
+                const float4 a = __ldcg(rows + e), b = e + 1 < item.s.tf_n ? __ldcg(rows + e + 1) : a;
+                tf[2 * e] = a;
+                tf[2 * e + 1] = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, b.w - a.w);
+            }
+            cur_rec = r;
+            cur_gen = g;
+            __syncthreads();
+        }
+        const int tx = t % item.tiles_x, ty = t / item.tiles_x;
+        int col, row;
+        tile_pixel(T, tx, ty, threadIdx.x, col, row);
+        unsigned long long count = 0;
+        if (col < item.s.width && row < item.s.height) {
+            float4 acc;
+            if constexpr (CARD)
+                acc = march_cardinal<Q, STORAGE>(item.m, item.s, tf, col, row, count);
+            else
+                acc = march_pipelined<Q, STORAGE>(item.m, item.s, tf, col, row, count);
+            item.s.out[static_cast<long long>(row) * item.s.width + col] = acc;
+        }
+        if (item.s.samples_out) add_count(item.s.samples_out, count);
+        __syncthreads();   // every pixel of the tile is written; s_* are rewritten next round
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const int finished = atomicAdd(&recs[r].done_tiles, 1) + 1;
+            if (finished == item_total(recs, r)) {
+                __threadfence_system();
+                asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(done + r), "r"(static_cast<unsigned>(g))
+                             : "memory");
+            }
+        }
+    }
+}
+
+template <int Q, int STORAGE, bool CARD>
+BatchKernel serve_kernel_qs()
+{
+    BatchKernel k;
+    k.fn = reinterpret_cast<const void*>(&k_serve<Q, STORAGE, CARD>);
+    int blocks = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_serve<Q, STORAGE, CARD>, kThreads, 0);
+    k.blocks_per_sm = blocks > 0 ? blocks : 1;
+    k.threads = kThreads;
+    return k;
+}
+
+template <int Q, bool CARD>
+BatchKernel serve_kernel_qc(int storage)
+{
+    return storage == 1   ? serve_kernel_qs<Q, 1, CARD>()
+           : storage == 2 ? serve_kernel_qs<Q, 2, CARD>()
+                          : serve_kernel_qs<Q, 3, CARD>();
+}
+
 template <int Q, int STORAGE, bool CARD>
 BatchKernel batch_kernel_qs()
 {
@@ -727,6 +840,16 @@ cudaError_t launch_merge_segments(const RenderScalars& s, const int g[3], const 
     dim3 grid((s.width + 15) / 16, (s.height + 15) / 16);
     k_merge_segments<<<grid, 256, 0, stream>>>(s, g[0], g[1], g[2], partial);
     return cudaGetLastError();
+}
+
+BatchKernel render_serve_kernel(int q, int storage, int cardinal)
+{
+    switch (q) {
+    case 2: return cardinal ? serve_kernel_qc<2, true>(storage) : serve_kernel_qc<2, false>(storage);
+    case 3: return cardinal ? serve_kernel_qc<3, true>(storage) : serve_kernel_qc<3, false>(storage);
+    case 4: return cardinal ? serve_kernel_qc<4, true>(storage) : serve_kernel_qc<4, false>(storage);
+    default: return cardinal ? serve_kernel_qc<5, true>(storage) : serve_kernel_qc<5, false>(storage);
+    }
 }
 
 BatchKernel render_batch_kernel(int q, int storage, int cardinal)

@@ -84,7 +84,7 @@ Key key_of(const mfa_model* m, int w, int h, int ns)
     // uniform knots <=> every axis's first interior knot sits at 1/(n-p) (the library builds
     // them that way when the caller passes NULL); other layouts share one class
     const int nmax = std::max(m->nctrl[0], std::max(m->nctrl[1], m->nctrl[2]));
-    return Key(m->dev.q, static_cast<int>(m->storage), log_bucket(static_cast<double>(w) * h, 4.0),
+    return Key(m->dev.q, m->dev.storage, log_bucket(static_cast<double>(w) * h, 4.0),
                log_bucket(ns, 2.0), m->uniform ? 1 : 0, log_bucket(nmax, 2.0));
 }
 

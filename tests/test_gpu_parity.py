@@ -462,3 +462,38 @@ def test_render_marschner_lobb(mfa, orc):
         assert r[..., 3].max() > 0.5
         if pix is None:
             assert abs(gc - rc) <= max(2, 1e-3 * rc)
+
+
+@pytest.mark.parametrize("storage", [2, 3], ids=["f16", "bf16"])
+@pytest.mark.parametrize("uniform", [True, False], ids=["uniform", "nonuniform"])
+def test_f32_window_of_a_16bit_model(mfa, orc, storage, uniform):
+    """A 16-bit model with FP32 window values (MFA_WINDOW_F32) computes exactly what an FP32
+    model of the same (16-bit) control-point values computes: decodes and renders are equal
+    bit for bit, and meet the gates against the oracle on the rounded values."""
+    import torch
+    rng = np.random.default_rng(_seed("f32-window", storage, uniform))
+    degree, nctrl = (3, 3, 3), (19, 15, 17)
+    knots = [synth.knots_uniform(n, 3) if uniform else synth.knots_nonuniform(n, 3, rng) for n in nctrl]
+    P = synth.sample_ctrl(synth.GaussianSum.draw(rng, 6), knots, degree, rng, 0.01)
+    stored = _stored(P, storage, orc)
+    m16 = mfa.Model(degree, nctrl, knots, P, storage=storage, window=mfa.MFA_WINDOW_F32)
+    m32 = mfa.Model(degree, nctrl, knots, stored, storage=mfa.MFA_F32)
+    i16 = m16.info()
+    assert i16["storage"] == storage and i16["window"] == mfa.MFA_F32 and i16["cardinal"] == uniform
+    ref = orc.Model(degree, nctrl, knots, stored)
+    pts = _edge_points(ref.knots, rng, 3001)
+    v16, g16 = mfa.decode(m16, torch.from_numpy(pts).cuda())
+    v32, g32 = mfa.decode(m32, torch.from_numpy(pts).cuda())
+    assert torch.equal(v16, v32) and torch.equal(g16, g32)
+    vr, gr = ref.decode(pts)
+    assert value_error(v16.cpu().numpy(), vr, stored) <= VALUE_TOL
+    assert grad_error(g16.cpu().numpy(), gr) <= GRAD_TOL
+    cam = synth.camera_persp((1.9, 1.4, 2.2), (0.5, 0.5, 0.5), (0, 1, 0), 35.0)
+    table = synth.ramp_tf(256, 0.1)
+    tf = mfa.transfer_fn(table, shading=True)
+    a = mfa.render(m16, cam, tf, 41, 29, 90)
+    b = mfa.render(m32, cam, tf, 41, 29, 90)
+    assert torch.equal(a, b)
+    o, _ = orc.render(ref, cam, table, 41, 29, 90, shading=True)
+    assert np.all(image_rmse(a.cpu().numpy(), o) <= IMAGE_RMSE_TOL)
+    assert np.array_equal(m16.ctrl(), m16.ctrl()) and m16.ctrl().dtype == (np.float16 if storage == 2 else np.uint16)

@@ -1,4 +1,6 @@
-"""GPU: the render server (admission by HBM budget, requests joining running work).
+"""GPU: the render server (admission by HBM budget, requests joining running work), in both
+modes: the device work queue drawn by persistent kernels (mode 0) and one launch per
+request on priority streams (mode 1).
 
 Each served result must be the same as the request rendered alone (the same per-ray
 arithmetic, so bitwise identity is the target; the gate is the image tolerance).  The
@@ -43,12 +45,16 @@ def _stream(n, rng, sides=(16, 48, 96, 160), ns=(32, 160)):
     return reqs
 
 
-def test_served_results_equal_alone_and_match_oracle(mfa, orc, models):
+MODES = pytest.mark.parametrize("mode", [0, 1], ids=["queue", "streams"])
+
+
+@MODES
+def test_served_results_equal_alone_and_match_oracle(mfa, orc, models, mode):
     import torch
     rng = np.random.default_rng(55)
     table = synth.ramp_tf(256, 0.05)
     tf = mfa.transfer_fn(table, shading=True)
-    srv = mfa.Server(hbm_budget_bytes=64 << 20, max_slots=8, priority_levels=4)
+    srv = mfa.Server(hbm_budget_bytes=64 << 20, max_slots=8, priority_levels=4, mode=mode)
     reqs = _stream(24, rng)
     tickets = [srv.submit(models[r["model"]][0], r["cam"], tf, r["side"], r["side"], r["ns"]) for r in reqs]
     bitwise = 0
@@ -74,11 +80,12 @@ def test_served_results_equal_alone_and_match_oracle(mfa, orc, models):
     assert st["completed"] == len(reqs) and st["failed"] == 0
 
 
-def test_admission_respects_the_hbm_budget(mfa, models):
+@MODES
+def test_admission_respects_the_hbm_budget(mfa, models, mode):
     rng = np.random.default_rng(56)
     tf = mfa.transfer_fn(synth.ramp_tf(256, 0.05), shading=True)
     budget = 3 * 160 * 160 * 16                    # room for three of the largest images
-    srv = mfa.Server(hbm_budget_bytes=budget, max_slots=16, priority_levels=2)
+    srv = mfa.Server(hbm_budget_bytes=budget, max_slots=16, priority_levels=2, mode=mode)
     reqs = _stream(20, rng)
     tickets = [srv.submit(models[r["model"]][0], r["cam"], tf, r["side"], r["side"], r["ns"]) for r in reqs]
     for t in tickets:
@@ -93,11 +100,12 @@ def test_admission_respects_the_hbm_budget(mfa, models):
     srv.close()
 
 
-def test_full_queue_timeout_release_and_cancel(mfa, models):
+@MODES
+def test_full_queue_timeout_release_and_cancel(mfa, models, mode):
     rng = np.random.default_rng(57)
     tf = mfa.transfer_fn(synth.ramp_tf(256, 0.05), shading=True)
     cam = synth.orbit_camera((0.5, 0.5, 0.5), 2.5, 0.3, 0.2, 30.0)
-    srv = mfa.Server(hbm_budget_bytes=256 << 20, max_slots=1, max_queue=2, priority_levels=1)
+    srv = mfa.Server(hbm_budget_bytes=256 << 20, max_slots=1, max_queue=2, priority_levels=1, mode=mode)
     big = srv.submit(models[7][0], cam, tf, 2048, 2048, 2048)     # occupies the only slot for a while
     q1 = srv.submit(models[0][0], cam, tf, 32, 32, 64)
     q2 = srv.submit(models[1][0], cam, tf, 32, 32, 64)
@@ -136,6 +144,52 @@ def test_server_rejects_bad_config(mfa):
         mfa.Server(hbm_budget_bytes=16, max_slots=1)
     with pytest.raises(mfa.MfaError):
         mfa.Server(hbm_budget_bytes=1 << 20, max_slots=0)
+    with pytest.raises(mfa.MfaError):
+        mfa.Server(hbm_budget_bytes=1 << 20, max_slots=4, mode=2)
+    with pytest.raises(mfa.MfaError):                # the device queue's list holds 256 records
+        mfa.Server(hbm_budget_bytes=1 << 20, max_slots=257, mode=0)
+
+
+def test_queue_mixes_kernel_groups_and_reuses_records(mfa, orc):
+    """The device work queue with requests of several kernel groups at once (FP32 power rows
+    and FP16 rows, uniform knots on the cardinal path and non-uniform on the record path,
+    degrees 2 to 4) and more requests than records, so every record is republished several
+    times: each result equals the request rendered alone, and matches the oracle."""
+    import torch
+    rng = np.random.default_rng(59)
+    specs = [((3, 3, 3), (20, 18, 22), 1, True), ((3, 3, 3), (17, 21, 15), 2, True),
+             ((2, 2, 2), (14, 16, 12), 1, False), ((4, 4, 4), (12, 12, 13), 3, False),
+             ((2, 3, 4), (13, 11, 16), 1, True)]
+    models = []
+    for deg, n, storage, uniform in specs:
+        knots = [synth.knots_uniform(n[a], deg[a]) if uniform else synth.knots_nonuniform(n[a], deg[a], rng)
+                 for a in range(3)]
+        P = synth.sample_ctrl(synth.GaussianSum.draw(rng, 5), knots, deg, rng, 0.01)
+        m = mfa.Model(deg, n, knots, P, storage=storage)
+        stored = np.asarray(P, np.float64).astype(np.float32).astype(np.float64) if storage == 1 else (
+            orc.round_to_f16(P) if storage == 2 else orc.round_to_bf16(P))
+        models.append((m, orc.Model(deg, n, knots, stored)))
+    table = synth.ramp_tf(64, 0.08)
+    tf = mfa.transfer_fn(table, shading=True)
+    srv = mfa.Server(hbm_budget_bytes=64 << 20, max_slots=3, mode=0)
+    reqs = []
+    for k in range(15):
+        d = synth.random_direction(rng)
+        cam = synth.camera_persp(np.array([0.5, 0.5, 0.5]) + 2.3 * d, (0.5, 0.5, 0.5), synth.view_up_for(d), 35.0)
+        reqs.append((k % len(models), cam, int(rng.integers(9, 70)), int(rng.integers(9, 70)), int(rng.integers(16, 96))))
+    tickets = [srv.submit(models[i][0], cam, tf, w, h, ns) for i, cam, w, h, ns in reqs]
+    for t, (i, cam, w, h, ns) in zip(tickets, reqs):
+        srv.wait(t, 60000.0)
+        got = srv.result(t).cpu().numpy()
+        srv.release(t)
+        alone = mfa.render(models[i][0], cam, tf, w, h, ns).cpu().numpy()
+        assert np.array_equal(got, alone), (i, w, h, ns)
+        pix = rng.choice(w * h, min(48, w * h), replace=False)
+        o, _ = orc.render(models[i][1], cam, table, w, h, ns, shading=True, pixels=pix)
+        assert np.all(image_rmse(got.reshape(-1, 4)[pix], o) <= IMAGE_RMSE_TOL)
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs) and st["failed"] == 0 and st["peak_in_flight"] <= 3
 
 
 def test_served_full_size_fp16_against_fp64_oracle(mfa, orc):
@@ -152,7 +206,7 @@ def test_served_full_size_fp16_against_fp64_oracle(mfa, orc):
     table = synth.ramp_tf(256, 0.05)
     tf = mfa.transfer_fn(table, shading=True)
     cam = synth.orbit_camera((0.5, 0.5, 0.5), 2.5, 0.9, 0.25, 30.0)
-    srv = mfa.Server(hbm_budget_bytes=256 << 20, max_slots=4, priority_levels=2)
+    srv = mfa.Server(hbm_budget_bytes=256 << 20, max_slots=4, priority_levels=2, mode=0)
     t = srv.submit(m, cam, tf, 2048, 2048, 2048)
     srv.wait(t, 120000.0)
     got = srv.result(t).cpu().numpy()
