@@ -93,8 +93,14 @@ mfa_model* mfa_model_create_ex(const int degree[3], const int nctrl[3], const do
  * each value is widened to FP32 per query).  MFA_WINDOW_F32: FP32 window values whatever
  * the storage type -- the stored 16-bit values are widened exactly once, at creation, so
  * a 16-bit model computes the same sums at the speed of an FP32 one, with an FP32 model's
- * window bytes. */
-enum { MFA_WINDOW_AUTO = 0, MFA_WINDOW_F32 = 1 };
+ * window bytes.  MFA_WINDOW_COMPACT: no window -- the control points are kept once, as a
+ * zero-padded plain array of the storage type ((n_x+4)(n_y+4)(n_z+4) values), and the
+ * kernels gather each support row value by value: slower per query, but a model of 1-1.5x
+ * its plain size instead of 8-16x (for models that would not otherwise fit in L2 or in
+ * memory).  Compact models keep no per-cell bounds, so the isosurface search queries every
+ * sample and render variant 7 falls back to the default; render variants 1, 2, 3 and 5
+ * run as the default too. */
+enum { MFA_WINDOW_AUTO = 0, MFA_WINDOW_F32 = 1, MFA_WINDOW_COMPACT = 2 };
 
 /* As mfa_model_create_ex, with the window chosen (MFA_WINDOW_*; MFA_ERR_ARG otherwise). */
 mfa_model* mfa_model_create_opts(const int degree[3], const int nctrl[3], const double* const knots[3],
@@ -113,7 +119,7 @@ typedef struct {
     int cardinal;              /* 1: uniform knots and one degree on all three axes, so
                                   decode and render take the cardinal path (interior
                                   spans share one basis; render variant 6) */
-    mfa_dtype window;          /* type of the window values the kernels read */
+    int window;                /* the MFA_WINDOW_* choice the model was created with */
 } mfa_model_info;
 
 /* Fills *info.  MFA_ERR_ARG on NULL arguments. */

@@ -266,9 +266,12 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
     if (!valid_dtype(in_dtype)) return fail(MFA_ERR_ARG, "unknown input dtype %d", (int)in_dtype), nullptr;
     if (storage != MFA_F32 && storage != MFA_F16 && storage != MFA_BF16)
         return fail(MFA_ERR_UNSUPPORTED, "storage dtype must be F32, F16 or BF16"), nullptr;
-    if (window != MFA_WINDOW_AUTO && window != MFA_WINDOW_F32)
+    if (window != MFA_WINDOW_AUTO && window != MFA_WINDOW_F32 && window != MFA_WINDOW_COMPACT)
         return fail(MFA_ERR_ARG, "window = %d is not one of the MFA_WINDOW_* choices", window), nullptr;
-    const mfa_dtype wstore = window == MFA_WINDOW_F32 ? MFA_F32 : storage;   // type of the window values
+    const bool compact = window == MFA_WINDOW_COMPACT;
+    // window type (ModelDev::storage): layer pairs of FP32 or of the storage type's values, or
+    // the compact plain array of the storage type
+    const int wstore = compact ? storage + 3 : (window == MFA_WINDOW_F32 ? MFA_F32 : storage);
     int qmax = 0;
     for (int a = 0; a < 3; ++a) {
         if (degree[a] < 1 || degree[a] > kMaxDegree)
@@ -277,7 +280,11 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
             return fail(MFA_ERR_ARG, "nctrl[%d] = %d must be in degree+1..2^24", a, nctrl[a]), nullptr;
         qmax = degree[a] + 1 > qmax ? degree[a] + 1 : qmax;
     }
-    const long long nxp = nctrl[0] + kPad, nyp = nctrl[1] + kPad, nzp = nctrl[2] + kPad;
+    // padded sizes: kPad zeros past the end of every axis; compact FP32 models pad x to a
+    // multiple of 4 with at least 6 zeros, so that their rows load as aligned 16-byte vectors
+    const bool compact32 = window == MFA_WINDOW_COMPACT && storage == MFA_F32;
+    const long long nxp = compact32 ? (nctrl[0] + 6 + 3) / 4 * 4 : nctrl[0] + kPad;
+    const long long nyp = nctrl[1] + kPad, nzp = nctrl[2] + kPad;
     if (nxp * nyp * nzp >= (1LL << 31))
         return fail(MFA_ERR_UNSUPPORTED, "model too large: (nx+4)(ny+4)(nz+4) must stay below 2^31"), nullptr;
 
@@ -325,15 +332,17 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
         off_rec[a] = tab;
         tab = align_up(tab + sizeof(float) * rec_stride(Q) * (n - p), 256);
     }
-    const size_t off_cell = tab;   // per knot-span cell {min, max} of its support
-    const size_t ncells = static_cast<size_t>(nctrl[0] - degree[0]) * (nctrl[1] - degree[1]) * (nctrl[2] - degree[2]);
+    const size_t off_cell = tab;   // per knot-span cell {min, max} of its support (not on compact models)
+    const size_t ncells =
+        compact ? 0 : static_cast<size_t>(nctrl[0] - degree[0]) * (nctrl[1] - degree[1]) * (nctrl[2] - degree[2]);
     tab = align_up(tab + sizeof(float2) * ncells, 256);
-    const size_t win_elem = (wstore == MFA_F32 ? 4 : 2) * window_values(Q);   // one window entry
+    const size_t val_bytes = storage == MFA_F32 ? 4 : 2;
+    const size_t win_elem = compact ? val_bytes : (wstore == MFA_F32 ? 4 : 2) * window_values(Q);   // one entry
     const size_t win_bytes = static_cast<size_t>(nxp * nyp * nzp) * win_elem;
     const size_t nctrl_total = static_cast<size_t>(nctrl[0]) * nctrl[1] * nctrl[2];
-    const size_t raw_bytes = nctrl_total * (storage == MFA_F32 ? 4 : 2);
-    const size_t off_raw = tab;   // the stored control points, plain array
-    tab = align_up(tab + raw_bytes, 256);
+    const size_t raw_bytes = nctrl_total * val_bytes;
+    const size_t off_raw = tab;   // the stored control points, plain array (staging only on compact models)
+    if (!compact) tab = align_up(tab + raw_bytes, 256);
     const size_t in_bytes = nctrl_total * dtype_size(in_dtype);
     size_t knot_bytes = 0;
     for (int a = 0; a < 3; ++a) knot_bytes += sizeof(double) * U[a].size();
@@ -342,8 +351,9 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
     const size_t coef_bytes = pow_rows ? sizeof(double) * Q * Q * (nctrl[0] - degree[0]) : 0;
 
     void* d_stage = nullptr;   // uploaded knots, stats, x coefficients and input control points; freed below
-    const size_t stage_bytes =
-        align_up(knot_bytes, 256) + 256 + align_up(coef_bytes, 256) + (ctrl_on_device ? 0 : in_bytes);
+    const size_t stage_raw = compact ? align_up(raw_bytes, 256) : 0;
+    const size_t stage_bytes = align_up(knot_bytes, 256) + 256 + align_up(coef_bytes, 256) + stage_raw +
+                               (ctrl_on_device ? 0 : in_bytes);
     cudaError_t e;
     auto cleanup = [&](int code, const char* what, cudaError_t err) -> mfa_model* {
         if (err != cudaSuccess) cuda_fail(err, what); else fail(code, "%s", what);
@@ -368,7 +378,7 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
     int* d_stats = reinterpret_cast<int*>(stage + align_up(knot_bytes, 256));
     double* d_coef = pow_rows ? reinterpret_cast<double*>(stage + align_up(knot_bytes, 256) + 256) : nullptr;
     void* d_in = ctrl_on_device ? const_cast<void*>(ctrl)
-                                : stage + align_up(knot_bytes, 256) + 256 + align_up(coef_bytes, 256);
+                                : stage + align_up(knot_bytes, 256) + 256 + align_up(coef_bytes, 256) + stage_raw;
     if (!ctrl_on_device && (e = cudaMemcpyAsync(d_in, ctrl, in_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cleanup(0, "upload control points", e);
 
@@ -386,16 +396,17 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
                                   const_cast<int*>(A.grid), A.G, a == 0 ? d_coef : nullptr, st)) != cudaSuccess)
             return cleanup(0, "span tables", e);
     }
-    void* d_raw = tabs + off_raw;
+    void* d_raw = compact ? static_cast<void*>(stage + align_up(knot_bytes, 256) + 256 + align_up(coef_bytes, 256))
+                          : static_cast<void*>(tabs + off_raw);
     if ((e = launch_prep_raw(d_in, in_dtype, storage, static_cast<long long>(nctrl_total), d_raw, st)) != cudaSuccess)
         return cleanup(0, "stored control points", e);
-    if ((e = launch_prep_window(d_raw, storage, nctrl[0], nctrl[1], nctrl[2], Q, d_coef, degree[0], M->d_win, wstore,
-                                st)) != cudaSuccess)
+    if ((e = launch_prep_window(d_raw, storage, nctrl[0], nctrl[1], nctrl[2], static_cast<int>(nxp), Q, d_coef,
+                                degree[0], M->d_win, wstore, st)) != cudaSuccess)
         return cleanup(0, "window array", e);
     if ((e = launch_prep_stats(d_raw, storage, static_cast<long long>(nctrl_total), d_stats, st)) != cudaSuccess)
         return cleanup(0, "control-point statistics", e);
-    float2* d_cell = reinterpret_cast<float2*>(tabs + off_cell);
-    if ((e = launch_prep_cells(d_raw, storage, degree, nctrl, d_cell, st)) != cudaSuccess)
+    float2* d_cell = compact ? nullptr : reinterpret_cast<float2*>(tabs + off_cell);
+    if (!compact && (e = launch_prep_cells(d_raw, storage, degree, nctrl, d_cell, st)) != cudaSuccess)
         return cleanup(0, "cell bounds", e);
     int stats[3];
     if ((e = cudaMemcpyAsync(stats, d_stats, sizeof stats, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -414,7 +425,8 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
     M->vmax = ord2f(stats[1]);
     M->maxabs = ord2f(stats[2]);
     M->dev.win = M->d_win;
-    M->dev.raw = d_raw;
+    M->dev.raw = compact ? nullptr : d_raw;
+    M->window = window;
     M->dev.nxp = static_cast<int>(nxp);
     M->dev.nyp = static_cast<int>(nyp);
     M->dev.nzp = static_cast<int>(nzp);
@@ -468,7 +480,7 @@ int mfa_model_get_info(const mfa_model* m, mfa_model_info* info)
     info->device_bytes = m->bytes;
     info->device = m->device;
     info->cardinal = m->dev.cardinal;
-    info->window = static_cast<mfa_dtype>(m->dev.storage);
+    info->window = m->window;
     return MFA_OK;
 }
 
@@ -509,6 +521,7 @@ int mfa_render_ex(const mfa_model* m, const mfa_camera* cam, const mfa_transfer_
     cudaStream_t st = current_stream();
     unsigned* bits = nullptr;   // variant 7: per-cell visibility under this transfer function
     cudaError_t e = cudaSuccess;
+    if (variant == 7 && !m->dev.cell) variant = 0;   // no cell bounds (compact models): no skipping
     if (variant == 7) {
         cudaMemPool_t pool;
         const size_t words = (static_cast<size_t>(m->dev.ncx) * m->dev.ncy * m->dev.ncz + 31) / 32;

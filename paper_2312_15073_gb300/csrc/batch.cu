@@ -2,7 +2,7 @@
 // include/mfa.h).
 //
 // A submission writes a work table on the host (pinned memory).  Requests are grouped by
-// model degree class Q = p_max + 1 and control-point storage type; the table holds one
+// model degree class Q = p_max + 1, window type and knot path; the table holds one
 // BatchHead per group (tile counter = 0, item count, tile count, where the items start),
 // then each group's BatchItems (model tables, camera frame, transfer-function scalars,
 // first tile index), then every request's transfer-function rows.  The graph copies the
@@ -41,7 +41,7 @@ struct mfa_batch {
         void* d_table = nullptr;
         cudaEvent_t done = nullptr;
         bool pending = false;
-        std::map<int, GraphEntry> graphs;   // per set of groups present
+        std::map<unsigned long long, GraphEntry> graphs;   // per set of groups present (bit g = group g)
     } slot[2];
     int next = 0;
 };
@@ -61,7 +61,7 @@ void drop_graphs(mfa_batch* b)
 
 // Builds the graph for one slot and one set of groups: the table upload, then one
 // persistent kernel per group, each depending only on the upload.
-cudaError_t build_graph(mfa_batch* b, mfa_batch::Slot& s, int mask, GraphEntry* out)
+cudaError_t build_graph(mfa_batch* b, mfa_batch::Slot& s, unsigned long long mask, GraphEntry* out)
 {
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
@@ -72,7 +72,7 @@ cudaError_t build_graph(mfa_batch* b, mfa_batch::Slot& s, int mask, GraphEntry* 
     e = cudaGraphAddMemcpyNode1D(&copy, graph, nullptr, 0, s.d_table, s.h_table, b->table_bytes,
                                  cudaMemcpyHostToDevice);
     for (int g = 0; g < kBatchGroups && e == cudaSuccess; ++g) {
-        if (!(mask & (1 << g))) continue;
+        if (!(mask & (1ull << g))) continue;
         const BatchKernel k = render_batch_kernel(batch_group_q(g), batch_group_storage(g), batch_group_cardinal(g));
         void* table = s.d_table;
         int group = g, shape = b->shape;
@@ -209,7 +209,7 @@ int mfa_batch_render(mfa_batch* b, const mfa_render_request* reqs, int n)
     for (int g = 0; g < kBatchGroups; ++g) off += sizeof(BatchItem) * items[g].size();
     size_t tf_off = align256(off), tf_used = 0;
     off = kBatchItemsOffset;
-    int mask = 0;
+    unsigned long long mask = 0;
     for (int g = 0; g < kBatchGroups; ++g) {
         heads[g].n_items = static_cast<int>(items[g].size());
         heads[g].total_tiles = static_cast<int>(tiles[g]);
@@ -225,7 +225,7 @@ int mfa_batch_render(mfa_batch* b, const mfa_render_request* reqs, int n)
         if (!items[g].empty()) {
             std::memcpy(h + off, items[g].data(), sizeof(BatchItem) * items[g].size());
             off += sizeof(BatchItem) * items[g].size();
-            mask |= 1 << g;
+            mask |= 1ull << g;
         }
     }
     std::memcpy(h, heads, sizeof heads);

@@ -251,9 +251,9 @@ __device__ __forceinline__ void cardinal_basis(float t, float (&M)[Q], float (&G
 // r3[a] = P[k+2][j][i+a] (a 128-bit load of the entry's second half).
 template <int Q>
 struct PairF32 {
-    static __device__ __forceinline__ void load(const void* win, int idx, f2 (&pr)[qpair(Q)])
+    static __device__ __forceinline__ void load(const ModelDev& M, int idx, f2 (&pr)[qpair(Q)])
     {
-        const float* e = static_cast<const float*>(win) + static_cast<long long>(window_values(Q)) * idx;
+        const float* e = static_cast<const float*>(M.win) + static_cast<long long>(window_values(Q)) * idx;
         if constexpr (qpair(Q) == 2) {
             asm("ld.global.nc.v2.b64 {%0, %1}, [%2];" : "=l"(pr[0].v), "=l"(pr[1].v) : "l"(e));
         } else {
@@ -264,11 +264,11 @@ struct PairF32 {
         if constexpr (qpair(Q) == 6)
             asm("ld.global.nc.v2.b64 {%0, %1}, [%2];" : "=l"(pr[4].v), "=l"(pr[5].v) : "l"(e + 32));
     }
-    static __device__ __forceinline__ void load_triple(const void* win, int idx, f2 (&pr)[4], float (&r3)[4])
+    static __device__ __forceinline__ void load_triple(const ModelDev& M, int idx, f2 (&pr)[4], float (&r3)[4])
     {
         static_assert(Q == 3, "third-layer rows exist in degree-class-3 windows only");
-        load(win, idx, pr);
-        const float* e = static_cast<const float*>(win) + static_cast<long long>(window_values(Q)) * idx;
+        load(M, idx, pr);
+        const float* e = static_cast<const float*>(M.win) + static_cast<long long>(window_values(Q)) * idx;
         asm("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
             : "=f"(r3[0]), "=f"(r3[1]), "=f"(r3[2]), "=f"(r3[3])
             : "l"(e + 8));
@@ -296,9 +296,9 @@ struct Pair16 {
         const float2 x = cvt(bits);
         return pk2(x.x, x.y);
     }
-    static __device__ __forceinline__ void load(const void* win, int idx, f2 (&pr)[qpair(Q)])
+    static __device__ __forceinline__ void load(const ModelDev& M, int idx, f2 (&pr)[qpair(Q)])
     {
-        const unsigned short* e = static_cast<const unsigned short*>(win) + static_cast<long long>(window_values(Q)) * idx;
+        const unsigned short* e = static_cast<const unsigned short*>(M.win) + static_cast<long long>(window_values(Q)) * idx;
         if constexpr (qpair(Q) == 2) {
             const uint2 w = __ldg(reinterpret_cast<const uint2*>(e));
             pr[0] = cvt2(w.x);
@@ -316,11 +316,11 @@ struct Pair16 {
             pr[5] = cvt2(w.y);
         }
     }
-    static __device__ __forceinline__ void load_triple(const void* win, int idx, f2 (&pr)[4], float (&r3)[4])
+    static __device__ __forceinline__ void load_triple(const ModelDev& M, int idx, f2 (&pr)[4], float (&r3)[4])
     {
         static_assert(Q == 3, "third-layer rows exist in degree-class-3 windows only");
-        load(win, idx, pr);
-        const unsigned short* e = static_cast<const unsigned short*>(win) + static_cast<long long>(window_values(Q)) * idx;
+        load(M, idx, pr);
+        const unsigned short* e = static_cast<const unsigned short*>(M.win) + static_cast<long long>(window_values(Q)) * idx;
         const uint2 w = __ldg(reinterpret_cast<const uint2*>(e + 8));
         const float2 lo = cvt(w.x), hi = cvt(w.y);
         r3[0] = lo.x;
@@ -330,11 +330,74 @@ struct Pair16 {
     }
 };
 
+// The compact layout: the control points once, as the zero-padded plain array.  A window
+// entry index is the array index of P[k][j][i] (the padded sizes are the same), the layer
+// k+1 lies one padded layer (nxp nyp values) further, and every column pair is gathered
+// value by value (scalar loads; 16-bit values widened as above), zero past the ends.
+template <int Q, int VT>
+struct PairCompact {
+    static __device__ __forceinline__ float value(const ModelDev& M, long long i)
+    {
+        if constexpr (VT == 1) {
+            return __ldg(static_cast<const float*>(M.win) + i);
+        } else {
+            const unsigned short h = __ldg(static_cast<const unsigned short*>(M.win) + i);
+            return VT == 2 ? __half2float(__ushort_as_half(h)) : __uint_as_float(static_cast<unsigned>(h) << 16);
+        }
+    }
+    // FP32 rows of up to four values: the aligned 32 bytes around them in two 16-byte loads
+    // (rows of a compact FP32 model start 16-byte aligned: nxp is a multiple of 4, with at
+    // least 6 values of padding), then a two-step select by the row's offset in them.
+    static constexpr bool kVector = VT == 1 && Q <= 4;
+    static __device__ __forceinline__ void row4(const ModelDev& M, long long idx, float (&o)[4])
+    {
+        const float* base = static_cast<const float*>(M.win) + (idx & ~3ll);
+        const float4 v0 = __ldg(reinterpret_cast<const float4*>(base));
+        const float4 v1 = __ldg(reinterpret_cast<const float4*>(base + 4));
+        const bool s2 = (idx & 2) != 0, s1 = (idx & 1) != 0;
+        const float a0 = s2 ? v0.z : v0.x, a1 = s2 ? v0.w : v0.y, a2 = s2 ? v1.x : v0.z, a3 = s2 ? v1.y : v0.w,
+                    a4 = s2 ? v1.z : v1.x;
+        o[0] = s1 ? a1 : a0;
+        o[1] = s1 ? a2 : a1;
+        o[2] = s1 ? a3 : a2;
+        o[3] = s1 ? a4 : a3;
+    }
+    static __device__ __forceinline__ void load(const ModelDev& M, int idx, f2 (&pr)[qpair(Q)])
+    {
+        const long long layer = static_cast<long long>(M.nxp) * M.nyp;
+        if constexpr (kVector) {
+            float lo[4], hi[4];
+            row4(M, idx, lo);
+            row4(M, idx + layer, hi);
+#pragma unroll
+            for (int a = 0; a < qpair(Q); ++a) pr[a] = pk2(lo[a], hi[a]);
+        } else {
+#pragma unroll
+            for (int a = 0; a < qpair(Q); ++a) pr[a] = pk2(value(M, idx + a), value(M, idx + a + layer));
+        }
+    }
+    static __device__ __forceinline__ void load_triple(const ModelDev& M, int idx, f2 (&pr)[4], float (&r3)[4])
+    {
+        static_assert(Q == 3, "third-layer rows exist in degree class 3 only");
+        load(M, idx, pr);
+        const long long layer2 = 2ll * M.nxp * M.nyp;
+        if constexpr (kVector) {
+            row4(M, idx + layer2, r3);
+        } else {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) r3[a] = value(M, idx + a + layer2);
+        }
+    }
+};
+
 template <int Q, int STORAGE>
 struct PairLoader;
-template <int Q> struct PairLoader<Q, 1> : PairF32<Q> {};          // MFA_F32
-template <int Q> struct PairLoader<Q, 2> : Pair16<Q, false> {};    // MFA_F16
-template <int Q> struct PairLoader<Q, 3> : Pair16<Q, true> {};     // MFA_BF16
+template <int Q> struct PairLoader<Q, 1> : PairF32<Q> {};          // MFA_F32 layer pairs
+template <int Q> struct PairLoader<Q, 2> : Pair16<Q, false> {};    // MFA_F16 layer pairs
+template <int Q> struct PairLoader<Q, 3> : Pair16<Q, true> {};     // MFA_BF16 layer pairs
+template <int Q> struct PairLoader<Q, 4> : PairCompact<Q, 1> {};   // compact FP32
+template <int Q> struct PairLoader<Q, 5> : PairCompact<Q, 2> {};   // compact FP16
+template <int Q> struct PairLoader<Q, 6> : PairCompact<Q, 3> {};   // compact BF16
 
 // ----------------------------------------------------------------------------------------
 // the x-pass: power rows (FP32 models) or basis-weighted rows (16-bit models)
@@ -564,7 +627,7 @@ __device__ __forceinline__ float4 contract_triple(const ModelDev& M, int base, c
         float r3[4];
         int idx = base + b * M.nxp;
         MFA_DBG_INDEX(M.dbg, idx, static_cast<long long>(M.nxp) * M.nyp * M.nzp, kDbgWindow);
-        PairLoader<3, STORAGE>::load_triple(M.win, idx, pr, r3);
+        PairLoader<3, STORAGE>::load_triple(M, idx, pr, r3);
         f2 A, B;
         float A3, B3;
         x_row<3, STORAGE>(pr, X, A, B);
@@ -626,7 +689,7 @@ __device__ __forceinline__ float4 contract_pairs(const ModelDev& M, int base, co
                 f2 pr[qpair(Q)];
                 int idx = base + m * pair_step + b * M.nxp;   // Q = 5 also reads entry idx + 1
                 MFA_DBG_INDEX(M.dbg, idx, static_cast<long long>(M.nxp) * M.nyp * M.nzp - (qpair(Q) == 6), kDbgWindow);
-                PairLoader<Q, STORAGE>::load(M.win, idx, pr);
+                PairLoader<Q, STORAGE>::load(M, idx, pr);
                 f2 A, B;
                 x_row<Q, STORAGE>(pr, X, A, B);
                 if (b == 0) {
@@ -672,7 +735,7 @@ __device__ __forceinline__ float contract_value(const ModelDev& M, int base, con
             float r3[4];
             int idx = base + b * M.nxp;
             MFA_DBG_INDEX(M.dbg, idx, static_cast<long long>(M.nxp) * M.nyp * M.nzp, kDbgWindow);
-            PairLoader<3, STORAGE>::load_triple(M.win, idx, pr, r3);
+            PairLoader<3, STORAGE>::load_triple(M, idx, pr, r3);
             const f2 A = x_row_value<3, STORAGE>(pr, X);
             const float A3 = x_row3_value<STORAGE>(r3, X);
             const float nyb = lo2(ny[b]);
@@ -692,7 +755,7 @@ __device__ __forceinline__ float contract_value(const ModelDev& M, int base, con
                 f2 pr[qpair(Q)];
                 int idx = base + m * pair_step + b * M.nxp;
                 MFA_DBG_INDEX(M.dbg, idx, static_cast<long long>(M.nxp) * M.nyp * M.nzp - (qpair(Q) == 6), kDbgWindow);
-                PairLoader<Q, STORAGE>::load(M.win, idx, pr);
+                PairLoader<Q, STORAGE>::load(M, idx, pr);
                 const f2 A = x_row_value<Q, STORAGE>(pr, X);
                 CC = b == 0 ? mul2(ny[0], A) : fma2(ny[b], A, CC);
             }

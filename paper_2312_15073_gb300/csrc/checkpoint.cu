@@ -43,9 +43,21 @@ extern "C" int mfa_model_get_ctrl(const mfa_model* m, void* host_out)
     if (int rc = check_model_device(m)) return rc;
     const int nx = m->nctrl[0], ny = m->nctrl[1], nz = m->nctrl[2];
     const size_t bytes = static_cast<size_t>(nx) * ny * nz * storage_bytes(m->storage);
-    // the plain array of stored values is the model's own copy: one device-to-host copy
+    // the plain array of stored values is the model's own copy: one device-to-host copy;
+    // compact models hold them only in the zero-padded window, read as a 3-D region
     cudaStream_t st = current_stream();
-    cudaError_t e = cudaMemcpyAsync(host_out, m->dev.raw, bytes, cudaMemcpyDeviceToHost, st);
+    cudaError_t e;
+    if (m->dev.raw) {
+        e = cudaMemcpyAsync(host_out, m->dev.raw, bytes, cudaMemcpyDeviceToHost, st);
+    } else {
+        const size_t elem = storage_bytes(m->storage);
+        cudaMemcpy3DParms p = {};
+        p.srcPtr = make_cudaPitchedPtr(const_cast<void*>(m->dev.win), elem * m->dev.nxp, m->dev.nxp, m->dev.nyp);
+        p.dstPtr = make_cudaPitchedPtr(host_out, elem * nx, nx, ny);
+        p.extent = make_cudaExtent(elem * nx, ny, nz);
+        p.kind = cudaMemcpyDeviceToHost;
+        e = cudaMemcpy3DAsync(&p, st);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? MFA_OK : cuda_fail(e, "read control points");
 }

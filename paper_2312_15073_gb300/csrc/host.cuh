@@ -20,6 +20,7 @@ struct mfa_model {
     float vmin = 0.0f, vmax = 0.0f, maxabs = 0.0f;
     size_t bytes = 0;
     bool uniform = true;        // every axis has clamped uniform knots
+    int window = MFA_WINDOW_AUTO;   // the MFA_WINDOW_* choice the model was built with
     std::vector<double> knots[3];   // the FP64 knot vectors (host copy, for mfa_model_save)
     void* d_win = nullptr;      // window array
     void* d_tables = nullptr;   // kup, grid and records of the three axes, one allocation

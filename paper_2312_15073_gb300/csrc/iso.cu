@@ -67,7 +67,7 @@ struct RayQuery<Q, STORAGE, true> {
         locate(M, u, v, w, t);
         int ci = (c[2].j * M.ncy + c[1].j) * M.ncx + c[0].j;
         MFA_DBG_INDEX(M.dbg, ci, static_cast<long long>(M.ncx) * M.ncy * M.ncz, kDbgCell);
-        const float2 r = __ldg(M.cell + ci);
+        const float2 r = M.cell ? __ldg(M.cell + ci) : make_float2(-INFINITY, INFINITY);   // none: query
         bounded = iso < r.x || iso > r.y;
         if (iso < r.x) return r.x - iso;
         if (iso > r.y) return r.y - iso;
@@ -127,7 +127,7 @@ struct RayQuery<Q, STORAGE, false> {
         for (int a = 0; a < 3; ++a) axis_update<Q>(M.ax[a], c[a], x[a]);
         int ci = ((c[2].s - M.ax[2].p) * M.ncy + (c[1].s - M.ax[1].p)) * M.ncx + (c[0].s - M.ax[0].p);
         MFA_DBG_INDEX(M.dbg, ci, static_cast<long long>(M.ncx) * M.ncy * M.ncz, kDbgCell);
-        const float2 r = __ldg(M.cell + ci);
+        const float2 r = M.cell ? __ldg(M.cell + ci) : make_float2(-INFINITY, INFINITY);   // none: query
         bounded = iso < r.x || iso > r.y;
         if (iso < r.x) return r.x - iso;
         if (iso > r.y) return r.y - iso;
@@ -283,6 +283,9 @@ cudaError_t iso_q(const ModelDev& m, const RenderParams& rp, float iso, float* d
     case 1: return iso_qs<Q, 1>(m, rp, iso, depth, shape, st);
     case 2: return iso_qs<Q, 2>(m, rp, iso, depth, shape, st);
     case 3: return iso_qs<Q, 3>(m, rp, iso, depth, shape, st);
+    case 4: return iso_qs<Q, 4>(m, rp, iso, depth, shape, st);
+    case 5: return iso_qs<Q, 5>(m, rp, iso, depth, shape, st);
+    case 6: return iso_qs<Q, 6>(m, rp, iso, depth, shape, st);
     default: return cudaErrorInvalidValue;
     }
 }

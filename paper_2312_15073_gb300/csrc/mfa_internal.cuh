@@ -48,6 +48,15 @@ constexpr int kRecHead = 4;
 __host__ __device__ constexpr int window_values(int q) { return q == 3 ? 16 : 8; }
 __host__ __device__ constexpr int qpair(int q) { return (q + 1) / 2 * 2; }
 __host__ __device__ constexpr int rec_stride(int q) { return ((kRecHead + q * qpair(q)) + 3) / 4 * 4; }
+// Window types (ModelDev::storage, a kernel template parameter): 1..3 layer-pair windows
+// with FP32 / FP16 / BF16 values; 4..6 the compact layout, the control points once as a
+// zero-padded plain array [n_z+4][n_y+4][nxp] of FP32 / FP16 / BF16 (nxp = n_x+4, or for
+// FP32 n_x+6 rounded up to a multiple of 4), whose layer pairs the kernels gather row by
+// row (about 1.1x the plain array instead of 8x).
+constexpr int kWindowTypes = 6;
+__host__ __device__ constexpr bool compact_window(int storage) { return storage >= 4; }
+__host__ __device__ constexpr int window_value_type(int storage) { return storage >= 4 ? storage - 3 : storage; }
+
 // Whether a model's window rows hold power forms (FP32, degree classes 2..4) rather than
 // control points: degree class 5 (degree 4) keeps control points on every storage type,
 // since its rows share their fifth column with the next entry, which leaves no room for a
@@ -89,15 +98,18 @@ struct ModelDev {
     AxisDev ax[3];
     const void* win;    // window array (see above)
     const void* raw;    // the stored control points, plain [n_z][n_y][n_x], of type raw_storage
+                        // (NULL on compact models, whose window holds them)
     int nxp, nyp, nzp;  // padded sizes n + kPad
     int q;              // Q = max degree + 1 (kernel template parameter)
-    int storage;        // mfa_dtype of the window values (kernel template parameter)
+    int storage;        // window type (kernel template parameter): 1..3 layer pairs of FP32 / FP16
+                        // / BF16 values, 4..6 compact plain array of FP32 / FP16 / BF16
     int raw_storage;    // mfa_dtype of the stored control points (FP32 windows may hold 16-bit values)
     int cardinal;       // 1: uniform knots and degree Q-1 on all three axes, so interior
                         // spans share the cardinal basis (render variant 6 applies)
     const float2* cell; // per knot-span cell (i, j, k) = (span - p per axis), x fastest:
                         // {min, max} of the stored control points of its support, which
-                        // bound the model on the cell (convex hull property)
+                        // bound the model on the cell (convex hull property); NULL on
+                        // compact models (no bounds: every sample is queried)
     int ncx, ncy, ncz;  // cells per axis, n - p
     unsigned* dbg;      // debug word (debug builds) or NULL
 };
@@ -152,16 +164,16 @@ struct BatchHead {
     int items_offset;   // bytes from the start of the table
 };
 // Groups: (record / cardinal path) x (storage F32/F16/BF16) x (Q = 2..5).
-constexpr int kBatchGroups = 24;
-constexpr int kBatchItemsOffset = 512;    // heads occupy the first 512 bytes
+constexpr int kBatchGroups = 48;
+constexpr int kBatchItemsOffset = 1024;   // heads occupy the first 1024 bytes
 static_assert(kBatchGroups * sizeof(BatchHead) <= kBatchItemsOffset, "batch heads overflow");
 __host__ __device__ constexpr int batch_group(int q, int storage, int cardinal)
 {
-    return (cardinal * 3 + (storage - 1)) * 4 + (q - 2);
+    return (cardinal * kWindowTypes + (storage - 1)) * 4 + (q - 2);
 }
 __host__ __device__ constexpr int batch_group_q(int g) { return g % 4 + 2; }
-__host__ __device__ constexpr int batch_group_storage(int g) { return g / 4 % 3 + 1; }
-__host__ __device__ constexpr int batch_group_cardinal(int g) { return g / 12; }
+__host__ __device__ constexpr int batch_group_storage(int g) { return g / 4 % kWindowTypes + 1; }
+__host__ __device__ constexpr int batch_group_cardinal(int g) { return g / (4 * kWindowTypes); }
 
 // launchers (defined in the .cu files), all asynchronous on `stream`
 cudaError_t launch_prep_axis(const double* d_knots, int n, int p, int q, float* kup, float* rec, int* grid,
@@ -171,8 +183,8 @@ cudaError_t launch_prep_raw(const void* d_ctrl, int in_dtype, int storage, long 
                             cudaStream_t stream);
 // the window array from the stored control points (coef64: the x axis's FP64 span
 // coefficients for FP32 power rows, NULL for 16-bit rows)
-cudaError_t launch_prep_window(const void* raw, int raw_storage, int nx, int ny, int nz, int q, const double* coef64,
-                               int px, void* win, int storage, cudaStream_t stream);
+cudaError_t launch_prep_window(const void* raw, int raw_storage, int nx, int ny, int nz, int nxp, int q,
+                               const double* coef64, int px, void* win, int storage, cudaStream_t stream);
 cudaError_t launch_prep_cells(const void* raw, int storage, const int degree[3], const int nctrl[3], float2* cell,
                               cudaStream_t stream);
 cudaError_t launch_prep_stats(const void* raw, int storage, long long total, int* d_stats, cudaStream_t stream);

@@ -148,11 +148,12 @@ __device__ __forceinline__ double raw_at(const void* raw, int storage, int nx, i
 // 16-bit windows copy the stored values bit for bit.  FP32 windows with coef64 (the x
 // axis's FP64 span coefficients, [span][c][r]) store each row's power form on its x span
 // i: W_c = sum_r c_{c,r} P[i + r], summed in FP64 from the exact stored values and rounded
-// once; entries with no span (i >= n_x - p_x) are zero.
-__global__ void k_window(const void* __restrict__ raw, int raw_storage, int nx, int ny, int nz, int q,
+// once; entries with no span (i >= n_x - p_x) are zero.  Compact windows (storage 4..6) are
+// the zero-padded plain array of the stored values, one value per entry.
+__global__ void k_window(const void* __restrict__ raw, int raw_storage, int nx, int ny, int nz, int nxp, int q,
                          const double* __restrict__ coef64, int px, void* __restrict__ win, int storage)
 {
-    const int nxp = nx + kPad, nyp = ny + kPad, nzp = nz + kPad;
+    const int nyp = ny + kPad, nzp = nz + kPad;
     const long long total = static_cast<long long>(nxp) * nyp * nzp;
     for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
          e += static_cast<long long>(gridDim.x) * blockDim.x) {
@@ -160,6 +161,14 @@ __global__ void k_window(const void* __restrict__ raw, int raw_storage, int nx, 
         const long long jk = e / nxp;
         const int j = static_cast<int>(jk % nyp);
         const int k = static_cast<int>(jk / nyp);
+        if (storage >= 4) {   // compact layout: the padded plain array itself
+            const double x = raw_at(raw, raw_storage, nx, ny, nz, i, j, k);
+            if (storage == 4)
+                static_cast<float*>(win)[e] = static_cast<float>(x);
+            else
+                static_cast<unsigned short*>(win)[e] = to16(x, storage - 3);
+            continue;
+        }
         // P[r][a] = P[k + r][j][i + a] for the entry's layers r = 0..2 and columns a = 0..3
         double P[3][4];
 #pragma unroll
@@ -308,11 +317,12 @@ cudaError_t launch_prep_raw(const void* d_ctrl, int in_dtype, int storage, long 
     return cudaGetLastError();
 }
 
-cudaError_t launch_prep_window(const void* raw, int raw_storage, int nx, int ny, int nz, int q, const double* coef64,
-                               int px, void* win, int storage, cudaStream_t stream)
+cudaError_t launch_prep_window(const void* raw, int raw_storage, int nx, int ny, int nz, int nxp, int q,
+                               const double* coef64, int px, void* win, int storage, cudaStream_t stream)
 {
-    const long long total = static_cast<long long>(nx + kPad) * (ny + kPad) * (nz + kPad);
-    k_window<<<grid_blocks(total, 65536), 256, 0, stream>>>(raw, raw_storage, nx, ny, nz, q, coef64, px, win, storage);
+    const long long total = static_cast<long long>(nxp) * (ny + kPad) * (nz + kPad);
+    k_window<<<grid_blocks(total, 65536), 256, 0, stream>>>(raw, raw_storage, nx, ny, nz, nxp, q, coef64, px, win,
+                                                            storage);
     return cudaGetLastError();
 }
 

@@ -86,6 +86,9 @@ cudaError_t decode_qcg(const ModelDev& m, const float* pts, long long n, float* 
     case 1: k_decode<Q, 1, CARD, GRAD><<<blocks, 256, 0, st>>>(m, pts, n, val, grad); break;
     case 2: k_decode<Q, 2, CARD, GRAD><<<blocks, 256, 0, st>>>(m, pts, n, val, grad); break;
     case 3: k_decode<Q, 3, CARD, GRAD><<<blocks, 256, 0, st>>>(m, pts, n, val, grad); break;
+    case 4: k_decode<Q, 4, CARD, GRAD><<<blocks, 256, 0, st>>>(m, pts, n, val, grad); break;
+    case 5: k_decode<Q, 5, CARD, GRAD><<<blocks, 256, 0, st>>>(m, pts, n, val, grad); break;
+    case 6: k_decode<Q, 6, CARD, GRAD><<<blocks, 256, 0, st>>>(m, pts, n, val, grad); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

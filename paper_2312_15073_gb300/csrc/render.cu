@@ -421,37 +421,48 @@ cudaError_t render_qs(const ModelDev& m, const RenderParams& rp, int variant, in
 {
     const TileShape T = tile_shape(shape);
     dim3 grid((rp.s.width + T.tw - 1) / T.tw, (rp.s.height + T.th - 1) / T.th);
-    switch (variant) {
-    case 2: k_render<Q, STORAGE, 2><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
-    case 1: k_render<Q, STORAGE, 1><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
-    case 7:   // empty-space skipping (needs the visibility bits; without them, variant 6 / 4)
-        if (m.cardinal && rp.s.cell_vis)
-            k_render<Q, STORAGE, 7><<<grid, kThreads, 0, st>>>(m, rp, shape);
-        else if (rp.s.cell_vis)
-            k_render<Q, STORAGE, 8><<<grid, kThreads, 0, st>>>(m, rp, shape);
-        else if (m.cardinal)
-            k_render<Q, STORAGE, 6><<<grid, kThreads, 0, st>>>(m, rp, shape);
-        else
-            k_render<Q, STORAGE, 4><<<grid, kThreads, 0, st>>>(m, rp, shape);
-        break;
-    case 0:   // default: the cardinal path where it applies, else variant 4
-    case 6:
+    if constexpr (compact_window(STORAGE)) {
+        // the compact layout has the production marches only: the cardinal path where it
+        // applies, else variant 4; variant 7 (skipping) needs cell bounds, which compact
+        // models do not keep
         if (m.cardinal)
             k_render<Q, STORAGE, 6><<<grid, kThreads, 0, st>>>(m, rp, shape);
         else
             k_render<Q, STORAGE, 4><<<grid, kThreads, 0, st>>>(m, rp, shape);
-        break;
-    case 4: k_render<Q, STORAGE, 4><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
-    case 5:
-        if constexpr (Q <= 4) {
-            k_render<Q, STORAGE, 5><<<grid, kThreads, 0, st>>>(m, rp, shape);
-        } else {
-            k_render<Q, STORAGE, 4><<<grid, kThreads, 0, st>>>(m, rp, shape);   // bricks hold 4-wide rows
+        return cudaGetLastError();
+    } else {
+        switch (variant) {
+        case 2: k_render<Q, STORAGE, 2><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
+        case 1: k_render<Q, STORAGE, 1><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
+        case 7:   // empty-space skipping (needs the visibility bits; without them, variant 6 / 4)
+            if (m.cardinal && rp.s.cell_vis)
+                k_render<Q, STORAGE, 7><<<grid, kThreads, 0, st>>>(m, rp, shape);
+            else if (rp.s.cell_vis)
+                k_render<Q, STORAGE, 8><<<grid, kThreads, 0, st>>>(m, rp, shape);
+            else if (m.cardinal)
+                k_render<Q, STORAGE, 6><<<grid, kThreads, 0, st>>>(m, rp, shape);
+            else
+                k_render<Q, STORAGE, 4><<<grid, kThreads, 0, st>>>(m, rp, shape);
+            break;
+        case 0:   // default: the cardinal path where it applies, else variant 4
+        case 6:
+            if (m.cardinal)
+                k_render<Q, STORAGE, 6><<<grid, kThreads, 0, st>>>(m, rp, shape);
+            else
+                k_render<Q, STORAGE, 4><<<grid, kThreads, 0, st>>>(m, rp, shape);
+            break;
+        case 4: k_render<Q, STORAGE, 4><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
+        case 5:
+            if constexpr (Q <= 4) {
+                k_render<Q, STORAGE, 5><<<grid, kThreads, 0, st>>>(m, rp, shape);
+            } else {
+                k_render<Q, STORAGE, 4><<<grid, kThreads, 0, st>>>(m, rp, shape);   // bricks hold 4-wide rows
+            }
+            break;
+        default: k_render<Q, STORAGE, 3><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
         }
-        break;
-    default: k_render<Q, STORAGE, 3><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
 }
 
 template <int Q>
@@ -461,6 +472,9 @@ cudaError_t render_q(const ModelDev& m, const RenderParams& rp, int variant, int
     case 1: return render_qs<Q, 1>(m, rp, variant, shape, st);
     case 2: return render_qs<Q, 2>(m, rp, variant, shape, st);
     case 3: return render_qs<Q, 3>(m, rp, variant, shape, st);
+    case 4: return render_qs<Q, 4>(m, rp, variant, shape, st);
+    case 5: return render_qs<Q, 5>(m, rp, variant, shape, st);
+    case 6: return render_qs<Q, 6>(m, rp, variant, shape, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -579,6 +593,9 @@ cudaError_t segments_q(const ModelDev& m, const RenderParams& rp, bool cardinal,
     case 1: return segments_qs<Q, 1>(m, rp, cardinal, shape, g, partial, st);
     case 2: return segments_qs<Q, 2>(m, rp, cardinal, shape, g, partial, st);
     case 3: return segments_qs<Q, 3>(m, rp, cardinal, shape, g, partial, st);
+    case 4: return segments_qs<Q, 4>(m, rp, cardinal, shape, g, partial, st);
+    case 5: return segments_qs<Q, 5>(m, rp, cardinal, shape, g, partial, st);
+    case 6: return segments_qs<Q, 6>(m, rp, cardinal, shape, g, partial, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -760,9 +777,14 @@ BatchKernel serve_kernel_qs()
 template <int Q, bool CARD>
 BatchKernel serve_kernel_qc(int storage)
 {
-    return storage == 1   ? serve_kernel_qs<Q, 1, CARD>()
-           : storage == 2 ? serve_kernel_qs<Q, 2, CARD>()
-                          : serve_kernel_qs<Q, 3, CARD>();
+    switch (storage) {
+    case 1: return serve_kernel_qs<Q, 1, CARD>();
+    case 2: return serve_kernel_qs<Q, 2, CARD>();
+    case 3: return serve_kernel_qs<Q, 3, CARD>();
+    case 4: return serve_kernel_qs<Q, 4, CARD>();
+    case 5: return serve_kernel_qs<Q, 5, CARD>();
+    default: return serve_kernel_qs<Q, 6, CARD>();
+    }
 }
 
 template <int Q, int STORAGE, bool CARD>
@@ -780,9 +802,14 @@ BatchKernel batch_kernel_qs()
 template <int Q, bool CARD>
 BatchKernel batch_kernel_qc(int storage)
 {
-    return storage == 1   ? batch_kernel_qs<Q, 1, CARD>()
-           : storage == 2 ? batch_kernel_qs<Q, 2, CARD>()
-                          : batch_kernel_qs<Q, 3, CARD>();
+    switch (storage) {
+    case 1: return batch_kernel_qs<Q, 1, CARD>();
+    case 2: return batch_kernel_qs<Q, 2, CARD>();
+    case 3: return batch_kernel_qs<Q, 3, CARD>();
+    case 4: return batch_kernel_qs<Q, 4, CARD>();
+    case 5: return batch_kernel_qs<Q, 5, CARD>();
+    default: return batch_kernel_qs<Q, 6, CARD>();
+    }
 }
 
 template <int Q>

@@ -140,7 +140,7 @@ def test_host_side_argument_checks(libmfa):
     assert not L.mfa_model_create_ex(ctypes.byref(deg), ctypes.byref(nc), None, ctrl.ctypes.data, 0, 0)
     assert "storage" in L.mfa_last_error().decode()
     L.mfa_model_create_opts.restype = ctypes.c_void_p
-    for window in (-1, 2, 7):                                           # not an MFA_WINDOW_* choice
+    for window in (-1, 3, 7):                                           # not an MFA_WINDOW_* choice
         assert not L.mfa_model_create_opts(ctypes.byref(deg), ctypes.byref(nc), None, ctrl.ctypes.data, 0, 1, window)
         assert "window" in L.mfa_last_error().decode()
     L.mfa_model_destroy(None)          # a no-op

@@ -33,14 +33,16 @@ CASES = [((3, 3, 3), (22, 18, 20), True, 1), ((3, 3, 3), (17, 19, 21), False, 1)
          ((3, 3, 3), (24, 20, 16), True, 2), ((2, 2, 2), (15, 13, 14), False, 3)]
 
 
-@pytest.mark.parametrize("degree,nctrl,uniform,storage", CASES)
-def test_iso_matches_oracle(mfa, orc, degree, nctrl, uniform, storage):
+@pytest.mark.parametrize("degree,nctrl,uniform,storage,window",
+                         [c + (0,) for c in CASES] + [CASES[0] + (2,), CASES[3] + (2,), CASES[1] + (2,)])
+def test_iso_matches_oracle(mfa, orc, degree, nctrl, uniform, storage, window):
+    """window 2: compact models, which keep no cell bounds (every sample is queried)."""
     import torch
     rng = np.random.default_rng(zlib.crc32(repr((degree, nctrl, uniform, storage)).encode()))
     knots = [synth.knots_uniform(nctrl[a], degree[a]) if uniform else synth.knots_nonuniform(nctrl[a], degree[a], rng)
              for a in range(3)]
     P = synth.sample_ctrl(synth.GaussianSum.draw(rng, 6), knots, degree, rng, 0.01)
-    m = mfa.Model(degree, nctrl, knots, P, storage=storage)
+    m = mfa.Model(degree, nctrl, knots, P, storage=storage, window=window)
     stored = _stored(P, storage, orc)
     ref = orc.Model(degree, nctrl, knots, stored)
     iso = float(np.percentile(stored, 65))

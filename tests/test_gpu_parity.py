@@ -62,13 +62,13 @@ def _edge_points(knots, rng, n_random):
     return np.concatenate(pts)
 
 
-def _make(mfa, orc, rng, degree, nctrl, uniform, storage=1, field=None):
+def _make(mfa, orc, rng, degree, nctrl, uniform, storage=1, field=None, window=0):
     knots = [synth.knots_uniform(nctrl[a], degree[a]) if uniform[a] else synth.knots_nonuniform(nctrl[a], degree[a], rng)
              for a in range(3)]
     if field is None:
         field = synth.GaussianSum.draw(rng, 6)
     P = synth.sample_ctrl(field, knots, degree, rng, 0.01)
-    model = mfa.Model(degree, nctrl, knots, P, storage=storage)
+    model = mfa.Model(degree, nctrl, knots, P, storage=storage, window=window)
     ref = orc.Model(degree, nctrl, knots, _stored(P, storage, orc))
     return model, ref, P
 
@@ -479,7 +479,7 @@ def test_f32_window_of_a_16bit_model(mfa, orc, storage, uniform):
     m16 = mfa.Model(degree, nctrl, knots, P, storage=storage, window=mfa.MFA_WINDOW_F32)
     m32 = mfa.Model(degree, nctrl, knots, stored, storage=mfa.MFA_F32)
     i16 = m16.info()
-    assert i16["storage"] == storage and i16["window"] == mfa.MFA_F32 and i16["cardinal"] == uniform
+    assert i16["storage"] == storage and i16["window"] == mfa.MFA_WINDOW_F32 and i16["cardinal"] == uniform
     ref = orc.Model(degree, nctrl, knots, stored)
     pts = _edge_points(ref.knots, rng, 3001)
     v16, g16 = mfa.decode(m16, torch.from_numpy(pts).cuda())
@@ -497,3 +497,60 @@ def test_f32_window_of_a_16bit_model(mfa, orc, storage, uniform):
     o, _ = orc.render(ref, cam, table, 41, 29, 90, shading=True)
     assert np.all(image_rmse(a.cpu().numpy(), o) <= IMAGE_RMSE_TOL)
     assert np.array_equal(m16.ctrl(), m16.ctrl()) and m16.ctrl().dtype == (np.float16 if storage == 2 else np.uint16)
+
+
+# ----------------------------------------------------------------------------------------
+# the compact layout (MFA_WINDOW_COMPACT): the control points once, gathered value by value
+# ----------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("degree,nctrl,uniform", CASES)
+@pytest.mark.parametrize("storage", [1, 2, 3], ids=["f32", "f16", "bf16"])
+def test_compact_decode_matches_oracle(mfa, orc, degree, nctrl, uniform, storage):
+    """Decodes of a compact model against the oracle on the stored values (spans bit-exact,
+    value and gradient gates); 16-bit compact models equal the 16-bit layer-pair window's
+    results bit for bit (the same values enter the same sums), and every model reads back
+    its stored control points."""
+    import torch
+    rng = np.random.default_rng(_seed("compact", degree, nctrl, uniform, storage))
+    model, ref, P = _make(mfa, orc, rng, degree, nctrl, uniform, storage, window=mfa.MFA_WINDOW_COMPACT)
+    assert model.info()["window"] == mfa.MFA_WINDOW_COMPACT
+    pts = _edge_points(ref.knots, rng, 3001)
+    val, grad = mfa.decode(model, torch.from_numpy(pts).cuda())
+    spans = mfa.locate_spans(model, torch.from_numpy(pts).cuda())
+    v_ref, g_ref, s_ref = ref.decode(pts, spans=True)
+    np.testing.assert_array_equal(spans.cpu().numpy(), s_ref)
+    assert value_error(val.cpu().numpy(), v_ref, ref.ctrl) <= VALUE_TOL
+    assert grad_error(grad.cpu().numpy(), g_ref) <= GRAD_TOL
+    pairs = mfa.Model(degree, nctrl, [np.asarray(k) for k in ref.knots], P, storage=storage)
+    if storage != 1:
+        v2, g2 = mfa.decode(pairs, torch.from_numpy(pts).cuda())
+        assert torch.equal(v2, val) and torch.equal(g2, grad)
+    assert np.array_equal(model.ctrl(), pairs.ctrl())
+
+
+@pytest.mark.parametrize("degree,nctrl,uniform,cam,W,H,ns,shading", RENDER_CASES)
+@pytest.mark.parametrize("storage", [1, 2], ids=["f32", "f16"])
+def test_compact_render_matches_oracle(mfa, orc, degree, nctrl, uniform, cam, W, H, ns, shading, storage):
+    rng = np.random.default_rng(_seed("compact-render", degree, nctrl, cam, storage))
+    model, ref, _ = _make(mfa, orc, rng, degree, nctrl, uniform, storage, window=mfa.MFA_WINDOW_COMPACT)
+    if storage != 1:
+        ref = orc.Model(ref.degree, ref.nctrl, ref.knots, _stored(ref.ctrl, storage, orc))
+    job = synth.RenderJob(_camera(cam, rng), W, H, ns, synth.ramp_tf(256, 0.08), shading)
+    g, r, gc, rc = _render_both(mfa, orc, model, ref, job)
+    assert np.all(image_rmse(g, r) <= IMAGE_RMSE_TOL)
+    assert abs(gc - rc) <= max(2, 1e-3 * rc)
+
+
+def test_compact_fp16_device_bytes(mfa):
+    """A compact FP16 model holds at most 2.5x its plain FP16 bytes on the device (the padded
+    array and the per-axis tables), against about 8x for its layer-pair window."""
+    rng = np.random.default_rng(61)
+    n = (96, 80, 72)
+    P = rng.standard_normal(n[::-1])
+    raw = 2 * np.prod(n)
+    compact = mfa.Model((3, 3, 3), n, None, P, storage=mfa.MFA_F16, window=mfa.MFA_WINDOW_COMPACT)
+    pairs = mfa.Model((3, 3, 3), n, None, P, storage=mfa.MFA_F16)
+    print("device bytes / raw FP16 bytes: compact", compact.info()["device_bytes"] / raw, "pairs",
+          pairs.info()["device_bytes"] / raw)
+    assert compact.info()["device_bytes"] <= 2.5 * raw
+    assert pairs.info()["device_bytes"] >= 6 * raw

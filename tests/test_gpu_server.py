@@ -151,21 +151,23 @@ def test_server_rejects_bad_config(mfa):
 
 
 def test_queue_mixes_kernel_groups_and_reuses_records(mfa, orc):
-    """The device work queue with requests of several kernel groups at once (FP32 power rows
-    and FP16 rows, uniform knots on the cardinal path and non-uniform on the record path,
-    degrees 2 to 4) and more requests than records, so every record is republished several
-    times: each result equals the request rendered alone, and matches the oracle."""
+    """The device work queue with requests of several kernel groups at once (FP32 power rows,
+    FP16 rows and compact models, uniform knots on the cardinal path and non-uniform on the
+    record path, degrees 2 to 4) and more requests than records, so every record is
+    republished several times: each result equals the request rendered alone, and matches
+    the oracle."""
     import torch
     rng = np.random.default_rng(59)
-    specs = [((3, 3, 3), (20, 18, 22), 1, True), ((3, 3, 3), (17, 21, 15), 2, True),
-             ((2, 2, 2), (14, 16, 12), 1, False), ((4, 4, 4), (12, 12, 13), 3, False),
-             ((2, 3, 4), (13, 11, 16), 1, True)]
+    specs = [((3, 3, 3), (20, 18, 22), 1, True, 0), ((3, 3, 3), (17, 21, 15), 2, True, 0),
+             ((2, 2, 2), (14, 16, 12), 1, False, 0), ((4, 4, 4), (12, 12, 13), 3, False, 0),
+             ((2, 3, 4), (13, 11, 16), 1, True, 0), ((3, 3, 3), (15, 19, 17), 2, True, 2),
+             ((3, 3, 3), (16, 14, 18), 1, False, 2)]
     models = []
-    for deg, n, storage, uniform in specs:
+    for deg, n, storage, uniform, window in specs:
         knots = [synth.knots_uniform(n[a], deg[a]) if uniform else synth.knots_nonuniform(n[a], deg[a], rng)
                  for a in range(3)]
         P = synth.sample_ctrl(synth.GaussianSum.draw(rng, 5), knots, deg, rng, 0.01)
-        m = mfa.Model(deg, n, knots, P, storage=storage)
+        m = mfa.Model(deg, n, knots, P, storage=storage, window=window)
         stored = np.asarray(P, np.float64).astype(np.float32).astype(np.float64) if storage == 1 else (
             orc.round_to_f16(P) if storage == 2 else orc.round_to_bf16(P))
         models.append((m, orc.Model(deg, n, knots, stored)))
@@ -173,7 +175,7 @@ def test_queue_mixes_kernel_groups_and_reuses_records(mfa, orc):
     tf = mfa.transfer_fn(table, shading=True)
     srv = mfa.Server(hbm_budget_bytes=64 << 20, max_slots=3, mode=0)
     reqs = []
-    for k in range(15):
+    for k in range(21):
         d = synth.random_direction(rng)
         cam = synth.camera_persp(np.array([0.5, 0.5, 0.5]) + 2.3 * d, (0.5, 0.5, 0.5), synth.view_up_for(d), 35.0)
         reqs.append((k % len(models), cam, int(rng.integers(9, 70)), int(rng.integers(9, 70)), int(rng.integers(16, 96))))
