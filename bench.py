@@ -243,6 +243,63 @@ def oracle_rates(wl, budget_s: float, seed: int = 7):
     return ns1 / t1, len(pts) / td, info
 
 
+def oracle_checks(keep):
+    """Errors of the kept GPU results against the FP64 oracle (part of the cpu_baseline leg):
+    the small workload's full image; 4096 pixels of each of the 16 batched images; for the
+    precision sweep, per storage type, the value and gradient errors of 2^22 decoded points
+    and the image RMSE of a seeded pixel sample, each as kernel error (oracle on the same
+    rounded control points) and total error (oracle on the FP64 values)."""
+    import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from metrics import grad_error, image_rmse, value_error
+    oracle.build()
+    out = {}
+    if "c1" in keep:
+        wl = keep["c1"]["wl"]
+        spec, job = wl.model, wl.render
+        ref = oracle.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl64.astype(np.float32).astype(np.float64))
+        r, _ = oracle.render(ref, job.camera, job.tf, job.width, job.height, job.n_samples, shading=job.shading,
+                             ert_alpha=job.ert_alpha)
+        rm = image_rmse(keep["c1"]["img"], r)
+        out["c1_full_image_rmse"] = {"per_channel": rm.tolist(), "max": float(rm.max()), "gate": 1e-3}
+    if "c4" in keep:
+        rows = []
+        for sp, job, pix, got in keep["c4"]:
+            ref = oracle.Model(sp.degree, sp.nctrl, sp.knots, np.asarray(sp.ctrl, np.float64))
+            r, _ = oracle.render(ref, job.camera, job.tf, job.width, job.height, job.n_samples, shading=job.shading,
+                                 pixels=pix)
+            rows.append(float(image_rmse(got, r).max()))
+        out["c4_per_model_rmse"] = {"pixels_per_model": 4096, "max_channel_rmse": rows, "max": max(rows),
+                                    "gate": 1e-3}
+    if "c3" in keep:
+        wl = keep["c3"]["wl"]
+        spec, job = wl.model, wl.render
+        pix, pts = keep["c3"]["pixels"], wl.decode_points
+        exact = oracle.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl64)
+        v_x, g_x = exact.decode(pts)
+        r_x, _ = oracle.render(exact, job.camera, job.tf, job.width, job.height, job.n_samples, shading=True,
+                               pixels=pix)
+        del exact
+        c3 = {"points": len(pts), "pixels": len(pix)}
+        for name, rounding in (("f32", lambda P: P.astype(np.float32).astype(np.float64)),
+                               ("f16", oracle.round_to_f16), ("bf16", oracle.round_to_bf16)):
+            got = keep["c3"][name]
+            stored = rounding(spec.ctrl64)
+            ref = oracle.Model(spec.degree, spec.nctrl, spec.knots, stored)
+            v_k, g_k = ref.decode(pts)
+            r_k, _ = oracle.render(ref, job.camera, job.tf, job.width, job.height, job.n_samples, shading=True,
+                                   pixels=pix)
+            c3[name] = {"kernel": {"value": value_error(got["val"], v_k, stored), "gradient": grad_error(got["grad"], g_k),
+                                   "image_rmse": float(image_rmse(got["img"], r_k).max())},
+                        "total": {"value": value_error(got["val"], v_x, spec.ctrl64),
+                                  "gradient": grad_error(got["grad"], g_x),
+                                  "image_rmse": float(image_rmse(got["img"], r_x).max())}}
+            del ref, stored
+        c3["gates"] = {"value": 1e-5, "gradient": 1e-4, "image_rmse": 1e-3, "applies_to": "kernel error"}
+        out["c3_precision_errors"] = c3
+    return out
+
+
 # ------------------------------------------------------------------------------------------
 # reference arm: the oracle, as it stands
 # ------------------------------------------------------------------------------------------
@@ -480,7 +537,9 @@ def run_ours(args):
         "gpu_launches": (3 if tuned.get("variant") == 7 else 2) * args.steps,
         "clocks": clk,
     }
+    keep = {}   # GPU results the oracle checks in the cpu_baseline leg
     if ws == 1 and not args.no_side_rows:
+        line["c1"] = c1_small(mfa, torch, keep)
         line["precision"] = storage_throughput(mfa, torch, spec, job, tf)
         line["segments"] = segments_throughput(mfa, torch, model, job, tf, render_s)
         line["isosurface"] = iso_throughput(mfa, torch, spec, model, job, tf)
@@ -488,8 +547,8 @@ def run_ours(args):
         line["encoding"] = encode_throughput(mfa, torch)
         line["render_quality"] = render_quality(mfa, torch)
         line["query_sweep"] = query_sweep(mfa, torch)
-        line["c3_precision"] = c3_precision(mfa, torch)
-        line["batch"] = batch_throughput(mfa, torch)
+        line["c3_precision"] = c3_precision(mfa, torch, keep)
+        line["batch"] = batch_throughput(mfa, torch, keep)
         line["empty_space"] = empty_space(mfa, torch, spec, model, job)
     if ws == 1 and not args.no_serve:
         line["serving"] = dict(run_serve(mfa, rates=args.serve_rates, duration=args.serve_duration,
@@ -515,6 +574,8 @@ def run_ours(args):
                                     f"{o1['render_s']:.1f} s) + {o1['decode_points']} decode points "
                                     f"({o1['decode_s']:.1f} s) on one thread")},
         }
+        if keep:
+            line["oracle_checks"] = oracle_checks(keep)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -666,7 +727,7 @@ def empty_space(mfa, torch, spec, model, job, frames=5):
     return out
 
 
-def batch_throughput(mfa, torch, reps=3):
+def batch_throughput(mfa, torch, keep, reps=3):
     """The batched workload: 16 models (degrees 2, 3, 4; uniform and non-uniform knots;
     32..256 control points per axis), one image each (256^2..1024^2, 256..1024 samples):
     one CUDA-graph launch of the persistent batch kernels (tile shape from the batch
@@ -695,6 +756,12 @@ def batch_throughput(mfa, torch, reps=3):
         return a.elapsed_time(b) / reps, int(cnt.item()) / reps
 
     ms_batch, samples = timed(lambda: batch.render(reqs))
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(4004)
+    keep["c4"] = []
+    for (sp, job), q in zip(pairs, reqs):   # 4096 seeded pixels of each batched image
+        pix = rng.choice(job.width * job.height, min(4096, job.width * job.height), replace=False)
+        keep["c4"].append((sp, job, pix, q.out.cpu().numpy().reshape(-1, 4)[pix].astype(np.float64)))
     ms_single, _ = timed(lambda: [mfa.render(q.model, q.cam, q.tf, q.width, q.height, q.n_samples, out=q.out,
                                              samples_out=cnt) for q in reqs])
     batch.close()
@@ -705,11 +772,12 @@ def batch_throughput(mfa, torch, reps=3):
             "ms_separate_launches": ms_single}
 
 
-def c3_precision(mfa, torch, frames=3):
+def c3_precision(mfa, torch, keep, frames=3):
     """The precision-sweep workload: degree 3, 512x512x256 control points on non-uniform
     knots (turbulence), perspective 2048^2, 2048 samples per ray, Phong; one frame time and
     sample rate per storage type (FP32, FP16, BF16 from the same FP64 values), default
-    kernel (variant 4: the record path)."""
+    kernel (variant 4: the record path).  The decode of 2^22 points and a seeded pixel sample
+    of each frame are kept in `keep` for the oracle's error check."""
     import synth
     wl = synth.config3(dtype_in=np.float64)
     spec, job = wl.model, wl.render
@@ -717,6 +785,11 @@ def c3_precision(mfa, torch, frames=3):
     tf = mfa.transfer_fn(job.tf, shading=True)
     img = torch.empty((H, W, 4), device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    pts = torch.from_numpy(wl.decode_points).cuda()
+    rng = np.random.default_rng(3003)
+    pix = np.concatenate([rng.choice(W * H, 16384, replace=False)] +
+                         [r * W + np.arange(W) for r in rng.choice(H, 4, replace=False)])
+    keep["c3"] = {"wl": wl, "pixels": pix}
     out = {"model": "degree 3, 512x512x256, non-uniform knots, turbulence", "image": f"{W}x{H}", "n_samples": NS}
     for storage, name in ((mfa.MFA_F32, "f32"), (mfa.MFA_F16, "f16"), (mfa.MFA_BF16, "bf16")):
         m = mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl, storage=storage)
@@ -733,21 +806,56 @@ def c3_precision(mfa, torch, frames=3):
         samples = int(cnt.item()) / frames
         out[name] = {"ms_per_frame": ms, "samples_per_s": samples / (ms / 1e3),
                      "model_bytes": m.info()["device_bytes"]}
+        v, g = mfa.decode(m, pts)
+        keep["c3"][name] = {"val": v.cpu().numpy(), "grad": g.cpu().numpy(),
+                            "img": img.cpu().numpy().reshape(-1, 4)[pix].astype(np.float64)}
         m.close()
     return out
+
+
+def c1_small(mfa, torch, keep, frames=20):
+    """The small workload: degree 3, 32^3 FP64 control points (stored FP32), orthographic
+    256^2, 128 samples per ray, no shading; frames/s and samples/s, the image kept in `keep`
+    for the oracle's full-image check."""
+    import synth
+    wl = synth.config1()
+    spec, job = wl.model, wl.render
+    m = mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl)
+    tf = mfa.transfer_fn(job.tf, shading=job.shading, ert_alpha=job.ert_alpha)
+    img = torch.empty((job.height, job.width, 4), device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    mfa.render(m, job.camera, tf, job.width, job.height, job.n_samples, out=img)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(frames):
+        mfa.render(m, job.camera, tf, job.width, job.height, job.n_samples, out=img, samples_out=cnt)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b) / frames
+    samples = int(cnt.item()) / frames
+    keep["c1"] = {"wl": wl, "img": img.cpu().numpy().astype(np.float64)}
+    m.close()
+    return {"model": "degree 3, 32^3 control points (FP64 input, FP32 storage), 8 Gaussians + noise",
+            "image": f"{job.width}x{job.height} orthographic", "n_samples": job.n_samples, "ms_per_frame": ms,
+            "frames_per_s": 1e3 / ms, "samples_per_frame": samples, "samples_per_s": samples / (ms / 1e3)}
 
 
 def query_sweep(mfa, torch, n_pts=1 << 22, reps=5):
     """Value+gradient query rate against the control-point count and the degree (the
     paper's query-time study, Fig. 8, in spirit): 2^22 uniform random points per model,
-    uniform knots, random control points (the rate does not depend on the values)."""
+    uniform knots, random control points (the rate does not depend on the values); the
+    layer-pair window layout and the compact one (the control points once)."""
     rng = np.random.default_rng(20231215)
     pts = torch.rand((n_pts, 3), device="cuda", generator=torch.Generator(device="cuda").manual_seed(8))
     val = torch.empty(n_pts, device="cuda")
     grad = torch.empty((n_pts, 3), device="cuda")
     rows = []
-    for degree, n in ((3, 32), (3, 64), (3, 128), (3, 256), (3, 512), (1, 128), (2, 128), (4, 128)):
-        m = mfa.Model((degree,) * 3, (n,) * 3, None, rng.standard_normal((n, n, n), dtype=np.float32))
+    for degree, n, storage, window in ((3, 32, 1, 0), (3, 64, 1, 0), (3, 128, 1, 0), (3, 256, 1, 0), (3, 512, 1, 0),
+                                       (1, 128, 1, 0), (2, 128, 1, 0), (4, 128, 1, 0), (3, 128, 1, 2), (3, 256, 1, 2),
+                                       (3, 512, 1, 2), (3, 256, 2, 0), (3, 256, 2, 2)):
+        m = mfa.Model((degree,) * 3, (n,) * 3, None, rng.standard_normal((n, n, n), dtype=np.float32), storage=storage,
+                      window=window)
         for _ in range(3):
             mfa.decode(m, pts, val, grad)
         torch.cuda.synchronize()
@@ -758,8 +866,9 @@ def query_sweep(mfa, torch, n_pts=1 << 22, reps=5):
         b.record()
         b.synchronize()
         ms = a.elapsed_time(b) / reps
-        rows.append({"degree": degree, "nctrl": n, "model_bytes": m.info()["device_bytes"], "ms": ms,
-                     "queries_per_s": n_pts / (ms / 1e3)})
+        rows.append({"degree": degree, "nctrl": n, "storage": {1: "f32", 2: "f16"}[storage],
+                     "layout": {0: "window", 2: "compact"}[window], "model_bytes": m.info()["device_bytes"],
+                     "ms": ms, "queries_per_s": n_pts / (ms / 1e3)})
         m.close()
     return {"points": n_pts, "rows": rows}
 

@@ -676,12 +676,17 @@ __global__ void __launch_bounds__(kThreads, min_blocks<Q, CARD>()) k_render_batc
 // Thread 0 of a CTA walks the active list (most urgent first), skips records of other
 // groups and exhausted ones, and claims a tile of the first record that has one (atomicAdd
 // on the record's ticket word; the claim is checked against the record's generation and
-// tile count, see ServeRecord).  Records and the list are rewritten by the host while the
+// tile count, see ServeRecord).  Its next claims go straight to the same record (one atomic
+// instead of the walk's chain of dependent loads) until that record runs out or
+// kServeRewalk claims have passed.  Records and the list are rewritten by the host while the
 // kernel runs, so they are read through L2 (ld.cg), never from a possibly stale L1 line.
 // After a tile, the CTA counts it done; the CTA that finishes a record's last tile
 // publishes the record's generation to host-mapped memory (system-scope release), which the
 // server thread polls.  A CTA that finds nothing to claim exits: no wait anywhere.
 __device__ __forceinline__ int item_total(const ServeRecord* recs, int r) { return __ldcg(&recs[r].total_tiles); }
+
+// Tiles a CTA claims from the record it is on before it walks the active list again.
+constexpr int kServeRewalk = 8;
 
 template <int Q, int STORAGE, bool CARD>
 __global__ void __launch_bounds__(kThreads, min_blocks<Q, CARD>())
@@ -693,10 +698,40 @@ __global__ void __launch_bounds__(kThreads, min_blocks<Q, CARD>())
     __shared__ int s_rec, s_tile, s_gen;
     const TileShape T = tile_shape(shape);
     int cur_rec = -1, cur_gen = -1;
+    // thread 0 only: the record it claimed from last, its generation and tile count, and the
+    // claims made since the list was last walked
+    int last_rec = -1, last_gen = 0, last_total = 0, since_walk = 0;
     for (;;) {
         if (threadIdx.x == 0) {
             int rec = -1, tile = 0, gen = 0;
-            const int n = min(__ldcg(&queue->n_active), kServeMaxActive);
+            // another tile of the same record: one atomic, checked against the claim's
+            // generation and the record's tile count already known; the list is walked again
+            // after kServeRewalk claims so that newly published urgent requests get tiles soon
+            if (last_rec >= 0 && since_walk < kServeRewalk) {
+                ServeRecord* R = recs + last_rec;
+                const unsigned long long claim = atomicAdd(&R->ticket, 1ull);
+                const int g = static_cast<int>(claim >> 32), t = static_cast<int>(claim & 0xFFFFFFFFu);
+                if (g != last_gen) {
+                    // the record was republished since: a claim of its current generation is
+                    // as valid as any (and must not be dropped), so check it as the walk does
+                    const int total = __ldcg(&R->total_tiles);
+                    if (g == __ldcg(&R->gen) && t < total) {
+                        last_gen = g;
+                        last_total = total;
+                    }
+                }
+                if (g == last_gen && t < last_total) {
+                    rec = last_rec;
+                    tile = t;
+                    gen = g;
+                    ++since_walk;
+                }
+            }
+            const int n = rec >= 0 ? 0 : min(__ldcg(&queue->n_active), kServeMaxActive);
+            if (rec < 0) {
+                since_walk = 0;
+                last_rec = -1;
+            }
             for (int a = 0; a < n && rec < 0; ++a) {
                 const int r = __ldcg(&queue->active[a]);
                 ServeRecord* R = recs + r;
@@ -707,10 +742,14 @@ __global__ void __launch_bounds__(kThreads, min_blocks<Q, CARD>())
                     continue;   // exhausted, or being republished
                 const unsigned long long claim = atomicAdd(&R->ticket, 1ull);
                 const int g = static_cast<int>(claim >> 32), t = static_cast<int>(claim & 0xFFFFFFFFu);
-                if (g == __ldcg(&R->gen) && t < __ldcg(&R->total_tiles)) {
+                const int claim_total = __ldcg(&R->total_tiles);   // of the claim's generation when valid
+                if (g == __ldcg(&R->gen) && t < claim_total) {
                     rec = r;
                     tile = t;
                     gen = g;
+                    last_rec = r;
+                    last_gen = g;
+                    last_total = claim_total;
                 }
             }
             s_rec = rec;

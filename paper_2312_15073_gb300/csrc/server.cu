@@ -417,7 +417,11 @@ void worker_main(mfa_server* s)
                 s->done_cv.notify_all();
                 continue;   // freed slots: admit again
             }
-            s->cv.wait_for(lk, std::chrono::microseconds(20));   // poll the completions again soon
+            // poll the completions again soon: a short yield (a timed wait sleeps for the
+            // timer slack, tens of microseconds, and every request would pay it)
+            lk.unlock();
+            std::this_thread::yield();
+            lk.lock();
             continue;
         }
         s->cv.wait_for(lk, std::chrono::milliseconds(50));
