@@ -505,7 +505,7 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": "k_render", "achieved": achieved_tflops, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops, "traffic": render_traffic(),
                      "traffic_note": "DRAM bytes per launch from ncu (model and image stay in L2; "
-                                     "algorithmic bytes: 89 MiB layer-pair window of power rows + 16 MiB image)",
+                                     "algorithmic bytes: 70 MiB layer-pair window of power rows + 16 MiB image)",
                      "tuned": tuned,
                      "flops_per_sample": flops_sample,
                      "flops_note": "algorithmic count (sum-factorised contraction + span-local Cox-de Boor "
