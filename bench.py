@@ -853,7 +853,8 @@ def query_sweep(mfa, torch, n_pts=1 << 22, reps=5):
     rows = []
     for degree, n, storage, window in ((3, 32, 1, 0), (3, 64, 1, 0), (3, 128, 1, 0), (3, 256, 1, 0), (3, 512, 1, 0),
                                        (1, 128, 1, 0), (2, 128, 1, 0), (4, 128, 1, 0), (3, 128, 1, 2), (3, 256, 1, 2),
-                                       (3, 512, 1, 2), (3, 256, 2, 0), (3, 256, 2, 2)):
+                                       (3, 512, 1, 2), (3, 256, 2, 0), (3, 256, 2, 2), (3, 256, 3, 2),
+                                       (3, 512, 2, 2)):
         m = mfa.Model((degree,) * 3, (n,) * 3, None, rng.standard_normal((n, n, n), dtype=np.float32), storage=storage,
                       window=window)
         for _ in range(3):
@@ -866,7 +867,7 @@ def query_sweep(mfa, torch, n_pts=1 << 22, reps=5):
         b.record()
         b.synchronize()
         ms = a.elapsed_time(b) / reps
-        rows.append({"degree": degree, "nctrl": n, "storage": {1: "f32", 2: "f16"}[storage],
+        rows.append({"degree": degree, "nctrl": n, "storage": {1: "f32", 2: "f16", 3: "bf16"}[storage],
                      "layout": {0: "window", 2: "compact"}[window], "model_bytes": m.info()["device_bytes"],
                      "ms": ms, "queries_per_s": n_pts / (ms / 1e3)})
         m.close()

@@ -93,10 +93,13 @@ mfa_model* mfa_model_create_ex(const int degree[3], const int nctrl[3], const do
  * each value is widened to FP32 per query).  MFA_WINDOW_F32: FP32 window values whatever
  * the storage type -- the stored 16-bit values are widened exactly once, at creation, so
  * a 16-bit model computes the same sums at the speed of an FP32 one, with an FP32 model's
- * window bytes.  MFA_WINDOW_COMPACT: no window -- the control points are kept once, as a
- * zero-padded plain array of the storage type ((n_x+4)(n_y+4)(n_z+4) values), and the
- * kernels gather each support row value by value: slower per query, but a model of 1-1.5x
- * its plain size instead of 8-16x (for models that would not otherwise fit in L2 or in
+ * window bytes.  MFA_WINDOW_COMPACT: no layer-pair window.  FP32 models keep the zero-
+ * padded plain array of their control points ((n_x+4 rounded up to a multiple of 4) x
+ * (n_y+4) x (n_z+4) values; a support row is two aligned 16-byte loads); FP16 / BF16
+ * models keep it as entries of eight values, one entry every S = 8 - (largest degree)
+ * positions of an x-row (8/S times the plain size, 1.6x at degree 3), so that every
+ * support row is one aligned 16-byte load.  Slower per query, but a model of 1-2x its
+ * plain size instead of 8-16x (for models that would not otherwise fit in L2 or in
  * memory).  Compact models keep no per-cell bounds, so the isosurface search queries every
  * sample and render variant 7 falls back to the default; render variants 1, 2, 3 and 5
  * run as the default too. */

@@ -280,10 +280,10 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
             return fail(MFA_ERR_ARG, "nctrl[%d] = %d must be in degree+1..2^24", a, nctrl[a]), nullptr;
         qmax = degree[a] + 1 > qmax ? degree[a] + 1 : qmax;
     }
-    // padded sizes: kPad zeros past the end of every axis; compact FP32 models pad x to a
-    // multiple of 4 with at least 6 zeros, so that their rows load as aligned 16-byte vectors
-    const bool compact32 = window == MFA_WINDOW_COMPACT && storage == MFA_F32;
-    const long long nxp = compact32 ? (nctrl[0] + 6 + 3) / 4 * 4 : nctrl[0] + kPad;
+    // padded sizes: kPad zeros past the end of every axis; compact models round x up to a
+    // multiple of their entry stride, so that their rows are whole entries of eight values
+    const int cstride = compact_stride(qmax, wstore);
+    const long long nxp = compact ? (nctrl[0] + kPad + cstride - 1) / cstride * cstride : nctrl[0] + kPad;
     const long long nyp = nctrl[1] + kPad, nzp = nctrl[2] + kPad;
     if (nxp * nyp * nzp >= (1LL << 31))
         return fail(MFA_ERR_UNSUPPORTED, "model too large: (nx+4)(ny+4)(nz+4) must stay below 2^31"), nullptr;
@@ -337,8 +337,12 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
         compact ? 0 : static_cast<size_t>(nctrl[0] - degree[0]) * (nctrl[1] - degree[1]) * (nctrl[2] - degree[2]);
     tab = align_up(tab + sizeof(float2) * ncells, 256);
     const size_t val_bytes = storage == MFA_F32 ? 4 : 2;
-    const size_t win_elem = compact ? val_bytes : (wstore == MFA_F32 ? 4 : 2) * window_values(Q);   // one entry
-    const size_t win_bytes = static_cast<size_t>(nxp * nyp * nzp) * win_elem;
+    // a layer-pair entry per padded position, or entries of eight values per cstride positions
+    // (compact: eight spare values at the end, which an FP32 row's second load may touch)
+    const size_t win_bytes = compact ? (static_cast<size_t>(nxp / cstride * nyp * nzp) * compact_values(wstore) + 8) *
+                                           val_bytes
+                                     : static_cast<size_t>(nxp * nyp * nzp) * (wstore == MFA_F32 ? 4 : 2) *
+                                           window_values(Q);
     const size_t nctrl_total = static_cast<size_t>(nctrl[0]) * nctrl[1] * nctrl[2];
     const size_t raw_bytes = nctrl_total * val_bytes;
     const size_t off_raw = tab;   // the stored control points, plain array (staging only on compact models)

@@ -330,50 +330,89 @@ struct Pair16 {
     }
 };
 
-// The compact layout: the control points once, as the zero-padded plain array.  A window
-// entry index is the array index of P[k][j][i] (the padded sizes are the same), the layer
-// k+1 lies one padded layer (nxp nyp values) further, and every column pair is gathered
-// value by value (scalar loads; 16-bit values widened as above), zero past the ends.
+// The compact layout: the stored values at V / S times the zero-padded plain array, no layer
+// pairs, S = compact_stride(Q, type), V = compact_values(type).  Each padded x-row of n_xp
+// values (n_xp a multiple of S) is kept as n_xp / S entries of V values, entry e holding the
+// row's values S e .. S e + V - 1 (zeros past the row's end).  16-bit types: eight values
+// every S = 9 - Q positions (1.6x at degree 3), so the Q values of any support row lie
+// inside the entry it starts in: one aligned 16-byte load per row.  FP32: four values every
+// four positions (the plain array), a row read as its entry and the next (two aligned
+// 16-byte loads, mostly from one 32-byte sector).  Then a select by the row's offset
+// s = i mod S in the entry, one step per bit of s.  A window index idx is the position of P[k][j][i] in the
+// padded plain array (below 2^31); since rows hold whole entries its entry is idx / S and
+// its offset idx mod S, and the layer k+1 lies n_xp n_yp positions further.  Values a
+// column pair needs beyond the Q of its row (the padding column of degree classes 3 and 5)
+// are zero; they meet zero basis values.
 template <int Q, int VT>
 struct PairCompact {
-    static __device__ __forceinline__ float value(const ModelDev& M, long long i)
+    static constexpr int S = compact_stride(Q, VT + 3);
+    static constexpr int QP = qpair(Q);
+    static __device__ __forceinline__ void entry_of(long long idx, unsigned& e, int& s)
     {
-        if constexpr (VT == 1) {
-            return __ldg(static_cast<const float*>(M.win) + i);
-        } else {
-            const unsigned short h = __ldg(static_cast<const unsigned short*>(M.win) + i);
-            return VT == 2 ? __half2float(__ushort_as_half(h)) : __uint_as_float(static_cast<unsigned>(h) << 16);
+        const unsigned u = static_cast<unsigned>(idx);
+        e = u / S;
+        s = static_cast<int>(u - e * S);
+    }
+    // FP32: the row's values v[s .. s + Q - 1] (zero past them) from its entry and the next
+    // one (eight values from two aligned 16-byte loads; s <= 3, so s + Q - 1 <= 7)
+    static __device__ __forceinline__ void row(const ModelDev& M, long long idx, float (&o)[QP])
+    {
+        static_assert(S == 4, "FP32 compact entries are four values every four positions");
+        unsigned e;
+        int s;
+        entry_of(idx, e, s);
+        const float* p = static_cast<const float*>(M.win) + 4ull * e;
+        const float4 v0 = __ldg(reinterpret_cast<const float4*>(p)), v1 = __ldg(reinterpret_cast<const float4*>(p + 4));
+        const float v[12] = { v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, 0.0f, 0.0f, 0.0f, 0.0f };
+        // b = v shifted by 2 (s & 2), o = b shifted by 1 (s & 1)
+        float b[QP + 1];
+#pragma unroll
+        for (int x = 0; x <= QP; ++x) b[x] = (s & 2) ? v[x + 2] : v[x];
+#pragma unroll
+        for (int x = 0; x < QP; ++x) o[x] = x < Q ? ((s & 1) ? b[x + 1] : b[x]) : 0.0f;
+    }
+    // 16-bit: the row's values as 32-bit words of two, word c = {v[s + 2c], v[s + 2c + 1]},
+    // from one 128-bit load: word shifts by the bits 2 and 1 of s, a byte permute by bit 0
+    static constexpr int NW = QP / 2;
+    static __device__ __forceinline__ void row16(const ModelDev& M, long long idx, unsigned (&o)[NW])
+    {
+        unsigned e;
+        int s;
+        entry_of(idx, e, s);
+        const uint4 q = __ldg(static_cast<const uint4*>(M.win) + e);
+        const unsigned W[4] = { q.x, q.y, q.z, q.w };
+        unsigned A[NW + 2], B[NW + 1];
+#pragma unroll
+        for (int x = 0; x < NW + 2; ++x) {
+            const unsigned lo = x < 4 ? W[x] : 0u, hi = x + 2 < 4 ? W[x + 2] : 0u;
+            A[x] = (S > 4 && (s & 4)) ? hi : lo;
         }
+#pragma unroll
+        for (int x = 0; x <= NW; ++x) B[x] = (s & 2) ? A[x + 1] : A[x];
+        const unsigned sel = (s & 1) ? 0x5432u : 0x3210u;
+#pragma unroll
+        for (int c = 0; c < NW; ++c) o[c] = __byte_perm(B[c], B[c + 1], sel);
     }
-    // FP32 rows of up to four values: the aligned 32 bytes around them in two 16-byte loads
-    // (rows of a compact FP32 model start 16-byte aligned: nxp is a multiple of 4, with at
-    // least 6 values of padding), then a two-step select by the row's offset in them.
-    static constexpr bool kVector = VT == 1 && Q <= 4;
-    static __device__ __forceinline__ void row4(const ModelDev& M, long long idx, float (&o)[4])
-    {
-        const float* base = static_cast<const float*>(M.win) + (idx & ~3ll);
-        const float4 v0 = __ldg(reinterpret_cast<const float4*>(base));
-        const float4 v1 = __ldg(reinterpret_cast<const float4*>(base + 4));
-        const bool s2 = (idx & 2) != 0, s1 = (idx & 1) != 0;
-        const float a0 = s2 ? v0.z : v0.x, a1 = s2 ? v0.w : v0.y, a2 = s2 ? v1.x : v0.z, a3 = s2 ? v1.y : v0.w,
-                    a4 = s2 ? v1.z : v1.x;
-        o[0] = s1 ? a1 : a0;
-        o[1] = s1 ? a2 : a1;
-        o[2] = s1 ? a3 : a2;
-        o[3] = s1 ? a4 : a3;
-    }
-    static __device__ __forceinline__ void load(const ModelDev& M, int idx, f2 (&pr)[qpair(Q)])
+    static __device__ __forceinline__ f2 cvt2(unsigned bits) { return Pair16<Q, VT == 3>::cvt2(bits); }
+    static __device__ __forceinline__ void load(const ModelDev& M, int idx, f2 (&pr)[QP])
     {
         const long long layer = static_cast<long long>(M.nxp) * M.nyp;
-        if constexpr (kVector) {
-            float lo[4], hi[4];
-            row4(M, idx, lo);
-            row4(M, idx + layer, hi);
+        if constexpr (VT == 1) {
+            float lo[QP], hi[QP];
+            row(M, idx, lo);
+            row(M, idx + layer, hi);
 #pragma unroll
-            for (int a = 0; a < qpair(Q); ++a) pr[a] = pk2(lo[a], hi[a]);
+            for (int a = 0; a < QP; ++a) pr[a] = pk2(lo[a], hi[a]);
         } else {
+            unsigned lo[NW], hi[NW];
+            row16(M, idx, lo);
+            row16(M, idx + layer, hi);
+            // column pairs {layer k, layer k+1} as the 16-bit window's words
 #pragma unroll
-            for (int a = 0; a < qpair(Q); ++a) pr[a] = pk2(value(M, idx + a), value(M, idx + a + layer));
+            for (int c = 0; c < NW; ++c) {
+                pr[2 * c] = cvt2(__byte_perm(lo[c], hi[c], 0x5410u));
+                pr[2 * c + 1] = cvt2(__byte_perm(lo[c], hi[c], 0x7632u));
+            }
         }
     }
     static __device__ __forceinline__ void load_triple(const ModelDev& M, int idx, f2 (&pr)[4], float (&r3)[4])
@@ -381,11 +420,17 @@ struct PairCompact {
         static_assert(Q == 3, "third-layer rows exist in degree class 3 only");
         load(M, idx, pr);
         const long long layer2 = 2ll * M.nxp * M.nyp;
-        if constexpr (kVector) {
-            row4(M, idx + layer2, r3);
+        if constexpr (VT == 1) {
+            row(M, idx + layer2, r3);
         } else {
+            unsigned w[NW];
+            row16(M, idx + layer2, w);
 #pragma unroll
-            for (int a = 0; a < 4; ++a) r3[a] = value(M, idx + a + layer2);
+            for (int c = 0; c < NW; ++c) {
+                const float2 x = Pair16<Q, VT == 3>::cvt(w[c]);
+                r3[2 * c] = x.x;
+                r3[2 * c + 1] = x.y;
+            }
         }
     }
 };

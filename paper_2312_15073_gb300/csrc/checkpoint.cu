@@ -43,22 +43,30 @@ extern "C" int mfa_model_get_ctrl(const mfa_model* m, void* host_out)
     if (int rc = check_model_device(m)) return rc;
     const int nx = m->nctrl[0], ny = m->nctrl[1], nz = m->nctrl[2];
     const size_t bytes = static_cast<size_t>(nx) * ny * nz * storage_bytes(m->storage);
-    // the plain array of stored values is the model's own copy: one device-to-host copy;
-    // compact models hold them only in the zero-padded window, read as a 3-D region
+    // the plain array of stored values is the model's own copy: one device-to-host copy.
+    // Compact models hold them only in their entries (the first S values of entry e are the
+    // padded row's positions S e .. S e + S - 1, S the entry stride): a pitched copy of those
+    // gives the padded plain array, trimmed here on the host.
     cudaStream_t st = current_stream();
     cudaError_t e;
     if (m->dev.raw) {
         e = cudaMemcpyAsync(host_out, m->dev.raw, bytes, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     } else {
         const size_t elem = storage_bytes(m->storage);
-        cudaMemcpy3DParms p = {};
-        p.srcPtr = make_cudaPitchedPtr(const_cast<void*>(m->dev.win), elem * m->dev.nxp, m->dev.nxp, m->dev.nyp);
-        p.dstPtr = make_cudaPitchedPtr(host_out, elem * nx, nx, ny);
-        p.extent = make_cudaExtent(elem * nx, ny, nz);
-        p.kind = cudaMemcpyDeviceToHost;
-        e = cudaMemcpy3DAsync(&p, st);
+        const size_t nxp = m->dev.nxp, nyp = m->dev.nyp, nzp = m->dev.nzp;
+        const size_t S = compact_stride(m->dev.q, m->dev.storage), V = compact_values(m->dev.storage);
+        std::vector<unsigned char> padded(nxp * nyp * nzp * elem);
+        e = cudaMemcpy2DAsync(padded.data(), S * elem, m->dev.win, V * elem, S * elem, nxp / S * nyp * nzp,
+                              cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) {
+            unsigned char* dst = static_cast<unsigned char*>(host_out);
+            for (size_t k = 0; k < static_cast<size_t>(nz); ++k)
+                for (size_t j = 0; j < static_cast<size_t>(ny); ++j)
+                    std::memcpy(dst + ((k * ny + j) * nx) * elem, padded.data() + ((k * nyp + j) * nxp) * elem, nx * elem);
+        }
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? MFA_OK : cuda_fail(e, "read control points");
 }
 

@@ -49,11 +49,22 @@ __host__ __device__ constexpr int window_values(int q) { return q == 3 ? 16 : 8;
 __host__ __device__ constexpr int qpair(int q) { return (q + 1) / 2 * 2; }
 __host__ __device__ constexpr int rec_stride(int q) { return ((kRecHead + q * qpair(q)) + 3) / 4 * 4; }
 // Window types (ModelDev::storage, a kernel template parameter): 1..3 layer-pair windows
-// with FP32 / FP16 / BF16 values; 4..6 the compact layout, the control points once as a
-// zero-padded plain array [n_z+4][n_y+4][nxp] of FP32 / FP16 / BF16 (nxp = n_x+4, or for
-// FP32 n_x+6 rounded up to a multiple of 4), whose layer pairs the kernels gather row by
-// row (about 1.1x the plain array instead of 8x).
+// with FP32 / FP16 / BF16 values; 4..6 the compact layout of FP32 / FP16 / BF16 values:
+// the zero-padded plain array [n_z+4][n_y+4][nxp] (nxp = n_x+4 rounded up to a multiple of
+// the stride S = compact_stride(q, storage)) kept as entries of V = compact_values(storage)
+// values, entry e of an x-row holding its values S e .. S e + V - 1, from which the kernels
+// gather layer pairs row by row (one 16-byte load per 16-bit row, two per FP32 row): V/S
+// times the padded plain array, 1x FP32 and 1.6x FP16 / BF16 at degree 3, instead of 8x.
 constexpr int kWindowTypes = 6;
+// Compact entries of window type storage (4..6) and degree class q: compact_values values
+// each, one every compact_stride positions of a padded x-row.  16-bit types: eight values
+// every 9 - q positions, so that a row of q values starting at any of an entry's first
+// 9 - q positions lies inside it (one 16-byte load per row, 8 / (9 - q) times the plain
+// array).  FP32: four values every four positions, the plain array itself, a row read as
+// its entry and the next one (two 16-byte loads); at 1.6x the FP32 values of a 256^3 model
+// no longer stay in L2, which costs more than the second load.
+__host__ __device__ constexpr int compact_stride(int q, int storage) { return storage == 4 ? 4 : 9 - q; }
+__host__ __device__ constexpr int compact_values(int storage) { return storage == 4 ? 4 : 8; }
 __host__ __device__ constexpr bool compact_window(int storage) { return storage >= 4; }
 __host__ __device__ constexpr int window_value_type(int storage) { return storage >= 4 ? storage - 3 : storage; }
 
@@ -102,7 +113,7 @@ struct ModelDev {
     int nxp, nyp, nzp;  // padded sizes n + kPad
     int q;              // Q = max degree + 1 (kernel template parameter)
     int storage;        // window type (kernel template parameter): 1..3 layer pairs of FP32 / FP16
-                        // / BF16 values, 4..6 compact plain array of FP32 / FP16 / BF16
+                        // / BF16 values, 4..6 compact entries of FP32 / FP16 / BF16 values
     int raw_storage;    // mfa_dtype of the stored control points (FP32 windows may hold 16-bit values)
     int cardinal;       // 1: uniform knots and degree Q-1 on all three axes, so interior
                         // spans share the cardinal basis (render variant 6 applies)

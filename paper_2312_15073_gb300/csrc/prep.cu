@@ -148,8 +148,8 @@ __device__ __forceinline__ double raw_at(const void* raw, int storage, int nx, i
 // 16-bit windows copy the stored values bit for bit.  FP32 windows with coef64 (the x
 // axis's FP64 span coefficients, [span][c][r]) store each row's power form on its x span
 // i: W_c = sum_r c_{c,r} P[i + r], summed in FP64 from the exact stored values and rounded
-// once; entries with no span (i >= n_x - p_x) are zero.  Compact windows (storage 4..6) are
-// the zero-padded plain array of the stored values, one value per entry.
+// once; entries with no span (i >= n_x - p_x) are zero.  Compact windows are built by
+// k_window_compact.
 __global__ void k_window(const void* __restrict__ raw, int raw_storage, int nx, int ny, int nz, int nxp, int q,
                          const double* __restrict__ coef64, int px, void* __restrict__ win, int storage)
 {
@@ -161,14 +161,6 @@ __global__ void k_window(const void* __restrict__ raw, int raw_storage, int nx, 
         const long long jk = e / nxp;
         const int j = static_cast<int>(jk % nyp);
         const int k = static_cast<int>(jk / nyp);
-        if (storage >= 4) {   // compact layout: the padded plain array itself
-            const double x = raw_at(raw, raw_storage, nx, ny, nz, i, j, k);
-            if (storage == 4)
-                static_cast<float*>(win)[e] = static_cast<float>(x);
-            else
-                static_cast<unsigned short*>(win)[e] = to16(x, storage - 3);
-            continue;
-        }
         // P[r][a] = P[k + r][j][i + a] for the entry's layers r = 0..2 and columns a = 0..3
         double P[3][4];
 #pragma unroll
@@ -215,6 +207,29 @@ __global__ void k_window(const void* __restrict__ raw, int raw_storage, int nx, 
                 w[c] = make_uint4(b[0], b[1], b[2], b[3]);
             }
         }
+    }
+}
+
+// The compact window (storage 4..6): per padded x-row of nxp positions (a multiple of the
+// stride S), entry e holds the V stored values at positions S e .. S e + V - 1, zero past
+// the grid; one thread per value slot.
+__global__ void k_window_compact(const void* __restrict__ raw, int raw_storage, int nx, int ny, int nz, int nxp,
+                                 int S, int V, void* __restrict__ win, int storage)
+{
+    const int ne = nxp / S;
+    const long long slots = static_cast<long long>(ne) * (ny + kPad) * (nz + kPad) * V;
+    for (long long v = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; v < slots;
+         v += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int c = static_cast<int>(v % V);
+        const long long ent = v / V;
+        const int i = static_cast<int>(ent % ne) * S + c;
+        const long long jk = ent / ne;
+        const int j = static_cast<int>(jk % (ny + kPad)), k = static_cast<int>(jk / (ny + kPad));
+        const double x = raw_at(raw, raw_storage, nx, ny, nz, i, j, k);
+        if (storage == 4)
+            static_cast<float*>(win)[v] = static_cast<float>(x);
+        else
+            static_cast<unsigned short*>(win)[v] = to16(x, storage - 3);
     }
 }
 
@@ -320,6 +335,16 @@ cudaError_t launch_prep_raw(const void* d_ctrl, int in_dtype, int storage, long 
 cudaError_t launch_prep_window(const void* raw, int raw_storage, int nx, int ny, int nz, int nxp, int q,
                                const double* coef64, int px, void* win, int storage, cudaStream_t stream)
 {
+    if (compact_window(storage)) {
+        const int S = compact_stride(q, storage), V = compact_values(storage);
+        const long long slots = static_cast<long long>(nxp) / S * (ny + kPad) * (nz + kPad) * V;
+        cudaError_t e = cudaMemsetAsync(static_cast<char*>(win) + slots * (storage == 4 ? 4 : 2), 0,
+                                        8 * (storage == 4 ? 4 : 2), stream);   // the spare values
+        if (e != cudaSuccess) return e;
+        k_window_compact<<<grid_blocks(slots, 65536), 256, 0, stream>>>(raw, raw_storage, nx, ny, nz, nxp, S, V, win,
+                                                                        storage);
+        return cudaGetLastError();
+    }
     const long long total = static_cast<long long>(nxp) * (ny + kPad) * (nz + kPad);
     k_window<<<grid_blocks(total, 65536), 256, 0, stream>>>(raw, raw_storage, nx, ny, nz, nxp, q, coef64, px, win,
                                                             storage);

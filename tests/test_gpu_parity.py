@@ -500,7 +500,9 @@ def test_f32_window_of_a_16bit_model(mfa, orc, storage, uniform):
 
 
 # ----------------------------------------------------------------------------------------
-# the compact layout (MFA_WINDOW_COMPACT): the control points once, gathered value by value
+# the compact layout (MFA_WINDOW_COMPACT): the plain array for FP32 (two loads per support
+# row); entries of eight control points every 8 - degree positions of a row for 16-bit
+# types (1.6x the plain array at degree 3, one load per support row)
 # ----------------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("degree,nctrl,uniform", CASES)
@@ -542,8 +544,9 @@ def test_compact_render_matches_oracle(mfa, orc, degree, nctrl, uniform, cam, W,
 
 
 def test_compact_fp16_device_bytes(mfa):
-    """A compact FP16 model holds at most 2.5x its plain FP16 bytes on the device (the padded
-    array and the per-axis tables), against about 8x for its layer-pair window."""
+    """A compact FP16 model holds at most 2.5x its plain FP16 bytes on the device (its entries
+    of eight values, 1.6x the padded array at degree 3, and the per-axis tables), against
+    about 8x for its layer-pair window."""
     rng = np.random.default_rng(61)
     n = (96, 80, 72)
     P = rng.standard_normal(n[::-1])
