@@ -658,10 +658,9 @@ __device__ __forceinline__ XIn<Q, STORAGE> xin_record(const float (&rec)[rec_str
 // packed as in contract_pairs, and the entry's third-layer row k0+2, run as plain FP32
 // FMAs beside it (the same x, y and z sums; no lane multiplies a padding layer).  Weights
 // arrive packed as for contract_pairs: nz[0] = {Nz_0, Nz_1}, nz[1] = {Nz_2, 0}.
-template <int STORAGE>
-__device__ __forceinline__ float4 contract_triple(const ModelDev& M, int base, const XIn<3, STORAGE>& Xin,
-                                                  const f2 (&ny)[3], const f2 (&dy)[3], const f2 (&nz)[2],
-                                                  const f2 (&dz)[2])
+template <int STORAGE, class Rows>
+__device__ __forceinline__ float4 contract_triple_rows(Rows&& rows, const XIn<3, STORAGE>& Xin, const f2 (&ny)[3],
+                                                       const f2 (&dy)[3], const f2 (&nz)[2], const f2 (&dz)[2])
 {
     const auto X = pack_x(Xin);
     f2 CC, DD, EE;
@@ -670,9 +669,7 @@ __device__ __forceinline__ float4 contract_triple(const ModelDev& M, int base, c
     for (int b = 0; b < 3; ++b) {
         f2 pr[4];
         float r3[4];
-        int idx = base + b * M.nxp;
-        MFA_DBG_INDEX(M.dbg, idx, static_cast<long long>(M.nxp) * M.nyp * M.nzp, kDbgWindow);
-        PairLoader<3, STORAGE>::load_triple(M, idx, pr, r3);
+        rows(b, pr, r3);
         f2 A, B;
         float A3, B3;
         x_row<3, STORAGE>(pr, X, A, B);
@@ -699,6 +696,25 @@ __device__ __forceinline__ float4 contract_triple(const ModelDev& M, int base, c
                        fmaf(nz2, D3, hsum2(mul2(nz[0], DD))), fmaf(dz2, C3, hsum2(mul2(dz[0], CC))));
 }
 
+// Window row b of a degree-class-3 support whose first row is entry `base`: the layer pair
+// (k0, k0+1) and the third layer's row.
+template <int STORAGE>
+__device__ __forceinline__ void window_row3(const ModelDev& M, int base, int b, f2 (&pr)[4], float (&r3)[4])
+{
+    int idx = base + b * M.nxp;
+    MFA_DBG_INDEX(M.dbg, idx, static_cast<long long>(M.nxp) * M.nyp * M.nzp, kDbgWindow);
+    PairLoader<3, STORAGE>::load_triple(M, idx, pr, r3);
+}
+
+template <int STORAGE>
+__device__ __forceinline__ float4 contract_triple(const ModelDev& M, int base, const XIn<3, STORAGE>& Xin,
+                                                  const f2 (&ny)[3], const f2 (&dy)[3], const f2 (&nz)[2],
+                                                  const f2 (&dz)[2])
+{
+    return contract_triple_rows<STORAGE>(
+        [&](int b, f2 (&pr)[4], float (&r3)[4]) { window_row3<STORAGE>(M, base, b, pr, r3); }, Xin, ny, dy, nz, dz);
+}
+
 // Sum-factorised contraction over the Q^3 support whose first row is window entry `base`
 // (= (k0 nyp + j0) nxp + i0 for the support origin (i0, j0, k0)):
 //   x-pass  A_jk = sum_i Nx_i P_ijk,  B_jk = sum_i Dx_i P_ijk   (x_row: a Horner sweep of the
@@ -714,6 +730,59 @@ __device__ __forceinline__ float4 contract_triple(const ModelDev& M, int base, c
 // added once at the end.  ny, dy hold each basis value twice, nz, dz the values of
 // functions (2m, 2m+1) (zero past Q).  Each lane is an ordinary FP32 FMA; the z sums add
 // their even and odd terms separately before the final addition.
+// The layer-pair contraction (Q != 3) over rows supplied by rows(m, b, pr): pr = the
+// column pairs of support row b in z-layer pair m.
+template <int Q, int STORAGE, class Rows>
+__device__ __forceinline__ float4 contract_rows(Rows&& rows, const XIn<Q, STORAGE>& Xin, const f2 (&ny)[Q],
+                                                const f2 (&dy)[Q], const f2 (&nz)[qpair(Q) / 2],
+                                                const f2 (&dz)[qpair(Q) / 2])
+{
+    const auto X = pack_x(Xin);
+    constexpr int NP = qpair(Q) / 2;
+    f2 F, FX, FY, FZ;
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+        f2 CC, DD, EE;
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+            f2 pr[qpair(Q)];
+            rows(m, b, pr);
+            f2 A, B;
+            x_row<Q, STORAGE>(pr, X, A, B);
+            if (b == 0) {
+                CC = mul2(ny[0], A);
+                DD = mul2(dy[0], A);
+                EE = mul2(ny[0], B);
+            } else {
+                CC = fma2(ny[b], A, CC);
+                DD = fma2(dy[b], A, DD);
+                EE = fma2(ny[b], B, EE);
+            }
+        }
+        if (m == 0) {
+            F = mul2(nz[0], CC);
+            FZ = mul2(dz[0], CC);
+            FY = mul2(nz[0], DD);
+            FX = mul2(nz[0], EE);
+        } else {
+            F = fma2(nz[m], CC, F);
+            FZ = fma2(dz[m], CC, FZ);
+            FY = fma2(nz[m], DD, FY);
+            FX = fma2(nz[m], EE, FX);
+        }
+    }
+    return make_float4(hsum2(F), hsum2(FX), hsum2(FY), hsum2(FZ));
+}
+
+// Window row b of z-layer pair m of the support whose first row is entry `base`.
+template <int Q, int STORAGE>
+__device__ __forceinline__ void window_row(const ModelDev& M, int base, int m, int b, f2 (&pr)[qpair(Q)])
+{
+    int idx = base + m * 2 * M.nxp * M.nyp + b * M.nxp;   // Q = 5 also reads entry idx + 1
+    MFA_DBG_INDEX(M.dbg, idx, static_cast<long long>(M.nxp) * M.nyp * M.nzp - (qpair(Q) == 6), kDbgWindow);
+    PairLoader<Q, STORAGE>::load(M, idx, pr);
+}
+
 template <int Q, int STORAGE>
 __device__ __forceinline__ float4 contract_pairs(const ModelDev& M, int base, const XIn<Q, STORAGE>& Xin,
                                                  const f2 (&ny)[Q], const f2 (&dy)[Q], const f2 (&nz)[qpair(Q) / 2],
@@ -722,44 +791,67 @@ __device__ __forceinline__ float4 contract_pairs(const ModelDev& M, int base, co
     if constexpr (Q == 3) {
         return contract_triple<STORAGE>(M, base, Xin, ny, dy, nz, dz);
     } else {
-        const auto X = pack_x(Xin);
-        constexpr int NP = qpair(Q) / 2;
-        const int pair_step = 2 * M.nxp * M.nyp;
-        f2 F, FX, FY, FZ;
+        return contract_rows<Q, STORAGE>(
+            [&](int m, int b, f2 (&pr)[qpair(Q)]) { window_row<Q, STORAGE>(M, base, m, b, pr); }, Xin, ny, dy, nz,
+            dz);
+    }
+}
+
+// The support of one query held in registers: the rows contract_pairs would load (for
+// degree class 3 the layer pair and the third layer's row of each entry), kept while a
+// ray's samples stay in one knot-span cell.
+template <int Q>
+struct SupportRegs {
+    f2 r[qpair(Q) / 2][Q][qpair(Q)];
+};
+template <>
+struct SupportRegs<3> {
+    f2 r[3][4];
+    float r3[3][4];
+};
+
+template <int Q, int STORAGE>
+__device__ __forceinline__ void load_support(const ModelDev& M, int base, SupportRegs<Q>& S)
+{
+    if constexpr (Q == 3) {
 #pragma unroll
-        for (int m = 0; m < NP; ++m) {
-            f2 CC, DD, EE;
+        for (int b = 0; b < 3; ++b) window_row3<STORAGE>(M, base, b, S.r[b], S.r3[b]);
+    } else {
 #pragma unroll
-            for (int b = 0; b < Q; ++b) {
-                f2 pr[qpair(Q)];
-                int idx = base + m * pair_step + b * M.nxp;   // Q = 5 also reads entry idx + 1
-                MFA_DBG_INDEX(M.dbg, idx, static_cast<long long>(M.nxp) * M.nyp * M.nzp - (qpair(Q) == 6), kDbgWindow);
-                PairLoader<Q, STORAGE>::load(M, idx, pr);
-                f2 A, B;
-                x_row<Q, STORAGE>(pr, X, A, B);
-                if (b == 0) {
-                    CC = mul2(ny[0], A);
-                    DD = mul2(dy[0], A);
-                    EE = mul2(ny[0], B);
-                } else {
-                    CC = fma2(ny[b], A, CC);
-                    DD = fma2(dy[b], A, DD);
-                    EE = fma2(ny[b], B, EE);
+        for (int m = 0; m < qpair(Q) / 2; ++m)
+#pragma unroll
+            for (int b = 0; b < Q; ++b) window_row<Q, STORAGE>(M, base, m, b, S.r[m][b]);
+    }
+}
+
+// contract_at on a support held in registers: the same sums in the same order.
+template <int Q, int STORAGE>
+__device__ __forceinline__ float4 contract_support(const SupportRegs<Q>& S, const XIn<Q, STORAGE>& X,
+                                                   const float (&Ny)[Q], const float (&Dy)[Q], const float (&Nz)[Q],
+                                                   const float (&Dz)[Q])
+{
+    f2 ny[Q], dy[Q], nz[qpair(Q) / 2], dz[qpair(Q) / 2];
+    pack_dup<Q>(Ny, ny);
+    pack_dup<Q>(Dy, dy);
+    pack_pairs<Q>(Nz, nz);
+    pack_pairs<Q>(Dz, dz);
+    if constexpr (Q == 3) {
+        return contract_triple_rows<STORAGE>(
+            [&](int b, f2 (&pr)[4], float (&r3)[4]) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    pr[c] = S.r[b][c];
+                    r3[c] = S.r3[b][c];
                 }
-            }
-            if (m == 0) {
-                F = mul2(nz[0], CC);
-                FZ = mul2(dz[0], CC);
-                FY = mul2(nz[0], DD);
-                FX = mul2(nz[0], EE);
-            } else {
-                F = fma2(nz[m], CC, F);
-                FZ = fma2(dz[m], CC, FZ);
-                FY = fma2(nz[m], DD, FY);
-                FX = fma2(nz[m], EE, FX);
-            }
-        }
-        return make_float4(hsum2(F), hsum2(FX), hsum2(FY), hsum2(FZ));
+            },
+            X, ny, dy, nz, dz);
+    } else {
+        return contract_rows<Q, STORAGE>(
+            [&](int m, int b, f2 (&pr)[qpair(Q)]) {
+#pragma unroll
+                for (int c = 0; c < qpair(Q); ++c) pr[c] = S.r[m][b][c];
+            },
+            X, ny, dy, nz, dz);
     }
 }
 

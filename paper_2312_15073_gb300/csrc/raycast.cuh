@@ -322,10 +322,16 @@ __device__ __forceinline__ float4 march_pipelined(const ModelDev& M, const Rende
 // cardinal), every span but the p-1 at each end of an axis carries the same basis
 // polynomials (cardinal_basis).  The ray is marched in span units x = (n - p) u, so the
 // span is j = floor(x) and its local coordinate t = x - j; the per-axis state is the span
-// index alone (no record in registers), and the support's first window entry is kept
-// until a span changes.  The end spans, whose functions see the repeated end knots, read
-// their record from global memory (L1-resident, a few hundred bytes per axis) for each
-// sample.  Software-pipelined like variant 4.
+// index alone (no record in registers).  For degree classes 2..4 the support itself (its
+// window rows) is kept in registers until a span changes, so a ray reads the window once
+// per knot-span cell it crosses rather than once per sample (on the 128^3 frame about 2.7
+// samples fall in each cell); the sums are the ones contract_at forms from the same rows.
+// The end spans, whose functions see the repeated end knots, read their record from
+// global memory (L1-resident, a few hundred bytes per axis) for each sample.
+// Software-pipelined like variant 4.  (The record path, variant 4, keeps no such cache:
+// with its three span records also in registers it needs two CTAs' budget or spills, and
+// its own workload, the 512x512x256 non-uniform model at 2048 samples, has about one
+// sample per cell: measured 25.1 ms without, 25.7 ms with.)
 //
 // SKIP (variant 7, empty-space skipping): P.cell_vis marks the knot-span cells whose value
 // range (the convex hull bound of their support) reaches a transfer-function row of
@@ -362,6 +368,12 @@ __device__ __forceinline__ float4 march_cardinal(const ModelDev& M, const Render
     CardAxis cx{ -INFINITY, 0, false }, cy{ -INFINITY, 0, false }, cz{ -INFINITY, 0, false };
     int base = 0;
     bool cell_vis = true;   // SKIP: the current cell may be visible
+    // the support of the current cell, in registers (degree classes 2..4; degree class 5's
+    // would take 180 registers): consecutive samples in one cell reuse it, so the window is
+    // read once per cell a ray visits instead of once per sample.  Not with skipping, whose
+    // rays query few of the cells they cross (the registers cost more than they save there).
+    constexpr bool CACHE = Q <= 4 && !SKIP;
+    SupportRegs<Q> sup;
 
     auto query_at = [&](int k, bool& vis) -> float4 {
         const float t = fmaf(static_cast<float>(k) + 0.5f, dt, t0);
@@ -391,6 +403,7 @@ __device__ __forceinline__ float4 march_cardinal(const ModelDev& M, const Render
                 MFA_DBG_INDEX(P.dbg, ci, static_cast<long long>(M.ncx) * M.ncy * M.ncz, kDbgCell);
                 cell_vis = (__ldg(P.cell_vis + (ci >> 5)) >> (ci & 31)) & 1u;
             }
+            if constexpr (CACHE) load_support<Q, STORAGE>(M, base, sup);
         }
         vis = cell_vis;
         if constexpr (SKIP) {
@@ -407,7 +420,11 @@ __device__ __forceinline__ float4 march_cardinal(const ModelDev& M, const Render
             cardinal_basis<Q>(ty, Ny, Dy);
             cardinal_basis<Q>(tz, Nz, Dz);
         }
-        float4 q = contract_at<Q, STORAGE>(M, base, X, Ny, Dy, Nz, Dz);   // value left unscaled (S.vmul)
+        float4 q;   // value left unscaled (S.vmul)
+        if constexpr (CACHE)
+            q = contract_support<Q, STORAGE>(sup, X, Ny, Dy, Nz, Dz);
+        else
+            q = contract_at<Q, STORAGE>(M, base, X, Ny, Dy, Nz, Dz);
         q.y *= gs[0];
         q.z *= gs[1];
         q.w *= gs[2];

@@ -45,12 +45,20 @@ constexpr int kMinBlocks = 4;
 // Degree class 5 (degree 4) off the cardinal path: the span records of three axes and a
 // 5x5x5 support do not fit in 128 registers (variant 4 spilled 720 bytes), so those kernels
 // take the register budget of three CTAs per SM.
-template <int Q, bool CARD>
-constexpr int min_blocks() { return Q <= 4 || CARD ? kMinBlocks : 3; }
-// The cardinal path (variant 6) holds no span records and would fit more CTAs per SM, but
-// with the packed layer-pair contraction 4 CTAs (128 registers) still measures best on the
-// 128^3 degree-3 1024^2 frame: FP32 4.87 ms against 5.05 ms at 5 CTAs (96 registers, with
-// spills), FP16 5.74 against 5.73 ms.
+// The cardinal path at degree class 4 keeps the support of the current cell in registers
+// (64 values; see march_cardinal) and takes the budget of three CTAs (160 registers, no
+// spills): the window is then read once per cell a ray visits, not once per sample, which
+// relieves the L1 data pipe that bounded the kernel.  Measured on the 128^3 degree-3
+// 1024^2 frame (bitwise the same image): FP32 4.25 ms without the cache at 4 CTAs, 3.83 ms
+// with it at 4 CTAs (128 registers, small spills), 3.61 ms at 3 CTAs; FP16 5.55, 5.07,
+// 4.84 ms.  Empty-space skipping (variant 7) visits few cells per ray and keeps no cache
+// (SKIP): 4 CTAs.
+template <int Q, bool CARD, bool SKIP = false>
+constexpr int min_blocks()
+{
+    if (CARD && Q == 4 && !SKIP) return 3;
+    return Q <= 4 || CARD ? kMinBlocks : 3;
+}
 
 // The whole ray of pixel (col, row): premultiplied RGBA; `count` += samples evaluated.
 // MODE = variant (see above).
@@ -344,7 +352,7 @@ __device__ __forceinline__ float4 march_bricked(const ModelDev& M, const RenderS
 // ----------------------------------------------------------------------------------------
 
 template <int Q, int STORAGE, int MODE>
-__global__ void __launch_bounds__(kThreads, min_blocks<Q, MODE == 6 || MODE == 7>()) k_render(ModelDev M, const __grid_constant__ RenderParams P,
+__global__ void __launch_bounds__(kThreads, min_blocks<Q, MODE == 6 || MODE == 7, MODE == 7>()) k_render(ModelDev M, const __grid_constant__ RenderParams P,
                                                                  int shape)
 {
     __shared__ float4 tf[kTfSmem];
