@@ -74,8 +74,8 @@ DECODE_WINDOW_BYTES = {1: 1 * 2 * 16, 2: 1 * 3 * 48, 3: 2 * 4 * 32, 4: 3 * 5 * 4
 # DRAM bytes (read + write) of one k_render launch on this workload, measured by an ncu
 # capture of the frame (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
 # kernel sources it was taken on (their SHA-256 is checked at run time; any change -> null).
-RENDER_TRAFFIC = {"src_sha256": "ec62885737197dcaadc37e4361b8f51c2025915c6004d5dc9760ecb9fb343b31",
-                  "bytes_per_launch": 16103936}
+RENDER_TRAFFIC = {"src_sha256": "77bd2264a17353bc9faec98e77d0f656e76a71b267f0d0f2ea39e91d5ed0d46e",
+                  "bytes_per_launch": 16100608}
 KERNEL_SOURCES = ["paper_2312_15073_gb300/csrc/render.cu", "paper_2312_15073_gb300/csrc/raycast.cuh",
                   "paper_2312_15073_gb300/csrc/bspline.cuh", "paper_2312_15073_gb300/csrc/mfa_internal.cuh"]
 
@@ -358,6 +358,11 @@ def run_reference(args):
 # our arm
 # ------------------------------------------------------------------------------------------
 
+# the rows after the timed step, in the order they run
+SIDE_ROWS = ["c1", "precision", "segments", "isosurface", "marschner_lobb", "encoding", "render_quality",
+             "query_sweep", "c3_precision", "batch", "empty_space"]
+
+
 def run_ours(args):
     import torch
     ws, rank, local = _dist()
@@ -538,18 +543,22 @@ def run_ours(args):
         "clocks": clk,
     }
     keep = {}   # GPU results the oracle checks in the cpu_baseline leg
+    side = {
+        "c1": lambda: c1_small(mfa, torch, keep),
+        "precision": lambda: storage_throughput(mfa, torch, spec, job, tf),
+        "segments": lambda: segments_throughput(mfa, torch, model, job, tf, render_s),
+        "isosurface": lambda: iso_throughput(mfa, torch, spec, model, job, tf),
+        "marschner_lobb": lambda: ml_throughput(mfa, torch, tf, peak_tflops),
+        "encoding": lambda: encode_throughput(mfa, torch),
+        "render_quality": lambda: render_quality(mfa, torch),
+        "query_sweep": lambda: query_sweep(mfa, torch),
+        "c3_precision": lambda: c3_precision(mfa, torch, keep),
+        "batch": lambda: batch_throughput(mfa, torch, keep),
+        "empty_space": lambda: empty_space(mfa, torch, spec, model, job),
+    }
     if ws == 1 and not args.no_side_rows:
-        line["c1"] = c1_small(mfa, torch, keep)
-        line["precision"] = storage_throughput(mfa, torch, spec, job, tf)
-        line["segments"] = segments_throughput(mfa, torch, model, job, tf, render_s)
-        line["isosurface"] = iso_throughput(mfa, torch, spec, model, job, tf)
-        line["marschner_lobb"] = ml_throughput(mfa, torch, tf, peak_tflops)
-        line["encoding"] = encode_throughput(mfa, torch)
-        line["render_quality"] = render_quality(mfa, torch)
-        line["query_sweep"] = query_sweep(mfa, torch)
-        line["c3_precision"] = c3_precision(mfa, torch, keep)
-        line["batch"] = batch_throughput(mfa, torch, keep)
-        line["empty_space"] = empty_space(mfa, torch, spec, model, job)
+        for name in args.side_rows or SIDE_ROWS:
+            line[name] = side[name]()
     if ws == 1 and not args.no_serve:
         line["serving"] = dict(run_serve(mfa, rates=args.serve_rates, duration=args.serve_duration,
                                          min_requests=args.serve_requests),
@@ -1017,6 +1026,9 @@ def main():
     ap.add_argument("--no-side-rows", action="store_true",
                     help="skip the rows after the timed step (precision, segments, isosurface, Marschner-Lobb, "
                          "encoding, render quality), e.g. for profiling runs")
+    ap.add_argument("--side-rows", nargs="+", choices=SIDE_ROWS, default=None,
+                    help="run only these rows after the timed step (default: all of them, in this order: "
+                         + ", ".join(SIDE_ROWS) + ")")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[20.0, 50.0, 100.0, 200.0],
                     help="request rates (1/s)")
     ap.add_argument("--serve-duration", type=float, default=5.0, help="minimum seconds of arrivals per rate")
