@@ -612,6 +612,28 @@ cudaError_t segments_q(const ModelDev& m, const RenderParams& rp, bool cardinal,
 // persistent batch
 // ----------------------------------------------------------------------------------------
 
+// The model tables a persistent kernel's march reads: the CTA's shared-memory copy of the
+// request, or a copy of it in registers.  The march reads a few of them at every knot-span
+// cell a ray enters, and from shared memory each is a dependent shared load on the critical
+// path: a one-request batch of the largest serving view (2048^2, 2048 samples) took 35.4 ms
+// that way against 31.6 ms from registers (a plain launch, which reads them as constant-bank
+// operands, 31.1 ms).  The register copy fits without spills on the cardinal path with FP32
+// layer-pair windows at degree classes 2..4; elsewhere it spilled (16 to 650 bytes), so those
+// kernels keep reading the shared copy.
+template <int Q, int STORAGE, bool CARD>
+__device__ __forceinline__ float4 march_item(const BatchItem& item, const float4* tf, int col, int row,
+                                             unsigned long long& count)
+{
+    if constexpr (!CARD) {
+        return march_pipelined<Q, STORAGE>(item.m, item.s, tf, col, row, count);
+    } else if constexpr (STORAGE == 1 && Q <= 4) {
+        const ModelDev m = item.m;
+        return march_cardinal<Q, STORAGE>(m, item.s, tf, col, row, count);
+    } else {
+        return march_cardinal<Q, STORAGE>(item.m, item.s, tf, col, row, count);
+    }
+}
+
 // Persistent CTAs over the requests of one (degree, storage) group: draw a tile, find its
 // request (tiles of one request are contiguous, so the previous request is checked
 // first), stage the request and its table in shared memory when it changes, render,
@@ -665,11 +687,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<Q, CARD>()) k_render_batc
         tile_pixel(T, tx, ty, threadIdx.x, col, row);
         unsigned long long count = 0;
         if (col < item.s.width && row < item.s.height) {
-            float4 acc;
-            if constexpr (CARD)
-                acc = march_cardinal<Q, STORAGE>(item.m, item.s, tf, col, row, count);
-            else
-                acc = march_pipelined<Q, STORAGE>(item.m, item.s, tf, col, row, count);
+            const float4 acc = march_item<Q, STORAGE, CARD>(item, tf, col, row, count);
             item.s.out[static_cast<long long>(row) * item.s.width + col] = acc;
         }
         if (item.s.samples_out) add_count(item.s.samples_out, count);
@@ -788,11 +806,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<Q, CARD>())
         tile_pixel(T, tx, ty, threadIdx.x, col, row);
         unsigned long long count = 0;
         if (col < item.s.width && row < item.s.height) {
-            float4 acc;
-            if constexpr (CARD)
-                acc = march_cardinal<Q, STORAGE>(item.m, item.s, tf, col, row, count);
-            else
-                acc = march_pipelined<Q, STORAGE>(item.m, item.s, tf, col, row, count);
+            const float4 acc = march_item<Q, STORAGE, CARD>(item, tf, col, row, count);
             item.s.out[static_cast<long long>(row) * item.s.width + col] = acc;
         }
         if (item.s.samples_out) add_count(item.s.samples_out, count);
