@@ -948,6 +948,37 @@ def serve_models(mfa, size_scale=1.0):
     return specs, f16, f32
 
 
+def serve_model_table(mfa, specs, f16, f32, tf, side=2048, ns=2048, frames=3):
+    """Per serving model: control points, device bytes and the time of one 2048^2 frame
+    with 2048 samples per ray (the largest serving view) for each way of holding it: FP32
+    (the plain path's models), FP16 with FP32 window values (the served path's models),
+    FP16 with 16-bit window values, and the compact FP16 layout."""
+    import torch
+    import synth
+    cam = synth.orbit_camera((0.5, 0.5, 0.5), 2.5, 0.7, 0.2, 30.0)
+    img = torch.empty((side, side, 4), device="cuda")
+    rows = []
+    for spec, m16w32, m32 in zip(specs, f16, f32):
+        row = {"nctrl": list(spec.nctrl), "plain_values_bytes_f16": 2 * int(np.prod(spec.nctrl))}
+        extra = [("f16", mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl64, storage=mfa.MFA_F16)),
+                 ("f16_compact", mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl64, storage=mfa.MFA_F16,
+                                           window=mfa.MFA_WINDOW_COMPACT))]
+        for name, m in [("f32", m32), ("f16_f32window", m16w32)] + extra:
+            mfa.render(m, cam, tf, side, side, ns, out=img)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(frames):
+                mfa.render(m, cam, tf, side, side, ns, out=img)
+            b.record()
+            b.synchronize()
+            row[name] = {"device_bytes": m.info()["device_bytes"], "ms_per_frame": a.elapsed_time(b) / frames}
+        for _, m in extra:
+            m.close()
+        rows.append(row)
+    return rows
+
+
 def serve_stream(mfa, server, models, tf, stream):
     """Submits the stream at its arrival times (a client thread sleeping until each one),
     waits for every ticket; returns (latencies ms, completed, rejected, wall seconds)."""
@@ -994,7 +1025,7 @@ def run_serve(mfa, rates, duration, size_scale=1.0, max_slots=16, min_requests=0
     specs, f16, f32 = serve_models(mfa, size_scale)
     tf = mfa.transfer_fn(synth.ramp_tf(256, 0.05), shading=True)
     budget = 2 << 30
-    out = {"models": [list(s.nctrl) for s in specs], "hbm_budget_bytes": budget, "rates": {}}
+    out = {"models": serve_model_table(mfa, specs, f16, f32, tf), "hbm_budget_bytes": budget, "rates": {}}
 
     def pct(v, q):
         v = sorted(v)
