@@ -8,7 +8,9 @@
 // Decode cuts the points into chunks and pipelines them over three helper streams of the
 // calling thread -- copy-in of chunk c+1 and copy-out of chunk c-1 run beside the kernel
 // on chunk c, the two copy directions on their own engines -- forked from and joined back
-// to the bound stream with events.  Render stages the whole image (its copy-out is small
+// to the bound stream with events.  The kernel stream has the device's greatest priority,
+// so that a decode issued beside a long render interleaves its chunks with the render's
+// tiles and its copies overlap the render, instead of all waiting for the render's end.  Render stages the whole image (its copy-out is small
 // next to the kernel).  Both calls are asynchronous on the bound stream like
 // cudaMemcpyAsync: the host buffers must stay valid, and are read or written, until that
 // stream has been synchronised; page-locked buffers let the copies overlap, pageable ones
@@ -22,7 +24,7 @@ using namespace mfa;
 
 namespace {
 
-constexpr long long kDecodeChunk = 1LL << 21;   // points per pipelined chunk
+constexpr long long kDecodeChunk = 1LL << 20;   // points per pipelined chunk
 constexpr int kMaxDevices = 64;
 
 std::mutex g_pool_mu;
@@ -72,8 +74,13 @@ struct IoStreams {
     {
         if (device == dev) return cudaSuccess;
         release();
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
         cudaError_t e = cudaStreamCreateWithFlags(&in, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&run, cudaStreamNonBlocking);
+        // the chunk kernels at the greatest priority: each is dispatched ahead of other
+        // work's pending CTAs as soon as its points have arrived, so the copies of the
+        // pipeline keep moving beside a long kernel instead of queueing behind it
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&run, cudaStreamNonBlocking, greatest);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&out, cudaStreamNonBlocking);
         for (int i = 0; i < kEvents && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
         if (e != cudaSuccess) {
