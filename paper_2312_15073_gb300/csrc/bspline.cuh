@@ -857,10 +857,10 @@ __device__ __forceinline__ float4 contract_support(const SupportRegs<Q>& S, cons
 
 // Value only: the x-, y- and z-sums of contract_pairs (contract_triple for Q = 3) without
 // the derivative sums, in the same order, so f is bit-identical to the value contract_pairs
-// returns.
-template <int Q, int STORAGE>
-__device__ __forceinline__ float contract_value(const ModelDev& M, int base, const XIn<Q, STORAGE>& Xin,
-                                                const f2 (&ny)[Q], const f2 (&nz)[qpair(Q) / 2])
+// returns; rows as for contract_rows / contract_triple_rows.
+template <int Q, int STORAGE, class Rows>
+__device__ __forceinline__ float contract_value_rows(Rows&& rows, const XIn<Q, STORAGE>& Xin, const f2 (&ny)[Q],
+                                                     const f2 (&nz)[qpair(Q) / 2])
 {
     const auto X = pack_x(Xin);
     if constexpr (Q == 3) {
@@ -870,9 +870,7 @@ __device__ __forceinline__ float contract_value(const ModelDev& M, int base, con
         for (int b = 0; b < 3; ++b) {
             f2 pr[4];
             float r3[4];
-            int idx = base + b * M.nxp;
-            MFA_DBG_INDEX(M.dbg, idx, static_cast<long long>(M.nxp) * M.nyp * M.nzp, kDbgWindow);
-            PairLoader<3, STORAGE>::load_triple(M, idx, pr, r3);
+            rows(b, pr, r3);
             const f2 A = x_row_value<3, STORAGE>(pr, X);
             const float A3 = x_row3_value<STORAGE>(r3, X);
             const float nyb = lo2(ny[b]);
@@ -882,7 +880,6 @@ __device__ __forceinline__ float contract_value(const ModelDev& M, int base, con
         return fmaf(lo2(nz[1]), C3, hsum2(mul2(nz[0], CC)));
     } else {
         constexpr int NP = qpair(Q) / 2;
-        const int pair_step = 2 * M.nxp * M.nyp;
         f2 F;
 #pragma unroll
         for (int m = 0; m < NP; ++m) {
@@ -890,9 +887,7 @@ __device__ __forceinline__ float contract_value(const ModelDev& M, int base, con
 #pragma unroll
             for (int b = 0; b < Q; ++b) {
                 f2 pr[qpair(Q)];
-                int idx = base + m * pair_step + b * M.nxp;
-                MFA_DBG_INDEX(M.dbg, idx, static_cast<long long>(M.nxp) * M.nyp * M.nzp - (qpair(Q) == 6), kDbgWindow);
-                PairLoader<Q, STORAGE>::load(M, idx, pr);
+                rows(m, b, pr);
                 const f2 A = x_row_value<Q, STORAGE>(pr, X);
                 CC = b == 0 ? mul2(ny[0], A) : fma2(ny[b], A, CC);
             }
@@ -900,6 +895,18 @@ __device__ __forceinline__ float contract_value(const ModelDev& M, int base, con
         }
         return hsum2(F);
     }
+}
+
+template <int Q, int STORAGE>
+__device__ __forceinline__ float contract_value(const ModelDev& M, int base, const XIn<Q, STORAGE>& Xin,
+                                                const f2 (&ny)[Q], const f2 (&nz)[qpair(Q) / 2])
+{
+    if constexpr (Q == 3)
+        return contract_value_rows<3, STORAGE>(
+            [&](int b, f2 (&pr)[4], float (&r3)[4]) { window_row3<STORAGE>(M, base, b, pr, r3); }, Xin, ny, nz);
+    else
+        return contract_value_rows<Q, STORAGE>(
+            [&](int m, int b, f2 (&pr)[qpair(Q)]) { window_row<Q, STORAGE>(M, base, m, b, pr); }, Xin, ny, nz);
 }
 
 // Contraction from the x-pass input and scalar y / z basis values.
