@@ -324,8 +324,9 @@ __device__ __forceinline__ float4 march_pipelined(const ModelDev& M, const Rende
 // span is j = floor(x) and its local coordinate t = x - j; the per-axis state is the span
 // index alone (no record in registers).  For degree classes 2..4 the support itself (its
 // window rows) is kept in registers until a span changes, so a ray reads the window once
-// per knot-span cell it crosses rather than once per sample (on the 128^3 frame about 2.7
-// samples fall in each cell); the sums are the ones contract_at forms from the same rows.
+// per knot-span cell it crosses rather than once per sample (on the 128^3 frame a warp
+// reloads at about one sample in four); the sums are the ones contract_at forms from the
+// same rows.
 // The end spans, whose functions see the repeated end knots, read their record from
 // global memory (L1-resident, a few hundred bytes per axis) for each sample.
 // Software-pipelined like variant 4.  (The record path, variant 4, keeps no such cache:
