@@ -380,7 +380,9 @@ def run_ours(args):
     wl = build_workload(with_points=True)
     spec, job = wl.model, wl.render
     p = spec.degree[0]
-    model = mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl)
+    # the FP32 window plus each knot-span cell's polynomial (render variant 8, the autotuner's
+    # candidate beside the others); decode and the side rows on this model use the window
+    model = mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl, window=mfa.MFA_WINDOW_PATCH)
     tf = mfa.transfer_fn(job.tf, shading=job.shading, ka=job.ka, kd=job.kd, ks=job.ks, shininess=job.shininess,
                          ert_alpha=job.ert_alpha)
     W, H, NS = job.width, job.height, job.n_samples
@@ -498,6 +500,8 @@ def run_ours(args):
         "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "model": "degree 3, 128^3 FP32 control points, 64 Gaussians + noise",
+                   "layout": "FP32 layer-pair window + per-cell polynomial patches (MFA_WINDOW_PATCH, "
+                             f"{model.info()['device_bytes'] / 1e6:.0f} MB on the device)",
                    "image": f"{W}x{H}", "n_samples": NS, "decode_points": n_pts,
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"replicas x{ws}"},
@@ -515,7 +519,8 @@ def run_ours(args):
                      "flops_per_sample": flops_sample,
                      "flops_note": "algorithmic count (sum-factorised contraction + span-local Cox-de Boor "
                                    "basis and derivative + chain rule, + TF/Phong/over); on uniform knots the "
-                                   "cardinal path executes 42 instead of 126 basis flops per sample",
+                                   "cardinal path executes 42 instead of 126 basis flops per sample, and variant 8 "
+                                   "(per-cell polynomial patches) evaluates monomials instead of any basis",
                      "peak_basis": f"{sms} SMs (cudaDeviceProp) x {FP32_LANES} FP32 lanes x 2 flop x "
                                    f"{sm_max_mhz:.0f} MHz (max SM clock, nvidia-smi)",
                      "peak_at_median_clock": fp32_peak_tflops(sms, clk["sm_mhz"])
@@ -909,13 +914,15 @@ def iso_throughput(mfa, torch, spec, model, job, tf, frames=5):
 def storage_throughput(mfa, torch, spec, job, tf, frames=5):
     """Samples/s of the same frame with FP32, FP16 and BF16 control points (the same
     FP64-rounded values, FP32 accumulation); 16-bit models with their own 16-bit window
-    values and with FP32 window values (MFA_WINDOW_F32)."""
+    values and with FP32 window values (MFA_WINDOW_F32); the FP32 model with per-cell
+    patches (MFA_WINDOW_PATCH, rendered by variant 8).  Default kernel of each model."""
     out = {}
     W, H, NS = job.width, job.height, job.n_samples
     img = torch.empty((H, W, 4), device="cuda")
     for storage, window, name in ((mfa.MFA_F32, 0, "f32"), (mfa.MFA_F16, 0, "f16"), (mfa.MFA_BF16, 0, "bf16"),
                                   (mfa.MFA_F16, mfa.MFA_WINDOW_F32, "f16_f32window"),
-                                  (mfa.MFA_BF16, mfa.MFA_WINDOW_F32, "bf16_f32window")):
+                                  (mfa.MFA_BF16, mfa.MFA_WINDOW_F32, "bf16_f32window"),
+                                  (mfa.MFA_F32, mfa.MFA_WINDOW_PATCH, "f32_patches")):
         m = mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl, storage=storage, window=window)
         cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
         mfa.render(m, job.camera, tf, W, H, NS, out=img)

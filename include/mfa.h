@@ -102,8 +102,12 @@ mfa_model* mfa_model_create_ex(const int degree[3], const int nctrl[3], const do
  * plain size instead of 8-16x (for models that would not otherwise fit in L2 or in
  * memory).  Compact models keep no per-cell bounds, so the isosurface search queries every
  * sample and render variant 7 falls back to the default; render variants 1, 2, 3 and 5
- * run as the default too. */
-enum { MFA_WINDOW_AUTO = 0, MFA_WINDOW_F32 = 1, MFA_WINDOW_COMPACT = 2 };
+ * run as the default too.  MFA_WINDOW_PATCH (FP32 storage, degree 3 on every axis, clamped
+ * uniform knots; MFA_ERR_UNSUPPORTED otherwise): the FP32 window, plus per knot-span cell
+ * the 64 coefficients of the model's polynomial on that cell in its local coordinates
+ * (computed in FP64 from the stored values, rounded once; 256 bytes per cell, about 7x the
+ * window), which render variant 8 evaluates with monomials instead of basis functions. */
+enum { MFA_WINDOW_AUTO = 0, MFA_WINDOW_F32 = 1, MFA_WINDOW_COMPACT = 2, MFA_WINDOW_PATCH = 3 };
 
 /* As mfa_model_create_ex, with the window chosen (MFA_WINDOW_*; MFA_ERR_ARG otherwise). */
 mfa_model* mfa_model_create_opts(const int degree[3], const int nctrl[3], const double* const knots[3],
@@ -195,7 +199,8 @@ typedef struct {
     unsigned long long* samples_out;  /* DEVICE counter or NULL: the number of samples
                                          evaluated (after box clipping and early
                                          termination) is ADDED to it */
-    int variant;                      /* kernel variant: 0 = library default (6 for a
+    int variant;                      /* kernel variant: 0 = library default (8 for a
+                                         model created with MFA_WINDOW_PATCH, 6 for a
                                          cardinal model, see mfa_model_info, else 4);
                                          1 = span records cached in registers along the
                                          ray, packed FP32x2 arithmetic; 2 = records cached,
@@ -216,9 +221,13 @@ typedef struct {
                                          by one sample: (1 - ert_alpha) x alpha at most),
                                          samples_out counts the evaluated samples; a pass over the cells builds
                                          the per-render visibility bits (one bit per cell,
-                                         from the staging pool).  Variants 1-6 differ only
-                                         in FP32 rounding order.
-                                         MFA_ERR_ARG outside 0..7. */
+                                         from the staging pool); 8 = per-cell polynomial
+                                         patches (MFA_WINDOW_PATCH models; otherwise the
+                                         default): 6 with each knot-span cell's
+                                         coefficients in place of its window rows and
+                                         monomials in place of the basis.  Variants 1-6
+                                         and 8 differ only in FP32 rounding order.
+                                         MFA_ERR_ARG outside 0..8. */
     int tile_shape;                   /* ray tile: 0 = 16x8 pixels per CTA with 8x4 per warp
                                          (default), 1 = 32x4 / 8x4, 2 = 8x16 / 4x8,
                                          3 = 16x8 / 16x2.  MFA_ERR_ARG outside 0..3. */
@@ -411,7 +420,7 @@ typedef struct {
  * launches each, CUDA events on the bound stream; synchronises it), stores the fastest as
  * the choice for the workload's class and returns it in *best; `all` (may be NULL)
  * receives up to max_all measured candidates, *n_all their count.  Candidates: variants
- * 1-5 and 7, plus 6 for cardinal models.  The class does not include the transfer
+ * 1-5 and 7, plus 6 for cardinal models and 8 for MFA_WINDOW_PATCH models.  The class does not include the transfer
  * function, so a stored variant 7 (chosen where this render's table is partly
  * transparent) also serves later renders with other tables: same images, at most its
  * visibility pass slower where nothing is transparent; batches run it as 6.  rgba_out is overwritten.  Any render argument error is returned as by mfa_render. */

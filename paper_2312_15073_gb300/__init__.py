@@ -25,7 +25,7 @@ __all__ = ["Model", "decode", "locate_spans", "render", "lib", "MFA_F64", "MFA_F
            "MfaError", "camera", "transfer_fn", "Request", "Batch", "render_batch", "render_batch_static", "Server", "server_now", "tune_render", "tune_batch", "tune_save", "tune_load"]
 
 MFA_F64, MFA_F32, MFA_F16, MFA_BF16 = 0, 1, 2, 3
-MFA_WINDOW_AUTO, MFA_WINDOW_F32, MFA_WINDOW_COMPACT = 0, 1, 2
+MFA_WINDOW_AUTO, MFA_WINDOW_F32, MFA_WINDOW_COMPACT, MFA_WINDOW_PATCH = 0, 1, 2, 3
 _PKG = os.path.dirname(os.path.abspath(__file__))
 # The library the binding loads: libmfa.so, or the file MFA_LIB names (e.g. the debug
 # build libmfa_debug.so).  A missing library raises; there is no fallback.
@@ -246,8 +246,10 @@ class Model:
     knots: None for clamped uniform, or a list of three FP64 arrays (entries may be None).
     storage: MFA_F32 / MFA_F16 / MFA_BF16 (default: F32 for 64/32-bit input).
     window: MFA_WINDOW_AUTO (the storage type's own window values), MFA_WINDOW_F32 (FP32
-    window values whatever the storage type: a 16-bit model at FP32 speed) or
-    MFA_WINDOW_COMPACT (no window: the control points once, gathered value by value).
+    window values whatever the storage type: a 16-bit model at FP32 speed),
+    MFA_WINDOW_COMPACT (no layer-pair window: the control points at 1-1.6x) or
+    MFA_WINDOW_PATCH (FP32, degree 3, uniform knots: the FP32 window plus each knot-span
+    cell's polynomial, rendered by variant 8; about 7x the window's bytes).
     """
 
     def __init__(self, degree, nctrl, knots, ctrl, storage: int | None = None, in_dtype: int | None = None,

@@ -250,6 +250,7 @@ void mfa_model_destroy(mfa_model* m)
     if (!m) return;
     DeviceGuard g(m->device);
     if (m->d_win) cudaFree(m->d_win);
+    if (m->d_patch) cudaFree(m->d_patch);
     if (m->d_tables) cudaFree(m->d_tables);
     delete m;
 }
@@ -266,7 +267,7 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
     if (!valid_dtype(in_dtype)) return fail(MFA_ERR_ARG, "unknown input dtype %d", (int)in_dtype), nullptr;
     if (storage != MFA_F32 && storage != MFA_F16 && storage != MFA_BF16)
         return fail(MFA_ERR_UNSUPPORTED, "storage dtype must be F32, F16 or BF16"), nullptr;
-    if (window != MFA_WINDOW_AUTO && window != MFA_WINDOW_F32 && window != MFA_WINDOW_COMPACT)
+    if (window != MFA_WINDOW_AUTO && window != MFA_WINDOW_F32 && window != MFA_WINDOW_COMPACT && window != MFA_WINDOW_PATCH)
         return fail(MFA_ERR_ARG, "window = %d is not one of the MFA_WINDOW_* choices", window), nullptr;
     const bool compact = window == MFA_WINDOW_COMPACT;
     // window type (ModelDev::storage): layer pairs of FP32 or of the storage type's values, or
@@ -280,6 +281,9 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
             return fail(MFA_ERR_ARG, "nctrl[%d] = %d must be in degree+1..2^24", a, nctrl[a]), nullptr;
         qmax = degree[a] + 1 > qmax ? degree[a] + 1 : qmax;
     }
+    const bool patches = window == MFA_WINDOW_PATCH;
+    if (patches && (storage != MFA_F32 || degree[0] != 3 || degree[1] != 3 || degree[2] != 3))
+        return fail(MFA_ERR_UNSUPPORTED, "MFA_WINDOW_PATCH needs FP32 storage and degree 3 on every axis"), nullptr;
     // padded sizes: kPad zeros past the end of every axis; compact models round x up to a
     // multiple of their entry stride, so that their rows are whole entries of eight values
     const int cstride = compact_stride(qmax, wstore);
@@ -306,6 +310,8 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
             if (!check_knots(U[a].data(), n, p, a)) return nullptr;
         }
     }
+    if (patches && !uniform)
+        return fail(MFA_ERR_UNSUPPORTED, "MFA_WINDOW_PATCH needs clamped uniform knots (the cardinal path)"), nullptr;
 
     mfa_model* M = new mfa_model();
     cudaGetDevice(&M->device);
@@ -351,8 +357,13 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
     size_t knot_bytes = 0;
     for (int a = 0; a < 3; ++a) knot_bytes += sizeof(double) * U[a].size();
     const bool pow_rows = power_rows(Q, wstore);
-    // FP64 power coefficients of the x spans (power rows only), used while building the window
-    const size_t coef_bytes = pow_rows ? sizeof(double) * Q * Q * (nctrl[0] - degree[0]) : 0;
+    // FP64 power coefficients of the spans, used while building the window (x, for power rows)
+    // and the patches (all three axes), [axis][span][k][r]
+    size_t coef_off[3], coef_bytes = 0;
+    for (int a = 0; a < 3; ++a) {
+        coef_off[a] = coef_bytes;
+        if ((a == 0 && pow_rows) || patches) coef_bytes += sizeof(double) * Q * Q * (nctrl[a] - degree[a]);
+    }
 
     void* d_stage = nullptr;   // uploaded knots, stats, x coefficients and input control points; freed below
     const size_t stage_raw = compact ? align_up(raw_bytes, 256) : 0;
@@ -380,7 +391,12 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
         koff += sizeof(double) * U[a].size();
     }
     int* d_stats = reinterpret_cast<int*>(stage + align_up(knot_bytes, 256));
-    double* d_coef = pow_rows ? reinterpret_cast<double*>(stage + align_up(knot_bytes, 256) + 256) : nullptr;
+    double* d_coefs[3];
+    for (int a = 0; a < 3; ++a)
+        d_coefs[a] = (a == 0 && pow_rows) || patches
+                         ? reinterpret_cast<double*>(stage + align_up(knot_bytes, 256) + 256 + coef_off[a])
+                         : nullptr;
+    double* d_coef = d_coefs[0];
     void* d_in = ctrl_on_device ? const_cast<void*>(ctrl)
                                 : stage + align_up(knot_bytes, 256) + 256 + align_up(coef_bytes, 256) + stage_raw;
     if (!ctrl_on_device && (e = cudaMemcpyAsync(d_in, ctrl, in_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
@@ -397,7 +413,7 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
         A.G = G[a];
         A.Gf = static_cast<float>(G[a]);
         if ((e = launch_prep_axis(d_knots[a], A.n, A.p, Q, const_cast<float*>(A.kup), const_cast<float*>(A.rec),
-                                  const_cast<int*>(A.grid), A.G, a == 0 ? d_coef : nullptr, st)) != cudaSuccess)
+                                  const_cast<int*>(A.grid), A.G, d_coefs[a], st)) != cudaSuccess)
             return cleanup(0, "span tables", e);
     }
     void* d_raw = compact ? static_cast<void*>(stage + align_up(knot_bytes, 256) + 256 + align_up(coef_bytes, 256))
@@ -409,6 +425,14 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
         return cleanup(0, "window array", e);
     if ((e = launch_prep_stats(d_raw, storage, static_cast<long long>(nctrl_total), d_stats, st)) != cudaSuccess)
         return cleanup(0, "control-point statistics", e);
+    size_t patch_bytes = 0;
+    if (patches) {
+        patch_bytes = sizeof(float) * 64 * static_cast<size_t>(nctrl[0] - 3) * (nctrl[1] - 3) * (nctrl[2] - 3);
+        if ((e = cudaMalloc(&M->d_patch, patch_bytes)) != cudaSuccess) return cleanup(0, "cudaMalloc(patches)", e);
+        const double* const cf[3] = { d_coefs[0], d_coefs[1], d_coefs[2] };
+        if ((e = launch_prep_patches(d_raw, storage, nctrl, cf, static_cast<float*>(M->d_patch), st)) != cudaSuccess)
+            return cleanup(0, "cell patches", e);
+    }
     float2* d_cell = compact ? nullptr : reinterpret_cast<float2*>(tabs + off_cell);
     if (!compact && (e = launch_prep_cells(d_raw, storage, degree, nctrl, d_cell, st)) != cudaSuccess)
         return cleanup(0, "cell bounds", e);
@@ -429,6 +453,7 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
     M->vmax = ord2f(stats[1]);
     M->maxabs = ord2f(stats[2]);
     M->dev.win = M->d_win;
+    M->dev.patch = static_cast<const float*>(M->d_patch);
     M->dev.raw = compact ? nullptr : d_raw;
     M->window = window;
     M->dev.nxp = static_cast<int>(nxp);
@@ -444,7 +469,7 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
     M->dev.ncz = nctrl[2] - degree[2];
     M->dev.dbg = debug_word(M->device);
     for (int a = 0; a < 3; ++a) M->dev.ax[a].dbg = M->dev.dbg;
-    M->bytes = tab + win_bytes;
+    M->bytes = tab + win_bytes + patch_bytes;
     return M;
 }
 
@@ -515,7 +540,7 @@ int mfa_render_ex(const mfa_model* m, const mfa_camera* cam, const mfa_transfer_
 {
     int variant = opts ? opts->variant : 0;
     int shape = opts ? opts->tile_shape : 0;
-    if (variant < 0 || variant > 7) return fail(MFA_ERR_ARG, "render variant %d outside 0..7", variant);
+    if (variant < 0 || variant > 8) return fail(MFA_ERR_ARG, "render variant %d outside 0..8", variant);
     if (shape < 0 || shape >= kTileShapes) return fail(MFA_ERR_ARG, "tile_shape %d outside 0..%d", shape, kTileShapes - 1);
     if (opts && opts->use_tuned && m) tuned_lookup(m, width, height, n_samples, &variant, &shape);
     RenderParams P;

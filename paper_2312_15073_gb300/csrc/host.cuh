@@ -23,6 +23,7 @@ struct mfa_model {
     int window = MFA_WINDOW_AUTO;   // the MFA_WINDOW_* choice the model was built with
     std::vector<double> knots[3];   // the FP64 knot vectors (host copy, for mfa_model_save)
     void* d_win = nullptr;      // window array
+    void* d_patch = nullptr;    // per-cell polynomial patches (MFA_WINDOW_PATCH models)
     void* d_tables = nullptr;   // kup, grid and records of the three axes, one allocation
     mfa::ModelDev dev{};
 };

@@ -108,6 +108,10 @@ struct AxisDev {
 struct ModelDev {
     AxisDev ax[3];
     const void* win;    // window array (see above)
+    const float* patch; // per knot-span cell (i, j, k) (x fastest), its 64 polynomial coefficients
+                        // c[a][b][c] of t_x^a t_y^b t_z^c (degree 3, FP32) as 8 entries of the
+                        // layer-pair layout: entry 4m + b holds {c[a][b][2m], c[a][b][2m+1]},
+                        // a = 0..3 (MFA_WINDOW_PATCH models only, else NULL)
     const void* raw;    // the stored control points, plain [n_z][n_y][n_x], of type raw_storage
                         // (NULL on compact models, whose window holds them)
     int nxp, nyp, nzp;  // padded sizes n + kPad
@@ -196,6 +200,10 @@ cudaError_t launch_prep_raw(const void* d_ctrl, int in_dtype, int storage, long 
 // coefficients for FP32 power rows, NULL for 16-bit rows)
 cudaError_t launch_prep_window(const void* raw, int raw_storage, int nx, int ny, int nz, int nxp, int q,
                                const double* coef64, int px, void* win, int storage, cudaStream_t stream);
+// The per-cell polynomial patches (degree 3 on every axis; layout at ModelDev::patch) from
+// the stored control points and each axis's FP64 span coefficients coef64[a] ([span][k][r]).
+cudaError_t launch_prep_patches(const void* raw, int raw_storage, const int nctrl[3], const double* const coef64[3],
+                                float* patch, cudaStream_t stream);
 cudaError_t launch_prep_cells(const void* raw, int storage, const int degree[3], const int nctrl[3], float2* cell,
                               cudaStream_t stream);
 cudaError_t launch_prep_stats(const void* raw, int storage, long long total, int* d_stats, cudaStream_t stream);

@@ -233,6 +233,66 @@ __global__ void k_window_compact(const void* __restrict__ raw, int raw_storage, 
     }
 }
 
+// Per-cell polynomial patches (degree 3): for cell (i, j, k) with support P[k+c][j+b][i+a],
+//   coefficient of t_x^qx t_y^qy t_z^qz = sum_{a,b,c} Cx[qx][a] Cy[qy][b] Cz[qz][c] P[k+c][j+b][i+a],
+// Cx[q][a] the power coefficient of t^q in the x span's function a (likewise y, z), summed
+// axis by axis in FP64 from the exact stored values and rounded once; one thread per cell.
+__global__ void k_patches(const void* __restrict__ raw, int raw_storage, int nx, int ny, int nz,
+                          const double* __restrict__ cx, const double* __restrict__ cy, const double* __restrict__ cz,
+                          float* __restrict__ patch)
+{
+    const int ncx = nx - 3, ncy = ny - 3, ncz = nz - 3;
+    const long long total = static_cast<long long>(ncx) * ncy * ncz;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int i = static_cast<int>(e % ncx);
+        const long long jk = e / ncx;
+        const int j = static_cast<int>(jk % ncy), k = static_cast<int>(jk / ncy);
+        const double* Cx = cx + static_cast<long long>(i) * 16;
+        const double* Cy = cy + static_cast<long long>(j) * 16;
+        const double* Cz = cz + static_cast<long long>(k) * 16;
+        double T[4][4][4];   // T[c][b][qx], then T[c][qy][qx], then T[qz][qy][qx]
+        for (int c = 0; c < 4; ++c)
+            for (int b = 0; b < 4; ++b) {
+                double P[4];
+                for (int a = 0; a < 4; ++a) P[a] = raw_at(raw, raw_storage, nx, ny, nz, i + a, j + b, k + c);
+                for (int q = 0; q < 4; ++q) {
+                    double w = 0.0;
+                    for (int a = 0; a < 4; ++a) w += Cx[q * 4 + a] * P[a];
+                    T[c][b][q] = w;
+                }
+            }
+        for (int c = 0; c < 4; ++c)
+            for (int qx = 0; qx < 4; ++qx) {
+                double v[4];
+                for (int q = 0; q < 4; ++q) {
+                    double w = 0.0;
+                    for (int b = 0; b < 4; ++b) w += Cy[q * 4 + b] * T[c][b][qx];
+                    v[q] = w;
+                }
+                for (int q = 0; q < 4; ++q) T[c][q][qx] = v[q];
+            }
+        for (int qy = 0; qy < 4; ++qy)
+            for (int qx = 0; qx < 4; ++qx) {
+                double v[4];
+                for (int q = 0; q < 4; ++q) {
+                    double w = 0.0;
+                    for (int c = 0; c < 4; ++c) w += Cz[q * 4 + c] * T[c][qy][qx];
+                    v[q] = w;
+                }
+                for (int q = 0; q < 4; ++q) T[q][qy][qx] = v[q];
+            }
+        // entry 4m + b: {c[a][b][2m], c[a][b][2m+1]} for a = 0..3 (qz = 2m, 2m+1)
+        float* out = patch + e * 64;
+        for (int m = 0; m < 2; ++m)
+            for (int b = 0; b < 4; ++b)
+                for (int a = 0; a < 4; ++a) {
+                    out[(4 * m + b) * 8 + 2 * a] = __double2float_rn(T[2 * m][b][a]);
+                    out[(4 * m + b) * 8 + 2 * a + 1] = __double2float_rn(T[2 * m + 1][b][a]);
+                }
+    }
+}
+
 // {min, max} over the (p_x+1)(p_y+1)(p_z+1) stored control points of each knot-span cell's
 // support, read from the plain array.
 __global__ void k_cell_range(const void* __restrict__ raw, int storage, int nx, int ny, int nz, int px, int py, int pz,
@@ -348,6 +408,15 @@ cudaError_t launch_prep_window(const void* raw, int raw_storage, int nx, int ny,
     const long long total = static_cast<long long>(nxp) * (ny + kPad) * (nz + kPad);
     k_window<<<grid_blocks(total, 65536), 256, 0, stream>>>(raw, raw_storage, nx, ny, nz, nxp, q, coef64, px, win,
                                                             storage);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_patches(const void* raw, int raw_storage, const int nctrl[3], const double* const coef64[3],
+                                float* patch, cudaStream_t stream)
+{
+    const long long total = static_cast<long long>(nctrl[0] - 3) * (nctrl[1] - 3) * (nctrl[2] - 3);
+    k_patches<<<grid_blocks(total, 65536), 128, 0, stream>>>(raw, raw_storage, nctrl[0], nctrl[1], nctrl[2], coef64[0],
+                                                             coef64[1], coef64[2], patch);
     return cudaGetLastError();
 }
 

@@ -456,6 +456,106 @@ __device__ __forceinline__ float4 march_cardinal(const ModelDev& M, const Render
     return acc;
 }
 
+// ----------------------------------------------------------------------------------------
+// variant 8: per-cell polynomial patches (MFA_WINDOW_PATCH models)
+// ----------------------------------------------------------------------------------------
+//
+// On a degree-3 model with uniform knots, the model restricted to knot-span cell (i, j, k) is
+// one tricubic polynomial in the cell's local coordinates (t_x, t_y, t_z) in [0,1)^3:
+// f = sum c[a][b][c] t_x^a t_y^b t_z^c, whose 64 coefficients ModelDev::patch holds (from the
+// span coefficients of each axis, end spans included).  The march is the cardinal one with
+// the cell's patch in registers in place of its window rows, and monomials in place of the
+// basis: the contraction runs the same packed passes with y weights {1, t, t^2, t^3} and
+// derivative weights {0, 1, 2t, 3t^2} (likewise z), and the x-pass is the Horner sweep of
+// the power rows.  No span records, no end-span branch and no basis evaluation per sample.
+template <int STORAGE>
+__device__ __forceinline__ float4 march_patch(const ModelDev& M, const RenderScalars& P,
+                                              const float4* __restrict__ tf, int col, int row,
+                                              unsigned long long& count)
+{
+    static_assert(STORAGE == 1, "patches are FP32");
+    float o[3], d[3], t0, t1;
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (!ray_box(P, col, row, o, d, t0, t1)) return acc;
+
+    const int ns = P.n_samples;
+    const float ert = P.ert_alpha;
+    const float dt = (t1 - t0) / static_cast<float>(ns);
+    const ShadeParams S = shade_params(P, d, 1.0f);
+    float om[3], dm[3], gs[3];   // ray in span units, gradient scale per axis
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float m = static_cast<float>(M.ax[a].n - M.ax[a].p);
+        om[a] = o[a] * m;
+        dm[a] = d[a] * m;
+        gs[a] = m;
+    }
+    CardAxis cx{ -INFINITY, 0, false }, cy{ -INFINITY, 0, false }, cz{ -INFINITY, 0, false };
+    SupportRegs<4> sup;
+
+    auto query_at = [&](int k) -> float4 {
+        const float t = fmaf(static_cast<float>(k) + 0.5f, dt, t0);
+        const float x = fmaf(t, dm[0], om[0]);
+        const float y = fmaf(t, dm[1], om[1]);
+        const float z = fmaf(t, dm[2], om[2]);
+        float tx = x - cx.jf, ty = y - cy.jf, tz = z - cz.jf;
+        const bool ox = !(tx >= 0.0f && tx < 1.0f);
+        const bool oy = !(ty >= 0.0f && ty < 1.0f);
+        const bool oz = !(tz >= 0.0f && tz < 1.0f);
+        if (ox | oy | oz) {
+            if (ox) {
+                card_update(M.ax[0], cx, x);
+                tx = x - cx.jf;
+            }
+            if (oy) {
+                card_update(M.ax[1], cy, y);
+                ty = y - cy.jf;
+            }
+            if (oz) {
+                card_update(M.ax[2], cz, z);
+                tz = z - cz.jf;
+            }
+            int cell = (cz.j * M.ncy + cy.j) * M.ncx + cx.j;
+            MFA_DBG_INDEX(M.dbg, cell, static_cast<long long>(M.ncx) * M.ncy * M.ncz, kDbgWindow);
+            const float* e = M.patch + static_cast<long long>(cell) * 64;
+#pragma unroll
+            for (int m = 0; m < 2; ++m)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    f2 (&pr)[4] = sup.r[m][b];
+                    asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
+                        : "=l"(pr[0].v), "=l"(pr[1].v), "=l"(pr[2].v), "=l"(pr[3].v)
+                        : "l"(e + (4 * m + b) * 8));
+                }
+        }
+        const float ty2 = ty * ty, tz2 = tz * tz;
+        const float Ny[4] = { 1.0f, ty, ty2, ty2 * ty }, Dy[4] = { 0.0f, 1.0f, 2.0f * ty, 3.0f * ty2 };
+        const float Nz[4] = { 1.0f, tz, tz2, tz2 * tz }, Dz[4] = { 0.0f, 1.0f, 2.0f * tz, 3.0f * tz2 };
+        float4 q = contract_support<4, STORAGE>(sup, xin_t<4>(tx), Ny, Dy, Nz, Dz);
+        q.y *= gs[0];
+        q.z *= gs[1];
+        q.w *= gs[2];
+        return q;
+    };
+
+    float4 q = query_at(0);
+    int k = 0;
+    while (k < ns) {
+        const float4 qn = query_at(min(k + 1, ns - 1));
+        const float4 c = sample_colour(tf, S, q);
+        const float wgt = (1.0f - acc.w) * c.w;
+        acc.x = fmaf(wgt, c.x, acc.x);
+        acc.y = fmaf(wgt, c.y, acc.y);
+        acc.z = fmaf(wgt, c.z, acc.z);
+        acc.w += wgt;
+        ++k;
+        if (acc.w >= ert) break;
+        q = qn;
+    }
+    count += static_cast<unsigned>(k);
+    return acc;
+}
+
 __device__ __forceinline__ void add_count(unsigned long long* dst, unsigned long long count)
 {
 #pragma unroll

@@ -352,7 +352,7 @@ __device__ __forceinline__ float4 march_bricked(const ModelDev& M, const RenderS
 // ----------------------------------------------------------------------------------------
 
 template <int Q, int STORAGE, int MODE>
-__global__ void __launch_bounds__(kThreads, min_blocks<Q, MODE == 6 || MODE == 7, MODE == 7>()) k_render(ModelDev M, const __grid_constant__ RenderParams P,
+__global__ void __launch_bounds__(kThreads, min_blocks<Q, MODE == 6 || MODE == 7 || MODE == 9, MODE == 7>()) k_render(ModelDev M, const __grid_constant__ RenderParams P,
                                                                  int shape)
 {
     __shared__ float4 tf[kTfSmem];
@@ -378,6 +378,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks<Q, MODE == 6 || MODE == 7
             acc = march_cardinal<Q, STORAGE, false, true>(M, P.s, tf, col, row, count);
         else if constexpr (MODE == 8)   // variant 7 off the cardinal path
             acc = march_pipelined<Q, STORAGE, false, true>(M, P.s, tf, col, row, count);
+        else if constexpr (MODE == 9)   // variant 8: per-cell patches
+            acc = march_patch<STORAGE>(M, P.s, tf, col, row, count);
         else
             acc = march<Q, STORAGE, MODE>(M, P.s, tf, col, row, count);
         P.s.out[static_cast<long long>(row) * P.s.width + col] = acc;
@@ -452,7 +454,15 @@ cudaError_t render_qs(const ModelDev& m, const RenderParams& rp, int variant, in
             else
                 k_render<Q, STORAGE, 4><<<grid, kThreads, 0, st>>>(m, rp, shape);
             break;
-        case 0:   // default: the cardinal path where it applies, else variant 4
+        case 0:   // default: the patches where the model has them, the cardinal path where it
+                  // applies, else variant 4
+            if constexpr (Q == 4 && STORAGE == 1) {
+                if (m.patch) {
+                    k_render<Q, STORAGE, 9><<<grid, kThreads, 0, st>>>(m, rp, shape);
+                    break;
+                }
+            }
+            [[fallthrough]];
         case 6:
             if (m.cardinal)
                 k_render<Q, STORAGE, 6><<<grid, kThreads, 0, st>>>(m, rp, shape);
@@ -460,6 +470,18 @@ cudaError_t render_qs(const ModelDev& m, const RenderParams& rp, int variant, in
                 k_render<Q, STORAGE, 4><<<grid, kThreads, 0, st>>>(m, rp, shape);
             break;
         case 4: k_render<Q, STORAGE, 4><<<grid, kThreads, 0, st>>>(m, rp, shape); break;
+        case 8:   // per-cell patches (MFA_WINDOW_PATCH models; otherwise the default)
+            if constexpr (Q == 4 && STORAGE == 1) {
+                if (m.patch) {
+                    k_render<Q, STORAGE, 9><<<grid, kThreads, 0, st>>>(m, rp, shape);
+                    break;
+                }
+            }
+            if (m.cardinal)
+                k_render<Q, STORAGE, 6><<<grid, kThreads, 0, st>>>(m, rp, shape);
+            else
+                k_render<Q, STORAGE, 4><<<grid, kThreads, 0, st>>>(m, rp, shape);
+            break;
         case 5:
             if constexpr (Q <= 4) {
                 k_render<Q, STORAGE, 5><<<grid, kThreads, 0, st>>>(m, rp, shape);

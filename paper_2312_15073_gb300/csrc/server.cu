@@ -441,7 +441,7 @@ mfa_server* mfa_server_create(const mfa_server_config* cfg)
     if (cfg->max_slots < 1 || cfg->max_slots > 4096) return fail(MFA_ERR_ARG, "max_slots outside 1..4096"), nullptr;
     if (cfg->max_queue < 1) return fail(MFA_ERR_ARG, "max_queue must be >= 1"), nullptr;
     if (cfg->priority_levels < 1 || cfg->priority_levels > 8) return fail(MFA_ERR_ARG, "priority_levels outside 1..8"), nullptr;
-    if (cfg->variant < 0 || cfg->variant > 7 || cfg->tile_shape < 0 || cfg->tile_shape >= kTileShapes)
+    if (cfg->variant < 0 || cfg->variant > 8 || cfg->tile_shape < 0 || cfg->tile_shape >= kTileShapes)
         return fail(MFA_ERR_ARG, "variant or tile_shape out of range"), nullptr;
     if (cfg->mode != 0 && cfg->mode != 1) return fail(MFA_ERR_ARG, "mode must be 0 (device queue) or 1"), nullptr;
     if (!(cfg->urgency_rate >= 0)) return fail(MFA_ERR_ARG, "urgency_rate must be >= 0"), nullptr;

@@ -41,7 +41,7 @@ int read_cache_file(const char* path)
         int q, s, pb, sb, u, nb, v, t;
         float ms;
         if (std::sscanf(line, "%d %d %d %d %d %d %d %d %f", &q, &s, &pb, &sb, &u, &nb, &v, &t, &ms) != 9) continue;
-        if (v < 1 || v > 7 || t < 0 || t >= kTileShapes) continue;
+        if (v < 1 || v > 8 || t < 0 || t >= kTileShapes) continue;
         g_cache[Key(q, s, pb, sb, u, nb)] = mfa_tune_result{ v, t, ms };
         ++loaded;
     }
@@ -122,8 +122,10 @@ int mfa_tune_render(const mfa_model* m, const mfa_camera* cam, const mfa_transfe
     int count = 0, rc = MFA_OK;
     // 6 is the cardinal path (cardinal models only), 7 empty-space skipping
     const bool cardinal = m && m->dev.cardinal;
-    for (int variant = 1; variant <= 7 && rc == MFA_OK; ++variant) {
+    const bool patch = m && m->dev.patch;
+    for (int variant = 1; variant <= 8 && rc == MFA_OK; ++variant) {
         if (variant == 6 && !cardinal) continue;
+        if (variant == 8 && !patch) continue;
         for (int shape = 0; shape < kTileShapes && rc == MFA_OK; ++shape) {
             mfa_render_opts o{};
             o.variant = variant;

@@ -90,11 +90,11 @@ def test_host_side_argument_checks(libmfa):
     assert "aligned" in L.mfa_last_error().decode()
     assert L.mfa_image_compare(0x1000, 0x2000, 10, 16, ctypes.byref(q)) == -1
     assert "11..32768" in L.mfa_last_error().decode()
-    # render options are checked before anything else: variants 0..7, tile shapes 0..3
+    # render options are checked before anything else: variants 0..8, tile shapes 0..3
     opts = mfa._Opts()
-    opts.variant = 8
+    opts.variant = 9
     assert L.mfa_render_ex(None, ctypes.byref(cam), ctypes.byref(tf.struct), 8, 8, 8, None, ctypes.byref(opts)) == -1
-    assert "0..7" in L.mfa_last_error().decode()
+    assert "0..8" in L.mfa_last_error().decode()
     opts.variant, opts.tile_shape = 7, 4
     assert L.mfa_render_ex(None, ctypes.byref(cam), ctypes.byref(tf.struct), 8, 8, 8, None, ctypes.byref(opts)) == -1
     assert "tile_shape" in L.mfa_last_error().decode()
@@ -140,9 +140,18 @@ def test_host_side_argument_checks(libmfa):
     assert not L.mfa_model_create_ex(ctypes.byref(deg), ctypes.byref(nc), None, ctrl.ctypes.data, 0, 0)
     assert "storage" in L.mfa_last_error().decode()
     L.mfa_model_create_opts.restype = ctypes.c_void_p
-    for window in (-1, 3, 7):                                           # not an MFA_WINDOW_* choice
+    for window in (-1, 4, 7):                                           # not an MFA_WINDOW_* choice
         assert not L.mfa_model_create_opts(ctypes.byref(deg), ctypes.byref(nc), None, ctrl.ctypes.data, 0, 1, window)
         assert "window" in L.mfa_last_error().decode()
+    # per-cell patches (MFA_WINDOW_PATCH = 3): FP32 storage, degree 3 on every axis, uniform knots
+    assert not L.mfa_model_create_opts(ctypes.byref(deg), ctypes.byref(nc), None, ctrl.ctypes.data, 0, 2, 3)
+    assert "MFA_WINDOW_PATCH" in L.mfa_last_error().decode()
+    deg2 = (ctypes.c_int * 3)(3, 2, 3)
+    assert not L.mfa_model_create_opts(ctypes.byref(deg2), ctypes.byref(nc), None, ctrl.ctypes.data, 0, 1, 3)
+    assert "MFA_WINDOW_PATCH" in L.mfa_last_error().decode()
+    kp = (ctypes.c_void_p * 3)(None, ok.ctypes.data, None)           # a non-uniform axis
+    assert not L.mfa_model_create_opts(ctypes.byref(deg), ctypes.byref(nc), ctypes.byref(kp), ctrl.ctypes.data, 0, 1, 3)
+    assert "MFA_WINDOW_PATCH" in L.mfa_last_error().decode()
     L.mfa_model_destroy(None)          # a no-op
 
 

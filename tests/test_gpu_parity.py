@@ -395,6 +395,68 @@ def test_render_cardinal_matches_oracle(mfa, orc, degree, nctrl, cam, storage):
     assert np.abs(imgs[6] - imgs[4]).max() <= 2e-3
 
 
+PATCH_CASES = [
+    ((4, 6, 40), "persp_inside"),     # no interior span on two axes: every cell an end cell
+    ((24, 20, 28), "persp"),
+    ((33, 17, 9), "ortho_axis"),      # rays along -z, positions on knots
+    ((16, 12, 14), "ortho_oblique"),
+]
+
+
+@pytest.mark.parametrize("nctrl,cam", PATCH_CASES)
+def test_render_patches_match_oracle(mfa, orc, nctrl, cam):
+    """Variant 8 (MFA_WINDOW_PATCH: each knot-span cell's tricubic polynomial, evaluated with
+    monomials) against the oracle; the patch model's variant 6 equals the same control points'
+    plain model bit for bit (the window is the same), and variant 8 on a model without patches
+    runs variant 6."""
+    import torch
+    rng = np.random.default_rng(_seed("patch", nctrl, cam))
+    model, ref, P = _make(mfa, orc, rng, (3, 3, 3), nctrl, (True, True, True), 1, window=mfa.MFA_WINDOW_PATCH)
+    plain = mfa.Model((3, 3, 3), nctrl, None, P)
+    assert model.info()["window"] == mfa.MFA_WINDOW_PATCH and model.info()["cardinal"]
+    assert model.info()["device_bytes"] > plain.info()["device_bytes"] + 250 * np.prod(np.subtract(nctrl, 3))
+    camera = _camera(cam, rng)
+    job = synth.RenderJob(camera, 40, 28, 150, synth.ramp_tf(256, 0.08), True)
+    tf = mfa.transfer_fn(job.tf, shading=True)
+    imgs, counts = {}, {}
+    for name, m, variant in (("patch", model, 8), ("win", model, 6), ("plain6", plain, 6), ("plain8", plain, 8)):
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        imgs[name] = mfa.render(m, camera, tf, job.width, job.height, job.n_samples, samples_out=cnt,
+                                variant=variant).cpu().numpy()
+        counts[name] = int(cnt.item())
+    np.testing.assert_array_equal(imgs["win"], imgs["plain6"])
+    np.testing.assert_array_equal(imgs["plain8"], imgs["plain6"])
+    rimg, rc = orc.render(ref, camera, job.tf, job.width, job.height, job.n_samples, shading=True)
+    rmse = image_rmse(imgs["patch"], rimg)
+    assert np.all(rmse <= IMAGE_RMSE_TOL), rmse
+    assert abs(counts["patch"] - rc) <= max(2, 1e-3 * rc)
+    assert rimg[..., 3].max() > 0.05
+    assert np.abs(imgs["patch"] - imgs["win"]).max() <= 2e-3
+
+
+def test_render_patches_full_size_persp_1024(mfa, orc):
+    """The render workload at full size with per-cell patches (variant 8): 4096 seeded pixels
+    and two full rows against the oracle."""
+    import torch
+    wl = synth.config2(with_points=False)
+    spec = wl.model
+    model = mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl, window=mfa.MFA_WINDOW_PATCH)
+    ref = orc.Model.from_spec(spec)
+    rng = np.random.default_rng(98)
+    W, H, job = wl.render.width, wl.render.height, wl.render
+    pix = np.concatenate([rng.choice(W * H, 4096, replace=False), np.arange(300 * W, 301 * W),
+                          np.arange(700 * W, 701 * W)])
+    tf = mfa.transfer_fn(job.tf, shading=job.shading, ka=job.ka, kd=job.kd, ks=job.ks, shininess=job.shininess,
+                         ert_alpha=job.ert_alpha)
+    img = mfa.render(model, job.camera, tf, W, H, job.n_samples, variant=8).cpu().numpy().astype(np.float64)
+    r, _ = orc.render(ref, job.camera, job.tf, W, H, job.n_samples, shading=job.shading, ka=job.ka, kd=job.kd,
+                      ks=job.ks, shininess=job.shininess, ert_alpha=job.ert_alpha, pixels=pix)
+    rmse = image_rmse(img.reshape(-1, 4)[pix], r)
+    print("1024^2 patches RMSE per channel:", rmse)
+    assert np.all(rmse <= IMAGE_RMSE_TOL)
+    assert r[:, 3].max() > 0.5
+
+
 def test_cardinal_flag(mfa, orc):
     """Which models take the cardinal path: exactly the clamped uniform knots (i/(n-p) in
     FP64) and one degree; knots off by even 1e-13 take the record path."""
