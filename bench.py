@@ -74,8 +74,8 @@ DECODE_WINDOW_BYTES = {1: 1 * 2 * 16, 2: 1 * 3 * 48, 3: 2 * 4 * 32, 4: 3 * 5 * 4
 # DRAM bytes (read + write) of one k_render launch on this workload, measured by an ncu
 # capture of the frame (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
 # kernel sources it was taken on (their SHA-256 is checked at run time; any change -> null).
-RENDER_TRAFFIC = {"src_sha256": "57d53d8422e86180c196eb15b76941c2843a8a75f4c445ba7afac1d0d61ccf13",
-                  "bytes_per_launch": 16101888}
+RENDER_TRAFFIC = {"src_sha256": "4066e3ae1e7869e90a18402a6d4796424a0d9fe9173c6be51b30fdc1a647b49e",
+                  "bytes_per_launch": 120997376}
 KERNEL_SOURCES = ["paper_2312_15073_gb300/csrc/render.cu", "paper_2312_15073_gb300/csrc/raycast.cuh",
                   "paper_2312_15073_gb300/csrc/bspline.cuh", "paper_2312_15073_gb300/csrc/mfa_internal.cuh"]
 
@@ -513,8 +513,9 @@ def run_ours(args):
         "decode_queries_per_s": n_pts / (statistics.mean(decode_ms) / 1e3),
         "roofline": {"bound": "alu", "kernel": "k_render", "achieved": achieved_tflops, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops, "traffic": render_traffic(),
-                     "traffic_note": "DRAM bytes per launch from ncu (model and image stay in L2; "
-                                     "algorithmic bytes: 70 MiB layer-pair window of power rows + 16 MiB image)",
+                     "traffic_note": "DRAM bytes per launch from ncu (variant 8: the patches of the cells the "
+                                     "rays reach, 110 MB read, the rest of the 478 MiB patch array untouched or "
+                                     "from L2; the 16 MiB image written)",
                      "tuned": tuned,
                      "flops_per_sample": flops_sample,
                      "flops_note": "algorithmic count (sum-factorised contraction + span-local Cox-de Boor "
