@@ -569,9 +569,11 @@ def run_ours(args):
         line["serving"] = dict(run_serve(mfa, rates=args.serve_rates, duration=args.serve_duration,
                                          min_requests=args.serve_requests),
                                note="Poisson requests (sides 512..2048, 512..2048 samples) on 8 resident degree-3 "
-                                    "models; served = FP16 control points (FP32 window values), up to 16 requests "
-                                    "in flight drawn tile by tile from the device work queue; plain = FP32 control "
-                                    "points, one request at a time in arrival order, one launch each; latency from "
+                                    "models; served = FP16 control points (FP32 window and per-cell patches built "
+                                    "from them), up to 16 requests in flight drawn tile by tile from the device "
+                                    "work queue; plain_f32 = FP32 control points (default window), one request "
+                                    "at a time in arrival order, one launch each; plain_f16 = the served models "
+                                    "run as plain_f32 (the queue's own share of the difference); latency from "
                                     "scheduled arrival to completion")
     if ws == 1 and not args.no_cpu_baseline:
         r_rate, d_rate, info = oracle_rates(wl, budget_s=args.cpu_budget)
@@ -946,11 +948,11 @@ def storage_throughput(mfa, torch, spec, job, tf, frames=5):
 # ------------------------------------------------------------------------------------------
 
 def serve_models(mfa, size_scale=1.0):
-    """The 8 serving models twice: FP16 control points with FP32 window values (served
-    path) and FP32 (plain path)."""
+    """The 8 serving models twice: FP16 control points with an FP32 window and per-cell
+    patches built from them (served path) and FP32 with the default window (plain path)."""
     import synth
     specs = synth.config5_models(size_scale)
-    f16 = [mfa.Model(s.degree, s.nctrl, s.knots, s.ctrl64, storage=mfa.MFA_F16, window=mfa.MFA_WINDOW_F32)
+    f16 = [mfa.Model(s.degree, s.nctrl, s.knots, s.ctrl64, storage=mfa.MFA_F16, window=mfa.MFA_WINDOW_PATCH)
            for s in specs]
     f32 = [mfa.Model(s.degree, s.nctrl, s.knots, s.ctrl64, storage=mfa.MFA_F32) for s in specs]
     return specs, f16, f32
@@ -959,19 +961,19 @@ def serve_models(mfa, size_scale=1.0):
 def serve_model_table(mfa, specs, f16, f32, tf, side=2048, ns=2048, frames=3):
     """Per serving model: control points, device bytes and the time of one 2048^2 frame
     with 2048 samples per ray (the largest serving view) for each way of holding it: FP32
-    (the plain path's models), FP16 with FP32 window values (the served path's models),
-    FP16 with 16-bit window values, and the compact FP16 layout."""
+    (the plain path's models), FP16 with per-cell patches (the served path's models), FP16
+    with FP32 window values, FP16 with 16-bit window values, and the compact FP16 layout."""
     import torch
     import synth
     cam = synth.orbit_camera((0.5, 0.5, 0.5), 2.5, 0.7, 0.2, 30.0)
     img = torch.empty((side, side, 4), device="cuda")
     rows = []
-    for spec, m16w32, m32 in zip(specs, f16, f32):
+    for spec, m16p, m32 in zip(specs, f16, f32):
         row = {"nctrl": list(spec.nctrl), "plain_values_bytes_f16": 2 * int(np.prod(spec.nctrl))}
-        extra = [("f16", mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl64, storage=mfa.MFA_F16)),
-                 ("f16_compact", mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl64, storage=mfa.MFA_F16,
-                                           window=mfa.MFA_WINDOW_COMPACT))]
-        for name, m in [("f32", m32), ("f16_f32window", m16w32)] + extra:
+        extra = [(name, mfa.Model(spec.degree, spec.nctrl, spec.knots, spec.ctrl64, storage=mfa.MFA_F16, window=w))
+                 for name, w in (("f16_f32window", mfa.MFA_WINDOW_F32), ("f16", mfa.MFA_WINDOW_AUTO),
+                                 ("f16_compact", mfa.MFA_WINDOW_COMPACT))]
+        for name, m in [("f32", m32), ("f16_patches", m16p)] + extra:
             mfa.render(m, cam, tf, side, side, ns, out=img)
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1043,7 +1045,8 @@ def run_serve(mfa, rates, duration, size_scale=1.0, max_slots=16, min_requests=0
         stream = synth.config5_requests(rate, max(duration, min_requests / rate))
         row = {"requests": len(stream)}
         for name, models, cfg in (("served_f16", f16, dict(max_slots=max_slots, mode=0)),
-                                  ("plain_f32", f32, dict(max_slots=1, priority_levels=1, mode=1))):
+                                  ("plain_f32", f32, dict(max_slots=1, priority_levels=1, mode=1)),
+                                  ("plain_f16", f16, dict(max_slots=1, priority_levels=1, mode=1))):
             srv = mfa.Server(hbm_budget_bytes=budget, max_queue=4096, **cfg)
             lat, done, rej, wall = serve_stream(mfa, srv, models, tf, stream)
             srv.close()

@@ -102,11 +102,12 @@ mfa_model* mfa_model_create_ex(const int degree[3], const int nctrl[3], const do
  * plain size instead of 8-16x (for models that would not otherwise fit in L2 or in
  * memory).  Compact models keep no per-cell bounds, so the isosurface search queries every
  * sample and render variant 7 falls back to the default; render variants 1, 2, 3 and 5
- * run as the default too.  MFA_WINDOW_PATCH (FP32 storage, degree 3 on every axis, clamped
- * uniform knots; MFA_ERR_UNSUPPORTED otherwise): the FP32 window, plus per knot-span cell
- * the 64 coefficients of the model's polynomial on that cell in its local coordinates
- * (computed in FP64 from the stored values, rounded once; 256 bytes per cell, about 7x the
- * window), which render variant 8 evaluates with monomials instead of basis functions. */
+ * run as the default too.  MFA_WINDOW_PATCH (degree 3 on every axis, clamped uniform
+ * knots; MFA_ERR_UNSUPPORTED otherwise; any storage type): an FP32 window (as
+ * MFA_WINDOW_F32), plus per knot-span cell the 64 coefficients of the model's polynomial on
+ * that cell in its local coordinates (computed in FP64 from the stored values, rounded once
+ * to FP32; 256 bytes per cell, about 7x the window), which render variant 8 -- and the
+ * batch and serving kernels -- evaluate with monomials instead of basis functions. */
 enum { MFA_WINDOW_AUTO = 0, MFA_WINDOW_F32 = 1, MFA_WINDOW_COMPACT = 2, MFA_WINDOW_PATCH = 3 };
 
 /* As mfa_model_create_ex, with the window chosen (MFA_WINDOW_*; MFA_ERR_ARG otherwise). */

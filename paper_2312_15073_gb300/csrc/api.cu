@@ -267,12 +267,14 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
     if (!valid_dtype(in_dtype)) return fail(MFA_ERR_ARG, "unknown input dtype %d", (int)in_dtype), nullptr;
     if (storage != MFA_F32 && storage != MFA_F16 && storage != MFA_BF16)
         return fail(MFA_ERR_UNSUPPORTED, "storage dtype must be F32, F16 or BF16"), nullptr;
-    if (window != MFA_WINDOW_AUTO && window != MFA_WINDOW_F32 && window != MFA_WINDOW_COMPACT && window != MFA_WINDOW_PATCH)
+    if (window != MFA_WINDOW_AUTO && window != MFA_WINDOW_F32 && window != MFA_WINDOW_COMPACT &&
+        window != MFA_WINDOW_PATCH)
         return fail(MFA_ERR_ARG, "window = %d is not one of the MFA_WINDOW_* choices", window), nullptr;
     const bool compact = window == MFA_WINDOW_COMPACT;
     // window type (ModelDev::storage): layer pairs of FP32 or of the storage type's values, or
     // the compact plain array of the storage type
-    const int wstore = compact ? storage + 3 : (window == MFA_WINDOW_F32 ? MFA_F32 : storage);
+    const int wstore =
+        compact ? storage + 3 : (window == MFA_WINDOW_F32 || window == MFA_WINDOW_PATCH ? MFA_F32 : storage);
     int qmax = 0;
     for (int a = 0; a < 3; ++a) {
         if (degree[a] < 1 || degree[a] > kMaxDegree)
@@ -282,8 +284,8 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
         qmax = degree[a] + 1 > qmax ? degree[a] + 1 : qmax;
     }
     const bool patches = window == MFA_WINDOW_PATCH;
-    if (patches && (storage != MFA_F32 || degree[0] != 3 || degree[1] != 3 || degree[2] != 3))
-        return fail(MFA_ERR_UNSUPPORTED, "MFA_WINDOW_PATCH needs FP32 storage and degree 3 on every axis"), nullptr;
+    if (patches && (degree[0] != 3 || degree[1] != 3 || degree[2] != 3))
+        return fail(MFA_ERR_UNSUPPORTED, "MFA_WINDOW_PATCH needs degree 3 on every axis"), nullptr;
     // padded sizes: kPad zeros past the end of every axis; compact models round x up to a
     // multiple of their entry stride, so that their rows are whole entries of eight values
     const int cstride = compact_stride(qmax, wstore);

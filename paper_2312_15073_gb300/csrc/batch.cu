@@ -73,7 +73,8 @@ cudaError_t build_graph(mfa_batch* b, mfa_batch::Slot& s, unsigned long long mas
                                  cudaMemcpyHostToDevice);
     for (int g = 0; g < kBatchGroups && e == cudaSuccess; ++g) {
         if (!(mask & (1ull << g))) continue;
-        const BatchKernel k = render_batch_kernel(batch_group_q(g), batch_group_storage(g), batch_group_cardinal(g));
+        const BatchKernel k = render_batch_kernel(batch_group_q(g), batch_group_storage(g), batch_group_cardinal(g),
+                                                  batch_group_patch(g));
         void* table = s.d_table;
         int group = g, shape = b->shape;
         void* args[] = { &table, &group, &shape };
@@ -185,7 +186,8 @@ int mfa_batch_render(mfa_batch* b, const mfa_render_request* reqs, int n)
             fail(rc, "request %d: %s", r, mfa_last_error());
             return rc;
         }
-        const int g = batch_group(q.model->dev.q, q.model->dev.storage, q.model->dev.cardinal);
+        const ModelDev& md = q.model->dev;
+        const int g = batch_group(md.q, md.storage, md.cardinal, md.patch != nullptr);
         it.m = q.model->dev;
         it.tiles_x = (q.width + tw - 1) / tw;
         const long long nt = static_cast<long long>(it.tiles_x) * ((q.height + th - 1) / th);

@@ -178,17 +178,21 @@ struct BatchHead {
     int total_tiles;
     int items_offset;   // bytes from the start of the table
 };
-// Groups: (record / cardinal path) x (storage F32/F16/BF16) x (Q = 2..5).
-constexpr int kBatchGroups = 48;
+// Groups: (record / cardinal path) x window type x (Q = 2..5), and one group of models with
+// per-cell patches (cardinal path, degree class 4, FP32 window values).
+constexpr int kPatchGroup = 2 * kWindowTypes * 4;
+constexpr int kBatchGroups = kPatchGroup + 1;
 constexpr int kBatchItemsOffset = 1024;   // heads occupy the first 1024 bytes
 static_assert(kBatchGroups * sizeof(BatchHead) <= kBatchItemsOffset, "batch heads overflow");
-__host__ __device__ constexpr int batch_group(int q, int storage, int cardinal)
+static_assert(kBatchGroups <= 64, "group sets are 64-bit masks");
+__host__ __device__ constexpr int batch_group(int q, int storage, int cardinal, bool patch)
 {
-    return (cardinal * kWindowTypes + (storage - 1)) * 4 + (q - 2);
+    return patch ? kPatchGroup : (cardinal * kWindowTypes + (storage - 1)) * 4 + (q - 2);
 }
-__host__ __device__ constexpr int batch_group_q(int g) { return g % 4 + 2; }
-__host__ __device__ constexpr int batch_group_storage(int g) { return g / 4 % kWindowTypes + 1; }
-__host__ __device__ constexpr int batch_group_cardinal(int g) { return g / (4 * kWindowTypes); }
+__host__ __device__ constexpr int batch_group_q(int g) { return g == kPatchGroup ? 4 : g % 4 + 2; }
+__host__ __device__ constexpr int batch_group_storage(int g) { return g == kPatchGroup ? 1 : g / 4 % kWindowTypes + 1; }
+__host__ __device__ constexpr int batch_group_cardinal(int g) { return g == kPatchGroup ? 1 : g / (4 * kWindowTypes); }
+__host__ __device__ constexpr bool batch_group_patch(int g) { return g == kPatchGroup; }
 
 // launchers (defined in the .cu files), all asynchronous on `stream`
 cudaError_t launch_prep_axis(const double* d_knots, int n, int p, int q, float* kup, float* rec, int* grid,
@@ -227,7 +231,7 @@ struct BatchKernel {
     int blocks_per_sm;
     int threads;
 };
-BatchKernel render_batch_kernel(int q, int storage, int cardinal);
+BatchKernel render_batch_kernel(int q, int storage, int cardinal, bool patch);
 
 // Serving work queue (mfa_server_*, device-queue mode).  Each admitted request occupies a
 // record of a ring in device memory; a request's ray tiles are claimed by atomicAdd on the
@@ -256,7 +260,7 @@ struct ServeQueue {
 // (ServeRecord* records, const ServeQueue* queue, unsigned* done (host-mapped: done[r] =
 // generation once record r's last tile is finished), int group, int tile_shape).  Its CTAs
 // claim tiles of the group's active records in list order and exit when none is left.
-BatchKernel render_serve_kernel(int q, int storage, int cardinal);
+BatchKernel render_serve_kernel(int q, int storage, int cardinal, bool patch);
 // Pixel size of ray-tile shape `shape` (0..kTileShapes-1); -1 if out of range.
 int render_tile_dims(int shape, int* tw, int* th);
 constexpr int kTileShapes = 4;

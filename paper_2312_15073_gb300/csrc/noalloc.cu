@@ -89,7 +89,8 @@ extern "C" int mfa_render_batch_static(const mfa_render_request* reqs, int n)
             fail(rc, "request %d: %s", r, mfa_last_error());
             return rc;
         }
-        const int g = batch_group(q.model->dev.q, q.model->dev.storage, q.model->dev.cardinal);
+        const ModelDev& md = q.model->dev;
+        const int g = batch_group(md.q, md.storage, md.cardinal, md.patch != nullptr);
         group_of[r] = g;
         it.m = q.model->dev;
         it.tiles_x = (q.width + tw - 1) / tw;
@@ -140,7 +141,8 @@ extern "C" int mfa_render_batch_static(const mfa_render_request* reqs, int n)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     for (int g = 0; g < kBatchGroups; ++g) {
         if (!count[g]) continue;
-        const BatchKernel k = render_batch_kernel(batch_group_q(g), batch_group_storage(g), batch_group_cardinal(g));
+        const BatchKernel k = render_batch_kernel(batch_group_q(g), batch_group_storage(g), batch_group_cardinal(g),
+                                                  batch_group_patch(g));
         BatchHead* tp = static_cast<BatchHead*>(table);
         int group = g, shape = 0;
         void* args[] = { &tp, &group, &shape };

@@ -354,8 +354,8 @@ __device__ __forceinline__ float4 march_bricked(const ModelDev& M, const RenderS
 // ----------------------------------------------------------------------------------------
 
 template <int Q, int STORAGE, int MODE>
-__global__ void __launch_bounds__(kThreads, min_blocks<Q, MODE == 6 || MODE == 7 || MODE == 9, MODE == 7>()) k_render(ModelDev M, const __grid_constant__ RenderParams P,
-                                                                 int shape)
+__global__ void __launch_bounds__(kThreads, min_blocks<Q, MODE == 6 || MODE == 7 || MODE == 9, MODE == 7>())
+    k_render(ModelDev M, const __grid_constant__ RenderParams P, int shape)
 {
     __shared__ float4 tf[kTfSmem];
     stage_tf(tf, P.tf, P.s.tf_n);
@@ -644,11 +644,14 @@ cudaError_t segments_q(const ModelDev& m, const RenderParams& rp, bool cardinal,
 // operands, 31.1 ms).  The register copy fits without spills on the cardinal path with FP32
 // layer-pair windows at degree classes 2..4; elsewhere it spilled (16 to 650 bytes), so those
 // kernels keep reading the shared copy.
-template <int Q, int STORAGE, bool CARD>
+template <int Q, int STORAGE, bool CARD, bool PATCH>
 __device__ __forceinline__ float4 march_item(const BatchItem& item, const float4* tf, int col, int row,
                                              unsigned long long& count)
 {
-    if constexpr (!CARD) {
+    if constexpr (PATCH) {   // the group of models with per-cell patches (degree class 4, FP32)
+        const ModelDev m = item.m;
+        return march_patch<STORAGE>(m, item.s, tf, col, row, count);
+    } else if constexpr (!CARD) {
         return march_pipelined<Q, STORAGE>(item.m, item.s, tf, col, row, count);
     } else if constexpr (STORAGE == 1 && Q <= 4) {
         const ModelDev m = item.m;
@@ -662,8 +665,9 @@ __device__ __forceinline__ float4 march_item(const BatchItem& item, const float4
 // request (tiles of one request are contiguous, so the previous request is checked
 // first), stage the request and its table in shared memory when it changes, render,
 // repeat until the counter passes the group's last tile.  One kernel per group keeps each
-// degree's (and each path's) register allocation free of the others'.
-template <int Q, int STORAGE, bool CARD>
+// degree's (and each path's) register allocation free of the others'.  PATCH: the group of
+// models with per-cell patches (render variant 8).
+template <int Q, int STORAGE, bool CARD, bool PATCH = false>
 __global__ void __launch_bounds__(kThreads, min_blocks<Q, CARD>()) k_render_batch(BatchHead* __restrict__ table, int group,
                                                                        int shape)
 {
@@ -711,7 +715,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<Q, CARD>()) k_render_batc
         tile_pixel(T, tx, ty, threadIdx.x, col, row);
         unsigned long long count = 0;
         if (col < item.s.width && row < item.s.height) {
-            const float4 acc = march_item<Q, STORAGE, CARD>(item, tf, col, row, count);
+            const float4 acc = march_item<Q, STORAGE, CARD, PATCH>(item, tf, col, row, count);
             item.s.out[static_cast<long long>(row) * item.s.width + col] = acc;
         }
         if (item.s.samples_out) add_count(item.s.samples_out, count);
@@ -738,7 +742,7 @@ __device__ __forceinline__ int item_total(const ServeRecord* recs, int r) { retu
 // Tiles a CTA claims from the record it is on before it walks the active list again.
 constexpr int kServeRewalk = 8;
 
-template <int Q, int STORAGE, bool CARD>
+template <int Q, int STORAGE, bool CARD, bool PATCH = false>
 __global__ void __launch_bounds__(kThreads, min_blocks<Q, CARD>())
     k_serve(ServeRecord* __restrict__ recs, const ServeQueue* __restrict__ queue, unsigned* __restrict__ done,
             int group, int shape)
@@ -830,7 +834,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<Q, CARD>())
         tile_pixel(T, tx, ty, threadIdx.x, col, row);
         unsigned long long count = 0;
         if (col < item.s.width && row < item.s.height) {
-            const float4 acc = march_item<Q, STORAGE, CARD>(item, tf, col, row, count);
+            const float4 acc = march_item<Q, STORAGE, CARD, PATCH>(item, tf, col, row, count);
             item.s.out[static_cast<long long>(row) * item.s.width + col] = acc;
         }
         if (item.s.samples_out) add_count(item.s.samples_out, count);
@@ -847,13 +851,13 @@ __global__ void __launch_bounds__(kThreads, min_blocks<Q, CARD>())
     }
 }
 
-template <int Q, int STORAGE, bool CARD>
+template <int Q, int STORAGE, bool CARD, bool PATCH = false>
 BatchKernel serve_kernel_qs()
 {
     BatchKernel k;
-    k.fn = reinterpret_cast<const void*>(&k_serve<Q, STORAGE, CARD>);
+    k.fn = reinterpret_cast<const void*>(&k_serve<Q, STORAGE, CARD, PATCH>);
     int blocks = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_serve<Q, STORAGE, CARD>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_serve<Q, STORAGE, CARD, PATCH>, kThreads, 0);
     k.blocks_per_sm = blocks > 0 ? blocks : 1;
     k.threads = kThreads;
     return k;
@@ -872,13 +876,13 @@ BatchKernel serve_kernel_qc(int storage)
     }
 }
 
-template <int Q, int STORAGE, bool CARD>
+template <int Q, int STORAGE, bool CARD, bool PATCH = false>
 BatchKernel batch_kernel_qs()
 {
     BatchKernel k;
-    k.fn = reinterpret_cast<const void*>(&k_render_batch<Q, STORAGE, CARD>);
+    k.fn = reinterpret_cast<const void*>(&k_render_batch<Q, STORAGE, CARD, PATCH>);
     int blocks = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_render_batch<Q, STORAGE, CARD>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_render_batch<Q, STORAGE, CARD, PATCH>, kThreads, 0);
     k.blocks_per_sm = blocks > 0 ? blocks : 1;
     k.threads = kThreads;
     return k;
@@ -954,8 +958,9 @@ cudaError_t launch_merge_segments(const RenderScalars& s, const int g[3], const 
     return cudaGetLastError();
 }
 
-BatchKernel render_serve_kernel(int q, int storage, int cardinal)
+BatchKernel render_serve_kernel(int q, int storage, int cardinal, bool patch)
 {
+    if (patch) return serve_kernel_qs<4, 1, true, true>();
     switch (q) {
     case 2: return cardinal ? serve_kernel_qc<2, true>(storage) : serve_kernel_qc<2, false>(storage);
     case 3: return cardinal ? serve_kernel_qc<3, true>(storage) : serve_kernel_qc<3, false>(storage);
@@ -964,8 +969,9 @@ BatchKernel render_serve_kernel(int q, int storage, int cardinal)
     }
 }
 
-BatchKernel render_batch_kernel(int q, int storage, int cardinal)
+BatchKernel render_batch_kernel(int q, int storage, int cardinal, bool patch)
 {
+    if (patch) return batch_kernel_qs<4, 1, true, true>();
     switch (q) {
     case 2: return batch_kernel_q<2>(storage, cardinal);
     case 3: return batch_kernel_q<3>(storage, cardinal);

@@ -240,7 +240,8 @@ int publish_record(mfa_server* s, Ticket* t, int r)
     R.gen = t->gen;
     R.total_tiles = R.item.tiles_x * ((t->height + th - 1) / th);
     R.done_tiles = 0;
-    R.group = batch_group(t->model->dev.q, t->model->dev.storage, t->model->dev.cardinal);
+    const ModelDev& md = t->model->dev;
+    R.group = batch_group(md.q, md.storage, md.cardinal, md.patch != nullptr);
     R.ticket = static_cast<unsigned long long>(static_cast<unsigned>(t->gen)) << 32;
     const size_t body = offsetof(ServeRecord, gen);
     cudaError_t e = cudaMemcpyAsync(reinterpret_cast<char*>(s->d_recs + r) + body, reinterpret_cast<char*>(&R) + body,
@@ -286,7 +287,8 @@ void publish_wave(mfa_server* s, const std::vector<Ticket*>& admitted, const std
     const int slot = (s->queue_next + 3) % 4;   // the event of the list just uploaded
     for (int g = 0; g < kBatchGroups && e == cudaSuccess; ++g) {
         if (!groups[g]) continue;
-        const BatchKernel k = render_serve_kernel(batch_group_q(g), batch_group_storage(g), batch_group_cardinal(g));
+        const BatchKernel k = render_serve_kernel(batch_group_q(g), batch_group_storage(g), batch_group_cardinal(g),
+                                                  batch_group_patch(g));
         ServeRecord* recs = s->d_recs;
         const ServeQueue* q = s->d_queue;
         unsigned* done = s->d_done;

@@ -24,14 +24,16 @@ def mfa():
 def _models(mfa, orc):
     rng = np.random.default_rng(404)
     out = []
-    specs = [((3, 3, 3), (24, 20, 28), True, 1), ((2, 2, 2), (16, 18, 12), False, 1),
-             ((4, 4, 4), (14, 12, 13), True, 1), ((3, 3, 3), (30, 26, 22), False, 2),
-             ((2, 3, 4), (12, 15, 18), True, 3)]
-    for deg, n, uni, storage in specs:
+    # (degree, nctrl, uniform knots, storage, window): the first model carries per-cell
+    # patches (its own kernel group), the second is the same kind on the plain window
+    specs = [((3, 3, 3), (22, 18, 20), True, 1, 3), ((3, 3, 3), (24, 20, 28), True, 1, 0),
+             ((2, 2, 2), (16, 18, 12), False, 1, 0), ((4, 4, 4), (14, 12, 13), True, 1, 0),
+             ((3, 3, 3), (30, 26, 22), False, 2, 0), ((2, 3, 4), (12, 15, 18), True, 3, 0)]
+    for deg, n, uni, storage, window in specs:
         knots = [synth.knots_uniform(n[a], deg[a]) if uni else synth.knots_nonuniform(n[a], deg[a], rng)
                  for a in range(3)]
         P = synth.sample_ctrl(synth.GaussianSum.draw(rng, 8), knots, deg, rng, 0.01)
-        m = mfa.Model(deg, n, knots, P, storage=storage)
+        m = mfa.Model(deg, n, knots, P, storage=storage, window=window)
         stored = {1: lambda x: x.astype(np.float32).astype(np.float64), 2: orc.round_to_f16,
                   3: orc.round_to_bf16}[storage](P)
         out.append((m, orc.Model(deg, n, knots, stored)))
@@ -147,7 +149,7 @@ def test_autotuner_render_and_batch(mfa, orc, tmp_path):
     reqs, jobs = _requests(mfa, models, rng)
     m, ref, cam, table, tf, W, H, ns = jobs[0]
     best, allr = mfa.tune_render(m, cam, tf, W, H, ns, reps=2)
-    n_variants = 7 if m.info()["cardinal"] else 6
+    n_variants = 6 + int(m.info()["cardinal"]) + int(m.info()["window"] == mfa.MFA_WINDOW_PATCH)
     assert len(allr) == 4 * n_variants and all(r["ms"] > 0 for r in allr)
     assert best["ms"] == min(r["ms"] for r in allr)
     a = mfa.render(m, cam, tf, W, H, ns, use_tuned=True)

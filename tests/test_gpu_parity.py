@@ -403,16 +403,19 @@ PATCH_CASES = [
 ]
 
 
+@pytest.mark.parametrize("storage", [1, 2], ids=["f32", "f16"])
 @pytest.mark.parametrize("nctrl,cam", PATCH_CASES)
-def test_render_patches_match_oracle(mfa, orc, nctrl, cam):
+def test_render_patches_match_oracle(mfa, orc, nctrl, cam, storage):
     """Variant 8 (MFA_WINDOW_PATCH: each knot-span cell's tricubic polynomial, evaluated with
-    monomials) against the oracle; the patch model's variant 6 equals the same control points'
-    plain model bit for bit (the window is the same), and variant 8 on a model without patches
-    runs variant 6."""
+    monomials) against the oracle on the stored values; the patch model's variant 6 equals the
+    same stored values' FP32-window model bit for bit (the window is the same), and variant 8
+    on a model without patches runs variant 6."""
     import torch
-    rng = np.random.default_rng(_seed("patch", nctrl, cam))
-    model, ref, P = _make(mfa, orc, rng, (3, 3, 3), nctrl, (True, True, True), 1, window=mfa.MFA_WINDOW_PATCH)
-    plain = mfa.Model((3, 3, 3), nctrl, None, P)
+    rng = np.random.default_rng(_seed("patch", nctrl, cam, storage))
+    model, ref, P = _make(mfa, orc, rng, (3, 3, 3), nctrl, (True, True, True), storage,
+                          window=mfa.MFA_WINDOW_PATCH)
+    plain = mfa.Model((3, 3, 3), nctrl, None, P, storage=storage,
+                      window=mfa.MFA_WINDOW_F32 if storage != 1 else mfa.MFA_WINDOW_AUTO)
     assert model.info()["window"] == mfa.MFA_WINDOW_PATCH and model.info()["cardinal"]
     assert model.info()["device_bytes"] > plain.info()["device_bytes"] + 250 * np.prod(np.subtract(nctrl, 3))
     camera = _camera(cam, rng)

@@ -152,8 +152,9 @@ def test_server_rejects_bad_config(mfa):
 
 def test_queue_mixes_kernel_groups_and_reuses_records(mfa, orc):
     """The device work queue with requests of several kernel groups at once (FP32 power rows,
-    FP16 rows and compact models, uniform knots on the cardinal path and non-uniform on the
-    record path, degrees 2 to 4) and more requests than records, so every record is
+    FP16 rows, compact models and models with per-cell patches in FP32 and FP16, uniform
+    knots on the cardinal path and non-uniform on the record path, degrees 2 to 4) and more
+    requests than records, so every record is
     republished several times: each result equals the request rendered alone, and matches
     the oracle."""
     import torch
@@ -161,7 +162,8 @@ def test_queue_mixes_kernel_groups_and_reuses_records(mfa, orc):
     specs = [((3, 3, 3), (20, 18, 22), 1, True, 0), ((3, 3, 3), (17, 21, 15), 2, True, 0),
              ((2, 2, 2), (14, 16, 12), 1, False, 0), ((4, 4, 4), (12, 12, 13), 3, False, 0),
              ((2, 3, 4), (13, 11, 16), 1, True, 0), ((3, 3, 3), (15, 19, 17), 2, True, 2),
-             ((3, 3, 3), (16, 14, 18), 1, False, 2)]
+             ((3, 3, 3), (16, 14, 18), 1, False, 2), ((3, 3, 3), (18, 16, 20), 1, True, 3),
+             ((3, 3, 3), (14, 17, 15), 2, True, 3)]
     models = []
     for deg, n, storage, uniform, window in specs:
         knots = [synth.knots_uniform(n[a], deg[a]) if uniform else synth.knots_nonuniform(n[a], deg[a], rng)
