@@ -102,12 +102,13 @@ mfa_model* mfa_model_create_ex(const int degree[3], const int nctrl[3], const do
  * plain size instead of 8-16x (for models that would not otherwise fit in L2 or in
  * memory).  Compact models keep no per-cell bounds, so the isosurface search queries every
  * sample and render variant 7 falls back to the default; render variants 1, 2, 3 and 5
- * run as the default too.  MFA_WINDOW_PATCH (degree 3 on every axis, clamped uniform
- * knots; MFA_ERR_UNSUPPORTED otherwise; any storage type): an FP32 window (as
+ * run as the default too.  MFA_WINDOW_PATCH (degree 3 on every axis; MFA_ERR_UNSUPPORTED
+ * otherwise; any knots and storage type): an FP32 window (as
  * MFA_WINDOW_F32), plus per knot-span cell the 64 coefficients of the model's polynomial on
  * that cell in its local coordinates (computed in FP64 from the stored values, rounded once
- * to FP32; 256 bytes per cell, about 7x the window), which render variant 8 -- and the
- * batch and serving kernels -- evaluate with monomials instead of basis functions. */
+ * to FP32; 256 bytes per cell, about 7x the window), which render variant 8 -- and, on
+ * uniform knots, the default and the batch and serving kernels -- evaluate with monomials
+ * instead of basis functions. */
 enum { MFA_WINDOW_AUTO = 0, MFA_WINDOW_F32 = 1, MFA_WINDOW_COMPACT = 2, MFA_WINDOW_PATCH = 3 };
 
 /* As mfa_model_create_ex, with the window chosen (MFA_WINDOW_*; MFA_ERR_ARG otherwise). */
@@ -201,8 +202,9 @@ typedef struct {
                                          evaluated (after box clipping and early
                                          termination) is ADDED to it */
     int variant;                      /* kernel variant: 0 = library default (8 for a
-                                         model created with MFA_WINDOW_PATCH, 6 for a
-                                         cardinal model, see mfa_model_info, else 4);
+                                         cardinal model created with MFA_WINDOW_PATCH, 6
+                                         for a cardinal model, see mfa_model_info, else
+                                         4: the batch and serving kernels' choice too);
                                          1 = span records cached in registers along the
                                          ray, packed FP32x2 arithmetic; 2 = records cached,
                                          scalar FP32; 3 = nothing cached, scalar FP32;
@@ -226,8 +228,11 @@ typedef struct {
                                          patches (MFA_WINDOW_PATCH models; otherwise the
                                          default): 6 with each knot-span cell's
                                          coefficients in place of its window rows and
-                                         monomials in place of the basis.  Variants 1-6
-                                         and 8 differ only in FP32 rounding order.
+                                         monomials in place of the basis; off the
+                                         cardinal path the spans come from the records'
+                                         bounds (chosen explicitly or by the tuner, not
+                                         by default).  Variants 1-6 and 8 differ only in
+                                         FP32 rounding order.
                                          MFA_ERR_ARG outside 0..8. */
     int tile_shape;                   /* ray tile: 0 = 16x8 pixels per CTA with 8x4 per warp
                                          (default), 1 = 32x4 / 8x4, 2 = 8x16 / 4x8,

@@ -248,8 +248,8 @@ class Model:
     window: MFA_WINDOW_AUTO (the storage type's own window values), MFA_WINDOW_F32 (FP32
     window values whatever the storage type: a 16-bit model at FP32 speed),
     MFA_WINDOW_COMPACT (no layer-pair window: the control points at 1-1.6x) or
-    MFA_WINDOW_PATCH (FP32, degree 3, uniform knots: the FP32 window plus each knot-span
-    cell's polynomial, rendered by variant 8; about 7x the window's bytes).
+    MFA_WINDOW_PATCH (degree 3: the FP32 window plus each knot-span cell's polynomial,
+    rendered by variant 8; about 7x the window's bytes).
     """
 
     def __init__(self, degree, nctrl, knots, ctrl, storage: int | None = None, in_dtype: int | None = None,

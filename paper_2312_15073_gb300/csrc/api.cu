@@ -312,8 +312,6 @@ mfa_model* model_create(const int degree[3], const int nctrl[3], const double* c
             if (!check_knots(U[a].data(), n, p, a)) return nullptr;
         }
     }
-    if (patches && !uniform)
-        return fail(MFA_ERR_UNSUPPORTED, "MFA_WINDOW_PATCH needs clamped uniform knots (the cardinal path)"), nullptr;
 
     mfa_model* M = new mfa_model();
     cudaGetDevice(&M->device);

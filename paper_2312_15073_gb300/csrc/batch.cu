@@ -187,7 +187,7 @@ int mfa_batch_render(mfa_batch* b, const mfa_render_request* reqs, int n)
             return rc;
         }
         const ModelDev& md = q.model->dev;
-        const int g = batch_group(md.q, md.storage, md.cardinal, md.patch != nullptr);
+        const int g = batch_group(md.q, md.storage, md.cardinal, md.patch != nullptr && md.cardinal);
         it.m = q.model->dev;
         it.tiles_x = (q.width + tw - 1) / tw;
         const long long nt = static_cast<long long>(it.tiles_x) * ((q.height + th - 1) / th);

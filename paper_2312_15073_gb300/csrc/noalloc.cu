@@ -90,7 +90,7 @@ extern "C" int mfa_render_batch_static(const mfa_render_request* reqs, int n)
             return rc;
         }
         const ModelDev& md = q.model->dev;
-        const int g = batch_group(md.q, md.storage, md.cardinal, md.patch != nullptr);
+        const int g = batch_group(md.q, md.storage, md.cardinal, md.patch != nullptr && md.cardinal);
         group_of[r] = g;
         it.m = q.model->dev;
         it.tiles_x = (q.width + tw - 1) / tw;

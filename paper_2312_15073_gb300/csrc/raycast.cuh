@@ -556,6 +556,100 @@ __device__ __forceinline__ float4 march_patch(const ModelDev& M, const RenderSca
     return acc;
 }
 
+// Variant 8 on a model with non-uniform knots: the same patch march with each axis's span
+// tracked through its records, of which it reads the head only: the span's first knot U_s,
+// 1/h and its FP32 bounds [lo, hi).  The cell's local coordinate is t = (u - U_s)/h, the
+// coordinate its patch coefficients are in, and d/du = (1/h) d/dt.
+struct PatchAxis {
+    int s;                  // knot span (p .. n-1), -1 before the first sample
+    float u0, ih, lo, hi;   // the record head
+};
+
+__device__ __forceinline__ void patch_axis_update(const AxisDev& A, PatchAxis& C, float u)
+{
+    if (C.s >= 0 && u >= C.lo && u < C.hi) return;
+    int s = C.s < 0 ? locate_span(A, u) : walk_span(A, u, C.s);
+    int r = s - A.p;
+    MFA_DBG_INDEX(A.dbg, r, A.n - A.p, kDbgRecord);
+    const float4 h = __ldg(reinterpret_cast<const float4*>(A.rec + static_cast<long long>(r) * rec_stride(4)));
+    C.s = s;
+    C.u0 = h.x;
+    C.ih = h.y;
+    C.lo = h.z;
+    C.hi = h.w;
+}
+
+template <int STORAGE>
+__device__ __forceinline__ float4 march_patch_records(const ModelDev& M, const RenderScalars& P,
+                                                      const float4* __restrict__ tf, int col, int row,
+                                                      unsigned long long& count)
+{
+    static_assert(STORAGE == 1, "patches are FP32");
+    float o[3], d[3], t0, t1;
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (!ray_box(P, col, row, o, d, t0, t1)) return acc;
+
+    const int ns = P.n_samples;
+    const float ert = P.ert_alpha;
+    const float dt = (t1 - t0) / static_cast<float>(ns);
+    const ShadeParams S = shade_params(P, d, 1.0f);
+    PatchAxis cx{ -1, 0.0f, 0.0f, 0.0f, 0.0f }, cy = cx, cz = cx;
+    SupportRegs<4> sup;
+
+    auto query_at = [&](int k) -> float4 {
+        const float t = fmaf(static_cast<float>(k) + 0.5f, dt, t0);
+        const float u = clamp01(fmaf(t, d[0], o[0]));
+        const float v = clamp01(fmaf(t, d[1], o[1]));
+        const float w = clamp01(fmaf(t, d[2], o[2]));
+        const bool ox = !(cx.s >= 0 && u >= cx.lo && u < cx.hi);
+        const bool oy = !(cy.s >= 0 && v >= cy.lo && v < cy.hi);
+        const bool oz = !(cz.s >= 0 && w >= cz.lo && w < cz.hi);
+        if (ox | oy | oz) {
+            if (ox) patch_axis_update(M.ax[0], cx, u);
+            if (oy) patch_axis_update(M.ax[1], cy, v);
+            if (oz) patch_axis_update(M.ax[2], cz, w);
+            int cell = ((cz.s - 3) * M.ncy + (cy.s - 3)) * M.ncx + (cx.s - 3);
+            MFA_DBG_INDEX(M.dbg, cell, static_cast<long long>(M.ncx) * M.ncy * M.ncz, kDbgWindow);
+            const float* e = M.patch + static_cast<long long>(cell) * 64;
+#pragma unroll
+            for (int m = 0; m < 2; ++m)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    f2 (&pr)[4] = sup.r[m][b];
+                    asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
+                        : "=l"(pr[0].v), "=l"(pr[1].v), "=l"(pr[2].v), "=l"(pr[3].v)
+                        : "l"(e + (4 * m + b) * 8));
+                }
+        }
+        const float tx = (u - cx.u0) * cx.ih, ty = (v - cy.u0) * cy.ih, tz = (w - cz.u0) * cz.ih;
+        const float ty2 = ty * ty, tz2 = tz * tz;
+        const float Ny[4] = { 1.0f, ty, ty2, ty2 * ty }, Dy[4] = { 0.0f, 1.0f, 2.0f * ty, 3.0f * ty2 };
+        const float Nz[4] = { 1.0f, tz, tz2, tz2 * tz }, Dz[4] = { 0.0f, 1.0f, 2.0f * tz, 3.0f * tz2 };
+        float4 q = contract_support<4, STORAGE>(sup, xin_t<4>(tx), Ny, Dy, Nz, Dz);
+        q.y *= cx.ih;
+        q.z *= cy.ih;
+        q.w *= cz.ih;
+        return q;
+    };
+
+    float4 q = query_at(0);
+    int k = 0;
+    while (k < ns) {
+        const float4 qn = query_at(min(k + 1, ns - 1));
+        const float4 c = sample_colour(tf, S, q);
+        const float wgt = (1.0f - acc.w) * c.w;
+        acc.x = fmaf(wgt, c.x, acc.x);
+        acc.y = fmaf(wgt, c.y, acc.y);
+        acc.z = fmaf(wgt, c.z, acc.z);
+        acc.w += wgt;
+        ++k;
+        if (acc.w >= ert) break;
+        q = qn;
+    }
+    count += static_cast<unsigned>(k);
+    return acc;
+}
+
 __device__ __forceinline__ void add_count(unsigned long long* dst, unsigned long long count)
 {
 #pragma unroll

@@ -354,7 +354,7 @@ __device__ __forceinline__ float4 march_bricked(const ModelDev& M, const RenderS
 // ----------------------------------------------------------------------------------------
 
 template <int Q, int STORAGE, int MODE>
-__global__ void __launch_bounds__(kThreads, min_blocks<Q, MODE == 6 || MODE == 7 || MODE == 9, MODE == 7>())
+__global__ void __launch_bounds__(kThreads, min_blocks<Q, MODE == 6 || MODE == 7 || MODE >= 9, MODE == 7>())
     k_render(ModelDev M, const __grid_constant__ RenderParams P, int shape)
 {
     __shared__ float4 tf[kTfSmem];
@@ -382,6 +382,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks<Q, MODE == 6 || MODE == 7
             acc = march_pipelined<Q, STORAGE, false, true>(M, P.s, tf, col, row, count);
         else if constexpr (MODE == 9)   // variant 8: per-cell patches
             acc = march_patch<STORAGE>(M, P.s, tf, col, row, count);
+        else if constexpr (MODE == 10)   // variant 8 off the cardinal path
+            acc = march_patch_records<STORAGE>(M, P.s, tf, col, row, count);
         else
             acc = march<Q, STORAGE, MODE>(M, P.s, tf, col, row, count);
         P.s.out[static_cast<long long>(row) * P.s.width + col] = acc;
@@ -456,10 +458,10 @@ cudaError_t render_qs(const ModelDev& m, const RenderParams& rp, int variant, in
             else
                 k_render<Q, STORAGE, 4><<<grid, kThreads, 0, st>>>(m, rp, shape);
             break;
-        case 0:   // default: the patches where the model has them, the cardinal path where it
-                  // applies, else variant 4
+        case 0:   // default: the patches on a cardinal model that has them (the batch and
+                  // serving kernels' choice too), the cardinal path where it applies, else 4
             if constexpr (Q == 4 && STORAGE == 1) {
-                if (m.patch) {
+                if (m.patch && m.cardinal) {
                     k_render<Q, STORAGE, 9><<<grid, kThreads, 0, st>>>(m, rp, shape);
                     break;
                 }
@@ -475,7 +477,10 @@ cudaError_t render_qs(const ModelDev& m, const RenderParams& rp, int variant, in
         case 8:   // per-cell patches (MFA_WINDOW_PATCH models; otherwise the default)
             if constexpr (Q == 4 && STORAGE == 1) {
                 if (m.patch) {
-                    k_render<Q, STORAGE, 9><<<grid, kThreads, 0, st>>>(m, rp, shape);
+                    if (m.cardinal)
+                        k_render<Q, STORAGE, 9><<<grid, kThreads, 0, st>>>(m, rp, shape);
+                    else
+                        k_render<Q, STORAGE, 10><<<grid, kThreads, 0, st>>>(m, rp, shape);
                     break;
                 }
             }

@@ -241,7 +241,7 @@ int publish_record(mfa_server* s, Ticket* t, int r)
     R.total_tiles = R.item.tiles_x * ((t->height + th - 1) / th);
     R.done_tiles = 0;
     const ModelDev& md = t->model->dev;
-    R.group = batch_group(md.q, md.storage, md.cardinal, md.patch != nullptr);
+    R.group = batch_group(md.q, md.storage, md.cardinal, md.patch != nullptr && md.cardinal);
     R.ticket = static_cast<unsigned long long>(static_cast<unsigned>(t->gen)) << 32;
     const size_t body = offsetof(ServeRecord, gen);
     cudaError_t e = cudaMemcpyAsync(reinterpret_cast<char*>(s->d_recs + r) + body, reinterpret_cast<char*>(&R) + body,

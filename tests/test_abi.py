@@ -143,12 +143,9 @@ def test_host_side_argument_checks(libmfa):
     for window in (-1, 4, 7):                                           # not an MFA_WINDOW_* choice
         assert not L.mfa_model_create_opts(ctypes.byref(deg), ctypes.byref(nc), None, ctrl.ctypes.data, 0, 1, window)
         assert "window" in L.mfa_last_error().decode()
-    # per-cell patches (MFA_WINDOW_PATCH = 3): degree 3 on every axis, uniform knots
+    # per-cell patches (MFA_WINDOW_PATCH = 3): degree 3 on every axis
     deg2 = (ctypes.c_int * 3)(3, 2, 3)
     assert not L.mfa_model_create_opts(ctypes.byref(deg2), ctypes.byref(nc), None, ctrl.ctypes.data, 0, 1, 3)
-    assert "MFA_WINDOW_PATCH" in L.mfa_last_error().decode()
-    kp = (ctypes.c_void_p * 3)(None, ok.ctypes.data, None)           # a non-uniform axis
-    assert not L.mfa_model_create_opts(ctypes.byref(deg), ctypes.byref(nc), ctypes.byref(kp), ctrl.ctypes.data, 0, 1, 3)
     assert "MFA_WINDOW_PATCH" in L.mfa_last_error().decode()
     L.mfa_model_destroy(None)          # a no-op
 

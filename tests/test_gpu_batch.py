@@ -25,10 +25,12 @@ def _models(mfa, orc):
     rng = np.random.default_rng(404)
     out = []
     # (degree, nctrl, uniform knots, storage, window): the first model carries per-cell
-    # patches (its own kernel group), the second is the same kind on the plain window
+    # patches (its own kernel group), the second is the same kind on the plain window; the
+    # last carries patches on non-uniform knots (the record path's group, as its default)
     specs = [((3, 3, 3), (22, 18, 20), True, 1, 3), ((3, 3, 3), (24, 20, 28), True, 1, 0),
              ((2, 2, 2), (16, 18, 12), False, 1, 0), ((4, 4, 4), (14, 12, 13), True, 1, 0),
-             ((3, 3, 3), (30, 26, 22), False, 2, 0), ((2, 3, 4), (12, 15, 18), True, 3, 0)]
+             ((3, 3, 3), (30, 26, 22), False, 2, 0), ((2, 3, 4), (12, 15, 18), True, 3, 0),
+             ((3, 3, 3), (17, 21, 15), False, 2, 3)]
     for deg, n, uni, storage, window in specs:
         knots = [synth.knots_uniform(n[a], deg[a]) if uni else synth.knots_nonuniform(n[a], deg[a], rng)
                  for a in range(3)]

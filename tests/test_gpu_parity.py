@@ -396,39 +396,45 @@ def test_render_cardinal_matches_oracle(mfa, orc, degree, nctrl, cam, storage):
 
 
 PATCH_CASES = [
-    ((4, 6, 40), "persp_inside"),     # no interior span on two axes: every cell an end cell
-    ((24, 20, 28), "persp"),
-    ((33, 17, 9), "ortho_axis"),      # rays along -z, positions on knots
-    ((16, 12, 14), "ortho_oblique"),
+    ((4, 6, 40), "persp_inside", (True, True, True)),   # no interior span on two axes
+    ((24, 20, 28), "persp", (True, True, True)),
+    ((33, 17, 9), "ortho_axis", (True, True, True)),    # rays along -z, positions on knots
+    ((16, 12, 14), "ortho_oblique", (True, True, True)),
+    ((22, 18, 20), "persp", (False, False, False)),     # non-uniform knots: spans from the records
+    ((15, 19, 13), "persp_inside", (False, True, False)),
 ]
 
 
 @pytest.mark.parametrize("storage", [1, 2], ids=["f32", "f16"])
-@pytest.mark.parametrize("nctrl,cam", PATCH_CASES)
-def test_render_patches_match_oracle(mfa, orc, nctrl, cam, storage):
+@pytest.mark.parametrize("nctrl,cam,uniform", PATCH_CASES)
+def test_render_patches_match_oracle(mfa, orc, nctrl, cam, uniform, storage):
     """Variant 8 (MFA_WINDOW_PATCH: each knot-span cell's tricubic polynomial, evaluated with
-    monomials) against the oracle on the stored values; the patch model's variant 6 equals the
-    same stored values' FP32-window model bit for bit (the window is the same), and variant 8
-    on a model without patches runs variant 6."""
+    monomials) against the oracle on the stored values, on uniform knots (cardinal spans) and
+    non-uniform ones (spans from the records); the patch model's variant 6 equals the same
+    stored values' FP32-window model bit for bit (the window is the same; off the cardinal
+    path both run variant 4), variant 8 on a model without patches runs the default, and
+    the default takes the patches on uniform knots only."""
     import torch
-    rng = np.random.default_rng(_seed("patch", nctrl, cam, storage))
-    model, ref, P = _make(mfa, orc, rng, (3, 3, 3), nctrl, (True, True, True), storage,
-                          window=mfa.MFA_WINDOW_PATCH)
-    plain = mfa.Model((3, 3, 3), nctrl, None, P, storage=storage,
+    rng = np.random.default_rng(_seed("patch", nctrl, cam, uniform, storage))
+    model, ref, P = _make(mfa, orc, rng, (3, 3, 3), nctrl, uniform, storage, window=mfa.MFA_WINDOW_PATCH)
+    plain = mfa.Model((3, 3, 3), nctrl, [np.asarray(k) for k in ref.knots], P, storage=storage,
                       window=mfa.MFA_WINDOW_F32 if storage != 1 else mfa.MFA_WINDOW_AUTO)
-    assert model.info()["window"] == mfa.MFA_WINDOW_PATCH and model.info()["cardinal"]
+    assert model.info()["window"] == mfa.MFA_WINDOW_PATCH and model.info()["cardinal"] == all(uniform)
     assert model.info()["device_bytes"] > plain.info()["device_bytes"] + 250 * np.prod(np.subtract(nctrl, 3))
     camera = _camera(cam, rng)
     job = synth.RenderJob(camera, 40, 28, 150, synth.ramp_tf(256, 0.08), True)
     tf = mfa.transfer_fn(job.tf, shading=True)
     imgs, counts = {}, {}
-    for name, m, variant in (("patch", model, 8), ("win", model, 6), ("plain6", plain, 6), ("plain8", plain, 8)):
+    for name, m, variant in (("patch", model, 8), ("win", model, 6), ("plain6", plain, 6), ("plain8", plain, 8),
+                             ("default", model, 0)):
         cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
         imgs[name] = mfa.render(m, camera, tf, job.width, job.height, job.n_samples, samples_out=cnt,
                                 variant=variant).cpu().numpy()
         counts[name] = int(cnt.item())
     np.testing.assert_array_equal(imgs["win"], imgs["plain6"])
     np.testing.assert_array_equal(imgs["plain8"], imgs["plain6"])
+    # the default takes the patches on the cardinal path only (as the batch kernels do)
+    np.testing.assert_array_equal(imgs["default"], imgs["patch" if all(uniform) else "plain6"])
     rimg, rc = orc.render(ref, camera, job.tf, job.width, job.height, job.n_samples, shading=True)
     rmse = image_rmse(imgs["patch"], rimg)
     assert np.all(rmse <= IMAGE_RMSE_TOL), rmse
