@@ -5,7 +5,8 @@ linear fields from Greville control points (value and gradient); the convex-hull
 bound; central finite differences; the derivative-as-lower-degree-spline identity;
 the span-local sum against the full sum over every control point on tiny models with
 unequal sizes and degrees per axis (a transposed index fails it); clamping and
-threading invariance of decode.
+threading invariance of decode; per span a polynomial of degree p along each axis, with
+C^(p-1) continuity and a jump of the p-th derivative at each simple interior knot.
 """
 import numpy as np
 import pytest
@@ -151,3 +152,48 @@ def test_decode_clamps_and_is_thread_invariant(orc):
     for i in range(0, 4000, 97):
         for a in range(3):
             assert s1[i, a] == orc.find_span(m.knots[a], m.degree[a], float(cl[i, a]))
+
+
+@pytest.mark.parametrize("deg,uniform", [((3, 3, 3), True), ((3, 3, 3), False), ((2, 4, 3), False)])
+def test_polynomial_per_span_and_knot_continuity(orc, deg, uniform):
+    """Along each axis the model is, inside one knot span, a polynomial of degree p in u
+    (the per-cell patch view of the model), and at a simple interior knot the polynomials
+    of the two neighbouring spans agree in value and in the first p-1 derivatives while
+    the p-th derivative jumps (C^(p-1) continuity, no more).  A span boundary placed
+    off its knot, or a wrong knot difference in a basis factor, breaks one of the three."""
+    from numpy.polynomial import polynomial as npp
+    rng = np.random.default_rng(27)
+    n = (9, 8, 10)
+    knots = [knots_uniform(n[a], deg[a]) if uniform else knots_nonuniform(n[a], deg[a], rng) for a in range(3)]
+    P = rng.normal(size=(n[2], n[1], n[0]))
+    m = orc.Model(deg, n, knots, P)
+    tau = np.linspace(0.05, 0.95, 9)                      # inside the span, off its ends
+
+    def fit(x, a, lo, hi):
+        """Degree-p fit of u -> f on [lo, hi] in tau = (u - lo)/(hi - lo); the fit residual."""
+        f = []
+        for t in tau:
+            y = x.copy()
+            y[a] = lo + t * (hi - lo)
+            f.append(m.eval(y)[0])
+        c, (res, *_) = npp.polyfit(tau, f, deg[a], full=True)
+        return c, float(np.sqrt(res[0] / len(tau))) if len(res) else 0.0
+
+    for a in range(3):
+        p, U = deg[a], knots[a]
+        for s in range(p + 1, n[a]):                      # interior knot U_s between spans s-1 and s
+            x = rng.uniform(0, 1, 3)
+            K, hl, hr = U[s], U[s] - U[s - 1], U[s + 1] - U[s]
+            cl, rl = fit(x, a, U[s - 1], K)
+            cr, rr = fit(x, a, K, U[s + 1])
+            scale = max(1.0, np.abs(cl).max(), np.abs(cr).max())
+            assert rl <= 1e-12 * scale and rr <= 1e-12 * scale, (a, s, rl, rr)
+            # derivatives in u at the knot: left fit at tau = 1, right fit at tau = 0
+            h = min(hl, hr)
+            dl, dr = [], []
+            for j in range(p + 1):
+                dl.append(npp.polyval(1.0, npp.polyder(cl, j)) * (h / hl) ** j)
+                dr.append(npp.polyval(0.0, npp.polyder(cr, j)) * (h / hr) ** j)
+            for j in range(p):
+                assert abs(dl[j] - dr[j]) <= 1e-9 * scale, (a, s, j, dl[j], dr[j])
+            assert abs(dl[p] - dr[p]) > 1e-6 * scale, (a, s, dl[p], dr[p])
